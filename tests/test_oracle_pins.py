@@ -1,0 +1,518 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+textbook tableaux (tests/golden), values the paper prints, invariants, or a
+brute-force dense solve assembled independently in the test.  They are chosen so
+that a dropped term, a wrong sign or index, or a transposed operand fails one.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import numpy.polynomial.legendre as npleg
+import pytest
+from numpy.polynomial import Polynomial
+
+import oracle as O
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers (test side)
+
+def _golden_rows(name):
+    rows = []
+    with open(f"{GOLDEN}/{name}") as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line)
+    return rows
+
+
+def _numpy_gl_nodes(s):
+    """Independent Gauss-Lobatto nodes: numpy roots of P'_{s-1}."""
+    inner = npleg.Legendre.basis(s - 1).deriv().roots()
+    x = np.concatenate([[-1.0], np.sort(inner.real), [1.0]])
+    return (x + 1) / 2
+
+
+def _numpy_Q(s):
+    """Independent integration matrix via numpy polynomial integration."""
+    t = _numpy_gl_nodes(s)
+    Q = np.zeros((s, s))
+    for j in range(s):
+        others = np.delete(t, j)
+        lj = Polynomial.fromroots(others) / np.prod(t[j] - others)
+        Lj = lj.integ(lbnd=0.0)
+        Q[:, j] = Lj(t)
+    return Q, t
+
+
+def _lap1d(n):
+    h = 1.0 / (n + 1)
+    return (np.diag(-2 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)) / h ** 2
+
+
+def _lap(dim, n):
+    """Dense d-dim Laplacian as a Kronecker sum (x fastest)."""
+    L1, I = _lap1d(n), np.eye(n)
+    if dim == 1:
+        return L1
+    if dim == 2:
+        return np.kron(I, L1) + np.kron(L1, I)
+    return np.kron(np.kron(I, I), L1) + np.kron(np.kron(I, L1), I) + np.kron(np.kron(L1, I), I)
+
+
+def _sine_mode(dim, n, k):
+    x = np.arange(1, n + 1) / (n + 1)
+    comps = [np.sin(k[a] * np.pi * x) for a in range(dim)]
+    if dim == 1:
+        return comps[0]
+    if dim == 2:
+        return np.outer(comps[1], comps[0]).reshape(-1)
+    return np.einsum("k,j,i->kji", comps[2], comps[1], comps[0]).reshape(-1)
+
+
+def _d(k, n):
+    """Eigenvalue d(k) of the 1D 2nd-order FD Laplacian (Sec. 4.1), dx = 1/(n+1)."""
+    dx = 1.0 / (n + 1)
+    return (-2 + 2 * math.cos(k * math.pi * dx)) / dx ** 2
+
+
+def _pade(z, s):
+    """Diagonal (s-1, s-1) Pade approximant of exp(z): stability function of Lobatto IIIA."""
+    N = s - 1
+    num = sum(math.factorial(2 * N - j) * math.factorial(N) /
+              (math.factorial(2 * N) * math.factorial(j) * math.factorial(N - j)) * z ** j for j in range(N + 1))
+    den = sum(math.factorial(2 * N - j) * math.factorial(N) /
+              (math.factorial(2 * N) * math.factorial(j) * math.factorial(N - j)) * (-z) ** j for j in range(N + 1))
+    return num / den
+
+
+FULL = O.MGParams(vcycles=0, mg_tol=1e-15, mg_maxcycles=60)
+
+
+# ---------------------------------------------------------------- nodes and Q (Sec. 2.1)
+
+def test_gauss_lobatto_nodes_match_golden_and_numpy():
+    for row in _golden_rows("gauss_lobatto_nodes.txt"):
+        s, rest = row.split(None, 1)
+        s = int(s)
+        want = [eval(v, {"sqrt": math.sqrt}) for v in rest.split("|")]
+        got = O.gauss_lobatto(s)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+    for s in range(2, 10):
+        np.testing.assert_allclose(O.gauss_lobatto(s), _numpy_gl_nodes(s), rtol=0, atol=1e-14)
+
+
+def test_q_matches_lobatto_iiia_tableau():
+    tab = {}
+    for row in _golden_rows("lobatto_iiia_tableau.txt"):
+        parts = row.split()
+        s, m = int(parts[0]), int(parts[1])
+        tab.setdefault(s, {})[m] = [float(Fraction(v)) for v in parts[2:]]
+    for s, rows in tab.items():
+        Q = O.qmatrix(s)
+        for m, vals in rows.items():
+            np.testing.assert_allclose(Q[m], vals, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5, 6, 7])
+def test_q_structure_and_exactness(s):
+    Q = O.qmatrix(s)
+    t = O.gauss_lobatto(s)
+    # first row zero (q_{0,i} = 0), row sums are the node positions
+    assert np.all(Q[0] == 0.0)
+    np.testing.assert_allclose(Q.sum(axis=1), t, atol=1e-15)
+    # every row integrates polynomials of degree <= s-1 exactly (interpolatory rule)
+    for k in range(s):
+        np.testing.assert_allclose(Q @ t ** k, t ** (k + 1) / (k + 1), atol=2e-15)
+    # the last row (Lobatto quadrature over the whole interval) is exact to degree 2s-3
+    for k in range(2 * s - 2):
+        assert abs(Q[-1] @ t ** k - 1.0 / (k + 1)) < 3e-15
+    # ... and not beyond
+    assert abs(Q[-1] @ t ** (2 * s - 2) - 1.0 / (2 * s - 1)) > 1e-8
+    # independent construction
+    Qn, _ = _numpy_Q(s)
+    np.testing.assert_allclose(Q, Qn, atol=1e-13)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_collocation_stability_function_is_pade(s):
+    """Collocation = IRK with A = Q, b = last row (Eq. BT): R(z) = 1 + z b^T (I - zQ)^-1 1
+    must be the (s-1, s-1) Pade approximant of exp (Lobatto IIIA)."""
+    Q = O.qmatrix(s)
+    # the node-0 stage is explicit (row 0 of Q is zero): R(z) = last stage of (I - zQ)Y = 1
+    for z in [-0.3, -1.0, -7.5, -40.0, 0.2]:
+        Y = np.linalg.solve(np.eye(s) - z * Q, np.ones(s))
+        assert abs(Y[-1] - _pade(z, s)) < 1e-13 * max(1, abs(_pade(z, s)))
+
+
+# ---------------------------------------------------------------- spatial operator (Sec. 4.1)
+
+@pytest.mark.parametrize("dim,n", [(1, 15), (1, 127), (2, 15), (3, 7)])
+def test_laplacian_sine_modes_are_eigenvectors(dim, n):
+    nu = 0.7
+    for k in [(1, 1, 1), (3, 2, 1), (n, 1, 2)]:
+        u = _sine_mode(dim, n, k)
+        lam = nu * sum(_d(k[a], n) for a in range(dim))
+        Au = O.apply_A(dim, n, nu, u)
+        np.testing.assert_allclose(Au, lam * u, atol=1e-9 * abs(lam))
+
+
+@pytest.mark.parametrize("dim,n", [(1, 7), (2, 7), (3, 3)])
+def test_operator_matches_dense_assembly(dim, n):
+    c = 0.013
+    L = np.eye(n ** dim) - c * _lap(dim, n)
+    e = np.random.default_rng(1).standard_normal(n ** dim)
+    np.testing.assert_allclose(O.apply_L(dim, n, c, e), L @ e, atol=1e-11)
+
+
+# ---------------------------------------------------------------- MG components (Sec. 4.1.1)
+
+def _matrix_of(f, nin, nout):
+    M = np.zeros((nout, nin))
+    for q in range(nin):
+        e = np.zeros(nin)
+        e[q] = 1.0
+        M[:, q] = f(e)
+    return M
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_full_weighting_and_linear_interpolation_are_adjoint(dim):
+    n = 7
+    nc = 3
+    R = _matrix_of(lambda v: O.restrict_fw(dim, n, v), n ** dim, nc ** dim)
+    P = _matrix_of(lambda v: O.prolong_add(dim, n, v, np.zeros(n ** dim)), nc ** dim, n ** dim)
+    np.testing.assert_allclose(P, 2 ** dim * R.T, atol=1e-15)
+    assert np.allclose(R.sum(axis=1), 1.0)            # rows of FW sum to one
+
+
+def test_full_weighting_and_interpolation_closed_forms_on_quadratic():
+    n, nc = 31, 15
+    h, H = 1.0 / (n + 1), 1.0 / (nc + 1)
+    xf = np.arange(1, n + 1) * h
+    xc = np.arange(1, nc + 1) * H
+    f = lambda x: x * (1 - x)                           # f'' = -2
+    # FW: (f(X-h) + 2 f(X) + f(X+h))/4 = f(X) + h^2 f''/4
+    np.testing.assert_allclose(O.restrict_fw(1, n, f(xf)), f(xc) - h ** 2 / 2, atol=1e-15)
+    # linear interpolation: even fine points are copies, odd are f(x) + h^2 f''/2
+    Pf = O.prolong_add(1, n, f(xc), np.zeros(n))
+    want = f(xf).copy()
+    want[0::2] -= h ** 2                                # 1-based odd points (0-based even)
+    np.testing.assert_allclose(Pf, want, atol=1e-15)
+
+
+def test_jacobi_first_sweep_from_zero_closed_form():
+    dim, n, c = 2, 15, 0.004
+    h = 1.0 / (n + 1)
+    D = 1 + 2 * dim * c / h ** 2
+    f = np.random.default_rng(2).standard_normal(n ** dim)
+    mg = O.MGParams(smoother=0, omega=2 / 3)
+    e = O.smooth(mg, dim, n, c, f, np.zeros(n ** dim))
+    np.testing.assert_allclose(e, (2 / 3) * f / D, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_red_black_gauss_seidel_colouring(dim):
+    """After a red-then-black sweep (omega = 1) the black rows hold exactly,
+    red = (i+j+k) even in 1-based interior indices (Sec. 4.1.2 smoother)."""
+    n, c = 7, 0.01
+    rng = np.random.default_rng(3)
+    f, e0 = rng.standard_normal(n ** dim), rng.standard_normal(n ** dim)
+    mg = O.MGParams(smoother=1, omega=1.0)
+    e = O.smooth(mg, dim, n, c, f, e0)
+    r = f - O.apply_L(dim, n, c, e)
+    idx = np.indices((n,) * dim).reshape(dim, -1)[::-1] + 1     # (i, j, k) 1-based, x fastest
+    black = (idx.sum(axis=0) % 2) == 1
+    assert np.abs(r[black]).max() < 1e-12
+    assert np.abs(r[~black]).max() > 1e-3
+    # the red values equal a Gauss-Seidel row solve with the ORIGINAL black neighbours
+    L = np.eye(n ** dim) - c * _lap(dim, n)
+    red = ~black
+    Dg = np.diag(L)
+    e_red = (f - (L - np.diag(Dg)) @ e0) / Dg
+    np.testing.assert_allclose(e[red], e_red[red], atol=1e-12)
+
+
+@pytest.mark.parametrize("dim,n,smoother", [(1, 7, 0), (1, 15, 1), (2, 7, 0), (2, 15, 1), (3, 7, 0), (3, 7, 1)])
+def test_multigrid_converges_to_dense_solve(dim, n, smoother):
+    c = 0.02
+    L = np.eye(n ** dim) - c * _lap(dim, n)
+    b = np.random.default_rng(4).standard_normal(n ** dim)
+    want = np.linalg.solve(L, b)
+    mg = O.MGParams(smoother=smoother, omega=(1.0 if smoother else 2 / 3), vcycles=0,
+                    mg_tol=1e-15, mg_maxcycles=60)
+    got, cycles = O.mg_solve(mg, dim, n, c, b, np.zeros(n ** dim))
+    assert cycles >= 1
+    np.testing.assert_allclose(got, want, atol=1e-13 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("dim,smoother", [(1, 0), (2, 0), (2, 1), (3, 1)])
+def test_vcycle_iteration_matrix(dim, smoother):
+    """V-cycle error propagation: contraction, and the exact solution is a fixed point."""
+    n = 7 if dim == 3 else 15
+    c = 0.01
+    mg = O.MGParams(smoother=smoother, omega=(1.0 if smoother else 2 / 3), vcycles=1)
+    zero = np.zeros(n ** dim)
+    E = _matrix_of(lambda v: O.mg_solve(mg, dim, n, c, zero, v)[0], n ** dim, n ** dim)
+    rho = max(abs(np.linalg.eigvals(E)))
+    assert rho < (0.35 if smoother == 0 else 0.12)
+    L = np.eye(n ** dim) - c * _lap(dim, n)
+    b = np.random.default_rng(5).standard_normal(n ** dim)
+    ustar = np.linalg.solve(L, b)
+    u1, _ = O.mg_solve(mg, dim, n, c, b, ustar)
+    np.testing.assert_allclose(u1, ustar, atol=1e-13)
+
+
+def test_coarsest_grid_is_solved_exactly():
+    for dim in (1, 2, 3):
+        n, c = 3, 0.3
+        L = np.eye(n ** dim) - c * _lap(dim, n)
+        b = np.random.default_rng(6).standard_normal(n ** dim)
+        u, _ = O.mg_solve(O.MGParams(vcycles=1), dim, n, c, b, np.zeros(n ** dim))
+        np.testing.assert_allclose(u, np.linalg.solve(L, b), atol=1e-14)
+
+
+def test_full_solve_stops_on_tolerance_or_stall():
+    dim, n, c = 2, 15, 0.01
+    b = np.random.default_rng(7).standard_normal(n ** dim)
+    mg = O.MGParams(vcycles=0, mg_tol=1e-12, mg_stall=0.75, mg_maxcycles=50)
+    u, cyc = O.mg_solve(mg, dim, n, c, b, np.zeros(n ** dim))
+    r = np.abs(b - O.apply_L(dim, n, c, u)).max()
+    assert r <= 1e-12 * max(1.0, np.abs(b).max()) or cyc == 50
+    assert 5 <= cyc < 50
+    # from the exact solution no cycle is needed
+    L = np.eye(n ** dim) - c * _lap(dim, n)
+    _, cyc0 = O.mg_solve(mg, dim, n, c, b, np.linalg.solve(L, b))
+    assert cyc0 == 0
+
+
+# ---------------------------------------------------------------- SDC (Sec. 2.2, 3)
+
+def _collocation_dense(dim, n, s, nu, dt, u0):
+    """Direct solve of (I - dt Q x A) Y = Y0 (Eq. bigPmatk_2), node-major layout."""
+    Q, _ = _numpy_Q(s)
+    A = nu * _lap(dim, n)
+    N = n ** dim
+    M = np.eye(s * N) - dt * np.kron(Q, A)
+    Y = np.linalg.solve(M, np.tile(u0, s))
+    return Y.reshape(s, N)
+
+
+@pytest.mark.parametrize("dim,n,s", [(1, 15, 3), (2, 7, 5), (3, 3, 3)])
+def test_sweep_is_identity_on_collocation_solution(dim, n, s):
+    nu, dt = 1.0, 0.01
+    u0 = np.random.default_rng(8).standard_normal(n ** dim)
+    Y = _collocation_dense(dim, n, s, nu, dt, u0)
+    F = np.stack([O.apply_A(dim, n, nu, y) for y in Y])
+    U1, F1, _ = O.sweep(dim, n, s, nu, dt, FULL, Y, F)
+    np.testing.assert_allclose(U1, Y, atol=1e-13 * np.abs(Y).max())
+    assert O.residual(dim, n, s, nu, dt, Y, F) < 1e-13
+
+
+@pytest.mark.parametrize("s", [3, 5])
+def test_sweep_follows_scalar_recurrence_on_a_sine_mode(s):
+    """With exact solves and a single eigenmode, every sweep iterate is the mode times
+    the scalar iterate of Eq. lamdtI: (I - z Q_I) Y^{k+1} = Y0 + z (Q - Q_I) Y^k."""
+    dim, n, nu, dt = 2, 15, 1.0, 0.02
+    k = (2, 3)
+    mode = _sine_mode(dim, n, k)
+    lam = nu * (_d(2, n) + _d(3, n))
+    z = lam * dt
+    Q, t = _numpy_Q(s)
+    QI = np.zeros((s, s))
+    for m in range(1, s):
+        QI[m, 1:m + 1] = np.diff(t)[:m]                  # gamma_1..gamma_m (Eq. Qbe)
+    Y = np.ones(s)                                       # spread initial value
+    U = np.tile(mode, (s, 1))
+    F = np.stack([O.apply_A(dim, n, nu, u) for u in U])
+    for _ in range(4):
+        Y = np.linalg.solve(np.eye(s) - z * QI, np.ones(s) + z * (Q - QI) @ Y)
+        U, F, _ = O.sweep(dim, n, s, nu, dt, FULL, U, F)
+        np.testing.assert_allclose(U, np.outer(Y, mode), atol=1e-13)
+
+
+@pytest.mark.parametrize("s", [3, 5])
+def test_sdc_damping_factor_limits(s):
+    """Spectral radius of (I - z Q_I)^-1 z (Q - Q_I) (Eq. SDCMAT), Sec. 3.
+
+    z -> 0: it vanishes, for any nodes.  z -> -inf: the paper's nodes have no left
+    endpoint (q_{m,0} = 0) and the factor vanishes there too, but the Gauss-Lobatto
+    nodes used here include t_0, so node 0 stays fixed and the error on nodes 1..M is
+    multiplied by Qt_I^-1 (Qt_I - Qt) (Qt = Q without row/column 0).  For s = 3 that
+    matrix is [[1/3, 1/12], [-2/3, 7/12]] with complex eigenvalues of modulus
+    sqrt(det) = 1/2, so the stiff-limit damping of 3 Gauss-Lobatto nodes is exactly 1/2."""
+    Q = O.qmatrix(s)
+    t = O.gauss_lobatto(s)
+    QI = np.zeros((s, s))
+    for m in range(1, s):
+        QI[m, 1:m + 1] = np.diff(t)[:m]
+    rho = lambda z: max(abs(np.linalg.eigvals(np.linalg.solve(np.eye(s) - z * QI, z * (Q - QI)))))
+    assert rho(-1e-6) < 1e-5
+    assert abs(rho(-1e9) - rho(-1e11)) < 1e-6                  # the stiff limit exists
+    if s == 3:
+        assert abs(rho(-1e10) - 0.5) < 1e-8
+        Qt, QIt = Q[1:, 1:], QI[1:, 1:]
+        np.testing.assert_allclose(np.linalg.solve(QIt, QIt - Qt), [[1 / 3, 1 / 12], [-2 / 3, 7 / 12]], atol=1e-15)
+    assert max(rho(z) for z in [-0.5, -2, -5, -10, -50]) < 1
+
+
+def test_isdc_converges_to_collocation_pade_over_steps():
+    """Serial ISDC block by block: the end value of each step is R(lambda dt) times the
+    previous one on an eigenmode, R = Pade (s-1,s-1) (the collocation fixed point)."""
+    dim, n, s, nu, dt = 1, 31, 5, 1.0, 0.05
+    mode = _sine_mode(dim, n, (1,))
+    lam = nu * _d(1, n)
+    u = mode.copy()
+    for step in range(1, 4):
+        pf = O.PFASST(dim, n, s, 3, 1, nu, dt, FULL, nlevels=1)
+        pf.set_initial(u)
+        it, hist = pf.run(40, 1e-14)
+        u = pf.end_value()
+        np.testing.assert_allclose(u, _pade(lam * dt, s) ** step * mode, atol=2e-14)
+
+
+def test_paper_1d_decay_value():
+    """Sec. 4.1: k = L = nu = T = 1, dx = 1/128: the solution decays to about 5e-5 by T = 1."""
+    row = _golden_rows("paper_heat_1d_decay.txt")[0].split()
+    want, rtol = float(row[1]), float(row[2])
+    n, s, nu, dt = 127, 5, 1.0, 0.125
+    mode = _sine_mode(1, n, (1,))
+    u = mode.copy()
+    for _ in range(8):
+        pf = O.PFASST(1, n, s, 3, 1, nu, dt, FULL, nlevels=1)
+        pf.set_initial(u)
+        pf.run(40, 1e-13)
+        u = pf.end_value()
+    ratio = u[63] / mode[63]
+    assert abs(ratio - want) / want < rtol
+    # and the ODE solution is e^{nu d(1) T} to the collocation error, the PDE e^{-pi^2} to O(dx^2)
+    assert abs(ratio - math.exp(nu * _d(1, n))) < 1e-9
+    assert abs(ratio - math.exp(-math.pi ** 2)) / math.exp(-math.pi ** 2) < 1e-3
+
+
+def test_3d_with_nu_one_third_decays_like_1d():
+    """Sec. 4.2: nu = 1/3 in 3D gives the decay rate of the 1D test with nu = 1; since the
+    semi-discrete eigenvalue is 3 * d(1) / 3, the 3D end value is the 1D one times the mode."""
+    n, s, dt = 7, 3, 0.05
+    mg = FULL
+    p3 = O.PFASST(3, n, s, 3, 1, 1.0 / 3.0, dt, mg, nlevels=1)
+    p3.set_initial(_sine_mode(3, n, (1, 1, 1)))
+    p3.run(40, 1e-14)
+    p1 = O.PFASST(1, n, s, 3, 1, 1.0, dt, mg, nlevels=1)
+    p1.set_initial(_sine_mode(1, n, (1,)))
+    p1.run(40, 1e-14)
+    ratio1 = p1.end_value() / _sine_mode(1, n, (1,))
+    np.testing.assert_allclose(p3.end_value(), ratio1[0] * _sine_mode(3, n, (1, 1, 1)), atol=1e-14)
+
+
+# ---------------------------------------------------------------- transfers (Sec. 4.2.1)
+
+def test_fourth_order_interpolation_exact_on_cubics_away_from_walls():
+    n, nc = 63, 31
+    xc = np.arange(1, nc + 1) / (nc + 1)
+    xf = np.arange(1, n + 1) / (n + 1)
+    p = lambda x: 0.3 - x + 2 * x ** 2 - 1.5 * x ** 3
+    got = O.interp_add(1, n, 4, 1.0, p(xc), np.zeros(n))
+    # fine 1-based points 4..n-3 use only interior coarse taps
+    np.testing.assert_allclose(got[3:n - 3], p(xf)[3:n - 3], atol=1e-14)
+    # even fine points are injected coarse values; injection after interpolation is identity
+    np.testing.assert_allclose(O.inject(1, n, got), p(xc), atol=0)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_interpolation_odd_reflection_keeps_sine_modes(dim):
+    """Odd reflection at the walls: a sine mode interpolates with O(h^4) error everywhere,
+    including the points next to the walls."""
+    errs = []
+    for n in (15, 31) if dim == 3 else (31, 63):
+        nc = (n - 1) // 2
+        got = O.interp_add(dim, n, 4, 1.0, _sine_mode(dim, nc, (1, 2, 1)), np.zeros(n ** dim))
+        errs.append(np.abs(got - _sine_mode(dim, n, (1, 2, 1))).max())
+    assert errs[1] < errs[0] / 12                      # ~16x for 4th order
+
+
+def test_time_interpolation_reproduces_quadratics():
+    tc = O.gauss_lobatto(3)
+    for t in O.gauss_lobatto(5):
+        w = O.lagrange_weights(tc, t)
+        for k in range(3):
+            assert abs(w @ tc ** k - t ** k) < 1e-15
+
+
+# ---------------------------------------------------------------- FAS / PFASST (Sec. 2.3, 2.4)
+
+def _u0_modes(dim, n):
+    return _sine_mode(dim, n, (1, 1, 1)) + 0.5 * _sine_mode(dim, n, (3, 2, 1))
+
+
+@pytest.mark.parametrize("dim,n", [(1, 31), (2, 15)])
+def test_fas_coarse_sweep_keeps_converged_fine_solution(dim, n):
+    """If U_f is the fine collocation solution and the coarse solves are exact, the FAS
+    coarse problem is solved by the restricted U_f: the coarse correction is zero."""
+    s_f, nu, dt = 5, 1.0, 0.01
+    Y = _collocation_dense(dim, n, s_f, nu, dt, _u0_modes(dim, n))
+    pf = O.PFASST(dim, n, s_f, 3, 1, nu, dt, FULL)
+    pf.Uf[0] = Y
+    pf.Ff[0] = np.stack([O.apply_A(dim, n, nu, y) for y in Y])
+    res = pf.iteration()
+    np.testing.assert_allclose(pf.Uf[0], Y, atol=1e-13)
+    np.testing.assert_allclose(pf.Uc, pf.Uc0, atol=1e-13)
+    assert res[0] < 1e-12
+
+
+@pytest.mark.parametrize("vcycles", [0, 2])
+def test_pfasst_limit_is_serial_collocation(vcycles):
+    """Many PFASST iterations converge to the serial fine collocation solution over all
+    slices: on an eigenmode the end of slice p is R(z)^(p+1) times the mode."""
+    dim, n, P, s_f, nu, dt = 1, 31, 4, 5, 1.0, 0.01
+    mode = _sine_mode(dim, n, (2,))
+    z = nu * _d(2, n) * dt
+    mg = FULL if vcycles == 0 else O.MGParams(vcycles=vcycles, smoother=1, omega=1.0)
+    pf = O.PFASST(dim, n, s_f, 3, P, nu, dt, mg)
+    pf.set_initial(mode)
+    it, hist = pf.run(60, 1e-14)
+    assert hist[-1].max() < 1e-13
+    for p in range(P):
+        np.testing.assert_allclose(pf.Uf[p, -1], _pade(z, s_f) ** (p + 1) * mode, atol=1e-12)
+
+
+def test_pfasst_with_one_slice_and_full_solves_matches_dense_collocation():
+    dim, n, s_f, nu, dt = 2, 15, 5, 1.0, 0.005
+    u0 = _u0_modes(dim, n)
+    Y = _collocation_dense(dim, n, s_f, nu, dt, u0)
+    pf = O.PFASST(dim, n, s_f, 3, 1, nu, dt, FULL)
+    pf.set_initial(u0)
+    pf.run(60, 1e-14)
+    np.testing.assert_allclose(pf.Uf[0], Y, atol=1e-12)
+
+
+def test_predictor_does_p_plus_one_coarse_sweeps():
+    """Predictor (Sec. 2.4): with exact coarse solves and a single slice, one coarse sweep
+    from the spread value; the interpolated fine state after the predictor depends on
+    the number of coarse sweeps, which we check against a manual schedule."""
+    dim, n, s_f, s_c, nu, dt, P = 1, 15, 5, 3, 1.0, 0.02, 3
+    u0 = _u0_modes(dim, n)
+    pf = O.PFASST(dim, n, s_f, s_c, P, nu, dt, FULL)
+    pf.set_initial(u0)
+    pf.predict()
+    # manual: serial coarse chain where slice p does p+1 coarse sweeps (stages)
+    ref = O.PFASST(dim, n, s_f, s_c, P, nu, dt, FULL)
+    ref.set_initial(u0)
+    nc = (n - 1) // 2
+    # coarse state from the spread fine values
+    Uc = np.tile(O.inject(dim, n, u0), (P, s_c, 1))
+    Fc = np.stack([[O.apply_A(dim, nc, nu, u) for u in Uc[p]] for p in range(P)])
+    np.testing.assert_allclose(pf.Uc0, Uc, atol=0)
+    fas = pf.fas.copy()
+    for stage in range(P):
+        if stage > 0:
+            for p in range(P - 1, stage - 1, -1):
+                Uc[p, 0] = Uc[p - 1, -1]
+                Fc[p, 0] = O.apply_A(dim, nc, nu, Uc[p, 0])
+        for p in range(stage, P):
+            Uc[p], Fc[p], _ = O.sweep(dim, nc, s_c, nu, dt, FULL, Uc[p], Fc[p], np.ascontiguousarray(fas[p]))
+    np.testing.assert_allclose(pf.Uc, Uc, atol=1e-15)
