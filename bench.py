@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: DOF-sweeps/s of batched SDC + multigrid (two-level PFASST) at a fixed
+collocation residual, with the HBM-roofline fraction of the dominant kernel.
+
+Workload (default): 3D heat nu = 0.5 on [0,1]^3, 255^3 fine / 127^3 coarse grid, two-level
+PFASST with 5/3 Gauss-Lobatto nodes, 32 time slices batched on one GPU, dt = 0.002,
+u0 = 16 seeded sine modes with |k| <= 8, V(2,1) red-black Gauss-Seidel, 2 V-cycles per
+sub-step, FP32 V-cycles with FP64 SDC/FAS/residuals, 10 PFASST iterations.
+
+One step = one PFASST block solve through the C ABI: spread u0, predictor, iterations
+until the residual target.  The residual target and K_ref (the fine sweeps it takes)
+come from the plain FP64 GPU path run for the workload's 10 iterations (untimed).
+value = n^3 * M_fine * slices * K_ref / (time per step).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# algorithmic bytes per grid point of one launch, by kernel and data precision
+# (reads + writes a kernel cannot avoid)
+def algo_bytes_per_point(kernel: str, tsize: int, sf: int = 5, sc: int = 3) -> float:
+    t = tsize
+    return {
+        "residual0": 8 + 8 + 8 + t,            # read u_m, q_m, u_{m+1} (FP64), write f
+        "smooth_jacobi": 3 * t,                # read e, f, write e'
+        "smooth_rbgs": t + t / 2 + t / 2,      # read all e, f of one colour, write one colour
+        "residual_restrict": 2 * t + t / 8,    # read e, f, write coarse f (3D)
+        "prolong_add": 2 * t + t / 8,          # read/write e, read coarse e
+        "update_u": 8 + 8 + t,                 # read/write u (FP64), read e
+        "apply_A": 16.0,                       # read u, write F
+        "sf_rhs": 8 * sf + 8 * (sf - 1),       # read F at all nodes, write q per sub-step
+        "interp_correction": 16 * sf + 2 * 8 * sc / 8.0,
+        "colloc_residual": 16 * sf,
+        "copy": 16.0, "pack": 16.0, "unpack": 16.0, "zero": t,
+    }.get(kernel, 0.0)
+
+
+def dist_env():
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def sample_clocks_start():
+    try:
+        f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                 else os.devnull, "w")
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def sample_clocks_stop(p, f, gpu_index):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        out, _ = p.communicate(timeout=5)
+    except Exception:
+        p.kill()
+        out = ""
+    rows = []
+    for line in out.splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            if int(parts[0]) != gpu_index:
+                continue
+            rows.append(parts)
+        except ValueError:
+            continue
+    if f is not None:
+        f.write(out)
+        f.close()
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1407_6486_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1407_6486_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, n: int):
+    """DRAM bytes per grid point from a committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    e = d.get(f"{kernel}@{n}")
+    if not e or e.get("src_hash") != kernel_src_hash():
+        return None
+    return float(e["bytes_per_point"])
+
+
+def make_workload(name):
+    from paper_1407_6486_gb300 import inputs
+    if name == "heat3d":
+        return inputs.heat3d_c3()
+    if name == "heat3d-small":
+        return inputs.heat3d_c3(n=63, slices=8)
+    if name == "heat2d":
+        return inputs.heat2d_c2(vcycles=2, precision=1)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class OracleSample:
+    """The FP64 oracle on `slices` of the workload's slices: predictor once, then each
+    sample() times one PFASST iteration (fine sweeps, FAS restriction, coarse chain,
+    interpolation, residual) and returns (DOF-sweeps/s, seconds, cores)."""
+
+    def __init__(self, wl, slices: int):
+        import oracle as O
+        self.wl, self.slices = wl, slices
+        self.o = O.PFASST(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, slices, wl.nu, wl.dt,
+                          O.MGParams(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles), nlevels=wl.nlevels)
+        self.o.set_initial(wl.u0())
+        self.o.predict()
+
+    def sample(self):
+        t0 = time.perf_counter()
+        self.o.iteration()
+        t = time.perf_counter() - t0
+        dofs = self.wl.dofs * (self.wl.fine_nodes - 1) * self.slices
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        return dofs / t, t, cores
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    sl = args.ref_slices
+    orc = OracleSample(wl, sl)
+    for _ in range(args.warmup):
+        orc.sample()
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, t, cores = orc.sample()
+        vals.append(v)
+        secs.append(t)
+    value = len(vals) / sum(1.0 / v for v in vals)
+    sample = (f"one PFASST iteration (fine sweeps, FAS restriction, coarse chain, interpolation, residual) "
+              f"on {sl} of the {wl.slices} slices of {wl.name}, FP64 oracle")
+    line = {"impl": "reference", "metric": "DOF-sweeps/s", "value": value, "unit": "DOF-sweeps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name},
+            "cpu_baseline": {"value": value, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_1407_6486_gb300 as pmg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1407_6486_gb300 import _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    pmg.load()
+    wl = make_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    u0 = wl.u0()
+    u0_dev = torch.tensor(u0, device="cuda")
+    common = dict(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, interp_order=4)
+
+    # calibration: plain FP64 GPU path, the workload's iteration count -> residual target
+    ref = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                           nlevels=wl.nlevels, precision=0, **common)
+    ref.set_initial(u0_dev)
+    _, k_ref, r_ref = ref.iterate(wl.iterations, 0.0)
+    ref.close()
+    del ref
+    torch.cuda.empty_cache()
+    target = float(f"{r_ref * 1.0001:.3e}")
+
+    s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                         nlevels=wl.nlevels, precision=wl.precision, **common)
+    maxit = 4 * wl.iterations
+
+    def step():
+        s.set_initial(u0_dev)
+        return s.iterate(maxit, target)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    pmg.pfasst_mg_profile(s.h, True, 0 if args.profile_all else wl.dofs * wl.slices)
+    launches0 = s.launches()
+    cp, cf = sample_clocks_start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rc, it, res = step()
+        iters.append((rc, it, res))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sample_clocks_stop(cp, cf, local)
+    launches = s.launches() - launches0
+    stats = pmg.pfasst_mg_profile_read(s.h)
+    pmg.pfasst_mg_profile(s.h, False, 0)
+    if args.profile_all:
+        tot = sum(d["ms"] for d in stats)
+        for d in sorted(stats, key=lambda d: -d["ms"]):
+            print(f"{d['kernel']:>18} n={d['n']:>4} prec={d['precision']} launches/step={d['launches'] / args.steps:8.0f} "
+                  f"ms/step={d['ms'] / args.steps:9.2f} share={d['ms'] / tot:6.1%}", file=sys.stderr)
+        stats = [d for d in stats if d["n"] == wl.n and d["points"] >= wl.dofs * wl.slices * d["launches"]]
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    dof_sweeps = wl.dofs * (wl.fine_nodes - 1) * wl.slices * k_ref
+    value = world * dof_sweeps / (ms / 1000.0)
+
+    # end to end through the C ABI with host buffers (h2d of u0, d2h of the end value)
+    u0_host = torch.tensor(u0).pin_memory()
+    out_host = torch.empty(wl.dofs, dtype=torch.float64).pin_memory()
+    out_np = out_host.numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pmg.pfasst_mg_set_initial(s.h, u0_host.numpy())
+        s.iterate(maxit, target)
+        pmg.pfasst_mg_get_solution(s.h, wl.slices - 1, wl.fine_nodes - 1, out_np)
+    torch.cuda.synchronize()
+    e2e_ms = 1000 * (time.perf_counter() - t0) / args.steps
+    t = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+
+    # roofline of the dominant kernel (by summed launch time on the fine grid)
+    peak, peak_kind = measured_peak_gbs()
+    dom = max(stats, key=lambda d: d["ms"]) if stats else None
+    roof = None
+    if dom:
+        ts = 4 if dom["precision"] == 1 else 8
+        bpp = algo_bytes_per_point(dom["kernel"], ts, wl.fine_nodes, wl.coarse_nodes)
+        achieved = bpp * dom["points"] / (dom["ms"] / 1000.0) / 1e9
+        tpp = traffic_for(dom["kernel"], dom["n"])
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tpp * dom["points"] / dom["launches"]) if tpp is not None else None,
+                "kernel": dom["kernel"], "grid": dom["n"], "launches": dom["launches"],
+                "avg_launch_ms": dom["ms"] / dom["launches"], "algo_bytes_per_point": bpp,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+    line = {
+        "metric": "DOF-sweeps/s", "value": value, "unit": "DOF-sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if wl.precision == 1 else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "grid": f"{wl.n}^{wl.dim}/{(wl.n - 1) // 2}^{wl.dim}",
+                   "slices": wl.slices, "nodes": f"{wl.fine_nodes}/{wl.coarse_nodes} Gauss-Lobatto",
+                   "smoother": "V(2,1) " + ("red-black Gauss-Seidel" if wl.smoother == 1 else "Jacobi 2/3"),
+                   "vcycles": wl.vcycles, "precision": "FP32 V-cycles, FP64 SDC/FAS" if wl.precision else "FP64",
+                   "K_ref": k_ref, "residual_target": target, "iterations": [it for _, it, _ in iters],
+                   "final_residual": iters[-1][2], "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "working set > 60 GB, far above the 129 MB L2; no flush"},
+        "roofline": roof,
+        "kernels": sorted(({"kernel": d["kernel"], "n": d["n"], "ms_per_step": d["ms"] / args.steps,
+                            "launches_per_step": d["launches"] / args.steps} for d in stats),
+                          key=lambda d: -d["ms_per_step"])[:8],
+        "e2e": {"value": world * dof_sweeps / (e2e_ms / 1000.0), "unit": "DOF-sweeps/s",
+                "h2d_bytes_per_step": wl.dofs * 8, "d2h_bytes_per_step": wl.dofs * 8, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, tsec, cores = OracleSample(wl, args.ref_slices).sample()
+        line["cpu_baseline"] = {"value": v, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one FP64 oracle PFASST iteration on {args.ref_slices} of the "
+                                          f"{wl.slices} slices ({tsec:.1f} s)"}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "heat3d-small", "heat2d"])
+    ap.add_argument("--ref-slices", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-all", action="store_true",
+                    help="time every launch (not only fine-grid ones) and print the breakdown to stderr")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * pfasst_mg.h -- C ABI of a GB300 (sm_103a) library for batched SDC sweeps with
+ * geometric-multigrid sub-step solves, interwoven with two-level PFASST.
+ *
+ * What it computes ("Interweaving PFASST and Parallel Multigrid", Minion, Speck,
+ * Bolten, Emmett, Ruprecht):
+ *   the heat equation u_t = nu Lap u on [0,1]^d, d = 1, 2, 3, zero Dirichlet walls,
+ *   2nd-order finite differences with n interior points per axis, h = 1/(n+1)
+ *   (Sec. 4.1, Sec. 4.2);  time slices of length dt, each integrated by the
+ *   collocation method on Gauss-Lobatto nodes (Sec. 2.1, Eq. collocationM);
+ *   SDC sweeps with implicit-Euler sub-steps (Sec. 2.2, Eq. sdc-be), whose
+ *   sub-step equations (I - dt_m nu Lap_h) u_{m+1} = rhs (Eq. SDCcompactLIII)
+ *   are solved by geometric multigrid V-cycles, either a fixed small number of
+ *   them (inexact SDC, Sec. 2.3.1) or to a tolerance (Sec. 4.2.1);  two-level
+ *   PFASST with an FAS-corrected coarse level (Sec. 2.3, 2.4), where all time
+ *   slices, which PFASST treats as parallel, run as one batch on one GPU.
+ *
+ * Conventions
+ *   - Every function returns PMG_OK (0) on success, PMG_NOT_CONVERGED (1) when an
+ *     iteration limit was reached, or a negative PMG_ERR_* code.  No C++ exception
+ *     crosses this boundary.  pfasst_mg_last_error() gives a message.
+ *   - All device work is ordered on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  Functions that return host data synchronise it.
+ *   - Grid functions passed in or out use the dense layout [z][y][x], x fastest,
+ *     interior points only (n^d doubles); wall values are zero and not stored.
+ *   - Pointers are borrowed for the duration of the call only; the handle owns all
+ *     device state it allocated.  A caller-provided workspace must outlive the handle.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef PFASST_MG_H
+#define PFASST_MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define PMG_OK                0
+#define PMG_NOT_CONVERGED     1   /* max_iter reached before the tolerance       */
+#define PMG_ERR_INVALID_ARG  -1   /* bad pointer, size or option                 */
+#define PMG_ERR_OOM          -2   /* device allocation failed / workspace short  */
+#define PMG_ERR_CUDA         -3   /* a CUDA runtime call or kernel launch failed */
+#define PMG_ERR_DIVERGED     -4   /* NaN/Inf or growing residual                 */
+#define PMG_ERR_TIMEOUT      -5   /* a bounded device-side wait gave up          */
+#define PMG_ERR_UNSUPPORTED  -6   /* valid but not implemented combination       */
+
+/* ---- problem description ------------------------------------------------- */
+
+/* Spatial grid: dim in {1,2,3}; n interior points per axis on the finest level,
+ * n = 2^p - 1 with 3 <= n <= 1023 so that the multigrid hierarchy n -> (n-1)/2
+ * reaches 3 points (Sec. 4.1.1 "standard geometric multigrid"). */
+typedef struct { int dim; int n; } pmg_grid;
+
+/* Collocation nodes of one level: count = M + 1 nodes in [0,1] including both
+ * endpoints; family 0 = Gauss-Lobatto (the only family implemented). */
+typedef struct { int count; int family; } pmg_nodes_desc;
+
+/* Level hierarchy: nlevels = 1 (SDC / parallel SDC) or 2 (PFASST / MLSDC).  The
+ * coarse level uses coarse_nodes (a subset of the fine nodes, e.g. 3 of 5
+ * Gauss-Lobatto nodes) and the grid (n-1)/2 (Sec. 2.3, spatial and temporal
+ * coarsening). */
+typedef struct { int nlevels; pmg_nodes_desc coarse_nodes; } pmg_levels;
+
+#define PMG_SMOOTHER_JACOBI 0     /* weighted Jacobi, omega (Sec. 4.1.1)          */
+#define PMG_SMOOTHER_RBGS   1     /* red-black Gauss-Seidel (Sec. 4.1.2, 4.2.1)   */
+#define PMG_PREC_FP64       0     /* everything in FP64                           */
+#define PMG_PREC_MIXED      1     /* V-cycles in FP32, SDC/FAS/residuals in FP64  */
+
+typedef struct {
+    int    smoother;      /* PMG_SMOOTHER_*                                          */
+    double omega;         /* relaxation weight (2/3 Jacobi, 1 Gauss-Seidel)          */
+    int    nu1, nu2;      /* pre-/post-smoothing sweeps per level (V(nu1,nu2))       */
+    int    vcycles;       /* > 0: V-cycles per sub-step solve; 0: solve to mg_tol    */
+    double mg_tol;        /* full solve: ||b - L u||_inf <= mg_tol * max(1,||b||_inf) */
+    double mg_stall;      /* full solve stops when new residual >= mg_stall * old    */
+    int    mg_maxcycles;  /* full solve cap on V-cycles                              */
+    int    precision;     /* PMG_PREC_*                                              */
+    int    interp_order;  /* spatial interpolation between PFASST levels: 2 or 4    */
+    int    use_graphs;    /* 1: replay each PFASST iteration as a captured CUDA graph */
+} pmg_options;
+
+typedef struct pmg_ctx *pmg_handle;
+
+/* Defaults: Jacobi omega 2/3, V(2,1), 2 V-cycles, tol 1e-12, stall 0.75, cap 50,
+ * FP64, 4th-order interpolation, graphs on. */
+void pfasst_mg_default_options(pmg_options *opt);
+
+/* Bytes of device workspace pfasst_mg_create needs for this problem.
+ * Errors: PMG_ERR_INVALID_ARG for an invalid description. */
+int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fine_nodes,
+                              const pmg_levels *levels, int slices, const pmg_options *opt,
+                              size_t *bytes);
+
+/* Create a solver for `slices` consecutive time slices of length dt (the PFASST
+ * block [0, slices*dt]) of u_t = nu Lap u.
+ *   grid, fine_nodes, levels, opt (NULL = defaults): as above;  nu > 0, dt > 0;
+ *   slices >= 1;  stream: a cudaStream_t or NULL;
+ *   workspace: device memory of >= pfasst_mg_workspace_bytes() bytes, 256-byte
+ *   aligned, owned by the caller, or NULL to let the library cudaMalloc its own.
+ * Errors: INVALID_ARG (bad sizes, n not 2^p-1, coarse nodes not a subset of the
+ * fine nodes), UNSUPPORTED, OOM, CUDA.  *out is NULL on error. */
+int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fine_nodes,
+                     const pmg_levels *levels, double nu, double dt, int slices,
+                     const pmg_options *opt, void *stream, void *workspace,
+                     size_t workspace_bytes, pmg_handle *out);
+
+/* Set the initial value u0 (n^d doubles, dense) and spread it to every node of every
+ * slice (start of the predictor, Sec. 2.4).  on_device: 1 if u0 is device memory. */
+int pfasst_mg_set_initial(pmg_handle h, const double *u0, int on_device);
+
+/* PFASST predictor (Sec. 2.4): FAS-restrict the spread values; in stage s, every
+ * slice p >= s takes the coarse end value of slice p-1 and does one coarse sweep
+ * (slice p does p+1 sweeps); interpolate the coarse correction.  With one level the
+ * predictor is the spread alone.  pfasst_mg_iterate calls it when needed. */
+int pfasst_mg_predict(pmg_handle h);
+
+/* One SDC sweep (Eq. sdc-be; sub-steps Eq. SDCcompactLIII solved by V-cycles) on
+ * every slice at `level` (0 = fine, batched over slices; 1 = coarse, FAS-corrected,
+ * serial chain over slices where slice p first receives the coarse end value of
+ * slice p-1 -- the blocking coarse communication of Sec. 2.4). */
+int pfasst_mg_sweep(pmg_handle h, int level);
+
+/* PFASST iterations (Sec. 2.4): fine sweep on all slices, FAS restriction, coarse
+ * chain, interpolation of the coarse correction, send-forward of fine end values,
+ * collocation residual (Eq. resid).  Runs the predictor first if it has not run.
+ * Stops after max_iter iterations or when the max-norm residual of every slice is
+ * <= tol.  iters_done / final_res (max over slices) may be NULL.
+ * Returns PMG_OK, PMG_NOT_CONVERGED, PMG_ERR_DIVERGED (NaN/Inf) or another error. */
+int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, double *final_res);
+
+/* Collocation residual r = U_0 + dt Q F(U) - U (Eq. resid) of the fine level,
+ * max norm over nodes and points, one value per slice into res_per_slice (host,
+ * `slices` doubles).  Synchronises the stream. */
+int pfasst_mg_residual(pmg_handle h, double *res_per_slice);
+
+/* Copy the fine solution at (slice, node) into out (n^d doubles, dense).
+ * node in [0, M]; node M of slice P-1 is the end of the block. */
+int pfasst_mg_get_solution(pmg_handle h, int slice, int node, double *out, int on_device);
+
+/* Copy the whole state of `level` (0 fine, 1 coarse): U as [slice][node][n^d],
+ * dense, into host memory out (slices*nodes*N doubles). Synchronises. */
+int pfasst_mg_get_state(pmg_handle h, int level, double *out);
+
+/* Start the next block: the end value of the last slice becomes the new initial
+ * value and is spread (the predictor runs again on the next iterate). */
+int pfasst_mg_advance(pmg_handle h);
+
+/* Number of kernel launches this handle has issued so far (for launch accounting). */
+long long pfasst_mg_launch_count(pmg_handle h);
+
+/* ---- launch profiling ------------------------------------------------------ */
+
+/* Per-kernel aggregate of CUDA-event timings taken on the handle's stream. */
+typedef struct {
+    int       kernel;      /* kernel identifier, see pfasst_mg_kernel_name()          */
+    int       n;           /* interior points per axis of the grid it ran on          */
+    int       precision;   /* 0 FP64, 1 FP32 data                                     */
+    long long launches;    /* launches recorded                                       */
+    long long points;      /* grid points covered, summed over launches and batch     */
+    double    ms;          /* summed launch durations (end event - start event)       */
+} pmg_kernel_stat;
+
+/* Record a CUDA event pair around every later launch that covers at least
+ * min_points grid points (enable = 1), or stop recording (enable = 0). */
+int pfasst_mg_profile(pmg_handle h, int enable, long long min_points);
+
+/* Synchronise, aggregate the recorded launches per (kernel, n, precision) into out
+ * (up to capacity entries), set *count to the number of aggregates, and clear the
+ * record.  Errors: INVALID_ARG, CUDA. */
+int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int *count);
+
+/* Name of a kernel identifier ("smooth_rbgs", ...); "unknown" if out of range. */
+const char *pfasst_mg_kernel_name(int kernel);
+
+/* Release the handle and any device memory it allocated.  NULL is accepted. */
+int pfasst_mg_destroy(pmg_handle h);
+
+/* Message of the last error on h (or of the last failed create when h is NULL). */
+const char *pfasst_mg_last_error(pmg_handle h);
+
+/* ---- standalone multigrid solve ------------------------------------------ */
+
+/* Solve (I - c Lap_h) u = b (the sub-step operator of Eq. SDCcompactLIII with
+ * c = dt_m nu) on `batch` independent grids by V(nu1,nu2)-cycles (Sec. 4.1.1):
+ * opt->vcycles cycles, or to opt->mg_tol with the stall rule if vcycles == 0.
+ * b, u: device pointers, [batch][n^d] dense; u holds the initial guess and
+ * receives the result.  cycles_done (host, may be NULL) gets the V-cycles of the
+ * slowest grid.  Allocates its scratch with cudaMallocAsync on `stream` and frees
+ * it before returning; synchronises the stream.
+ * Errors: INVALID_ARG, OOM, CUDA, DIVERGED. */
+int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const double *b,
+                              double *u, const pmg_options *opt, void *stream, int *cycles_done);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFASST_MG_H */

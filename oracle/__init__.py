@@ -218,6 +218,12 @@ class PFASST:
         self.dim, self.n, self.s_f, self.s_c = dim, n, s_f, s_c
         self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
         self.mg = mg
+        if nlevels > 1:
+            tf, tc = gauss_lobatto(s_f), gauss_lobatto(s_c)
+            if not all(np.min(np.abs(tf - t)) < 1e-14 for t in tc):
+                raise ValueError("coarse nodes must be a subset of the fine nodes")
+            if n < 7:
+                raise ValueError("two levels need n >= 7")
         self._c = _PFASST(dim, n, s_f, s_c if nlevels > 1 else 2, slices, nlevels,
                           interp_order, nu, dt, mg.c())
         Nf = n ** dim

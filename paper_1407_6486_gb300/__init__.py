@@ -1,0 +1,322 @@
+"""Python binding of the pfasst_mg C ABI (``include/pfasst_mg.h``).
+
+Batched SDC sweeps with geometric-multigrid sub-step solves and two-level PFASST
+for the heat equation ("Interweaving PFASST and Parallel Multigrid", Sec. 2 - 4),
+computed entirely by the CUDA kernels of ``libpfasst_mg.so`` (sm_103a).  This module
+only marshals arguments: the functions carry the C names, PyTorch supplies device
+memory (the solver workspace) and the CUDA stream.  There is no CPU fallback: if
+the library has not been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpfasst_mg.so")
+
+PMG_OK = 0
+PMG_NOT_CONVERGED = 1
+PMG_ERR_INVALID_ARG = -1
+PMG_ERR_OOM = -2
+PMG_ERR_CUDA = -3
+PMG_ERR_DIVERGED = -4
+PMG_ERR_TIMEOUT = -5
+PMG_ERR_UNSUPPORTED = -6
+PMG_SMOOTHER_JACOBI = 0
+PMG_SMOOTHER_RBGS = 1
+PMG_PREC_FP64 = 0
+PMG_PREC_MIXED = 1
+
+EXPORTS = [
+    "pfasst_mg_default_options", "pfasst_mg_workspace_bytes", "pfasst_mg_create",
+    "pfasst_mg_set_initial", "pfasst_mg_predict", "pfasst_mg_sweep", "pfasst_mg_iterate",
+    "pfasst_mg_residual", "pfasst_mg_get_solution", "pfasst_mg_get_state", "pfasst_mg_advance",
+    "pfasst_mg_launch_count", "pfasst_mg_destroy", "pfasst_mg_last_error",
+    "pfasst_mg_helmholtz_solve", "pfasst_mg_profile", "pfasst_mg_profile_read", "pfasst_mg_kernel_name",
+]
+
+
+class pmg_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int)]
+
+
+class pmg_nodes_desc(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("family", ctypes.c_int)]
+
+
+class pmg_levels(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int), ("coarse_nodes", pmg_nodes_desc)]
+
+
+class pmg_options(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("vcycles", ctypes.c_int), ("mg_tol", ctypes.c_double),
+                ("mg_stall", ctypes.c_double), ("mg_maxcycles", ctypes.c_int),
+                ("precision", ctypes.c_int), ("interp_order", ctypes.c_int),
+                ("use_graphs", ctypes.c_int)]
+
+
+class pmg_kernel_stat(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("n", ctypes.c_int), ("precision", ctypes.c_int),
+                ("launches", ctypes.c_longlong), ("points", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+
+class PMGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pfasst_mg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libpfasst_mg.so`` (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built: run __graft_entry__.build() "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(LIB_PATH)
+    L.pfasst_mg_default_options.argtypes = [ctypes.POINTER(pmg_options)]
+    L.pfasst_mg_default_options.restype = None
+    L.pfasst_mg_workspace_bytes.argtypes = [ctypes.POINTER(pmg_grid), ctypes.POINTER(pmg_nodes_desc),
+                                            ctypes.POINTER(pmg_levels), _I, ctypes.POINTER(pmg_options),
+                                            ctypes.POINTER(ctypes.c_size_t)]
+    L.pfasst_mg_create.argtypes = [ctypes.POINTER(pmg_grid), ctypes.POINTER(pmg_nodes_desc),
+                                   ctypes.POINTER(pmg_levels), _D, _D, _I, ctypes.POINTER(pmg_options),
+                                   _P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]
+    L.pfasst_mg_set_initial.argtypes = [_P, _P, _I]
+    L.pfasst_mg_predict.argtypes = [_P]
+    L.pfasst_mg_sweep.argtypes = [_P, _I]
+    L.pfasst_mg_iterate.argtypes = [_P, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D)]
+    L.pfasst_mg_residual.argtypes = [_P, _P]
+    L.pfasst_mg_get_solution.argtypes = [_P, _I, _I, _P, _I]
+    L.pfasst_mg_get_state.argtypes = [_P, _I, _P]
+    L.pfasst_mg_advance.argtypes = [_P]
+    L.pfasst_mg_launch_count.argtypes = [_P]
+    L.pfasst_mg_launch_count.restype = ctypes.c_longlong
+    L.pfasst_mg_destroy.argtypes = [_P]
+    L.pfasst_mg_last_error.argtypes = [_P]
+    L.pfasst_mg_last_error.restype = ctypes.c_char_p
+    L.pfasst_mg_helmholtz_solve.argtypes = [ctypes.POINTER(pmg_grid), _D, _I, _P, _P,
+                                            ctypes.POINTER(pmg_options), _P, ctypes.POINTER(_I)]
+    L.pfasst_mg_profile.argtypes = [_P, _I, ctypes.c_longlong]
+    L.pfasst_mg_profile_read.argtypes = [_P, ctypes.POINTER(pmg_kernel_stat), _I, ctypes.POINTER(_I)]
+    L.pfasst_mg_kernel_name.argtypes = [_I]
+    L.pfasst_mg_kernel_name.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("pfasst_mg_default_options", "pfasst_mg_launch_count", "pfasst_mg_last_error",
+                        "pfasst_mg_kernel_name"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc, h=None, allow=(PMG_OK,)):
+    if rc not in allow:
+        msg = load().pfasst_mg_last_error(h)
+        raise PMGError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- same-name wrappers
+
+def pfasst_mg_default_options(**overrides) -> pmg_options:
+    o = pmg_options()
+    load().pfasst_mg_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def pfasst_mg_workspace_bytes(grid, fine_nodes, levels, slices, opt) -> int:
+    nb = ctypes.c_size_t(0)
+    _check(load().pfasst_mg_workspace_bytes(ctypes.byref(grid), ctypes.byref(fine_nodes), ctypes.byref(levels),
+                                            slices, ctypes.byref(opt), ctypes.byref(nb)))
+    return nb.value
+
+
+def pfasst_mg_create(grid, fine_nodes, levels, nu, dt, slices, opt, stream=None, workspace=None):
+    """Returns (handle, workspace tensor).  The workspace is a torch uint8 CUDA tensor
+    that must stay alive as long as the handle (the caller keeps it)."""
+    import torch
+    nbytes = pfasst_mg_workspace_bytes(grid, fine_nodes, levels, slices, opt)
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p()
+    _check(load().pfasst_mg_create(ctypes.byref(grid), ctypes.byref(fine_nodes), ctypes.byref(levels), nu, dt,
+                                   slices, ctypes.byref(opt), _stream_ptr(stream), ctypes.c_void_p(workspace.data_ptr()),
+                                   nbytes, ctypes.byref(h)))
+    return h, workspace
+
+
+def pfasst_mg_set_initial(h, u0):
+    """u0: torch CUDA float64 tensor (n^d) or numpy float64 array (host)."""
+    import numpy as np
+    if hasattr(u0, "is_cuda"):
+        _check(load().pfasst_mg_set_initial(h, _dev_ptr(u0), 1), h)
+    else:
+        a = np.ascontiguousarray(u0, dtype=np.float64)
+        _check(load().pfasst_mg_set_initial(h, a.ctypes.data_as(ctypes.c_void_p), 0), h)
+
+
+def pfasst_mg_predict(h):
+    _check(load().pfasst_mg_predict(h), h)
+
+
+def pfasst_mg_sweep(h, level):
+    _check(load().pfasst_mg_sweep(h, level), h)
+
+
+def pfasst_mg_iterate(h, max_iter, tol):
+    """Returns (status, iterations done, final max residual)."""
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    rc = _check(load().pfasst_mg_iterate(h, max_iter, tol, ctypes.byref(it), ctypes.byref(res)), h,
+                allow=(PMG_OK, PMG_NOT_CONVERGED))
+    return rc, it.value, res.value
+
+
+def pfasst_mg_residual(h, slices):
+    import numpy as np
+    out = np.zeros(slices)
+    _check(load().pfasst_mg_residual(h, out.ctypes.data_as(ctypes.c_void_p)), h)
+    return out
+
+
+def pfasst_mg_get_solution(h, slice_, node, out):
+    """out: torch CUDA float64 tensor or numpy float64 array of n^d values."""
+    if hasattr(out, "is_cuda"):
+        _check(load().pfasst_mg_get_solution(h, slice_, node, _dev_ptr(out), 1), h)
+    else:
+        _check(load().pfasst_mg_get_solution(h, slice_, node, out.ctypes.data_as(ctypes.c_void_p), 0), h)
+    return out
+
+
+def pfasst_mg_get_state(h, level, out):
+    _check(load().pfasst_mg_get_state(h, level, out.ctypes.data_as(ctypes.c_void_p)), h)
+    return out
+
+
+def pfasst_mg_advance(h):
+    _check(load().pfasst_mg_advance(h), h)
+
+
+def pfasst_mg_launch_count(h) -> int:
+    return load().pfasst_mg_launch_count(h)
+
+
+def pfasst_mg_destroy(h):
+    _check(load().pfasst_mg_destroy(h))
+
+
+def pfasst_mg_last_error(h=None) -> str:
+    m = load().pfasst_mg_last_error(h)
+    return m.decode() if m else ""
+
+
+def pfasst_mg_helmholtz_solve(grid, c, batch, b, u, opt, stream=None) -> int:
+    """Solve (I - c Lap_h) u = b in place on u (torch CUDA float64, [batch, n^d]).
+    Returns the number of V-cycles done."""
+    cyc = ctypes.c_int(0)
+    _check(load().pfasst_mg_helmholtz_solve(ctypes.byref(grid), c, batch, _dev_ptr(b), _dev_ptr(u),
+                                            ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(cyc)))
+    return cyc.value
+
+
+def pfasst_mg_profile(h, enable, min_points=0):
+    _check(load().pfasst_mg_profile(h, 1 if enable else 0, min_points), h)
+
+
+def pfasst_mg_profile_read(h):
+    """Returns a list of dicts: kernel name, n, precision, launches, points, ms."""
+    cap = 256
+    arr = (pmg_kernel_stat * cap)()
+    cnt = ctypes.c_int(0)
+    _check(load().pfasst_mg_profile_read(h, arr, cap, ctypes.byref(cnt)), h)
+    return [dict(kernel=pfasst_mg_kernel_name(a.kernel), n=a.n, precision=a.precision, launches=a.launches,
+                 points=a.points, ms=a.ms) for a in arr[:min(cnt.value, cap)]]
+
+
+def pfasst_mg_kernel_name(k) -> str:
+    return load().pfasst_mg_kernel_name(k).decode()
+
+
+# ---------------------------------------------------------------- convenience handle
+
+class PFASSTSolver:
+    """Owns a pfasst_mg handle and its torch workspace; methods call the C ABI."""
+
+    def __init__(self, dim, n, fine_nodes, coarse_nodes, slices, nu, dt, nlevels=2, stream=None, **opts):
+        self.dim, self.n, self.sf, self.sc = dim, n, fine_nodes, coarse_nodes
+        self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
+        self.opt = pfasst_mg_default_options(**opts)
+        self.grid = pmg_grid(dim, n)
+        self.fnodes = pmg_nodes_desc(fine_nodes, 0)
+        self.levels = pmg_levels(nlevels, pmg_nodes_desc(coarse_nodes if nlevels == 2 else 0, 0))
+        self.h, self.workspace = pfasst_mg_create(self.grid, self.fnodes, self.levels, nu, dt, slices, self.opt, stream)
+
+    @property
+    def npts(self):
+        return self.n ** self.dim
+
+    def set_initial(self, u0):
+        pfasst_mg_set_initial(self.h, u0)
+
+    def predict(self):
+        pfasst_mg_predict(self.h)
+
+    def sweep(self, level=0):
+        pfasst_mg_sweep(self.h, level)
+
+    def iterate(self, max_iter, tol):
+        return pfasst_mg_iterate(self.h, max_iter, tol)
+
+    def residual(self):
+        return pfasst_mg_residual(self.h, self.slices)
+
+    def solution(self, slice_, node):
+        import numpy as np
+        return pfasst_mg_get_solution(self.h, slice_, node, np.zeros(self.npts))
+
+    def state(self, level=0):
+        import numpy as np
+        s = self.sf if level == 0 else self.sc
+        n = self.n if level == 0 else (self.n - 1) // 2
+        return pfasst_mg_get_state(self.h, level, np.zeros((self.slices, s, n ** self.dim)))
+
+    def advance(self):
+        pfasst_mg_advance(self.h)
+
+    def launches(self):
+        return pfasst_mg_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            pfasst_mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

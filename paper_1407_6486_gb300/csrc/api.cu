@@ -1,0 +1,903 @@
+// api.cu -- C ABI, host-side set-up and the PFASST / SDC / multigrid schedule.
+//
+// Host set-up computes, in long double: Gauss-Lobatto nodes (eigenvalues of the
+// Jacobi matrix of the (1,1) Jacobi polynomials, whose roots are those of P'_{s-1}),
+// the integration matrix Q of Sec. 2.1 (moment equations of the interpolatory rule),
+// the Lagrange time-interpolation matrix (barycentric form) and the exact inverse of
+// the 3^d coarsest multigrid operator (sine eigen-decomposition).  The device work is
+// the batched schedule of Sec. 2.2 - 2.4 on the kernels of kernels.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pfasst_mg.h"
+#include "pmg_internal.cuh"
+
+using namespace pmg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ----------------------------------------------------------------- nodes and Q
+
+// Gauss-Lobatto nodes on [0,1]: endpoints plus the N-1 roots of P'_N (N = s-1), found
+// by Sturm-sequence bisection on the symmetric tridiagonal Jacobi matrix of the
+// Jacobi(1,1) polynomials (zero diagonal, off-diagonal sqrt(k(k+2)/((2k+1)(2k+3)))).
+void gauss_lobatto(int s, long double *tau) {
+  const int N = s - 1, m = N - 1;
+  std::vector<long double> off(m > 1 ? m - 1 : 1);
+  for (int k = 1; k <= m - 1; ++k) off[k - 1] = sqrtl((long double)k * (k + 2) / ((2.0L * k + 1) * (2.0L * k + 3)));
+  auto count_below = [&](long double x) {
+    int cnt = 0;
+    long double d = 1.0L;
+    for (int i = 0; i < m; ++i) {
+      long double b2 = i > 0 ? off[i - 1] * off[i - 1] : 0.0L;
+      d = (0.0L - x) - (i > 0 ? b2 / d : 0.0L);
+      if (d == 0.0L) d = -1e-300L;
+      if (d < 0) ++cnt;
+    }
+    return cnt;
+  };
+  tau[0] = 0.0L;
+  tau[N] = 1.0L;
+  for (int r = 0; r < m; ++r) {  // r-th smallest eigenvalue
+    long double lo = -1.0L, hi = 1.0L;
+    for (int it = 0; it < 200; ++it) {
+      long double mid = 0.5L * (lo + hi);
+      if (count_below(mid) > r) hi = mid; else lo = mid;
+    }
+    tau[r + 1] = (0.5L * (lo + hi) + 1.0L) / 2.0L;
+  }
+}
+
+// Q[m][j]: weights of the interpolatory rule for the integral over [0, tau_m]:
+// sum_j Q[m][j] tau_j^k = tau_m^{k+1}/(k+1), k = 0..s-1 (Gaussian elimination).
+void integration_matrix(int s, const long double *tau, long double Q[kMaxNodes][kMaxNodes]) {
+  for (int m = 0; m < s; ++m) {
+    long double A[kMaxNodes][kMaxNodes + 1];
+    for (int k = 0; k < s; ++k) {
+      for (int j = 0; j < s; ++j) A[k][j] = powl(tau[j], k);
+      A[k][s] = powl(tau[m], k + 1) / (k + 1);
+    }
+    for (int col = 0; col < s; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < s; ++r)
+        if (fabsl(A[r][col]) > fabsl(A[piv][col])) piv = r;
+      for (int q = 0; q <= s; ++q) { long double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+      for (int r = 0; r < s; ++r) {
+        if (r == col) continue;
+        long double f = A[r][col] / A[col][col];
+        for (int q = col; q <= s; ++q) A[r][q] -= f * A[col][q];
+      }
+    }
+    for (int j = 0; j < s; ++j) Q[m][j] = A[j][s] / A[j][j];
+  }
+}
+
+// Lagrange weights of the coarse nodes tc at the point t (barycentric form)
+void lagrange_row(int sc, const long double *tc, long double t, double *row) {
+  for (int j = 0; j < sc; ++j)
+    if (fabsl(t - tc[j]) < 1e-15L) {
+      for (int q = 0; q < sc; ++q) row[q] = q == j ? 1.0 : 0.0;
+      return;
+    }
+  long double lam[kMaxNodes], den = 0.0L;
+  for (int j = 0; j < sc; ++j) {
+    lam[j] = 1.0L;
+    for (int i = 0; i < sc; ++i)
+      if (i != j) lam[j] /= (tc[j] - tc[i]);
+    den += lam[j] / (t - tc[j]);
+  }
+  for (int j = 0; j < sc; ++j) row[j] = (double)((lam[j] / (t - tc[j])) / den);
+}
+
+// exact inverse of (I - c Lap_h) on the 3^dim grid (h = 1/4) from the sine
+// eigenvectors v_k(i) = sqrt(1/2) sin(k pi (i+1)/4) of the 1D operator
+void coarsest_inverse(int dim, double c, std::vector<double> &out) {
+  const int N3 = dim == 1 ? 3 : (dim == 2 ? 9 : 27);
+  out.assign((size_t)N3 * N3, 0.0);
+  const long double pi = 3.14159265358979323846264338327950288L;
+  long double v[3][3], mu[3];
+  for (int k = 0; k < 3; ++k) {
+    mu[k] = (2.0L * cosl((k + 1) * pi / 4.0L) - 2.0L) * 16.0L;
+    for (int i = 0; i < 3; ++i) v[k][i] = sqrtl(0.5L) * sinl((k + 1) * pi * (i + 1) / 4.0L);
+  }
+  auto decode = [&](int p, int *ix) { ix[0] = p % 3; ix[1] = (p / 3) % 3; ix[2] = p / 9; };
+  for (int p = 0; p < N3; ++p)
+    for (int q = 0; q < N3; ++q) {
+      int pi3[3], qi3[3];
+      decode(p, pi3);
+      decode(q, qi3);
+      long double acc = 0.0L;
+      for (int kk = 0; kk < N3; ++kk) {
+        int ks[3];
+        decode(kk, ks);
+        long double lam = 1.0L, prod = 1.0L;
+        for (int a = 0; a < dim; ++a) {
+          lam -= (long double)c * mu[ks[a]];
+          prod *= v[ks[a]][pi3[a]] * v[ks[a]][qi3[a]];
+        }
+        acc += prod / lam;
+      }
+      out[(size_t)p * N3 + q] = (double)acc;
+    }
+}
+
+bool is_pow2_minus1(int n) { return n >= 3 && ((n + 1) & n) == 0; }
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ----------------------------------------------------------------- hierarchy
+
+struct Hier {
+  int L = 0;
+  Grid lev[kMaxLevels];
+  void *e[kMaxLevels] = {}, *e2[kMaxLevels] = {}, *f[kMaxLevels] = {};
+  Prec pr = F64;
+  size_t tsize = 8;
+};
+
+int mg_levels(int n) {
+  int L = 1;
+  while (n > 3) { n = (n - 1) / 2; ++L; }
+  return L;
+}
+
+// memory plan: a list of (pointer slot, bytes) carved from one block
+struct Plan {
+  std::vector<std::pair<void **, size_t>> items;
+  size_t total = 0;
+  void add(void **slot, size_t bytes) { items.push_back({slot, bytes}); total += align256(bytes); }
+  void carve(char *base) {
+    size_t o = 0;
+    for (auto &it : items) { *it.first = base + o; o += align256(it.second); }
+  }
+};
+
+}  // namespace
+
+// ----------------------------------------------------------------- handle
+
+struct pmg_ctx {
+  int dim = 0, nf = 0, nc = 0, sf = 0, sc = 0, P = 0, nlevels = 1;
+  double nu = 0, dt = 0;
+  pmg_options opt{};
+  cudaStream_t stream = nullptr;
+  Grid gf{}, gc{}, gd{};
+  long double tauf[kMaxNodes] = {}, tauc[kMaxNodes] = {};
+  SFCoef sff{}, sfc{};
+  ResCoef resf{};
+  FASCoef fas{};
+  InterpCoef interp{};
+  double cf_sub[kMaxNodes] = {}, cc_sub[kMaxNodes] = {};  // c_m = dt_m nu per sub-step
+  // device state
+  double *Uf = nullptr, *Ff = nullptr, *qf = nullptr, *u0 = nullptr, *dense = nullptr;
+  double *Uc = nullptr, *Fc = nullptr, *qc = nullptr, *tau = nullptr, *Uc0 = nullptr;
+  Hier H;
+  void *minv = nullptr;  // (sf-1 + sc-1) slots of N3*N3 in MG precision
+  int n3 = 3;
+  unsigned long long *red = nullptr;  // [3P]: rnorm, bnorm, colloc residual
+  int *active = nullptr;
+  unsigned long long *hred = nullptr;  // pinned
+  int *hactive = nullptr;              // pinned
+  void *ws = nullptr;
+  bool ws_owned = false;
+  bool predicted = false;
+  long long launches = 0;
+  Profiler prof;
+  std::string err;
+
+  Launch L() { return Launch{stream, &launches, &prof}; }
+  const void *minv_slot(int slot) const { return (const char *)minv + (size_t)slot * n3 * n3 * H.tsize; }
+};
+
+namespace {
+
+int fail(pmg_ctx *h, int code, const std::string &msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+#define PMG_CUDA(h, expr)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(h, PMG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+#define PMG_RET(expr)            \
+  do {                           \
+    int r_ = (expr);             \
+    if (r_ != PMG_OK) return r_; \
+  } while (0)
+
+int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,
+             const pmg_options *o, std::string &why) {
+  if (!grid || !fn || !lv) { why = "null description"; return PMG_ERR_INVALID_ARG; }
+  if (grid->dim < 1 || grid->dim > 3) { why = "dim must be 1, 2 or 3"; return PMG_ERR_INVALID_ARG; }
+  if (!is_pow2_minus1(grid->n) || grid->n > 1023) { why = "n must be 2^p - 1 in [3, 1023]"; return PMG_ERR_INVALID_ARG; }
+  if (fn->family != 0) { why = "only Gauss-Lobatto nodes (family 0)"; return PMG_ERR_UNSUPPORTED; }
+  if (fn->count < 2 || fn->count > kMaxNodes) { why = "fine node count must be in [2, 9]"; return PMG_ERR_INVALID_ARG; }
+  if (lv->nlevels != 1 && lv->nlevels != 2) { why = "nlevels must be 1 or 2"; return PMG_ERR_INVALID_ARG; }
+  if (lv->nlevels == 2) {
+    if (lv->coarse_nodes.family != 0) { why = "only Gauss-Lobatto coarse nodes"; return PMG_ERR_UNSUPPORTED; }
+    if (lv->coarse_nodes.count < 2 || lv->coarse_nodes.count > fn->count) { why = "bad coarse node count"; return PMG_ERR_INVALID_ARG; }
+    if (grid->n < 7) { why = "two levels need n >= 7"; return PMG_ERR_INVALID_ARG; }
+  }
+  if (slices < 1 || slices > 4096) { why = "slices must be in [1, 4096]"; return PMG_ERR_INVALID_ARG; }
+  if (o) {
+    if (o->smoother != PMG_SMOOTHER_JACOBI && o->smoother != PMG_SMOOTHER_RBGS) { why = "bad smoother"; return PMG_ERR_INVALID_ARG; }
+    if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 == 0 || o->nu1 > 16 || o->nu2 > 16) { why = "bad nu1/nu2"; return PMG_ERR_INVALID_ARG; }
+    if (o->vcycles < 0 || o->vcycles > 1000) { why = "bad vcycles"; return PMG_ERR_INVALID_ARG; }
+    if (o->vcycles == 0 && (o->mg_maxcycles < 1 || !(o->mg_tol > 0))) { why = "bad full-solve settings"; return PMG_ERR_INVALID_ARG; }
+    if (o->precision != PMG_PREC_FP64 && o->precision != PMG_PREC_MIXED) { why = "bad precision"; return PMG_ERR_INVALID_ARG; }
+    if (o->interp_order != 2 && o->interp_order != 4) { why = "interp_order must be 2 or 4"; return PMG_ERR_INVALID_ARG; }
+    if (!(o->omega > 0) || o->omega > 2) { why = "omega must be in (0, 2]"; return PMG_ERR_INVALID_ARG; }
+  }
+  return PMG_OK;
+}
+
+// multigrid hierarchy for `batch` grids of size n (levels n, (n-1)/2, ..., 3)
+void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smoother) {
+  H.L = mg_levels(n);
+  H.pr = pr;
+  H.tsize = pr == F64 ? 8 : 4;
+  int nl = n;
+  for (int l = 0; l < H.L; ++l) {
+    H.lev[l] = make_grid(dim, nl);
+    size_t bytes = (size_t)H.lev[l].slab * batch * H.tsize;
+    pl.add(&H.e[l], bytes);
+    pl.add(&H.f[l], bytes);
+    if (smoother == PMG_SMOOTHER_JACOBI) pl.add(&H.e2[l], bytes);
+    nl = (nl - 1) / 2;
+  }
+}
+
+void plan_ctx(Plan &pl, pmg_ctx *h) {
+  const size_t sf = (size_t)h->gf.slab * 8;
+  pl.add((void **)&h->Uf, sf * h->P * h->sf);
+  pl.add((void **)&h->Ff, sf * h->P * h->sf);
+  pl.add((void **)&h->qf, sf * h->P * (h->sf - 1));
+  pl.add((void **)&h->u0, sf);
+  pl.add((void **)&h->dense, sf);
+  if (h->nlevels == 2) {
+    const size_t sc = (size_t)h->gc.slab * 8;
+    pl.add((void **)&h->Uc, sc * h->P * h->sc);
+    pl.add((void **)&h->Fc, sc * h->P * h->sc);
+    pl.add((void **)&h->tau, sc * h->P * h->sc);
+    pl.add((void **)&h->Uc0, sc * h->P * h->sc);
+    pl.add((void **)&h->qc, sc * h->P * (h->sc - 1));
+  }
+  plan_hier(pl, h->H, h->dim, h->nf, h->P, h->opt.precision == PMG_PREC_MIXED ? F32 : F64, h->opt.smoother);
+  const int slots = (h->sf - 1) + (h->nlevels == 2 ? h->sc - 1 : 0);
+  pl.add(&h->minv, (size_t)slots * h->n3 * h->n3 * h->H.tsize);
+  pl.add((void **)&h->red, sizeof(unsigned long long) * 3 * h->P);
+  pl.add((void **)&h->active, sizeof(int) * h->P);
+}
+
+// ----------------------------------------------------------------- multigrid schedule
+
+struct MGCtx {
+  Launch L;
+  Hier *H;
+  const pmg_options *o;
+  unsigned long long *red;  // [2 * batch] norms (full-solve mode)
+  int *active;              // [batch]
+  unsigned long long *hred;
+  int *hactive;
+  pmg_ctx *h;               // for error messages (may be null)
+  cudaStream_t stream;
+};
+
+int smooth(MGCtx &M, int l, int B, double c, void *&cur, bool first) {
+  Hier &H = *M.H;
+  const pmg_options &o = *M.o;
+  if (o.smoother == PMG_SMOOTHER_JACOBI) {
+    void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
+    PMG_CUDA(M.h, k_smooth_jacobi(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], B, first));
+    cur = out;
+  } else {
+    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 0, first));
+    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 1, false));
+  }
+  return PMG_OK;
+}
+
+// one V(nu1,nu2)-cycle for (I - c Lap) e = f[l0] on levels l0..L-1; *eout = result
+int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void **eout) {
+  Hier &H = *M.H;
+  const pmg_options &o = *M.o;
+  void *cur[kMaxLevels];
+  for (int l = l0; l < H.L - 1; ++l) {
+    cur[l] = H.e[l];
+    if (o.nu1 == 0) PMG_CUDA(M.h, k_zero(M.L, H.lev[l], H.pr, cur[l], B));
+    for (int s = 0; s < o.nu1; ++s) PMG_RET(smooth(M, l, B, c, cur[l], s == 0));
+    PMG_CUDA(M.h, k_residual_restrict(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
+  }
+  const int lc = H.L - 1;
+  PMG_CUDA(M.h, k_coarse_solve(M.L, H.lev[lc], H.pr, minv, H.f[lc], H.e[lc], B));
+  cur[lc] = H.e[lc];
+  for (int l = lc - 1; l >= l0; --l) {
+    PMG_CUDA(M.h, k_prolong_add(M.L, H.lev[l], H.lev[l + 1], H.pr, cur[l + 1], cur[l], B));
+    for (int s = 0; s < o.nu2; ++s) PMG_RET(smooth(M, l, B, c, cur[l], false));
+  }
+  *eout = cur[l0];
+  return PMG_OK;
+}
+
+// Solve (I - c Lap) u1 = um + qm for B grids on hierarchy level l0 (fixed V-cycles or
+// full solve with the tolerance / stall rule).  *cycles = max cycles over the batch.
+int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const double *um, long long sum,
+                  const double *qm, long long sq, double *u1, long long s1, int *cycles) {
+  Hier &H = *M.H;
+  const pmg_options &o = *M.o;
+  const Grid &g = H.lev[l0];
+  if (o.vcycles > 0) {
+    for (int v = 0; v < o.vcycles; ++v) {
+      void *e = nullptr;
+      PMG_CUDA(M.h, k_residual0(M.L, g, c, H.pr, um, sum, qm, sq, u1, s1, H.f[l0], B, nullptr, nullptr));
+      PMG_RET(vcycle(M, l0, B, c, minv, &e));
+      PMG_CUDA(M.h, k_update_u(M.L, g, H.pr, u1, s1, e, B, nullptr));
+    }
+    if (cycles) *cycles = o.vcycles;
+    return PMG_OK;
+  }
+  // full solve (host-driven, per-grid activity mask)
+  std::vector<double> r(B), bn(B);
+  std::vector<int> done(B), cyc(B, 0);
+  auto norms = [&](std::vector<double> &rr, std::vector<double> *bb) -> int {
+    PMG_CUDA(M.h, cudaMemsetAsync(M.red, 0, sizeof(unsigned long long) * 2 * B, M.stream));
+    PMG_CUDA(M.h, k_residual0(M.L, g, c, H.pr, um, sum, qm, sq, u1, s1, H.f[l0], B, M.red, M.red + B));
+    PMG_CUDA(M.h, cudaMemcpyAsync(M.hred, M.red, sizeof(unsigned long long) * 2 * B, cudaMemcpyDeviceToHost, M.stream));
+    PMG_CUDA(M.h, cudaStreamSynchronize(M.stream));
+    for (int p = 0; p < B; ++p) {
+      unsigned long long rv = M.hred[p], bv = M.hred[B + p];
+      double rd, bd;
+      std::memcpy(&rd, &rv, 8);
+      std::memcpy(&bd, &bv, 8);
+      if (std::isnan(rd) || std::isinf(rd)) return fail(M.h, PMG_ERR_DIVERGED, "NaN/Inf in a sub-step residual");
+      rr[p] = rd;
+      if (bb) (*bb)[p] = bd < 1.0 ? 1.0 : bd;
+    }
+    return PMG_OK;
+  };
+  PMG_RET(norms(r, &bn));
+  int left = 0;
+  for (int p = 0; p < B; ++p) {
+    done[p] = !(r[p] > o.mg_tol * bn[p]);
+    left += !done[p];
+  }
+  std::vector<double> rn(B);
+  for (int it = 0; left > 0 && it < o.mg_maxcycles; ++it) {
+    for (int p = 0; p < B; ++p) M.hactive[p] = !done[p];
+    PMG_CUDA(M.h, cudaMemcpyAsync(M.active, M.hactive, sizeof(int) * B, cudaMemcpyHostToDevice, M.stream));
+    void *e = nullptr;
+    PMG_RET(vcycle(M, l0, B, c, minv, &e));
+    PMG_CUDA(M.h, k_update_u(M.L, g, H.pr, u1, s1, e, B, M.active));
+    PMG_RET(norms(rn, nullptr));
+    left = 0;
+    for (int p = 0; p < B; ++p) {
+      if (done[p]) continue;
+      ++cyc[p];
+      if (rn[p] >= o.mg_stall * r[p]) { done[p] = 1; continue; }
+      r[p] = rn[p];
+      if (!(r[p] > o.mg_tol * bn[p])) done[p] = 1;
+      left += !done[p];
+    }
+  }
+  int mx = 0;
+  for (int p = 0; p < B; ++p) mx = cyc[p] > mx ? cyc[p] : mx;
+  if (cycles) *cycles = mx;
+  return PMG_OK;
+}
+
+MGCtx mgctx(pmg_ctx *h) {
+  MGCtx M{h->L(), &h->H, &h->opt, h->red, h->active, h->hred, h->hactive, h, h->stream};
+  return M;
+}
+
+// ----------------------------------------------------------------- SDC / PFASST schedule
+
+// One SDC sweep (Eq. sdc-be) on slices [p0, p0+B) of `level` (0 fine, 1 coarse).
+int sweep(pmg_ctx *h, int level, int p0, int B) {
+  MGCtx M = mgctx(h);
+  const Grid &g = level ? h->gc : h->gf;
+  const int s = level ? h->sc : h->sf;
+  const long long stride = (long long)s * g.slab, sq = (long long)(s - 1) * g.slab;
+  double *U = (level ? h->Uc : h->Uf) + p0 * stride;
+  double *F = (level ? h->Fc : h->Ff) + p0 * stride;
+  double *q = (level ? h->qc : h->qf) + p0 * sq;
+  const double *tau = level ? h->tau + p0 * stride : nullptr;
+  const SFCoef &cf = level ? h->sfc : h->sff;
+  Launch Ln = h->L();
+  PMG_CUDA(h, k_sf_rhs(Ln, g, cf, F, stride, tau, stride, q, sq, B));
+  for (int m = 0; m < s - 1; ++m) {
+    const double c = level ? h->cc_sub[m] : h->cf_sub[m];
+    const int slot = level ? (h->sf - 1) + m : m;
+    PMG_RET(solve_substep(M, level, B, c, h->minv_slot(slot), U + m * g.slab, stride, q + m * g.slab, sq,
+                          U + (m + 1) * g.slab, stride, nullptr));
+    PMG_CUDA(h, k_apply_A(Ln, g, h->nu, U + (m + 1) * g.slab, stride, F + (m + 1) * g.slab, stride, B));
+  }
+  return PMG_OK;
+}
+
+int fas_restrict_all(pmg_ctx *h) {
+  const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
+  PMG_CUDA(h, k_fas_restrict(h->L(), h->gf, h->gc, h->fas, h->Uf, h->Ff, sfs, h->Uc, h->Fc, h->tau, h->Uc0, scs,
+                             h->P));
+  return PMG_OK;
+}
+
+// U_c[p][0] <- U_c[p-1][M_c] and F_c[p][0] = A_c U_c[p][0] for p in [p0, p0+B), p0 >= 1
+int coarse_receive(pmg_ctx *h, int p0, int B) {
+  const long long scs = (long long)h->sc * h->gc.slab;
+  PMG_CUDA(h, k_copy(h->L(), h->gc, h->Uc + (p0 - 1) * scs + (h->sc - 1) * h->gc.slab, scs, h->Uc + p0 * scs, scs, B));
+  PMG_CUDA(h, k_apply_A(h->L(), h->gc, h->nu, h->Uc + p0 * scs, scs, h->Fc + p0 * scs, scs, B));
+  return PMG_OK;
+}
+
+int interp_all(pmg_ctx *h) {
+  const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
+  PMG_CUDA(h, k_interp_correction(h->L(), h->gf, h->gc, h->interp, h->Uf, sfs, h->Uc, h->Uc0, scs, h->P));
+  PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf, h->gf.slab, h->Ff, h->gf.slab, h->P * h->sf));
+  return PMG_OK;
+}
+
+int predict(pmg_ctx *h) {
+  if (h->nlevels == 2) {
+    PMG_RET(fas_restrict_all(h));
+    for (int s = 0; s < h->P; ++s) {
+      if (s > 0) PMG_RET(coarse_receive(h, s, h->P - s));
+      PMG_RET(sweep(h, 1, s, h->P - s));
+    }
+    PMG_RET(interp_all(h));
+  }
+  h->predicted = true;
+  return PMG_OK;
+}
+
+int colloc_residual(pmg_ctx *h) {
+  const long long sfs = (long long)h->sf * h->gf.slab;
+  PMG_CUDA(h, cudaMemsetAsync(h->red + 2 * h->P, 0, sizeof(unsigned long long) * h->P, h->stream));
+  PMG_CUDA(h, k_colloc_residual(h->L(), h->gf, h->resf, h->Uf, h->Ff, sfs, h->P, h->red + 2 * h->P));
+  PMG_CUDA(h, cudaMemcpyAsync(h->hred + 2 * h->P, h->red + 2 * h->P, sizeof(unsigned long long) * h->P,
+                              cudaMemcpyDeviceToHost, h->stream));
+  return PMG_OK;
+}
+
+// one PFASST iteration (Sec. 2.4), residual copied to hred[2P..3P) asynchronously
+int iteration(pmg_ctx *h) {
+  const long long sfs = (long long)h->sf * h->gf.slab;
+  PMG_RET(sweep(h, 0, 0, h->P));
+  if (h->nlevels == 2) {
+    PMG_RET(fas_restrict_all(h));
+    for (int p = 0; p < h->P; ++p) {
+      if (p > 0) PMG_RET(coarse_receive(h, p, 1));
+      PMG_RET(sweep(h, 1, p, 1));
+    }
+    PMG_RET(interp_all(h));
+  }
+  if (h->P > 1) {  // send forward: U_f[p][0] <- U_f[p-1][M_f]
+    PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + (h->sf - 1) * h->gf.slab, sfs, h->Uf + sfs, sfs, h->P - 1));
+    PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf + sfs, sfs, h->Ff + sfs, sfs, h->P - 1));
+  }
+  PMG_RET(colloc_residual(h));
+  return PMG_OK;
+}
+
+double bits_to_double(unsigned long long v) {
+  double d;
+  std::memcpy(&d, &v, 8);
+  return d;
+}
+
+int spread(pmg_ctx *h) {
+  // F = A u0 once, then copy u0 and F to every node of every slice
+  PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->u0, 0, h->dense, 0, 1));
+  PMG_CUDA(h, k_copy(h->L(), h->gf, h->u0, 0, h->Uf, h->gf.slab, h->P * h->sf));
+  PMG_CUDA(h, k_copy(h->L(), h->gf, h->dense, 0, h->Ff, h->gf.slab, h->P * h->sf));
+  h->predicted = false;
+  return PMG_OK;
+}
+
+void fill_coefficients(pmg_ctx *h) {
+  long double Qf[kMaxNodes][kMaxNodes], Qc[kMaxNodes][kMaxNodes];
+  gauss_lobatto(h->sf, h->tauf);
+  integration_matrix(h->sf, h->tauf, Qf);
+  auto fill_sf = [&](SFCoef &cf, int s, const long double *t, long double Q[kMaxNodes][kMaxNodes], double *csub) {
+    std::memset(&cf, 0, sizeof cf);
+    cf.s = s;
+    for (int m = 0; m < s - 1; ++m) {
+      const long double dtm = (long double)h->dt * (t[m + 1] - t[m]);
+      csub[m] = (double)(dtm * h->nu);
+      for (int j = 0; j < s; ++j) {
+        long double w = (long double)h->dt * (Q[m + 1][j] - Q[m][j]);
+        if (j == m + 1) w -= dtm;
+        cf.W[m][j] = (double)w;
+      }
+    }
+  };
+  fill_sf(h->sff, h->sf, h->tauf, Qf, h->cf_sub);
+  std::memset(&h->resf, 0, sizeof h->resf);
+  h->resf.s = h->sf;
+  for (int m = 0; m < h->sf; ++m)
+    for (int i = 0; i < h->sf; ++i) h->resf.dtQ[m][i] = (double)((long double)h->dt * Qf[m][i]);
+  if (h->nlevels == 2) {
+    gauss_lobatto(h->sc, h->tauc);
+    integration_matrix(h->sc, h->tauc, Qc);
+    fill_sf(h->sfc, h->sc, h->tauc, Qc, h->cc_sub);
+    std::memset(&h->fas, 0, sizeof h->fas);
+    h->fas.sf = h->sf;
+    h->fas.sc = h->sc;
+    h->fas.nu = h->nu;
+    for (int j = 0; j < h->sc; ++j) {
+      h->fas.map[j] = -1;
+      for (int m = 0; m < h->sf; ++m)
+        if (fabsl(h->tauf[m] - h->tauc[j]) < 1e-13L) h->fas.map[j] = m;
+      for (int i = 0; i < h->sf; ++i) h->fas.dtQf[j][i] = (double)((long double)h->dt * Qf[h->fas.map[j]][i]);
+      for (int i = 0; i < h->sc; ++i) h->fas.dtQc[j][i] = (double)((long double)h->dt * Qc[j][i]);
+    }
+    std::memset(&h->interp, 0, sizeof h->interp);
+    h->interp.sf = h->sf;
+    h->interp.sc = h->sc;
+    h->interp.order = h->opt.interp_order;
+    for (int m = 0; m < h->sf; ++m) lagrange_row(h->sc, h->tauc, h->tauf[m], h->interp.T[m]);
+  }
+}
+
+int upload_minv(pmg_ctx *h) {
+  const int slots = (h->sf - 1) + (h->nlevels == 2 ? h->sc - 1 : 0);
+  std::vector<double> M;
+  std::vector<char> buf((size_t)slots * h->n3 * h->n3 * h->H.tsize);
+  for (int s = 0; s < slots; ++s) {
+    const double c = s < h->sf - 1 ? h->cf_sub[s] : h->cc_sub[s - (h->sf - 1)];
+    coarsest_inverse(h->dim, c, M);
+    for (size_t q = 0; q < M.size(); ++q) {
+      char *dst = buf.data() + ((size_t)s * h->n3 * h->n3 + q) * h->H.tsize;
+      if (h->H.tsize == 8) std::memcpy(dst, &M[q], 8);
+      else { float fv = (float)M[q]; std::memcpy(dst, &fv, 4); }
+    }
+  }
+  PMG_CUDA(h, cudaMemcpyAsync(h->minv, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PMG_OK;
+}
+
+pmg_ctx *make_ctx(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, double nu, double dt,
+                  int slices, const pmg_options *opt) {
+  pmg_ctx *h = new (std::nothrow) pmg_ctx();
+  if (!h) return nullptr;
+  if (opt) h->opt = *opt; else pfasst_mg_default_options(&h->opt);
+  h->dim = grid->dim;
+  h->nf = grid->n;
+  h->nc = (grid->n - 1) / 2;
+  h->sf = fn->count;
+  h->nlevels = lv->nlevels;
+  h->sc = lv->nlevels == 2 ? lv->coarse_nodes.count : 0;
+  h->P = slices;
+  h->nu = nu;
+  h->dt = dt;
+  h->gf = make_grid(h->dim, h->nf);
+  if (h->nlevels == 2) h->gc = make_grid(h->dim, h->nc);
+  h->n3 = h->dim == 1 ? 3 : (h->dim == 2 ? 9 : 27);
+  return h;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- C ABI
+
+extern "C" {
+
+void pfasst_mg_default_options(pmg_options *o) {
+  if (!o) return;
+  o->smoother = PMG_SMOOTHER_JACOBI;
+  o->omega = 2.0 / 3.0;
+  o->nu1 = 2;
+  o->nu2 = 1;
+  o->vcycles = 2;
+  o->mg_tol = 1e-12;
+  o->mg_stall = 0.75;
+  o->mg_maxcycles = 50;
+  o->precision = PMG_PREC_FP64;
+  o->interp_order = 4;
+  o->use_graphs = 1;
+}
+
+int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,
+                              const pmg_options *opt, size_t *bytes) {
+  std::string why;
+  int rc = validate(grid, fn, lv, slices, opt, why);
+  if (rc != PMG_OK) return fail(nullptr, rc, why);
+  if (!bytes) return fail(nullptr, PMG_ERR_INVALID_ARG, "bytes is null");
+  pmg_ctx *h = make_ctx(grid, fn, lv, 1.0, 1.0, slices, opt);
+  if (!h) return fail(nullptr, PMG_ERR_OOM, "host allocation failed");
+  Plan pl;
+  plan_ctx(pl, h);
+  *bytes = pl.total;
+  delete h;
+  return PMG_OK;
+}
+
+int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, double nu, double dt,
+                     int slices, const pmg_options *opt, void *stream, void *workspace, size_t workspace_bytes,
+                     pmg_handle *out) {
+  if (!out) return fail(nullptr, PMG_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  std::string why;
+  int rc = validate(grid, fn, lv, slices, opt, why);
+  if (rc != PMG_OK) return fail(nullptr, rc, why);
+  if (!(nu > 0) || !(dt > 0) || !std::isfinite(nu) || !std::isfinite(dt))
+    return fail(nullptr, PMG_ERR_INVALID_ARG, "nu and dt must be positive and finite");
+  pmg_ctx *h = make_ctx(grid, fn, lv, nu, dt, slices, opt);
+  if (!h) return fail(nullptr, PMG_ERR_OOM, "host allocation failed");
+  h->stream = (cudaStream_t)stream;
+  fill_coefficients(h);
+  if (h->nlevels == 2)
+    for (int j = 0; j < h->sc; ++j)
+      if (h->fas.map[j] < 0) {
+        delete h;
+        return fail(nullptr, PMG_ERR_INVALID_ARG, "coarse nodes are not a subset of the fine nodes");
+      }
+  Plan pl;
+  plan_ctx(pl, h);
+  if (workspace) {
+    if (workspace_bytes < pl.total || ((uintptr_t)workspace & 255)) {
+      delete h;
+      return fail(nullptr, PMG_ERR_OOM, "workspace too small or not 256-byte aligned");
+    }
+    h->ws = workspace;
+  } else {
+    cudaError_t e = cudaMalloc(&h->ws, pl.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return fail(nullptr, PMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->ws_owned = true;
+  }
+  pl.carve((char *)h->ws);
+  auto bail = [&](int code, const std::string &m) {
+    if (h->ws_owned) cudaFree(h->ws);
+    if (h->hred) cudaFreeHost(h->hred);
+    if (h->hactive) cudaFreeHost(h->hactive);
+    delete h;
+    return fail(nullptr, code, m);
+  };
+  if (cudaMallocHost(&h->hred, sizeof(unsigned long long) * 3 * h->P) != cudaSuccess ||
+      cudaMallocHost(&h->hactive, sizeof(int) * h->P) != cudaSuccess)
+    return bail(PMG_ERR_OOM, "pinned host allocation failed");
+  // zero everything: the pad columns of every grid function must stay zero
+  cudaError_t e = cudaMemsetAsync(h->ws, 0, pl.total, h->stream);
+  if (e != cudaSuccess) return bail(PMG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  if (upload_minv(h) != PMG_OK) return bail(PMG_ERR_CUDA, h->err);
+  *out = h;
+  return PMG_OK;
+}
+
+int pfasst_mg_set_initial(pmg_handle h, const double *u0, int on_device) {
+  if (!h || !u0) return fail(h, PMG_ERR_INVALID_ARG, "null argument");
+  const size_t N = (size_t)h->gf.nz * h->gf.ny * h->gf.n;
+  const double *src = u0;
+  if (!on_device) {
+    PMG_CUDA(h, cudaMemcpyAsync(h->dense, u0, N * 8, cudaMemcpyHostToDevice, h->stream));
+    src = h->dense;
+  }
+  PMG_CUDA(h, k_pack(h->L(), h->gf, src, 0, h->u0, 0, 1));
+  PMG_RET(spread(h));
+  if (!on_device) PMG_CUDA(h, cudaStreamSynchronize(h->stream));  // host buffer reusable on return
+  return PMG_OK;
+}
+
+int pfasst_mg_predict(pmg_handle h) {
+  if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
+  return predict(h);
+}
+
+int pfasst_mg_sweep(pmg_handle h, int level) {
+  if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
+  if (level == 0) return sweep(h, 0, 0, h->P);
+  if (level == 1 && h->nlevels == 2) {
+    for (int p = 0; p < h->P; ++p) {
+      if (p > 0) PMG_RET(coarse_receive(h, p, 1));
+      PMG_RET(sweep(h, 1, p, 1));
+    }
+    return PMG_OK;
+  }
+  return fail(h, PMG_ERR_INVALID_ARG, "level must be 0 or (with two levels) 1");
+}
+
+int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, double *final_res) {
+  if (!h || max_iter < 0) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  if (iters_done) *iters_done = 0;
+  if (!h->predicted) PMG_RET(predict(h));
+  double res = INFINITY;
+  for (int k = 0; k < max_iter; ++k) {
+    PMG_RET(iteration(h));
+    PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+    res = 0.0;
+    for (int p = 0; p < h->P; ++p) {
+      const double r = bits_to_double(h->hred[2 * h->P + p]);
+      if (!(r <= res)) res = r;
+    }
+    if (iters_done) *iters_done = k + 1;
+    if (final_res) *final_res = res;
+    if (std::isnan(res) || std::isinf(res)) return fail(h, PMG_ERR_DIVERGED, "collocation residual is NaN/Inf");
+    if (res <= tol) return PMG_OK;
+  }
+  return PMG_NOT_CONVERGED;
+}
+
+int pfasst_mg_residual(pmg_handle h, double *res) {
+  if (!h || !res) return fail(h, PMG_ERR_INVALID_ARG, "null argument");
+  PMG_RET(colloc_residual(h));
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int p = 0; p < h->P; ++p) res[p] = bits_to_double(h->hred[2 * h->P + p]);
+  return PMG_OK;
+}
+
+int pfasst_mg_get_solution(pmg_handle h, int slice, int node, double *out, int on_device) {
+  if (!h || !out || slice < 0 || slice >= h->P || node < 0 || node >= h->sf)
+    return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  const size_t N = (size_t)h->gf.nz * h->gf.ny * h->gf.n;
+  const double *src = h->Uf + ((long long)slice * h->sf + node) * h->gf.slab;
+  double *dst = on_device ? out : h->dense;
+  PMG_CUDA(h, k_unpack(h->L(), h->gf, src, 0, dst, 0, 1));
+  if (!on_device) PMG_CUDA(h, cudaMemcpyAsync(out, h->dense, N * 8, cudaMemcpyDeviceToHost, h->stream));
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PMG_OK;
+}
+
+int pfasst_mg_get_state(pmg_handle h, int level, double *out) {
+  if (!h || !out || level < 0 || level > 1 || (level == 1 && h->nlevels < 2))
+    return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  const Grid &g = level ? h->gc : h->gf;
+  const int s = level ? h->sc : h->sf;
+  const double *U = level ? h->Uc : h->Uf;
+  const size_t N = (size_t)g.nz * g.ny * g.n;
+  for (int p = 0; p < h->P; ++p)
+    for (int m = 0; m < s; ++m) {
+      PMG_CUDA(h, k_unpack(h->L(), g, U + ((long long)p * s + m) * g.slab, 0, h->dense, 0, 1));
+      PMG_CUDA(h, cudaMemcpyAsync(out + ((size_t)p * s + m) * N, h->dense, N * 8, cudaMemcpyDeviceToHost, h->stream));
+      PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+  return PMG_OK;
+}
+
+int pfasst_mg_advance(pmg_handle h) {
+  if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
+  const long long last = ((long long)(h->P - 1) * h->sf + (h->sf - 1)) * h->gf.slab;
+  PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + last, 0, h->u0, 0, 1));
+  return spread(h);
+}
+
+long long pfasst_mg_launch_count(pmg_handle h) { return h ? h->launches : -1; }
+
+int pfasst_mg_profile(pmg_handle h, int enable, long long min_points) {
+  if (!h || min_points < 0) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  h->prof.on = enable != 0;
+  h->prof.min_points = min_points;
+  return PMG_OK;
+}
+
+int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int *count) {
+  if (!h || !count || capacity < 0 || (capacity > 0 && !out)) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  std::vector<pmg_kernel_stat> agg;
+  for (const ProfRec &r : h->prof.recs) {
+    float ms = 0.f;
+    PMG_CUDA(h, cudaEventElapsedTime(&ms, r.a, r.b));
+    size_t q = 0;
+    for (; q < agg.size(); ++q)
+      if (agg[q].kernel == r.kid && agg[q].n == r.n && agg[q].precision == r.prec) break;
+    if (q == agg.size()) agg.push_back(pmg_kernel_stat{r.kid, r.n, r.prec, 0, 0, 0.0});
+    agg[q].launches += 1;
+    agg[q].points += r.pts;
+    agg[q].ms += ms;
+  }
+  h->prof.recs.clear();
+  h->prof.used = 0;
+  *count = (int)agg.size();
+  for (int q = 0; q < capacity && q < (int)agg.size(); ++q) out[q] = agg[q];
+  return PMG_OK;
+}
+
+const char *pfasst_mg_kernel_name(int kernel) {
+  static const char *names[K_COUNT] = {"residual0", "smooth_jacobi", "smooth_rbgs", "residual_restrict",
+                                       "prolong_add", "coarse_solve", "update_u", "zero", "apply_A", "sf_rhs",
+                                       "fas_restrict", "interp_correction", "colloc_residual", "copy", "pack",
+                                       "unpack"};
+  return kernel >= 0 && kernel < K_COUNT ? names[kernel] : "unknown";
+}
+
+int pfasst_mg_destroy(pmg_handle h) {
+  if (!h) return PMG_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  if (h->ws_owned && h->ws) cudaFree(h->ws);
+  if (h->hred) cudaFreeHost(h->hred);
+  if (h->hactive) cudaFreeHost(h->hactive);
+  delete h;
+  return PMG_OK;
+}
+
+const char *pfasst_mg_last_error(pmg_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const double *b, double *u,
+                              const pmg_options *opt, void *stream, int *cycles_done) {
+  pmg_nodes_desc fn{3, 0};
+  pmg_levels lv{1, {0, 0}};
+  std::string why;
+  int rc = validate(grid, &fn, &lv, batch < 1 ? 1 : batch, opt, why);
+  if (rc != PMG_OK) return fail(nullptr, rc, why);
+  if (batch < 1 || !b || !u || !(c >= 0) || !std::isfinite(c)) return fail(nullptr, PMG_ERR_INVALID_ARG, "bad argument");
+  pmg_options o;
+  if (opt) o = *opt; else pfasst_mg_default_options(&o);
+  cudaStream_t st = (cudaStream_t)stream;
+  Grid g = make_grid(grid->dim, grid->n);
+  Hier H;
+  Plan pl;
+  double *bp = nullptr, *up = nullptr;
+  void *minv = nullptr;
+  unsigned long long *red = nullptr;
+  int *active = nullptr;
+  pl.add((void **)&bp, (size_t)g.slab * batch * 8);
+  pl.add((void **)&up, (size_t)g.slab * batch * 8);
+  plan_hier(pl, H, grid->dim, grid->n, batch, o.precision == PMG_PREC_MIXED ? F32 : F64, o.smoother);
+  const int n3 = grid->dim == 1 ? 3 : (grid->dim == 2 ? 9 : 27);
+  pl.add(&minv, (size_t)n3 * n3 * H.tsize);
+  pl.add((void **)&red, sizeof(unsigned long long) * 2 * batch);
+  pl.add((void **)&active, sizeof(int) * batch);
+  void *block = nullptr;
+  if (cudaMallocAsync(&block, pl.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, PMG_ERR_OOM, "cudaMallocAsync failed");
+  }
+  pl.carve((char *)block);
+  unsigned long long *hred = nullptr;
+  int *hactive = nullptr;
+  int result = PMG_OK;
+  long long launches = 0;
+  do {
+    if (cudaMallocHost(&hred, sizeof(unsigned long long) * 2 * batch) != cudaSuccess ||
+        cudaMallocHost(&hactive, sizeof(int) * batch) != cudaSuccess) {
+      result = fail(nullptr, PMG_ERR_OOM, "pinned host allocation failed");
+      break;
+    }
+    std::vector<double> M;
+    coarsest_inverse(grid->dim, c, M);
+    std::vector<char> buf(M.size() * H.tsize);
+    for (size_t q = 0; q < M.size(); ++q) {
+      if (H.tsize == 8) std::memcpy(buf.data() + q * 8, &M[q], 8);
+      else { float fv = (float)M[q]; std::memcpy(buf.data() + q * 4, &fv, 4); }
+    }
+    Launch Ln{st, &launches, nullptr};
+    if (cudaMemsetAsync(block, 0, pl.total, st) != cudaSuccess ||
+        cudaMemcpyAsync(minv, buf.data(), buf.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        k_pack(Ln, g, b, (long long)g.nz * g.ny * g.n, bp, g.slab, batch) != cudaSuccess ||
+        k_pack(Ln, g, u, (long long)g.nz * g.ny * g.n, up, g.slab, batch) != cudaSuccess) {
+      result = fail(nullptr, PMG_ERR_CUDA, "set-up copy failed");
+      break;
+    }
+    MGCtx Mc{Ln, &H, &o, red, active, hred, hactive, nullptr, st};
+    int cyc = 0;
+    result = solve_substep(Mc, 0, batch, c, minv, bp, g.slab, nullptr, 0, up, g.slab, &cyc);
+    if (result != PMG_OK) break;
+    if (k_unpack(Ln, g, up, g.slab, u, (long long)g.nz * g.ny * g.n, batch) != cudaSuccess) {
+      result = fail(nullptr, PMG_ERR_CUDA, "unpack failed");
+      break;
+    }
+    if (cycles_done) *cycles_done = cyc;
+  } while (0);
+  cudaFreeAsync(block, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (hred) cudaFreeHost(hred);
+  if (hactive) cudaFreeHost(hactive);
+  if (result == PMG_OK && e != cudaSuccess) result = fail(nullptr, PMG_ERR_CUDA, cudaGetErrorString(e));
+  return result;
+}
+
+}  // extern "C"

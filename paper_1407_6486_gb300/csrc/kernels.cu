@@ -1,0 +1,643 @@
+// kernels.cu -- CUDA kernels of the pfasst_mg library (sm_103a).
+//
+// Generic, batched stencil kernels for every level of the space-time hierarchy:
+// the sub-step residual of Eq. SDCcompactLIII, weighted-Jacobi and red-black
+// Gauss-Seidel smoothing, residual + full-weighting restriction, d-linear
+// prolongation, the exact 3^d coarsest-grid solve (multigrid of Sec. 4.1.1), the
+// F = nu Lap_h U evaluation, the node-to-node quadrature S F of Eq. sdc-be, the FAS
+// restriction (Sec. 2.3), the 4th-order space / Lagrange time interpolation of the
+// coarse correction (Sec. 4.2.1) and the collocation residual of Eq. resid.
+//
+// Thread mapping: x (unit stride) across threadIdx.x, rows across (blockIdx.y,
+// threadIdx.y), (z, batch) across blockIdx.z, with grid-stride loops so any size is
+// covered.  All accesses stay inside the interior of each grid; the pad column is
+// never written.
+#include "pmg_internal.cuh"
+
+namespace pmg {
+namespace {
+
+#define PMG_FOR_POINTS(g, batch)                                                                   \
+  for (int zb = blockIdx.z; zb < (g).nz * (batch); zb += gridDim.z)                                \
+    for (int j = blockIdx.y * blockDim.y + threadIdx.y; j < (g).ny; j += gridDim.y * blockDim.y) \
+      for (int i = threadIdx.x; i < (g).n; i += blockDim.x)
+
+#define PMG_POINT(g)                 \
+  const int k = zb % (g).nz;         \
+  const int b = zb / (g).nz;         \
+  const long long off = ((long long)k * (g).ny + j) * (g).pitch + i
+
+void config(const Grid &g, int batch, dim3 &grid, dim3 &block) {
+  // 256 threads per block always, so every warp is full (the reductions use
+  // full-warp shuffles); small grids simply leave rows idle
+  int bx = g.pitch < 256 ? g.pitch : 256;
+  int by = 256 / bx;
+  block = dim3(bx, by, 1);
+  int gy = (g.ny + by - 1) / by;
+  long long gz = (long long)g.nz * batch;
+  if (gz > 65535) gz = 65535;
+  if (gz < 1) gz = 1;
+  grid = dim3(1, gy, (unsigned)gz);
+}
+
+// records a start event before a launch and the matching end event after it
+struct Scope {
+  const Launch &L;
+  ProfRec rec;
+  bool active = false;
+  Scope(const Launch &L_, KernelId kid, const Grid &g, int batch, int prec) : L(L_) {
+    const long long pts = (long long)g.n * g.ny * g.nz * batch;
+    if (L.prof && L.prof->on && pts >= L.prof->min_points) {
+      rec.kid = kid;
+      rec.n = g.n;
+      rec.prec = prec;
+      rec.pts = pts;
+      rec.a = L.prof->take();
+      rec.b = L.prof->take();
+      cudaEventRecord(rec.a, L.stream);
+      active = true;
+    }
+  }
+  cudaError_t done() {
+    if (L.counter) ++*L.counter;
+    cudaError_t e = cudaGetLastError();
+    if (active) {
+      cudaEventRecord(rec.b, L.stream);
+      L.prof->recs.push_back(rec);
+    }
+    return e;
+  }
+};
+
+// sum of the 2*DIM neighbours, zero outside the interior (Dirichlet 0)
+template <int DIM, typename T>
+__device__ __forceinline__ T nbsum(const T *__restrict__ u, const Grid &g, int i, int j, int k, long long off) {
+  T s = (i > 0 ? u[off - 1] : T(0)) + (i < g.n - 1 ? u[off + 1] : T(0));
+  if (DIM >= 2) s += (j > 0 ? u[off - g.pitch] : T(0)) + (j < g.n - 1 ? u[off + g.pitch] : T(0));
+  if (DIM >= 3) {
+    const long long pl = (long long)g.ny * g.pitch;
+    s += (k > 0 ? u[off - pl] : T(0)) + (k < g.n - 1 ? u[off + pl] : T(0));
+  }
+  return s;
+}
+
+// max-reduce nonnegative doubles (NaN wins) across a warp, one atomic per warp
+__device__ __forceinline__ void warp_max_atomic(double v, unsigned long long *dst) {
+  const unsigned full = 0xffffffffu;
+  for (int o = 16; o > 0; o >>= 1) {
+    double w = __shfl_xor_sync(full, v, o);
+    if (!(w <= v)) v = w;  // NaN propagates
+  }
+  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+// ------------------------------------------------------------------ multigrid
+
+// f = (u_m + q_m) - (I - c Lap_h) u_{m+1}  (FP64 arithmetic, stored as TO)
+template <int DIM, typename TO>
+__global__ void residual0_kernel(Grid g, double c, const double *__restrict__ um, long long sum,
+                                 const double *__restrict__ qm, long long sq, const double *__restrict__ u1,
+                                 long long s1, TO *__restrict__ f, int batch, unsigned long long *rnorm,
+                                 unsigned long long *bnorm) {
+  const double a = c * g.ih2;
+  for (int zb = blockIdx.z; zb < g.nz * batch; zb += gridDim.z) {
+    const int k = zb % g.nz, b = zb / g.nz;
+    double rmax = 0.0, bmax = 0.0;
+    for (int j = blockIdx.y * blockDim.y + threadIdx.y; j < g.ny; j += gridDim.y * blockDim.y)
+      for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+        const long long off = ((long long)k * g.ny + j) * g.pitch + i;
+        const double *U1 = u1 + b * s1;
+        const double uc = U1[off];
+        const double Lu = uc - a * (nbsum<DIM>(U1, g, i, j, k, off) - 2.0 * DIM * uc);
+        const double rhs = um[b * sum + off] + (qm ? qm[b * sq + off] : 0.0);
+        const double r = rhs - Lu;
+        f[b * g.slab + off] = (TO)r;
+        const double ar = fabs(r), ab = fabs(rhs);
+        if (!(ar <= rmax)) rmax = ar;
+        if (!(ab <= bmax)) bmax = ab;
+      }
+    if (rnorm) {
+      warp_max_atomic(rmax, rnorm + b);
+      warp_max_atomic(bmax, bnorm + b);
+    }
+  }
+}
+
+template <int DIM, typename T>
+__global__ void jacobi_kernel(Grid g, T c, T omega, const T *__restrict__ ein, T *__restrict__ eout,
+                              const T *__restrict__ f, int batch, int first) {
+  const T a = c * (T)g.ih2;
+  const T D = T(1) + T(2 * DIM) * a;
+  const T wD = omega / D;
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    const long long o = b * g.slab + off;
+    if (first) {
+      eout[o] = wD * f[o];
+    } else {
+      const T *E = ein + b * g.slab;
+      const T ec = E[off];
+      const T Le = ec - a * (nbsum<DIM>(E, g, i, j, k, off) - T(2 * DIM) * ec);
+      eout[o] = ec + wD * (f[o] - Le);
+    }
+  }
+}
+
+// red = (i+j+k) even in 1-based interior indices of the existing axes
+template <int DIM, typename T>
+__global__ void rbgs_kernel(Grid g, T c, T omega, T *e, const T *__restrict__ f, int batch, int colour,
+                            int first) {
+  const T a = c * (T)g.ih2;
+  const T D = T(1) + T(2 * DIM) * a;
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    const long long o = b * g.slab + off;
+    const int par = (i + j + k + DIM) & 1;
+    if (par != colour) {
+      if (first && colour == 0) e[o] = T(0);
+      continue;
+    }
+    if (first && colour == 0) {
+      e[o] = omega * (f[o] / D);
+      continue;
+    }
+    const T *E = e + b * g.slab;
+    const T gs = (f[o] + a * nbsum<DIM>(E, g, i, j, k, off)) / D;
+    e[o] = (T(1) - omega) * e[o] + omega * gs;
+  }
+}
+
+// fc(I) = sum of full-weighting taps of r = f - (I - c Lap_h) e around fine 2I+1
+template <int DIM, typename T>
+__global__ void resrestrict_kernel(Grid gf, Grid gc, T c, const T *__restrict__ e, const T *__restrict__ f,
+                                   T *__restrict__ fc, int batch) {
+  const T a = c * (T)gf.ih2;
+  const T w3[3] = {T(0.25), T(0.5), T(0.25)};
+  PMG_FOR_POINTS(gc, batch) {
+    PMG_POINT(gc);
+    const T *E = e + b * gf.slab;
+    const T *Fp = f + b * gf.slab;
+    T acc = T(0);
+    for (int cz = (DIM >= 3 ? -1 : 0); cz <= (DIM >= 3 ? 1 : 0); ++cz)
+      for (int cy = (DIM >= 2 ? -1 : 0); cy <= (DIM >= 2 ? 1 : 0); ++cy)
+        for (int cx = -1; cx <= 1; ++cx) {
+          const int fi = 2 * i + 1 + cx;
+          const int fj = DIM >= 2 ? 2 * j + 1 + cy : 0;
+          const int fk = DIM >= 3 ? 2 * k + 1 + cz : 0;
+          const long long fo = ((long long)fk * gf.ny + fj) * gf.pitch + fi;
+          const T ec = E[fo];
+          const T r = Fp[fo] - (ec - a * (nbsum<DIM>(E, gf, fi, fj, fk, fo) - T(2 * DIM) * ec));
+          T w = w3[cx + 1];
+          if (DIM >= 2) w *= w3[cy + 1];
+          if (DIM >= 3) w *= w3[cz + 1];
+          acc += w * r;
+        }
+    fc[b * gc.slab + off] = acc;
+  }
+}
+
+// linear interpolation taps of fine 0-based index i onto coarse 0-based indices
+__device__ __forceinline__ int lin_taps(int i, int nc, int *idx, float *w) {
+  const int i1 = i + 1;
+  if ((i1 & 1) == 0) {
+    idx[0] = i1 / 2 - 1;
+    w[0] = 1.0f;
+    return 1;
+  }
+  int t = 0;
+  const int lo = (i1 - 1) / 2 - 1, hi = (i1 + 1) / 2 - 1;
+  if (lo >= 0) { idx[t] = lo; w[t] = 0.5f; ++t; }
+  if (hi < nc) { idx[t] = hi; w[t] = 0.5f; ++t; }
+  return t;
+}
+
+template <int DIM, typename T>
+__global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ ec, T *__restrict__ e, int batch) {
+  PMG_FOR_POINTS(gf, batch) {
+    PMG_POINT(gf);
+    int ix[2], iy[2] = {0, 0}, iz[2] = {0, 0};
+    float wx[2], wy[2] = {1.f, 1.f}, wz[2] = {1.f, 1.f};
+    const int tx = lin_taps(i, gc.n, ix, wx);
+    const int ty = DIM >= 2 ? lin_taps(j, gc.n, iy, wy) : 1;
+    const int tz = DIM >= 3 ? lin_taps(k, gc.n, iz, wz) : 1;
+    const T *EC = ec + b * gc.slab;
+    T acc = T(0);
+    for (int cz = 0; cz < tz; ++cz)
+      for (int cy = 0; cy < ty; ++cy)
+        for (int cx = 0; cx < tx; ++cx)
+          acc += T(wx[cx] * wy[cy] * wz[cz]) * EC[((long long)iz[cz] * gc.ny + iy[cy]) * gc.pitch + ix[cx]];
+    e[b * gf.slab + off] += acc;
+  }
+}
+
+// exact solve on the 3^d grid: e = Minv f (Minv dense, row-major N3 x N3)
+template <int DIM, typename T>
+__global__ void coarse_solve_kernel(Grid g, const T *__restrict__ minv, const T *__restrict__ f, T *__restrict__ e,
+                                    int batch) {
+  constexpr int N3 = DIM == 1 ? 3 : (DIM == 2 ? 9 : 27);
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    const int p = (k * 3 + j) * 3 + i;
+    const T *Fb = f + b * g.slab;
+    T acc = T(0);
+    for (int q = 0; q < N3; ++q) {
+      const int qi = q % 3, qj = (q / 3) % 3, qk = q / 9;
+      acc += minv[p * N3 + q] * Fb[((long long)qk * g.ny + qj) * g.pitch + qi];
+    }
+    e[b * g.slab + off] = acc;
+  }
+}
+
+template <typename T>
+__global__ void update_u_kernel(Grid g, double *__restrict__ u, long long su, const T *__restrict__ e, int batch,
+                                const int *__restrict__ active) {
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    if (active && !active[b]) continue;
+    u[b * su + off] += (double)e[b * g.slab + off];
+  }
+}
+
+template <typename T>
+__global__ void zero_kernel(Grid g, T *__restrict__ e, int batch) {
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    e[b * g.slab + off] = T(0);
+  }
+}
+
+// ------------------------------------------------------------------ SDC / PFASST
+
+template <int DIM>
+__global__ void apply_A_kernel(Grid g, double nu, const double *__restrict__ u, long long su, double *__restrict__ F,
+                               long long sF, int batch) {
+  const double a = nu * g.ih2;
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    const double *U = u + b * su;
+    F[b * sF + off] = a * (nbsum<DIM>(U, g, i, j, k, off) - 2.0 * DIM * U[off]);
+  }
+}
+
+__global__ void sf_rhs_kernel(Grid g, SFCoef cf, const double *__restrict__ F, long long sF,
+                              const double *__restrict__ tau, long long stau, double *__restrict__ q, long long sq,
+                              int batch) {
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    double Fv[kMaxNodes];
+    for (int jn = 0; jn < cf.s; ++jn) Fv[jn] = F[b * sF + jn * g.slab + off];
+    double tprev = tau ? tau[b * stau + off] : 0.0;
+    for (int m = 0; m < cf.s - 1; ++m) {
+      double acc = 0.0;
+      for (int jn = 0; jn < cf.s; ++jn) acc += cf.W[m][jn] * Fv[jn];
+      if (tau) {
+        const double tnext = tau[b * stau + (m + 1) * g.slab + off];
+        acc += tnext - tprev;
+        tprev = tnext;
+      }
+      q[b * sq + m * g.slab + off] = acc;
+    }
+  }
+}
+
+// per coarse point: U_c,j = U_f,map j (injection), F_c,j = A_c U_c,j,
+// tau_j = inject(sum_i dtQf[j][i] F_f,i) - sum_i dtQc[j][i] F_c,i
+template <int DIM>
+__global__ void fas_restrict_kernel(Grid gf, Grid gc, FASCoef cf, const double *__restrict__ Uf,
+                                    const double *__restrict__ Ff, long long sfine, double *__restrict__ Uc,
+                                    double *__restrict__ Fc, double *__restrict__ tau, double *__restrict__ Uc0,
+                                    long long scoarse, int batch) {
+  const double ac = cf.nu * gc.ih2;
+  const long long plf = (long long)gf.ny * gf.pitch;
+  PMG_FOR_POINTS(gc, batch) {
+    PMG_POINT(gc);
+    const int fi = 2 * i + 1, fj = DIM >= 2 ? 2 * j + 1 : 0, fk = DIM >= 3 ? 2 * k + 1 : 0;
+    const long long fo = ((long long)fk * gf.ny + fj) * gf.pitch + fi;
+    double Fcv[kMaxNodes];
+    for (int jn = 0; jn < cf.sc; ++jn) {
+      const double *U = Uf + b * sfine + cf.map[jn] * gf.slab;
+      const double uc = U[fo];
+      double s = (i > 0 ? U[fo - 2] : 0.0) + (i < gc.n - 1 ? U[fo + 2] : 0.0);
+      if (DIM >= 2) s += (j > 0 ? U[fo - 2 * gf.pitch] : 0.0) + (j < gc.n - 1 ? U[fo + 2 * gf.pitch] : 0.0);
+      if (DIM >= 3) s += (k > 0 ? U[fo - 2 * plf] : 0.0) + (k < gc.n - 1 ? U[fo + 2 * plf] : 0.0);
+      Fcv[jn] = ac * (s - 2.0 * DIM * uc);
+      const long long co = b * scoarse + jn * gc.slab + off;
+      Uc[co] = uc;
+      Uc0[co] = uc;
+      Fc[co] = Fcv[jn];
+    }
+    for (int jn = 0; jn < cf.sc; ++jn) {
+      double If = 0.0;
+      for (int in = 0; in < cf.sf; ++in) If += cf.dtQf[jn][in] * Ff[b * sfine + in * gf.slab + fo];
+      double Ic = 0.0;
+      for (int in = 0; in < cf.sc; ++in) Ic += cf.dtQc[jn][in] * Fcv[in];
+      tau[b * scoarse + jn * gc.slab + off] = If - Ic;
+    }
+  }
+}
+
+// interpolation taps of fine 0-based index i onto coarse 1-based indices, with odd
+// reflection at the walls (index 0 and nc+1 are zero walls; -1 and nc+2 mirror 1, nc)
+__device__ __forceinline__ int interp_taps(int order, int i, int nc, int *idx, double *w) {
+  const int i1 = i + 1;
+  if ((i1 & 1) == 0) {
+    idx[0] = i1 / 2 - 1;
+    w[0] = 1.0;
+    return 1;
+  }
+  const int J = (i1 - 1) / 2;
+  int t = 0;
+  const int no = order == 2 ? 2 : 4;
+  const int base = order == 2 ? 0 : -1;
+  const double w2[2] = {0.5, 0.5};
+  const double w4[4] = {-1.0 / 16, 9.0 / 16, 9.0 / 16, -1.0 / 16};
+  for (int q = 0; q < no; ++q) {
+    int J1 = J + base + q;
+    double sg = 1.0;
+    if (J1 == 0 || J1 == nc + 1) continue;
+    if (J1 < 0) { J1 = -J1; sg = -1.0; }
+    if (J1 > nc + 1) { J1 = 2 * (nc + 1) - J1; sg = -1.0; }
+    idx[t] = J1 - 1;
+    w[t] = sg * (order == 2 ? w2[q] : w4[q]);
+    ++t;
+  }
+  return t;
+}
+
+template <int DIM>
+__global__ void interp_correction_kernel(Grid gf, Grid gc, InterpCoef cf, double *__restrict__ Uf, long long sfine,
+                                         const double *__restrict__ Uc, const double *__restrict__ Uc0,
+                                         long long scoarse, int batch) {
+  PMG_FOR_POINTS(gf, batch) {
+    PMG_POINT(gf);
+    int ix[4], iy[4] = {0}, iz[4] = {0};
+    double wx[4], wy[4] = {1.0}, wz[4] = {1.0};
+    const int tx = interp_taps(cf.order, i, gc.n, ix, wx);
+    const int ty = DIM >= 2 ? interp_taps(cf.order, j, gc.n, iy, wy) : 1;
+    const int tz = DIM >= 3 ? interp_taps(cf.order, k, gc.n, iz, wz) : 1;
+    double d[kMaxNodes];
+    for (int jn = 0; jn < cf.sc; ++jn) {
+      const double *A = Uc + b * scoarse + jn * gc.slab;
+      const double *B = Uc0 + b * scoarse + jn * gc.slab;
+      double acc = 0.0;
+      for (int cz = 0; cz < tz; ++cz)
+        for (int cy = 0; cy < ty; ++cy)
+          for (int cx = 0; cx < tx; ++cx) {
+            const long long co = ((long long)iz[cz] * gc.ny + iy[cy]) * gc.pitch + ix[cx];
+            acc += wx[cx] * wy[cy] * wz[cz] * (A[co] - B[co]);
+          }
+      d[jn] = acc;
+    }
+    for (int m = 0; m < cf.sf; ++m) {
+      double acc = 0.0;
+      for (int jn = 0; jn < cf.sc; ++jn) acc += cf.T[m][jn] * d[jn];
+      Uf[b * sfine + m * gf.slab + off] += acc;
+    }
+  }
+}
+
+__global__ void colloc_residual_kernel(Grid g, ResCoef cf, const double *__restrict__ U, const double *__restrict__ F,
+                                       long long stride, int batch, unsigned long long *out) {
+  for (int zb = blockIdx.z; zb < g.nz * batch; zb += gridDim.z) {
+    const int k = zb % g.nz, b = zb / g.nz;
+    double mx = 0.0;
+    for (int j = blockIdx.y * blockDim.y + threadIdx.y; j < g.ny; j += gridDim.y * blockDim.y)
+      for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+        const long long off = ((long long)k * g.ny + j) * g.pitch + i;
+        double Fv[kMaxNodes];
+        for (int in = 0; in < cf.s; ++in) Fv[in] = F[b * stride + in * g.slab + off];
+        const double u0 = U[b * stride + off];
+        for (int m = 1; m < cf.s; ++m) {
+          double v = u0;
+          for (int in = 0; in < cf.s; ++in) v += cf.dtQ[m][in] * Fv[in];
+          v -= U[b * stride + m * g.slab + off];
+          const double av = fabs(v);
+          if (!(av <= mx)) mx = av;
+        }
+      }
+    warp_max_atomic(mx, out + b);
+  }
+}
+
+__global__ void copy_kernel(Grid g, const double *__restrict__ src, long long ss, double *__restrict__ dst,
+                            long long sd, int batch) {
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    dst[b * sd + off] = src[b * ss + off];
+  }
+}
+
+__global__ void pack_kernel(Grid g, const double *__restrict__ dense, long long sdense, double *__restrict__ pad,
+                            long long spad, int batch) {
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    const long long dn = ((long long)k * g.ny + j) * g.n + i;
+    pad[b * spad + off] = dense[b * sdense + dn];
+  }
+}
+
+__global__ void unpack_kernel(Grid g, const double *__restrict__ pad, long long spad, double *__restrict__ dense,
+                              long long sdense, int batch) {
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    const long long dn = ((long long)k * g.ny + j) * g.n + i;
+    dense[b * sdense + dn] = pad[b * spad + off];
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+#define PMG_DIM_SWITCH(dim, CALL) \
+  switch (dim) {                  \
+    case 1: { constexpr int D = 1; CALL; } break; \
+    case 2: { constexpr int D = 2; CALL; } break; \
+    default: { constexpr int D = 3; CALL; } break; \
+  }
+
+cudaError_t k_residual0(const Launch &L, const Grid &g, double c, Prec pr, const double *um, long long sum,
+                        const double *qm, long long sq, const double *u1, long long s1, void *f, int batch,
+                        unsigned long long *rnorm, unsigned long long *bnorm) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_RESIDUAL0, g, batch, pr);
+  if (pr == F64)
+    PMG_DIM_SWITCH(g.dim, (residual0_kernel<D, double><<<gr, bl, 0, L.stream>>>(
+                              g, c, um, sum, qm, sq, u1, s1, (double *)f, batch, rnorm, bnorm)))
+  else
+    PMG_DIM_SWITCH(g.dim, (residual0_kernel<D, float><<<gr, bl, 0, L.stream>>>(
+                              g, c, um, sum, qm, sq, u1, s1, (float *)f, batch, rnorm, bnorm)))
+  return sc.done();
+}
+
+cudaError_t k_smooth_jacobi(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
+                            void *eout, const void *f, int batch, bool first) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_JACOBI, g, batch, pr);
+  if (pr == F64)
+    PMG_DIM_SWITCH(g.dim, (jacobi_kernel<D, double><<<gr, bl, 0, L.stream>>>(
+                              g, c, omega, (const double *)ein, (double *)eout, (const double *)f, batch, first)))
+  else
+    PMG_DIM_SWITCH(g.dim, (jacobi_kernel<D, float><<<gr, bl, 0, L.stream>>>(
+                              g, (float)c, (float)omega, (const float *)ein, (float *)eout, (const float *)f, batch,
+                              first)))
+  return sc.done();
+}
+
+cudaError_t k_smooth_rbgs(const Launch &L, const Grid &g, double c, double omega, Prec pr, void *e, const void *f,
+                          int batch, int colour, bool first) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_RBGS, g, batch, pr);
+  if (pr == F64)
+    PMG_DIM_SWITCH(g.dim, (rbgs_kernel<D, double><<<gr, bl, 0, L.stream>>>(g, c, omega, (double *)e,
+                                                                               (const double *)f, batch, colour, first)))
+  else
+    PMG_DIM_SWITCH(g.dim, (rbgs_kernel<D, float><<<gr, bl, 0, L.stream>>>(g, (float)c, (float)omega, (float *)e,
+                                                                              (const float *)f, batch, colour, first)))
+  return sc.done();
+}
+
+cudaError_t k_residual_restrict(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
+                                const void *f, void *fc, int batch) {
+  dim3 gr, bl;
+  config(gc, batch, gr, bl);
+  Scope sc(L, K_RESRESTRICT, gc, batch, pr);
+  if (pr == F64)
+    PMG_DIM_SWITCH(gf.dim, (resrestrict_kernel<D, double><<<gr, bl, 0, L.stream>>>(
+                               gf, gc, c, (const double *)e, (const double *)f, (double *)fc, batch)))
+  else
+    PMG_DIM_SWITCH(gf.dim, (resrestrict_kernel<D, float><<<gr, bl, 0, L.stream>>>(
+                               gf, gc, (float)c, (const float *)e, (const float *)f, (float *)fc, batch)))
+  return sc.done();
+}
+
+cudaError_t k_prolong_add(const Launch &L, const Grid &gf, const Grid &gc, Prec pr, const void *ec, void *e,
+                          int batch) {
+  dim3 gr, bl;
+  config(gf, batch, gr, bl);
+  Scope sc(L, K_PROLONG, gf, batch, pr);
+  if (pr == F64)
+    PMG_DIM_SWITCH(gf.dim,
+                   (prolong_kernel<D, double><<<gr, bl, 0, L.stream>>>(gf, gc, (const double *)ec, (double *)e, batch)))
+  else
+    PMG_DIM_SWITCH(gf.dim,
+                   (prolong_kernel<D, float><<<gr, bl, 0, L.stream>>>(gf, gc, (const float *)ec, (float *)e, batch)))
+  return sc.done();
+}
+
+cudaError_t k_coarse_solve(const Launch &L, const Grid &g3, Prec pr, const void *minv, const void *f, void *e,
+                           int batch) {
+  dim3 gr, bl;
+  config(g3, batch, gr, bl);
+  Scope sc(L, K_COARSE, g3, batch, pr);
+  if (pr == F64)
+    PMG_DIM_SWITCH(g3.dim, (coarse_solve_kernel<D, double><<<gr, bl, 0, L.stream>>>(
+                               g3, (const double *)minv, (const double *)f, (double *)e, batch)))
+  else
+    PMG_DIM_SWITCH(g3.dim, (coarse_solve_kernel<D, float><<<gr, bl, 0, L.stream>>>(
+                               g3, (const float *)minv, (const float *)f, (float *)e, batch)))
+  return sc.done();
+}
+
+cudaError_t k_update_u(const Launch &L, const Grid &g, Prec pr, double *u, long long su, const void *e, int batch,
+                       const int *active) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_UPDATE, g, batch, pr);
+  if (pr == F64)
+    update_u_kernel<double><<<gr, bl, 0, L.stream>>>(g, u, su, (const double *)e, batch, active);
+  else
+    update_u_kernel<float><<<gr, bl, 0, L.stream>>>(g, u, su, (const float *)e, batch, active);
+  return sc.done();
+}
+
+cudaError_t k_zero(const Launch &L, const Grid &g, Prec pr, void *e, int batch) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_ZERO, g, batch, pr);
+  if (pr == F64)
+    zero_kernel<double><<<gr, bl, 0, L.stream>>>(g, (double *)e, batch);
+  else
+    zero_kernel<float><<<gr, bl, 0, L.stream>>>(g, (float *)e, batch);
+  return sc.done();
+}
+
+cudaError_t k_apply_A(const Launch &L, const Grid &g, double nu, const double *u, long long su, double *F,
+                      long long sF, int batch) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_APPLY_A, g, batch, 0);
+  PMG_DIM_SWITCH(g.dim, (apply_A_kernel<D><<<gr, bl, 0, L.stream>>>(g, nu, u, su, F, sF, batch)))
+  return sc.done();
+}
+
+cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const double *F, long long sF,
+                     const double *tau, long long stau, double *q, long long sq, int batch) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_SF_RHS, g, batch, 0);
+  sf_rhs_kernel<<<gr, bl, 0, L.stream>>>(g, cf, F, sF, tau, stau, q, sq, batch);
+  return sc.done();
+}
+
+cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
+                           const double *Ff, long long sfine, double *Uc, double *Fc, double *tau, double *Uc0,
+                           long long scoarse, int batch) {
+  dim3 gr, bl;
+  config(gc, batch, gr, bl);
+  Scope sc(L, K_FAS, gc, batch, 0);
+  PMG_DIM_SWITCH(gf.dim, (fas_restrict_kernel<D><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, Ff, sfine, Uc, Fc, tau,
+                                                                             Uc0, scoarse, batch)))
+  return sc.done();
+}
+
+cudaError_t k_interp_correction(const Launch &L, const Grid &gf, const Grid &gc, const InterpCoef &cf, double *Uf,
+                                long long sfine, const double *Uc, const double *Uc0, long long scoarse, int batch) {
+  dim3 gr, bl;
+  config(gf, batch, gr, bl);
+  Scope sc(L, K_INTERP, gf, batch, 0);
+  PMG_DIM_SWITCH(gf.dim, (interp_correction_kernel<D><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Uc0,
+                                                                                  scoarse, batch)))
+  return sc.done();
+}
+
+cudaError_t k_colloc_residual(const Launch &L, const Grid &g, const ResCoef &cf, const double *U, const double *F,
+                              long long stride, int batch, unsigned long long *out) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_COLLOC, g, batch, 0);
+  colloc_residual_kernel<<<gr, bl, 0, L.stream>>>(g, cf, U, F, stride, batch, out);
+  return sc.done();
+}
+
+cudaError_t k_copy(const Launch &L, const Grid &g, const double *src, long long ss, double *dst, long long sd,
+                   int batch) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_COPY, g, batch, 0);
+  copy_kernel<<<gr, bl, 0, L.stream>>>(g, src, ss, dst, sd, batch);
+  return sc.done();
+}
+
+cudaError_t k_pack(const Launch &L, const Grid &g, const double *dense, long long sdense, double *pad, long long spad,
+                   int batch) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_PACK, g, batch, 0);
+  pack_kernel<<<gr, bl, 0, L.stream>>>(g, dense, sdense, pad, spad, batch);
+  return sc.done();
+}
+
+cudaError_t k_unpack(const Launch &L, const Grid &g, const double *pad, long long spad, double *dense,
+                     long long sdense, int batch) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_UNPACK, g, batch, 0);
+  unpack_kernel<<<gr, bl, 0, L.stream>>>(g, pad, spad, dense, sdense, batch);
+  return sc.done();
+}
+
+}  // namespace pmg

@@ -1,0 +1,144 @@
+// pmg_internal.cuh -- internal types and kernel launchers of the pfasst_mg library.
+//
+// Device layout of a grid function with n interior points per axis (n = 2^p - 1):
+// [z][y][x] with x padded to pitch = n + 1 = 2^p elements.  The pad element of each
+// row is zero and is never written, so rows start on 2^p-element boundaries (16-byte
+// aligned for both FP32 and FP64) and the zero Dirichlet wall needs no storage.
+// A batch of grid functions is addressed as ptr + b * stride.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace pmg {
+
+constexpr int kMaxNodes = 9;     // Gauss-Lobatto nodes per level (M + 1)
+constexpr int kMaxLevels = 11;   // n <= 1023 -> 9 multigrid levels
+
+enum Prec { F64 = 0, F32 = 1 };
+
+struct Grid {
+  int dim;          // 1, 2, 3
+  int n;            // interior points per axis
+  int pitch;        // n + 1
+  int ny, nz;       // n or 1 for missing axes
+  long long slab;   // elements of one grid function (nz * ny * pitch)
+  double ih2;       // 1 / h^2 = (n + 1)^2
+};
+
+inline Grid make_grid(int dim, int n) {
+  Grid g;
+  g.dim = dim;
+  g.n = n;
+  g.pitch = n + 1;
+  g.ny = dim >= 2 ? n : 1;
+  g.nz = dim >= 3 ? n : 1;
+  g.slab = (long long)g.nz * g.ny * g.pitch;
+  g.ih2 = (double)(n + 1) * (double)(n + 1);
+  return g;
+}
+
+// kernel identifiers for launch accounting and the event profiler
+enum KernelId {
+  K_RESIDUAL0 = 0, K_JACOBI, K_RBGS, K_RESRESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_ZERO,
+  K_APPLY_A, K_SF_RHS, K_FAS, K_INTERP, K_COLLOC, K_COPY, K_PACK, K_UNPACK, K_COUNT
+};
+
+// CUDA-event timing of individual launches on the launching stream (only launches
+// that cover at least min_points grid points are recorded)
+struct ProfRec {
+  int kid, n, prec;
+  long long pts;
+  cudaEvent_t a, b;
+};
+struct Profiler {
+  bool on = false;
+  long long min_points = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<ProfRec> recs;
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct Launch {
+  cudaStream_t stream;
+  long long *counter;  // incremented per kernel launch (may be null)
+  Profiler *prof;      // may be null
+};
+
+// sub-step right-hand side coefficients: q_m = sum_j W[m][j] F_j (+ tau_{m+1} - tau_m)
+struct SFCoef {
+  int s;                                 // nodes
+  double W[kMaxNodes - 1][kMaxNodes];    // dt (Q[m+1][j] - Q[m][j]) - [j == m+1] dt_m
+};
+
+// collocation residual coefficients: r_m = U_0 + sum_i dtQ[m][i] F_i - U_m
+struct ResCoef {
+  int s;
+  double dtQ[kMaxNodes][kMaxNodes];
+};
+
+// FAS restriction coefficients (coarse node j <-> fine node map[j])
+struct FASCoef {
+  int sf, sc;
+  int map[kMaxNodes];
+  double dtQf[kMaxNodes][kMaxNodes];     // rows map[j] of dt * Q_fine
+  double dtQc[kMaxNodes][kMaxNodes];     // dt * Q_coarse
+  double nu;
+};
+
+// coarse-correction interpolation: U_f,m += sum_j T[m][j] I_x (U_c,j - U_c0,j)
+struct InterpCoef {
+  int sf, sc, order;
+  double T[kMaxNodes][kMaxNodes];
+};
+
+// ---- multigrid kernels (precision of e, f chosen by Prec) ----
+cudaError_t k_residual0(const Launch &L, const Grid &g, double c, Prec pr, const double *um, long long sum,
+                        const double *qm, long long sq, const double *u1, long long s1, void *f, int batch,
+                        unsigned long long *rnorm, unsigned long long *bnorm);
+cudaError_t k_smooth_jacobi(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
+                            void *eout, const void *f, int batch, bool first);
+cudaError_t k_smooth_rbgs(const Launch &L, const Grid &g, double c, double omega, Prec pr, void *e, const void *f,
+                          int batch, int colour, bool first);
+cudaError_t k_residual_restrict(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
+                                const void *f, void *fc, int batch);
+cudaError_t k_prolong_add(const Launch &L, const Grid &gf, const Grid &gc, Prec pr, const void *ec, void *e, int batch);
+cudaError_t k_coarse_solve(const Launch &L, const Grid &g3, Prec pr, const void *minv, const void *f, void *e,
+                           int batch);
+cudaError_t k_update_u(const Launch &L, const Grid &g, Prec pr, double *u, long long su, const void *e, int batch,
+                       const int *active);
+cudaError_t k_zero(const Launch &L, const Grid &g, Prec pr, void *e, int batch);
+
+// ---- SDC / PFASST kernels (FP64) ----
+cudaError_t k_apply_A(const Launch &L, const Grid &g, double nu, const double *u, long long su, double *F,
+                      long long sF, int batch);
+cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const double *F, long long sF,
+                     const double *tau, long long stau, double *q, long long sq, int batch);
+cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
+                           const double *Ff, long long sfine, double *Uc, double *Fc, double *tau, double *Uc0,
+                           long long scoarse, int batch);
+cudaError_t k_interp_correction(const Launch &L, const Grid &gf, const Grid &gc, const InterpCoef &cf, double *Uf,
+                                long long sfine, const double *Uc, const double *Uc0, long long scoarse, int batch);
+cudaError_t k_colloc_residual(const Launch &L, const Grid &g, const ResCoef &cf, const double *U, const double *F,
+                              long long stride, int batch, unsigned long long *out);
+cudaError_t k_copy(const Launch &L, const Grid &g, const double *src, long long ss, double *dst, long long sd,
+                   int batch);
+cudaError_t k_pack(const Launch &L, const Grid &g, const double *dense, long long sdense, double *pad, long long spad,
+                   int batch);
+cudaError_t k_unpack(const Launch &L, const Grid &g, const double *pad, long long spad, double *dense,
+                     long long sdense, int batch);
+
+}  // namespace pmg

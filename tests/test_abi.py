@@ -1,0 +1,108 @@
+"""CPU checks of the C ABI boundary: the library loads without a GPU and exports
+every function that include/pfasst_mg.h declares; host-side validation works."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1407_6486_gb300 as pmg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"\b(pfasst_mg_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1407_6486_gb300 import _build
+    _build.build()
+    return pmg.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(pmg.EXPORTS) | declared
+
+
+def test_default_options(lib):
+    o = pmg.pfasst_mg_default_options()
+    assert o.nu1 == 2 and o.nu2 == 1 and o.vcycles == 2 and abs(o.omega - 2 / 3) < 1e-15
+    assert o.interp_order == 4 and o.precision == pmg.PMG_PREC_FP64
+
+
+def _ws(dim, n, sf, nl, sc, P, **kw):
+    o = pmg.pfasst_mg_default_options(**kw)
+    return pmg.pfasst_mg_workspace_bytes(pmg.pmg_grid(dim, n), pmg.pmg_nodes_desc(sf, 0),
+                                         pmg.pmg_levels(nl, pmg.pmg_nodes_desc(sc, 0)), P, o)
+
+
+def test_workspace_size_grows_with_problem(lib):
+    a = _ws(2, 31, 5, 2, 3, 4)
+    b = _ws(2, 63, 5, 2, 3, 4)
+    c = _ws(2, 63, 5, 2, 3, 8)
+    assert 0 < a < b < c
+    # FP64 fine state alone: U, F, q over slices and nodes, padded rows
+    assert b >= 8 * 64 * 63 * (5 + 5 + 4) * 4
+    # mixed precision halves the multigrid scratch
+    assert _ws(3, 31, 5, 2, 3, 4, precision=1) < _ws(3, 31, 5, 2, 3, 4, precision=0)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=4), dict(n=30), dict(n=1), dict(sf=1), dict(sf=12), dict(nl=3),
+    dict(sc=7), dict(P=0), dict(n=3, nl=2),
+])
+def test_invalid_descriptions_are_rejected(lib, bad):
+    p = dict(dim=2, n=31, sf=5, nl=2, sc=3, P=4)
+    p.update(bad)
+    with pytest.raises(pmg.PMGError) as ei:
+        _ws(p["dim"], p["n"], p["sf"], p["nl"], p["sc"], p["P"])
+    assert ei.value.code in (pmg.PMG_ERR_INVALID_ARG, pmg.PMG_ERR_UNSUPPORTED)
+    assert pmg.pfasst_mg_last_error()
+
+
+@pytest.mark.parametrize("opt", [dict(smoother=5), dict(nu1=0, nu2=0), dict(precision=3),
+                                 dict(interp_order=3), dict(omega=0.0), dict(vcycles=-1)])
+def test_invalid_options_are_rejected(lib, opt):
+    with pytest.raises(pmg.PMGError) as ei:
+        _ws(2, 31, 5, 2, 3, 4, **opt)
+    assert ei.value.code == pmg.PMG_ERR_INVALID_ARG
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.pfasst_mg_predict(None) == pmg.PMG_ERR_INVALID_ARG
+    assert lib.pfasst_mg_sweep(None, 0) == pmg.PMG_ERR_INVALID_ARG
+    assert lib.pfasst_mg_destroy(None) == pmg.PMG_OK
+    assert lib.pfasst_mg_launch_count(None) == -1
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1407_6486_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "pfasst_oracle" not in src and "orc_" not in src, f
+
+
+def test_create_rejects_nested_nodes_that_do_not_nest(lib):
+    """5 Gauss-Lobatto nodes are not a subset of 9 (only odd counts share the midpoint
+    with 3); the coarse level needs coincident nodes for point-wise restriction in time."""
+    h = ctypes.c_void_p()
+    o = pmg.pfasst_mg_default_options()
+    rc = lib.pfasst_mg_create(ctypes.byref(pmg.pmg_grid(1, 63)), ctypes.byref(pmg.pmg_nodes_desc(9, 0)),
+                              ctypes.byref(pmg.pmg_levels(2, pmg.pmg_nodes_desc(5, 0))), 1.0, 0.01, 2,
+                              ctypes.byref(o), None, None, 0, ctypes.byref(h))
+    assert rc == pmg.PMG_ERR_INVALID_ARG and not h.value
+    assert "subset" in pmg.pfasst_mg_last_error()

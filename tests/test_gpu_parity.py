@@ -1,0 +1,293 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: the FP64 path follows the oracle's algorithm step for step with fixed
+V-cycle counts, so the two differ only by rounding order: relative l2 <= 1e-12 on
+every compared state.  The mixed path (FP32 V-cycles, FP64 residuals, iterative
+refinement) converges to the same fixed point: <= 1e-9 relative l2 once both are
+converged to a collocation residual of 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1407_6486_gb300 as pmg
+from paper_1407_6486_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1407_6486_gb300 import _build
+    _build.build()
+    pmg.load()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def omega(sm):
+    return 1.0 if sm == 1 else 2.0 / 3.0
+
+
+# ---------------------------------------------------------------- multigrid alone
+
+@pytest.mark.parametrize("dim,n,sm,vc", [
+    (1, 3, 0, 1), (1, 63, 0, 2), (1, 1023, 1, 2), (2, 31, 0, 1), (2, 255, 1, 2), (2, 127, 0, 3),
+    (3, 7, 1, 1), (3, 15, 0, 2), (3, 31, 1, 2), (3, 63, 0, 1),
+])
+def test_vcycles_fp64_match_oracle(dim, n, sm, vc):
+    batch, c = 3, 0.37 / (n + 1) ** 2 * 4
+    rng = np.random.default_rng(dim * 1000 + n)
+    b = rng.standard_normal((batch, n ** dim))
+    u = rng.standard_normal((batch, n ** dim))
+    opt = pmg.pfasst_mg_default_options(smoother=sm, omega=omega(sm), vcycles=vc)
+    bt = torch.tensor(b, device="cuda")
+    ut = torch.tensor(u, device="cuda")
+    cyc = pmg.pfasst_mg_helmholtz_solve(pmg.pmg_grid(dim, n), c, batch, bt, ut, opt)
+    assert cyc == vc
+    mg = O.MGParams(smoother=sm, omega=omega(sm), vcycles=vc)
+    want = np.stack([O.mg_solve(mg, dim, n, c, b[q], u[q])[0] for q in range(batch)])
+    assert rel(ut.cpu().numpy(), want) < FP64_TOL
+
+
+@pytest.mark.parametrize("dim,n,sm", [(1, 127, 0), (2, 63, 1), (3, 15, 0)])
+def test_full_solve_matches_oracle(dim, n, sm):
+    batch, c = 2, 0.01
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal((batch, n ** dim))
+    opt = pmg.pfasst_mg_default_options(smoother=sm, omega=omega(sm), vcycles=0, mg_tol=1e-12)
+    ut = torch.zeros((batch, n ** dim), dtype=torch.float64, device="cuda")
+    cyc = pmg.pfasst_mg_helmholtz_solve(pmg.pmg_grid(dim, n), c, batch, torch.tensor(b, device="cuda"), ut, opt)
+    mg = O.MGParams(smoother=sm, omega=omega(sm), vcycles=0, mg_tol=1e-12)
+    outs = [O.mg_solve(mg, dim, n, c, b[q], np.zeros(n ** dim)) for q in range(batch)]
+    assert cyc == max(o[1] for o in outs)
+    assert rel(ut.cpu().numpy(), np.stack([o[0] for o in outs])) < 1e-11
+
+
+@pytest.mark.parametrize("dim,n,sm", [(2, 127, 0), (3, 31, 1)])
+def test_mixed_vcycle_and_refinement(dim, n, sm):
+    """FP32 V-cycles: one cycle matches the FP64 oracle to FP32 accuracy; the full solve
+    (FP64 residual, FP32 correction) refines to the FP64 solution."""
+    batch, c = 2, 0.02
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal((batch, n ** dim))
+    g = pmg.pmg_grid(dim, n)
+    ut = torch.zeros((batch, n ** dim), dtype=torch.float64, device="cuda")
+    opt1 = pmg.pfasst_mg_default_options(smoother=sm, omega=omega(sm), vcycles=1, precision=1)
+    pmg.pfasst_mg_helmholtz_solve(g, c, batch, torch.tensor(b, device="cuda"), ut, opt1)
+    mg1 = O.MGParams(smoother=sm, omega=omega(sm), vcycles=1)
+    want1 = np.stack([O.mg_solve(mg1, dim, n, c, b[q], np.zeros(n ** dim))[0] for q in range(batch)])
+    assert rel(ut.cpu().numpy(), want1) < 2e-6
+    ut.zero_()
+    optf = pmg.pfasst_mg_default_options(smoother=sm, omega=omega(sm), vcycles=0, precision=1, mg_tol=1e-12)
+    pmg.pfasst_mg_helmholtz_solve(g, c, batch, torch.tensor(b, device="cuda"), ut, optf)
+    mgf = O.MGParams(smoother=sm, omega=omega(sm), vcycles=0, mg_tol=1e-14, mg_maxcycles=60)
+    wantf = np.stack([O.mg_solve(mgf, dim, n, c, b[q], np.zeros(n ** dim))[0] for q in range(batch)])
+    assert rel(ut.cpu().numpy(), wantf) < 1e-11
+
+
+# ---------------------------------------------------------------- SDC / PFASST
+
+CASES = [
+    # dim, n, sf, sc, P, nlevels, smoother, vcycles, interp
+    (1, 63, 5, 3, 3, 2, 0, 2, 4),
+    (2, 31, 5, 3, 4, 2, 0, 1, 4),
+    (2, 63, 3, 2, 2, 2, 1, 2, 2),
+    (3, 15, 5, 3, 4, 2, 1, 2, 4),
+    (3, 7, 3, 2, 2, 2, 0, 1, 4),
+    (2, 31, 3, 0, 3, 1, 0, 2, 4),
+    (1, 127, 9, 3, 2, 2, 1, 1, 4),
+]
+
+
+def _u0(dim, n):
+    modes, amps = inputs.random_modes(dim, 4, 4, 99)
+    return inputs.sine_sum(dim, n, modes, amps)
+
+
+def _pair(dim, n, sf, sc, P, nl, sm, vc, interp, precision=0, dt=0.01, nu=1.0):
+    s = pmg.PFASSTSolver(dim, n, sf, sc if nl == 2 else 0, P, nu, dt, nlevels=nl, smoother=sm, omega=omega(sm),
+                         vcycles=vc, precision=precision, interp_order=interp)
+    o = O.PFASST(dim, n, sf, sc if nl == 2 else 2, P, nu, dt,
+                 O.MGParams(smoother=sm, omega=omega(sm), vcycles=vc), nlevels=nl, interp_order=interp)
+    u0 = _u0(dim, n)
+    s.set_initial(u0)
+    o.set_initial(u0)
+    return s, o
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"d{c[0]}n{c[1]}s{c[2]}x{c[3]}P{c[4]}L{c[5]}sm{c[6]}v{c[7]}" for c in CASES])
+def test_pfasst_state_matches_oracle_every_iteration(case):
+    dim, n, sf, sc, P, nl, sm, vc, interp = case
+    s, o = _pair(*case)
+    s.predict()
+    o.predict()
+    assert rel(s.state(0), o.Uf) < FP64_TOL
+    if nl == 2:
+        assert rel(s.state(1), o.Uc) < FP64_TOL
+    for k in range(3):
+        rc, it, res = s.iterate(1, 0.0)
+        ores = o.iteration()
+        assert rel(s.state(0), o.Uf) < FP64_TOL, f"iteration {k}"
+        if nl == 2:
+            assert rel(s.state(1), o.Uc) < FP64_TOL
+        gres = s.residual()
+        np.testing.assert_allclose(gres, ores, rtol=1e-7, atol=1e-13)
+    s.close()
+
+
+def test_sweep_entry_points_match_oracle():
+    dim, n, sf, sc, P = 2, 31, 5, 3, 3
+    s, o = _pair(dim, n, sf, sc, P, 2, 0, 2, 4)
+    s.sweep(0)
+    mg = O.MGParams(vcycles=2)
+    for p in range(P):
+        o.Uf[p], o.Ff[p], _ = O.sweep(dim, n, sf, 1.0, 0.01, mg, o.Uf[p], o.Ff[p])
+    assert rel(s.state(0), o.Uf) < FP64_TOL
+    s.close()
+
+
+def test_isdc_heat1d_workload_full_size():
+    """1D heat, 127 points, 3 nodes, single-level SDC, dt = 0.01 to T = 0.1, V(2,1)
+    Jacobi: sweep each step to residual 1e-9; same iteration counts and end values."""
+    wl = inputs.heat1d_c1()
+    s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, 0, 1, wl.nu, wl.dt, nlevels=1, smoother=wl.smoother,
+                         omega=wl.omega, vcycles=wl.vcycles)
+    o = O.PFASST(wl.dim, wl.n, wl.fine_nodes, 2, 1, wl.nu, wl.dt,
+                 O.MGParams(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles), nlevels=1)
+    u = wl.u0()
+    s.set_initial(u)
+    for step in range(wl.steps):
+        o.set_initial(u)
+        it_o, _ = o.run(wl.iterations, 1e-9)
+        rc, it_g, res = s.iterate(wl.iterations, 1e-9)
+        assert it_g == it_o and rc == pmg.PMG_OK
+        u = o.end_value()
+        assert rel(s.solution(0, wl.fine_nodes - 1), u) < FP64_TOL
+        s.advance()
+    s.close()
+
+
+def test_heat2d_workload_full_size_fp64():
+    """2D heat 255^2 / 127^2, 16 slices, 5/3 nodes, 2 V-cycles: 3 PFASST iterations."""
+    wl = inputs.heat2d_c2(vcycles=2, precision=0)
+    s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                         smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles)
+    o = O.PFASST(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                 O.MGParams(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles))
+    u0 = wl.u0()
+    s.set_initial(u0)
+    o.set_initial(u0)
+    o.predict()
+    for k in range(3):
+        ores = o.iteration()
+        rc, it, res = s.iterate(1, 0.0)
+        assert abs(res - ores.max()) <= 1e-7 * ores.max()
+    assert rel(s.state(0), o.Uf) < FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("dim,n,P,sm", [(2, 31, 2, 0), (3, 15, 4, 1)])
+def test_mixed_precision_reaches_fp64_fixed_point(dim, n, P, sm):
+    s, _ = _pair(dim, n, 5, 3, P, 2, sm, 2, 4, precision=1)
+    rc, it, res = s.iterate(200, 1e-12)
+    assert rc == pmg.PMG_OK and res <= 1e-12
+    o = O.PFASST(dim, n, 5, 3, P, 1.0, 0.01, O.MGParams(smoother=sm, omega=omega(sm), vcycles=0, mg_tol=1e-14))
+    o.set_initial(_u0(dim, n))
+    o.run(200, 1e-13)
+    assert rel(s.state(0), o.Uf) < MIXED_TOL
+    s.close()
+
+
+def test_full_solve_pfasst_matches_oracle():
+    dim, n, P = 2, 31, 2
+    s = pmg.PFASSTSolver(dim, n, 5, 3, P, 1.0, 0.01, vcycles=0, mg_tol=1e-12)
+    o = O.PFASST(dim, n, 5, 3, P, 1.0, 0.01, O.MGParams(vcycles=0, mg_tol=1e-12))
+    u0 = _u0(dim, n)
+    s.set_initial(u0)
+    o.set_initial(u0)
+    o.predict()
+    for _ in range(2):
+        o.iteration()
+    s.iterate(2, 0.0)
+    assert rel(s.state(0), o.Uf) < 1e-11
+    s.close()
+
+
+def _pade(z, s):
+    N = s - 1
+    c = [math.factorial(2 * N - j) * math.factorial(N) / (math.factorial(2 * N) * math.factorial(j)
+                                                           * math.factorial(N - j)) for j in range(N + 1)]
+    return sum(c[j] * z ** j for j in range(N + 1)) / sum(c[j] * (-z) ** j for j in range(N + 1))
+
+
+def test_heat3d_fixed_point_with_32_slices():
+    """3D heat (nu = 0.5, dt = 0.002, 16 sine modes |k| <= 8), 32 slices, 5/3 nodes, mixed
+    precision, red-black Gauss-Seidel, on a 63^3 / 31^3 grid where the iteration reaches
+    1e-10: on every sine mode the end of the block must be the serial collocation value
+    R(lambda dt)^32 (R = Pade (4,4), Gauss-Lobatto 5 nodes); the residual the GPU reports
+    must match a host recomputation on the last slice."""
+    wl = inputs.heat3d_c3(n=63, slices=32)
+    s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                         smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, precision=wl.precision)
+    s.set_initial(wl.u0())
+    rc, it, res = s.iterate(150, 1e-10)
+    assert rc == pmg.PMG_OK, (it, res)
+    n, h = wl.n, 1.0 / (wl.n + 1)
+    end = s.solution(wl.slices - 1, wl.fine_nodes - 1).reshape(n, n, n)
+    want = np.zeros_like(end)
+    x = np.arange(1, n + 1) * h
+    for k, a in zip(wl.modes, wl.amps):
+        lam = wl.nu * sum((2 * math.cos(kk * math.pi * h) - 2) / h ** 2 for kk in k)
+        amp = a * _pade(lam * wl.dt, wl.fine_nodes) ** wl.slices
+        want += amp * np.einsum("k,j,i->kji", np.sin(k[2] * np.pi * x), np.sin(k[1] * np.pi * x),
+                                np.sin(k[0] * np.pi * x))
+    assert np.abs(end - want).max() <= 1e-8 * np.abs(want).max()
+    U = np.stack([s.solution(wl.slices - 1, m).reshape(n, n, n) for m in range(wl.fine_nodes)])
+
+    def lap(u):
+        p = np.pad(u, 1)
+        return (p[2:, 1:-1, 1:-1] + p[:-2, 1:-1, 1:-1] + p[1:-1, 2:, 1:-1] + p[1:-1, :-2, 1:-1]
+                + p[1:-1, 1:-1, 2:] + p[1:-1, 1:-1, :-2] - 6 * u) / h ** 2
+
+    F = np.stack([wl.nu * lap(u) for u in U])
+    Q = O.qmatrix(wl.fine_nodes)
+    r = max(np.abs(U[0] + wl.dt * np.tensordot(Q[m], F, axes=1) - U[m]).max() for m in range(wl.fine_nodes))
+    gres = s.residual()[-1]
+    assert abs(r - gres) <= 1e-3 * gres + 1e-14
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, 1e-6)])
+def test_heat3d_workload_full_size_first_slices_match_oracle(precision, tol):
+    """The full 3D workload (255^3 / 127^3, 32 slices, as timed by bench.py): slice p
+    depends only on slices 0..p, so the oracle run on the first two slices reproduces
+    them.  Compared after the predictor and one PFASST iteration, all fine nodes.
+    FP64 path: rounding only (1e-12).  Mixed path: the FP32 V-cycle corrections carry
+    ~1e-7 relative rounding, bounded here by 1e-6 relative l2 on the unconverged state."""
+    wl = inputs.heat3d_c3(precision=precision)
+    s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                         smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, precision=precision)
+    u0 = wl.u0()
+    s.set_initial(u0)
+    s.iterate(1, 0.0)
+    gpu = np.stack([[s.solution(p, m) for m in range(wl.fine_nodes)] for p in range(2)])
+    s.close()
+    torch.cuda.empty_cache()
+    o = O.PFASST(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, 2, wl.nu, wl.dt,
+                 O.MGParams(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles))
+    o.set_initial(u0)
+    o.predict()
+    o.iteration()
+    assert rel(gpu, o.Uf) < tol
