@@ -193,6 +193,32 @@ const char *pfasst_mg_last_error(pmg_handle h);
 int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const double *b,
                               double *u, const pmg_options *opt, void *stream, int *cycles_done);
 
+/* ---- allocation-free multigrid solve -------------------------------------- */
+
+/* Same computation and arguments as pfasst_mg_helmholtz_solve, for callers that
+ * cannot allocate device memory: code running while a stream is captured into a
+ * CUDA graph (cudaMalloc is not allowed there), host frameworks that own all device
+ * memory through their own allocator, and latency-critical loops where an
+ * allocation would synchronise the device.  The paper has no counterpart; this is
+ * a deployment variant of the solve above.
+ *   - Scratch comes from one fixed 32 MiB device array inside this library (held
+ *     by every GPU that loads the library until the process exits); nothing is
+ *     allocated or freed, on the device or the host.
+ *   - Sizes whose scratch (padded b and u plus the multigrid hierarchy) exceeds
+ *     32 MiB are rejected with PMG_ERR_INVALID_ARG and a message giving the need;
+ *     e.g. a 3D 63^3 grid fits with batch 1 in FP64, a 3D 31^3 grid with batch 16.
+ *   - Only a fixed number of V-cycles (opt->vcycles >= 1) is supported; vcycles == 0
+ *     returns PMG_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before
+ *     any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents (each call
+ *     clears what it uses first).  Calls whose work overlaps on the GPU -- on
+ *     different streams, or from different host threads -- race on it; order them.
+ *   - The work is queued on `stream`; the call does not synchronise. */
+int pfasst_mg_helmholtz_solve_noalloc(const pmg_grid *grid, double c, int batch, const double *b,
+                                      double *u, const pmg_options *opt, void *stream, int *cycles_done);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,7 @@ EXPORTS = [
     "pfasst_mg_residual", "pfasst_mg_get_solution", "pfasst_mg_get_state", "pfasst_mg_advance",
     "pfasst_mg_launch_count", "pfasst_mg_destroy", "pfasst_mg_last_error",
     "pfasst_mg_helmholtz_solve", "pfasst_mg_profile", "pfasst_mg_profile_read", "pfasst_mg_kernel_name",
+    "pfasst_mg_helmholtz_solve_noalloc",
 ]
 
 
@@ -106,6 +107,8 @@ def load() -> ctypes.CDLL:
     L.pfasst_mg_last_error.restype = ctypes.c_char_p
     L.pfasst_mg_helmholtz_solve.argtypes = [ctypes.POINTER(pmg_grid), _D, _I, _P, _P,
                                             ctypes.POINTER(pmg_options), _P, ctypes.POINTER(_I)]
+    L.pfasst_mg_helmholtz_solve_noalloc.argtypes = [ctypes.POINTER(pmg_grid), _D, _I, _P, _P,
+                                                    ctypes.POINTER(pmg_options), _P, ctypes.POINTER(_I)]
     L.pfasst_mg_profile.argtypes = [_P, _I, ctypes.c_longlong]
     L.pfasst_mg_profile_read.argtypes = [_P, ctypes.POINTER(pmg_kernel_stat), _I, ctypes.POINTER(_I)]
     L.pfasst_mg_kernel_name.argtypes = [_I]
@@ -240,6 +243,17 @@ def pfasst_mg_helmholtz_solve(grid, c, batch, b, u, opt, stream=None) -> int:
     cyc = ctypes.c_int(0)
     _check(load().pfasst_mg_helmholtz_solve(ctypes.byref(grid), c, batch, _dev_ptr(b), _dev_ptr(u),
                                             ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(cyc)))
+    return cyc.value
+
+
+def pfasst_mg_helmholtz_solve_noalloc(grid, c, batch, b, u, opt, stream=None) -> int:
+    """Same as pfasst_mg_helmholtz_solve, but takes its scratch from a fixed 32 MiB
+    device array inside the library instead of allocating, for callers that may not
+    allocate (inside stream capture, under a framework-owned allocator).  Queued on
+    the stream, not synchronised.  Returns the number of V-cycles."""
+    cyc = ctypes.c_int(0)
+    _check(load().pfasst_mg_helmholtz_solve_noalloc(ctypes.byref(grid), c, batch, _dev_ptr(b), _dev_ptr(u),
+                                                    ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(cyc)))
     return cyc.value
 
 

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -901,3 +902,124 @@ int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const d
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------- allocation-free multigrid solve
+//
+// Some callers cannot allocate device memory: code that runs while a CUDA stream is
+// being captured into a graph (cudaMalloc is not permitted there), host frameworks
+// that own every byte of device memory through their own allocator and forbid raw
+// cudaMalloc, and latency-critical loops where an allocation would synchronise the
+// device.  pfasst_mg_helmholtz_solve_noalloc serves them: it runs the same V-cycles
+// as pfasst_mg_helmholtz_solve but takes its scratch from one fixed device array that
+// is part of this library, so it calls no allocator at all.
+
+namespace {
+
+// Fixed scratch of the allocation-free solve.  Every GPU that loads this library holds
+// these 32 MiB until the process exits.  In host code the name below is only a
+// stand-in; its device address comes from cudaGetSymbolAddress.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// device address of the scratch on the current device, looked up once per device
+int noalloc_base(void **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, PMG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(nullptr, PMG_ERR_UNSUPPORTED, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(nullptr, PMG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return PMG_OK;
+}
+
+// exact inverse of (I - c Lap_h) on the 3^dim grid into a caller array (no heap use);
+// same sine eigen-decomposition as coarsest_inverse
+void coarsest_inverse_into(int dim, double c, double *out) {
+  const int N3 = dim == 1 ? 3 : (dim == 2 ? 9 : 27);
+  const long double pi = 3.14159265358979323846264338327950288L;
+  long double v[3][3], mu[3];
+  for (int k = 0; k < 3; ++k) {
+    mu[k] = (2.0L * cosl((k + 1) * pi / 4.0L) - 2.0L) * 16.0L;
+    for (int i = 0; i < 3; ++i) v[k][i] = sqrtl(0.5L) * sinl((k + 1) * pi * (i + 1) / 4.0L);
+  }
+  for (int p = 0; p < N3; ++p)
+    for (int q = 0; q < N3; ++q) {
+      const int pi3[3] = {p % 3, (p / 3) % 3, p / 9}, qi3[3] = {q % 3, (q / 3) % 3, q / 9};
+      long double acc = 0.0L;
+      for (int kk = 0; kk < N3; ++kk) {
+        const int ks[3] = {kk % 3, (kk / 3) % 3, kk / 9};
+        long double lam = 1.0L, prod = 1.0L;
+        for (int a = 0; a < dim; ++a) {
+          lam -= (long double)c * mu[ks[a]];
+          prod *= v[ks[a]][pi3[a]] * v[ks[a]][qi3[a]];
+        }
+        acc += prod / lam;
+      }
+      out[p * N3 + q] = (double)acc;
+    }
+}
+
+}  // namespace
+
+extern "C" int pfasst_mg_helmholtz_solve_noalloc(const pmg_grid *grid, double c, int batch, const double *b,
+                                                 double *u, const pmg_options *opt, void *stream, int *cycles_done) {
+  pmg_nodes_desc fn{3, 0};
+  pmg_levels lv{1, {0, 0}};
+  std::string why;
+  int rc = validate(grid, &fn, &lv, batch < 1 ? 1 : batch, opt, why);
+  if (rc != PMG_OK) return fail(nullptr, rc, why);
+  if (batch < 1 || !b || !u || !(c >= 0) || !std::isfinite(c)) return fail(nullptr, PMG_ERR_INVALID_ARG, "bad argument");
+  pmg_options o;
+  if (opt) o = *opt; else pfasst_mg_default_options(&o);
+  if (o.vcycles < 1)
+    return fail(nullptr, PMG_ERR_UNSUPPORTED, "the allocation-free solve runs a fixed number of V-cycles (vcycles >= 1)");
+  cudaStream_t st = (cudaStream_t)stream;
+  Grid g = make_grid(grid->dim, grid->n);
+  Hier H;
+  Plan pl;
+  double *bp = nullptr, *up = nullptr;
+  void *minv = nullptr;
+  pl.add((void **)&bp, (size_t)g.slab * batch * 8);
+  pl.add((void **)&up, (size_t)g.slab * batch * 8);
+  plan_hier(pl, H, grid->dim, grid->n, batch, o.precision == PMG_PREC_MIXED ? F32 : F64, o.smoother);
+  const int n3 = grid->dim == 1 ? 3 : (grid->dim == 2 ? 9 : 27);
+  pl.add(&minv, (size_t)n3 * n3 * H.tsize);
+  if (pl.total > kNoAllocScratchBytes)
+    return fail(nullptr, PMG_ERR_INVALID_ARG,
+                "problem needs " + std::to_string(pl.total) + " bytes of scratch; the allocation-free solve has " +
+                    std::to_string(kNoAllocScratchBytes) + " (32 MiB)");
+  void *base = nullptr;
+  PMG_RET(noalloc_base(&base));
+  pl.carve((char *)base);
+  // coarsest-grid inverse, staged from the stack (a pageable copy returns after staging)
+  double minv64[27 * 27];
+  float minv32[27 * 27];
+  coarsest_inverse_into(grid->dim, c, minv64);
+  for (int q = 0; q < n3 * n3; ++q) minv32[q] = (float)minv64[q];
+  long long launches = 0;
+  Launch Ln{st, &launches, nullptr};
+  const long long dense = (long long)g.nz * g.ny * g.n;
+  // the array keeps the previous call's contents: clear it (pad columns must be zero)
+  if (cudaMemsetAsync(base, 0, pl.total, st) != cudaSuccess ||
+      cudaMemcpyAsync(minv, H.tsize == 8 ? (const void *)minv64 : (const void *)minv32, (size_t)n3 * n3 * H.tsize,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      k_pack(Ln, g, b, dense, bp, g.slab, batch) != cudaSuccess || k_pack(Ln, g, u, dense, up, g.slab, batch) != cudaSuccess)
+    return fail(nullptr, PMG_ERR_CUDA, "set-up of the allocation-free solve failed");
+  MGCtx Mc{Ln, &H, &o, nullptr, nullptr, nullptr, nullptr, nullptr, st};
+  PMG_RET(solve_substep(Mc, 0, batch, c, minv, bp, g.slab, nullptr, 0, up, g.slab, nullptr));
+  if (k_unpack(Ln, g, up, g.slab, u, dense, batch) != cudaSuccess)
+    return fail(nullptr, PMG_ERR_CUDA, "unpack of the allocation-free solve failed");
+  if (cycles_done) *cycles_done = o.vcycles;
+  return PMG_OK;
+}
