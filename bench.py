@@ -46,6 +46,14 @@ def algo_bytes_per_point(kernel: str, tsize: int, sf: int = 5, sc: int = 3) -> f
         "interp_correction": 16 * sf + 2 * 8 * sc / 8.0,
         "colloc_residual": 16 * sf,
         "copy": 16.0, "pack": 16.0, "unpack": 16.0, "zero": t,
+        "rbgs_sweep3d": 3 * t,                 # read e_in, f, write e_out (one fused red+black sweep)
+        "rbgs_sweep3d_zero": 2 * t,            # from e = 0: read f, write e
+        "rbgs_sweep3d_upd": 2 * t + 16,        # read e_in, f, read/write u (FP64): u += e
+        "resrestrict3d": 2 * t + t / 8,
+        "prolong3d": 2 * t + t / 8,
+        "resid_pt": 16 + t,                    # read u_m, q_m (FP64), write f
+        "fine_rhs_residual": 8 * sf + 8 * (sf - 1),  # read U at all nodes, write q per sub-step
+        "interp_space": 16 * sf + t * sf / 8.0,
     }.get(kernel, 0.0)
 
 
@@ -136,6 +144,8 @@ def make_workload(name):
         return inputs.heat3d_c3()
     if name == "heat3d-small":
         return inputs.heat3d_c3(n=63, slices=8)
+    if name == "heat3d-mid":  # small enough for ncu replays, large enough for the tiled kernels
+        return inputs.heat3d_c3(n=127, slices=12)
     if name == "heat2d":
         return inputs.heat2d_c2(vcycles=2, precision=1)
     raise SystemExit(f"unknown workload {name}")
@@ -210,19 +220,22 @@ def run_ours(args):
     u0_dev = torch.tensor(u0, device="cuda")
     common = dict(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, interp_order=4)
 
-    # calibration: plain FP64 GPU path, the workload's iteration count -> residual target
-    ref = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
-                           nlevels=wl.nlevels, precision=0, **common)
-    ref.set_initial(u0_dev)
-    _, k_ref, r_ref = ref.iterate(wl.iterations, 0.0)
-    ref.close()
-    del ref
-    torch.cuda.empty_cache()
-    target = float(f"{r_ref * 1.0001:.3e}")
+    if args.quick:
+        k_ref, target = wl.iterations, 0.0
+    else:
+        # calibration: plain FP64 GPU path, the workload's iteration count -> residual target
+        ref = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                               nlevels=wl.nlevels, precision=0, **common)
+        ref.set_initial(u0_dev)
+        _, k_ref, r_ref = ref.iterate(wl.iterations, 0.0)
+        ref.close()
+        del ref
+        torch.cuda.empty_cache()
+        target = float(f"{r_ref * 1.0001:.3e}")
 
     s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
                          nlevels=wl.nlevels, precision=wl.precision, **common)
-    maxit = 4 * wl.iterations
+    maxit = wl.iterations if args.quick else 4 * wl.iterations
 
     def step():
         s.set_initial(u0_dev)
@@ -264,17 +277,18 @@ def run_ours(args):
     value = world * dof_sweeps / (ms / 1000.0)
 
     # end to end through the C ABI with host buffers (h2d of u0, d2h of the end value)
+    e2e_steps = 0 if args.quick else args.steps
     u0_host = torch.tensor(u0).pin_memory()
     out_host = torch.empty(wl.dofs, dtype=torch.float64).pin_memory()
     out_np = out_host.numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         pmg.pfasst_mg_set_initial(s.h, u0_host.numpy())
         s.iterate(maxit, target)
         pmg.pfasst_mg_get_solution(s.h, wl.slices - 1, wl.fine_nodes - 1, out_np)
     torch.cuda.synchronize()
-    e2e_ms = 1000 * (time.perf_counter() - t0) / args.steps
+    e2e_ms = 1000 * (time.perf_counter() - t0) / max(e2e_steps, 1)
     t = torch.tensor([e2e_ms], device="cuda")
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -314,7 +328,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         v, tsec, cores = OracleSample(wl, args.ref_slices).sample()
         line["cpu_baseline"] = {"value": v, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one FP64 oracle PFASST iteration on {args.ref_slices} of the "
@@ -332,7 +346,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "heat3d-small", "heat2d"])
+    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d"])
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
+                         "no CPU baseline")
     ap.add_argument("--ref-slices", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true",

@@ -178,6 +178,7 @@ struct pmg_ctx {
   // device state
   double *Uf = nullptr, *Ff = nullptr, *qf = nullptr, *u0 = nullptr, *dense = nullptr;
   double *Uc = nullptr, *Fc = nullptr, *qc = nullptr, *tau = nullptr, *Uc0 = nullptr;
+  void *dU = nullptr;  // time-interpolated coarse correction [slice][fine node][coarse grid], MG precision
   Hier H;
   void *minv = nullptr;  // (sf-1 + sc-1) slots of N3*N3 in MG precision
   int n3 = 3;
@@ -188,8 +189,18 @@ struct pmg_ctx {
   void *ws = nullptr;
   bool ws_owned = false;
   bool predicted = false;
+  bool q_valid = false;  // F-free mode: qf holds the right-hand sides of the current U_f
   long long launches = 0;
   Profiler prof;
+  // CUDA graphs of the predictor and of one PFASST iteration (fixed V-cycle counts)
+  struct Captured {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+    bool with_prof = false;
+    long long prof_min = 0;
+    std::vector<ProfRec> recs;
+  } g_pred, g_iter;
+  cudaStream_t cap_stream = nullptr;
   std::string err;
 
   Launch L() { return Launch{stream, &launches, &prof}; }
@@ -253,7 +264,8 @@ void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smooth
     size_t bytes = (size_t)H.lev[l].slab * batch * H.tsize;
     pl.add(&H.e[l], bytes);
     pl.add(&H.f[l], bytes);
-    if (smoother == PMG_SMOOTHER_JACOBI) pl.add(&H.e2[l], bytes);
+    // second correction buffer: Jacobi ping-pong, or the out-of-place tiled 3D sweep
+    if (smoother == PMG_SMOOTHER_JACOBI || (dim == 3 && nl >= kTiled3dMinN)) pl.add(&H.e2[l], bytes);
     nl = (nl - 1) / 2;
   }
 }
@@ -274,6 +286,7 @@ void plan_ctx(Plan &pl, pmg_ctx *h) {
     pl.add((void **)&h->qc, sc * h->P * (h->sc - 1));
   }
   plan_hier(pl, h->H, h->dim, h->nf, h->P, h->opt.precision == PMG_PREC_MIXED ? F32 : F64, h->opt.smoother);
+  if (h->nlevels == 2) pl.add(&h->dU, (size_t)h->gc.slab * h->P * h->sf * h->H.tsize);
   const int slots = (h->sf - 1) + (h->nlevels == 2 ? h->sc - 1 : 0);
   pl.add(&h->minv, (size_t)slots * h->n3 * h->n3 * h->H.tsize);
   pl.add((void **)&h->red, sizeof(unsigned long long) * 3 * h->P);
@@ -294,12 +307,25 @@ struct MGCtx {
   cudaStream_t stream;
 };
 
-int smooth(MGCtx &M, int l, int B, double c, void *&cur, bool first) {
+// the z-marching tiled kernels pay off on large batched 3D grids; small or batch-1
+// grids (coarse levels, the serial coarse chain) keep the one-thread-per-point kernels
+bool tiled3d(const Grid &g, int B) {
+  return g.dim == 3 && g.n >= kTiled3dMinN && (long long)g.n * g.n * g.n * B >= (1LL << 24);
+}
+
+// one smoothing sweep on level l; with the tiled 3D red-black kernel and a non-null
+// u_upd the sweep's result is added to u_upd (stride su) instead of being stored
+int smooth(MGCtx &M, int l, int B, double c, void *&cur, bool first, double *u_upd = nullptr, long long su = 0) {
   Hier &H = *M.H;
   const pmg_options &o = *M.o;
   if (o.smoother == PMG_SMOOTHER_JACOBI) {
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
     PMG_CUDA(M.h, k_smooth_jacobi(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], B, first));
+    cur = out;
+  } else if (tiled3d(H.lev[l], B)) {
+    void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
+    PMG_CUDA(M.h, k_rbgs_sweep3d(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], u_upd, su, B, first,
+                                 u_upd != nullptr));
     cur = out;
   } else {
     PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 0, first));
@@ -308,23 +334,40 @@ int smooth(MGCtx &M, int l, int B, double c, void *&cur, bool first) {
   return PMG_OK;
 }
 
-// one V(nu1,nu2)-cycle for (I - c Lap) e = f[l0] on levels l0..L-1; *eout = result
-int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void **eout) {
+// one V(nu1,nu2)-cycle for (I - c Lap) e = f[l0] on levels l0..L-1, starting from
+// e = 0 (e_init null) or from e_init (a buffer of level l0); *eout = result.
+// If u_upd is non-null and the last post-smoothing sweep on level l0 can be fused
+// with the update, u_upd += e is done there and *fused is set (then *eout is stale).
+int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, void **eout,
+           double *u_upd = nullptr, long long su = 0, bool *fused = nullptr) {
   Hier &H = *M.H;
   const pmg_options &o = *M.o;
   void *cur[kMaxLevels];
+  if (fused) *fused = false;
   for (int l = l0; l < H.L - 1; ++l) {
-    cur[l] = H.e[l];
-    if (o.nu1 == 0) PMG_CUDA(M.h, k_zero(M.L, H.lev[l], H.pr, cur[l], B));
-    for (int s = 0; s < o.nu1; ++s) PMG_RET(smooth(M, l, B, c, cur[l], s == 0));
-    PMG_CUDA(M.h, k_residual_restrict(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
+    const bool zero = l > l0 || e_init == nullptr;
+    cur[l] = zero ? H.e[l] : e_init;
+    if (o.nu1 == 0 && zero) PMG_CUDA(M.h, k_zero(M.L, H.lev[l], H.pr, cur[l], B));
+    for (int s = 0; s < o.nu1; ++s) PMG_RET(smooth(M, l, B, c, cur[l], zero && s == 0));
+    if (tiled3d(H.lev[l], B))
+      PMG_CUDA(M.h, k_resrestrict3d(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
+    else
+      PMG_CUDA(M.h, k_residual_restrict(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
   }
   const int lc = H.L - 1;
   PMG_CUDA(M.h, k_coarse_solve(M.L, H.lev[lc], H.pr, minv, H.f[lc], H.e[lc], B));
   cur[lc] = H.e[lc];
   for (int l = lc - 1; l >= l0; --l) {
-    PMG_CUDA(M.h, k_prolong_add(M.L, H.lev[l], H.lev[l + 1], H.pr, cur[l + 1], cur[l], B));
-    for (int s = 0; s < o.nu2; ++s) PMG_RET(smooth(M, l, B, c, cur[l], false));
+    if (H.lev[l].dim == 3 && H.lev[l].n >= 15)
+      PMG_CUDA(M.h, k_prolong3d(M.L, H.lev[l], H.lev[l + 1], H.pr, cur[l + 1], cur[l], B));
+    else
+      PMG_CUDA(M.h, k_prolong_add(M.L, H.lev[l], H.lev[l + 1], H.pr, cur[l + 1], cur[l], B));
+    for (int s = 0; s < o.nu2; ++s) {
+      const bool last = l == l0 && s == o.nu2 - 1;
+      const bool fuse = last && u_upd && o.smoother == PMG_SMOOTHER_RBGS && tiled3d(H.lev[l], B);
+      PMG_RET(smooth(M, l, B, c, cur[l], false, fuse ? u_upd : nullptr, su));
+      if (fuse && fused) *fused = true;
+    }
   }
   *eout = cur[l0];
   return PMG_OK;
@@ -333,17 +376,25 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void **eout) {
 // Solve (I - c Lap) u1 = um + qm for B grids on hierarchy level l0 (fixed V-cycles or
 // full solve with the tolerance / stall rule).  *cycles = max cycles over the batch.
 int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const double *um, long long sum,
-                  const double *qm, long long sq, double *u1, long long s1, int *cycles) {
+                  const double *qm, long long sq, double *u1, long long s1, int *cycles, bool pointwise = false) {
   Hier &H = *M.H;
   const pmg_options &o = *M.o;
   const Grid &g = H.lev[l0];
   if (o.vcycles > 0) {
-    for (int v = 0; v < o.vcycles; ++v) {
-      void *e = nullptr;
+    // one residual of the sub-step equation, then the V-cycles iterate on the
+    // correction equation (I - c Lap) e = r from e = 0, then u1 += e: equal in exact
+    // arithmetic to vcycles V-cycles applied to u1 itself
+    void *e = nullptr;
+    bool fused = false;
+    if (pointwise)  // u_m + q_m already is the residual (see SFCoef)
+      PMG_CUDA(M.h, k_resid_pt(M.L, g, H.pr, um, sum, qm, sq, H.f[l0], B));
+    else
       PMG_CUDA(M.h, k_residual0(M.L, g, c, H.pr, um, sum, qm, sq, u1, s1, H.f[l0], B, nullptr, nullptr));
-      PMG_RET(vcycle(M, l0, B, c, minv, &e));
-      PMG_CUDA(M.h, k_update_u(M.L, g, H.pr, u1, s1, e, B, nullptr));
+    for (int v = 0; v < o.vcycles; ++v) {
+      const bool last = v == o.vcycles - 1;
+      PMG_RET(vcycle(M, l0, B, c, minv, e, &e, last ? u1 : nullptr, s1, last ? &fused : nullptr));
     }
+    if (!fused) PMG_CUDA(M.h, k_update_u(M.L, g, H.pr, u1, s1, e, B, nullptr));
     if (cycles) *cycles = o.vcycles;
     return PMG_OK;
   }
@@ -377,7 +428,7 @@ int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const dou
     for (int p = 0; p < B; ++p) M.hactive[p] = !done[p];
     PMG_CUDA(M.h, cudaMemcpyAsync(M.active, M.hactive, sizeof(int) * B, cudaMemcpyHostToDevice, M.stream));
     void *e = nullptr;
-    PMG_RET(vcycle(M, l0, B, c, minv, &e));
+    PMG_RET(vcycle(M, l0, B, c, minv, nullptr, &e));
     PMG_CUDA(M.h, k_update_u(M.L, g, H.pr, u1, s1, e, B, M.active));
     PMG_RET(norms(rn, nullptr));
     left = 0;
@@ -403,7 +454,31 @@ MGCtx mgctx(pmg_ctx *h) {
 
 // ----------------------------------------------------------------- SDC / PFASST schedule
 
+// With fixed V-cycle counts the fine level keeps no F = A U array: the end-of-iteration
+// pass (fine_residual) evaluates F from U, forms the collocation residual and the
+// right-hand sides q of the next fine sweep; the FAS restriction evaluates the fine F
+// at the coarse points only.  On GB300, whose FP64 rate is a small fraction of its FP32
+// rate, this removes most FP64 stencil work.  Full solves keep F (their sub-step
+// residuals need b = u_m + q_m).
+bool ffree(const pmg_ctx *h) { return h->opt.vcycles > 0; }
+
+// collocation residual of the fine level into red[2P..3P) (+ next right-hand sides
+// when F-free), copied to hred asynchronously
+int fine_residual(pmg_ctx *h) {
+  const long long sfs = (long long)h->sf * h->gf.slab;
+  PMG_CUDA(h, cudaMemsetAsync(h->red + 2 * h->P, 0, sizeof(unsigned long long) * h->P, h->stream));
+  if (ffree(h))
+    PMG_CUDA(h, k_fine_rhs_residual(h->L(), h->gf, h->resf, h->nu, h->Uf, sfs, h->qf, (long long)(h->sf - 1) * h->gf.slab,
+                                    h->P, h->red + 2 * h->P));
+  else
+    PMG_CUDA(h, k_colloc_residual(h->L(), h->gf, h->resf, h->Uf, h->Ff, sfs, h->P, h->red + 2 * h->P));
+  PMG_CUDA(h, cudaMemcpyAsync(h->hred + 2 * h->P, h->red + 2 * h->P, sizeof(unsigned long long) * h->P,
+                              cudaMemcpyDeviceToHost, h->stream));
+  return PMG_OK;
+}
+
 // One SDC sweep (Eq. sdc-be) on slices [p0, p0+B) of `level` (0 fine, 1 coarse).
+// F-free fine sweeps take q from the last fine_residual.
 int sweep(pmg_ctx *h, int level, int p0, int B) {
   MGCtx M = mgctx(h);
   const Grid &g = level ? h->gc : h->gf;
@@ -414,22 +489,26 @@ int sweep(pmg_ctx *h, int level, int p0, int B) {
   double *q = (level ? h->qc : h->qf) + p0 * sq;
   const double *tau = level ? h->tau + p0 * stride : nullptr;
   const SFCoef &cf = level ? h->sfc : h->sff;
+  const bool keepF = level == 1 || !ffree(h);
   Launch Ln = h->L();
-  PMG_CUDA(h, k_sf_rhs(Ln, g, cf, F, stride, tau, stride, q, sq, B));
+  if (keepF) PMG_CUDA(h, k_sf_rhs(Ln, g, cf, F, U, stride, tau, stride, q, sq, B));
   for (int m = 0; m < s - 1; ++m) {
     const double c = level ? h->cc_sub[m] : h->cf_sub[m];
     const int slot = level ? (h->sf - 1) + m : m;
     PMG_RET(solve_substep(M, level, B, c, h->minv_slot(slot), U + m * g.slab, stride, q + m * g.slab, sq,
-                          U + (m + 1) * g.slab, stride, nullptr));
-    PMG_CUDA(h, k_apply_A(Ln, g, h->nu, U + (m + 1) * g.slab, stride, F + (m + 1) * g.slab, stride, B));
+                          U + (m + 1) * g.slab, stride, nullptr, cf.sub_next != 0));
+    if (keepF) PMG_CUDA(h, k_apply_A(Ln, g, h->nu, U + (m + 1) * g.slab, stride, F + (m + 1) * g.slab, stride, B));
   }
   return PMG_OK;
 }
 
 int fas_restrict_all(pmg_ctx *h) {
   const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
-  PMG_CUDA(h, k_fas_restrict(h->L(), h->gf, h->gc, h->fas, h->Uf, h->Ff, sfs, h->Uc, h->Fc, h->tau, h->Uc0, scs,
-                             h->P));
+  if (ffree(h))
+    PMG_CUDA(h, k_fas_restrict_u(h->L(), h->gf, h->gc, h->fas, h->Uf, sfs, h->Uc, h->Fc, h->tau, h->Uc0, scs, h->P));
+  else
+    PMG_CUDA(h, k_fas_restrict(h->L(), h->gf, h->gc, h->fas, h->Uf, h->Ff, sfs, h->Uc, h->Fc, h->tau, h->Uc0, scs,
+                               h->P));
   return PMG_OK;
 }
 
@@ -443,12 +522,63 @@ int coarse_receive(pmg_ctx *h, int p0, int B) {
 
 int interp_all(pmg_ctx *h) {
   const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
-  PMG_CUDA(h, k_interp_correction(h->L(), h->gf, h->gc, h->interp, h->Uf, sfs, h->Uc, h->Uc0, scs, h->P));
-  PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf, h->gf.slab, h->Ff, h->gf.slab, h->P * h->sf));
+  PMG_CUDA(h, k_interp_time(h->L(), h->gc, h->interp, h->H.pr, h->Uc, h->Uc0, scs, h->dU, h->P));
+  PMG_CUDA(h, k_interp_space_add(h->L(), h->gf, h->gc, h->opt.interp_order, h->sf, h->H.pr, h->dU, h->Uf, sfs, h->P));
+  if (!ffree(h)) PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf, h->gf.slab, h->Ff, h->gf.slab, h->P * h->sf));
   return PMG_OK;
 }
 
-int predict(pmg_ctx *h) {
+// elapsed times of the event nodes of the last replay of a graph
+int harvest(pmg_ctx *h, pmg_ctx::Captured &G) {
+  for (const ProfRec &r : G.recs) {
+    float ms = 0.f;
+    PMG_CUDA(h, cudaEventElapsedTime(&ms, r.a, r.b));
+    h->prof.done.push_back(ProfDone{r.kid, r.n, r.prec, r.pts, ms});
+  }
+  return PMG_OK;
+}
+
+void drop_graph(pmg_ctx::Captured &G) {
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
+  G.recs.clear();
+}
+
+// run body on the caller's stream through a CUDA graph captured on a private stream
+// (captured again when the profiling settings changed since the last capture)
+int run_graph(pmg_ctx *h, pmg_ctx::Captured &G, int (*body)(pmg_ctx *)) {
+  if (G.exec && (G.with_prof != h->prof.on || G.prof_min != h->prof.min_points)) drop_graph(G);
+  if (!G.exec) {
+    if (!h->cap_stream) PMG_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = h->stream;
+    const long long before = h->launches;
+    h->stream = h->cap_stream;
+    h->prof.capture = &G.recs;
+    G.recs.clear();
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? body(h) : PMG_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &graph) : e;
+    h->stream = user;
+    h->prof.capture = nullptr;
+    G.kernels = h->launches - before;
+    h->launches = before;
+    if (rc != PMG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e2 != cudaSuccess) return fail(h, PMG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e2));
+    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { G.exec = nullptr; return fail(h, PMG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)); }
+    G.with_prof = h->prof.on;
+    G.prof_min = h->prof.min_points;
+  }
+  PMG_CUDA(h, cudaGraphLaunch(G.exec, h->stream));
+  h->launches += G.kernels;
+  return PMG_OK;
+}
+
+bool use_graphs(const pmg_ctx *h) { return h->opt.use_graphs && h->opt.vcycles > 0; }
+
+int predict_body(pmg_ctx *h) {
   if (h->nlevels == 2) {
     PMG_RET(fas_restrict_all(h));
     for (int s = 0; s < h->P; ++s) {
@@ -457,16 +587,21 @@ int predict(pmg_ctx *h) {
     }
     PMG_RET(interp_all(h));
   }
-  h->predicted = true;
-  return PMG_OK;
+  return ffree(h) ? fine_residual(h) : PMG_OK;  // right-hand sides of the first fine sweep
 }
 
-int colloc_residual(pmg_ctx *h) {
-  const long long sfs = (long long)h->sf * h->gf.slab;
-  PMG_CUDA(h, cudaMemsetAsync(h->red + 2 * h->P, 0, sizeof(unsigned long long) * h->P, h->stream));
-  PMG_CUDA(h, k_colloc_residual(h->L(), h->gf, h->resf, h->Uf, h->Ff, sfs, h->P, h->red + 2 * h->P));
-  PMG_CUDA(h, cudaMemcpyAsync(h->hred + 2 * h->P, h->red + 2 * h->P, sizeof(unsigned long long) * h->P,
-                              cudaMemcpyDeviceToHost, h->stream));
+int predict(pmg_ctx *h) {
+  if (use_graphs(h)) {
+    PMG_RET(run_graph(h, h->g_pred, predict_body));
+    if (!h->g_pred.recs.empty()) {
+      PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+      PMG_RET(harvest(h, h->g_pred));
+    }
+  } else {
+    PMG_RET(predict_body(h));
+  }
+  h->predicted = true;
+  h->q_valid = ffree(h);
   return PMG_OK;
 }
 
@@ -484,10 +619,9 @@ int iteration(pmg_ctx *h) {
   }
   if (h->P > 1) {  // send forward: U_f[p][0] <- U_f[p-1][M_f]
     PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + (h->sf - 1) * h->gf.slab, sfs, h->Uf + sfs, sfs, h->P - 1));
-    PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf + sfs, sfs, h->Ff + sfs, sfs, h->P - 1));
+    if (!ffree(h)) PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf + sfs, sfs, h->Ff + sfs, sfs, h->P - 1));
   }
-  PMG_RET(colloc_residual(h));
-  return PMG_OK;
+  return fine_residual(h);
 }
 
 double bits_to_double(unsigned long long v) {
@@ -502,6 +636,7 @@ int spread(pmg_ctx *h) {
   PMG_CUDA(h, k_copy(h->L(), h->gf, h->u0, 0, h->Uf, h->gf.slab, h->P * h->sf));
   PMG_CUDA(h, k_copy(h->L(), h->gf, h->dense, 0, h->Ff, h->gf.slab, h->P * h->sf));
   h->predicted = false;
+  h->q_valid = false;
   return PMG_OK;
 }
 
@@ -512,12 +647,13 @@ void fill_coefficients(pmg_ctx *h) {
   auto fill_sf = [&](SFCoef &cf, int s, const long double *t, long double Q[kMaxNodes][kMaxNodes], double *csub) {
     std::memset(&cf, 0, sizeof cf);
     cf.s = s;
+    cf.sub_next = h->opt.vcycles > 0;  // fixed V-cycle counts start from the pointwise residual
     for (int m = 0; m < s - 1; ++m) {
       const long double dtm = (long double)h->dt * (t[m + 1] - t[m]);
       csub[m] = (double)(dtm * h->nu);
       for (int j = 0; j < s; ++j) {
         long double w = (long double)h->dt * (Q[m + 1][j] - Q[m][j]);
-        if (j == m + 1) w -= dtm;
+        if (j == m + 1 && !cf.sub_next) w -= dtm;
         cf.W[m][j] = (double)w;
       }
     }
@@ -701,7 +837,11 @@ int pfasst_mg_predict(pmg_handle h) {
 
 int pfasst_mg_sweep(pmg_handle h, int level) {
   if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
-  if (level == 0) return sweep(h, 0, 0, h->P);
+  if (level == 0) {
+    if (ffree(h) && !h->q_valid) PMG_RET(fine_residual(h));
+    h->q_valid = false;
+    return sweep(h, 0, 0, h->P);
+  }
   if (level == 1 && h->nlevels == 2) {
     for (int p = 0; p < h->P; ++p) {
       if (p > 0) PMG_RET(coarse_receive(h, p, 1));
@@ -718,8 +858,12 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
   if (!h->predicted) PMG_RET(predict(h));
   double res = INFINITY;
   for (int k = 0; k < max_iter; ++k) {
-    PMG_RET(iteration(h));
+    if (ffree(h) && !h->q_valid) PMG_RET(fine_residual(h));  // after a standalone sweep
+    if (use_graphs(h)) PMG_RET(run_graph(h, h->g_iter, iteration));
+    else PMG_RET(iteration(h));
+    h->q_valid = ffree(h);
     PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (!h->g_iter.recs.empty() && use_graphs(h)) PMG_RET(harvest(h, h->g_iter));
     res = 0.0;
     for (int p = 0; p < h->P; ++p) {
       const double r = bits_to_double(h->hred[2 * h->P + p]);
@@ -735,7 +879,8 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
 
 int pfasst_mg_residual(pmg_handle h, double *res) {
   if (!h || !res) return fail(h, PMG_ERR_INVALID_ARG, "null argument");
-  PMG_RET(colloc_residual(h));
+  PMG_RET(fine_residual(h));
+  h->q_valid = ffree(h);
   PMG_CUDA(h, cudaStreamSynchronize(h->stream));
   for (int p = 0; p < h->P; ++p) res[p] = bits_to_double(h->hred[2 * h->P + p]);
   return PMG_OK;
@@ -788,20 +933,24 @@ int pfasst_mg_profile(pmg_handle h, int enable, long long min_points) {
 int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int *count) {
   if (!h || !count || capacity < 0 || (capacity > 0 && !out)) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
   PMG_CUDA(h, cudaStreamSynchronize(h->stream));
-  std::vector<pmg_kernel_stat> agg;
   for (const ProfRec &r : h->prof.recs) {
     float ms = 0.f;
     PMG_CUDA(h, cudaEventElapsedTime(&ms, r.a, r.b));
+    h->prof.done.push_back(ProfDone{r.kid, r.n, r.prec, r.pts, ms});
+  }
+  h->prof.recs.clear();
+  h->prof.used = 0;
+  std::vector<pmg_kernel_stat> agg;
+  for (const ProfDone &r : h->prof.done) {
     size_t q = 0;
     for (; q < agg.size(); ++q)
       if (agg[q].kernel == r.kid && agg[q].n == r.n && agg[q].precision == r.prec) break;
     if (q == agg.size()) agg.push_back(pmg_kernel_stat{r.kid, r.n, r.prec, 0, 0, 0.0});
     agg[q].launches += 1;
     agg[q].points += r.pts;
-    agg[q].ms += ms;
+    agg[q].ms += r.ms;
   }
-  h->prof.recs.clear();
-  h->prof.used = 0;
+  h->prof.done.clear();
   *count = (int)agg.size();
   for (int q = 0; q < capacity && q < (int)agg.size(); ++q) out[q] = agg[q];
   return PMG_OK;
@@ -810,14 +959,19 @@ int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int
 const char *pfasst_mg_kernel_name(int kernel) {
   static const char *names[K_COUNT] = {"residual0", "smooth_jacobi", "smooth_rbgs", "residual_restrict",
                                        "prolong_add", "coarse_solve", "update_u", "zero", "apply_A", "sf_rhs",
-                                       "fas_restrict", "interp_correction", "colloc_residual", "copy", "pack",
-                                       "unpack"};
+                                       "fas_restrict", "interp_space", "colloc_residual", "copy", "pack",
+                                       "unpack", "interp_time", "rbgs_sweep3d", "resrestrict3d", "prolong3d",
+                                       "resid_pt", "fine_rhs_residual", "rbgs_sweep3d_zero",
+                                       "rbgs_sweep3d_upd"};
   return kernel >= 0 && kernel < K_COUNT ? names[kernel] : "unknown";
 }
 
 int pfasst_mg_destroy(pmg_handle h) {
   if (!h) return PMG_OK;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  drop_graph(h->g_pred);
+  drop_graph(h->g_iter);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ws_owned && h->ws) cudaFree(h->ws);
   if (h->hred) cudaFreeHost(h->hred);
   if (h->hactive) cudaFreeHost(h->hactive);

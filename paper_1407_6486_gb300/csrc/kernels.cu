@@ -40,35 +40,6 @@ void config(const Grid &g, int batch, dim3 &grid, dim3 &block) {
   grid = dim3(1, gy, (unsigned)gz);
 }
 
-// records a start event before a launch and the matching end event after it
-struct Scope {
-  const Launch &L;
-  ProfRec rec;
-  bool active = false;
-  Scope(const Launch &L_, KernelId kid, const Grid &g, int batch, int prec) : L(L_) {
-    const long long pts = (long long)g.n * g.ny * g.nz * batch;
-    if (L.prof && L.prof->on && pts >= L.prof->min_points) {
-      rec.kid = kid;
-      rec.n = g.n;
-      rec.prec = prec;
-      rec.pts = pts;
-      rec.a = L.prof->take();
-      rec.b = L.prof->take();
-      cudaEventRecord(rec.a, L.stream);
-      active = true;
-    }
-  }
-  cudaError_t done() {
-    if (L.counter) ++*L.counter;
-    cudaError_t e = cudaGetLastError();
-    if (active) {
-      cudaEventRecord(rec.b, L.stream);
-      L.prof->recs.push_back(rec);
-    }
-    return e;
-  }
-};
-
 // sum of the 2*DIM neighbours, zero outside the interior (Dirichlet 0)
 template <int DIM, typename T>
 __device__ __forceinline__ T nbsum(const T *__restrict__ u, const Grid &g, int i, int j, int k, long long off) {
@@ -249,6 +220,15 @@ __global__ void coarse_solve_kernel(Grid g, const T *__restrict__ minv, const T 
 }
 
 template <typename T>
+__global__ void resid_pt_kernel(Grid g, const double *__restrict__ um, long long sum, const double *__restrict__ qm,
+                                long long sq, T *__restrict__ f, int batch) {
+  PMG_FOR_POINTS(g, batch) {
+    PMG_POINT(g);
+    f[b * g.slab + off] = (T)(um[b * sum + off] + qm[b * sq + off]);
+  }
+}
+
+template <typename T>
 __global__ void update_u_kernel(Grid g, double *__restrict__ u, long long su, const T *__restrict__ e, int batch,
                                 const int *__restrict__ active) {
   PMG_FOR_POINTS(g, batch) {
@@ -279,9 +259,9 @@ __global__ void apply_A_kernel(Grid g, double nu, const double *__restrict__ u, 
   }
 }
 
-__global__ void sf_rhs_kernel(Grid g, SFCoef cf, const double *__restrict__ F, long long sF,
-                              const double *__restrict__ tau, long long stau, double *__restrict__ q, long long sq,
-                              int batch) {
+__global__ void sf_rhs_kernel(Grid g, SFCoef cf, const double *__restrict__ F, const double *__restrict__ U,
+                              long long sF, const double *__restrict__ tau, long long stau, double *__restrict__ q,
+                              long long sq, int batch) {
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
     double Fv[kMaxNodes];
@@ -295,6 +275,7 @@ __global__ void sf_rhs_kernel(Grid g, SFCoef cf, const double *__restrict__ F, l
         acc += tnext - tprev;
         tprev = tnext;
       }
+      if (cf.sub_next) acc -= U[b * sF + (m + 1) * g.slab + off];
       q[b * sq + m * g.slab + off] = acc;
     }
   }
@@ -336,63 +317,119 @@ __global__ void fas_restrict_kernel(Grid gf, Grid gc, FASCoef cf, const double *
   }
 }
 
-// interpolation taps of fine 0-based index i onto coarse 1-based indices, with odd
-// reflection at the walls (index 0 and nc+1 are zero walls; -1 and nc+2 mirror 1, nc)
-__device__ __forceinline__ int interp_taps(int order, int i, int nc, int *idx, double *w) {
-  const int i1 = i + 1;
-  if ((i1 & 1) == 0) {
-    idx[0] = i1 / 2 - 1;
-    w[0] = 1.0;
-    return 1;
-  }
-  const int J = (i1 - 1) / 2;
-  int t = 0;
-  const int no = order == 2 ? 2 : 4;
-  const int base = order == 2 ? 0 : -1;
-  const double w2[2] = {0.5, 0.5};
-  const double w4[4] = {-1.0 / 16, 9.0 / 16, 9.0 / 16, -1.0 / 16};
-  for (int q = 0; q < no; ++q) {
-    int J1 = J + base + q;
-    double sg = 1.0;
-    if (J1 == 0 || J1 == nc + 1) continue;
-    if (J1 < 0) { J1 = -J1; sg = -1.0; }
-    if (J1 > nc + 1) { J1 = 2 * (nc + 1) - J1; sg = -1.0; }
-    idx[t] = J1 - 1;
-    w[t] = sg * (order == 2 ? w2[q] : w4[q]);
-    ++t;
-  }
-  return t;
-}
-
-template <int DIM>
-__global__ void interp_correction_kernel(Grid gf, Grid gc, InterpCoef cf, double *__restrict__ Uf, long long sfine,
-                                         const double *__restrict__ Uc, const double *__restrict__ Uc0,
-                                         long long scoarse, int batch) {
-  PMG_FOR_POINTS(gf, batch) {
-    PMG_POINT(gf);
-    int ix[4], iy[4] = {0}, iz[4] = {0};
-    double wx[4], wy[4] = {1.0}, wz[4] = {1.0};
-    const int tx = interp_taps(cf.order, i, gc.n, ix, wx);
-    const int ty = DIM >= 2 ? interp_taps(cf.order, j, gc.n, iy, wy) : 1;
-    const int tz = DIM >= 3 ? interp_taps(cf.order, k, gc.n, iz, wz) : 1;
+// time interpolation of the coarse correction on the coarse grid:
+// dU_m = sum_j T[m][j] (U_c,j - U_c0,j) for every fine node m (stored as T)
+template <typename T>
+__global__ void interp_time_kernel(Grid gc, InterpCoef cf, const double *__restrict__ Uc,
+                                   const double *__restrict__ Uc0, long long scoarse, T *__restrict__ dU, int batch) {
+  PMG_FOR_POINTS(gc, batch) {
+    PMG_POINT(gc);
     double d[kMaxNodes];
     for (int jn = 0; jn < cf.sc; ++jn) {
-      const double *A = Uc + b * scoarse + jn * gc.slab;
-      const double *B = Uc0 + b * scoarse + jn * gc.slab;
-      double acc = 0.0;
-      for (int cz = 0; cz < tz; ++cz)
-        for (int cy = 0; cy < ty; ++cy)
-          for (int cx = 0; cx < tx; ++cx) {
-            const long long co = ((long long)iz[cz] * gc.ny + iy[cy]) * gc.pitch + ix[cx];
-            acc += wx[cx] * wy[cy] * wz[cz] * (A[co] - B[co]);
-          }
-      d[jn] = acc;
+      const long long co = b * scoarse + jn * gc.slab + off;
+      d[jn] = Uc[co] - Uc0[co];
     }
     for (int m = 0; m < cf.sf; ++m) {
       double acc = 0.0;
       for (int jn = 0; jn < cf.sc; ++jn) acc += cf.T[m][jn] * d[jn];
-      Uf[b * sfine + m * gf.slab + off] += acc;
+      dU[((long long)b * cf.sf + m) * gc.slab + off] = (T)acc;
     }
+  }
+}
+
+// coarse value at 1-based index J of one axis with odd reflection at the walls
+// (J = 0 and nc+1 are the zero walls, J = -1 and nc+2 mirror J = 1 and nc)
+__device__ __forceinline__ int reflect_index(int J, int nc, float *sign) {
+  *sign = 1.f;
+  if (J >= 1 && J <= nc) return J - 1;
+  if (J == 0 || J == nc + 1) { *sign = 0.f; return 0; }
+  int r = J < 0 ? -J : 2 * (nc + 1) - J;
+  *sign = -1.f;
+  if (r < 1 || r > nc) { *sign = 0.f; return 0; }
+  return r - 1;
+}
+
+// per-axis interpolation taps of fine 0-based index i: 1-based coarse indices and
+// weights (4th order (-1,9,9,-1)/16 or linear at odd points, injection at even)
+__device__ __forceinline__ int interp_taps_raw(int order, int i, int *J, float *w) {
+  const int i1 = i + 1;
+  if ((i1 & 1) == 0) { J[0] = i1 / 2; w[0] = 1.f; return 1; }
+  const int c = (i1 - 1) / 2;
+  if (order == 2) { J[0] = c; J[1] = c + 1; w[0] = w[1] = 0.5f; return 2; }
+  J[0] = c - 1; J[1] = c; J[2] = c + 1; J[3] = c + 2;
+  w[0] = w[3] = -1.f / 16; w[1] = w[2] = 9.f / 16;
+  return 4;
+}
+
+// U_f,m += I_x dU_m on a fine tile of ITX x ITY x ITZ points: the coarse box (with
+// reflected wall values) is staged in shared memory and interpolated axis by axis
+constexpr int ITX = 32, ITY = 8, ITZ = 8;
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) interp_space_kernel(Grid gf, Grid gc, int order, int sf, const T *__restrict__ dU,
+                                                           double *__restrict__ Uf, long long sfine, int ntz) {
+  constexpr int TY = DIM >= 2 ? ITY : 1, TZ = DIM >= 3 ? ITZ : 1;
+  constexpr int CX = ITX / 2 + 4, CY = DIM >= 2 ? ITY / 2 + 4 : 1, CZ = DIM >= 3 ? ITZ / 2 + 4 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *C = (T *)smem_raw;                 // [CZ][CY][CX]
+  T *X = C + CZ * CY * CX;              // [CZ][CY][ITX]
+  T *Y = X + CZ * CY * ITX;             // [CZ][TY][ITX]
+  const int x0 = blockIdx.x * ITX, y0 = blockIdx.y * TY;
+  const int zt = blockIdx.z % ntz, b = blockIdx.z / ntz, z0 = zt * TZ;
+  const int cx0 = x0 / 2 - 1, cy0 = DIM >= 2 ? y0 / 2 - 1 : 1, cz0 = DIM >= 3 ? z0 / 2 - 1 : 1;
+  const int nc = gc.n, tid = threadIdx.x;
+  for (int m = 0; m < sf; ++m) {
+    const T *src = dU + ((long long)b * sf + m) * gc.slab;
+    for (int q = tid; q < CZ * CY * CX; q += blockDim.x) {
+      const int a = q % CX, bb = (q / CX) % CY, cc = q / (CX * CY);
+      float sx, sy = 1.f, sz = 1.f;
+      const int ix = reflect_index(cx0 + a, nc, &sx);
+      const int iy = DIM >= 2 ? reflect_index(cy0 + bb, nc, &sy) : 0;
+      const int iz = DIM >= 3 ? reflect_index(cz0 + cc, nc, &sz) : 0;
+      const float sg = sx * sy * sz;
+      C[q] = sg == 0.f ? T(0) : T(sg) * src[((long long)iz * gc.ny + iy) * gc.pitch + ix];
+    }
+    __syncthreads();
+    for (int q = tid; q < CZ * CY * ITX; q += blockDim.x) {  // x pass
+      const int x = q % ITX, row = q / ITX;
+      int J[4];
+      float w[4];
+      const int t = interp_taps_raw(order, x0 + x, J, w);
+      T acc = T(0);
+      for (int u = 0; u < t; ++u) acc += T(w[u]) * C[row * CX + (J[u] - cx0)];
+      X[q] = acc;
+    }
+    __syncthreads();
+    if (DIM >= 2) {
+      for (int q = tid; q < CZ * TY * ITX; q += blockDim.x) {  // y pass
+        const int x = q % ITX, y = (q / ITX) % TY, zc = q / (ITX * TY);
+        int J[4];
+        float w[4];
+        const int t = interp_taps_raw(order, y0 + y, J, w);
+        T acc = T(0);
+        for (int u = 0; u < t; ++u) acc += T(w[u]) * X[(zc * CY + (J[u] - cy0)) * ITX + x];
+        Y[q] = acc;
+      }
+      __syncthreads();
+    }
+    const T *Src = DIM >= 2 ? Y : X;
+    double *dst = Uf + (long long)b * sfine + (long long)m * gf.slab;
+    for (int q = tid; q < TZ * TY * ITX; q += blockDim.x) {  // z pass and update
+      const int x = q % ITX, y = (q / ITX) % TY, z = q / (ITX * TY);
+      const int i = x0 + x, j = y0 + y, k = z0 + z;
+      if (i >= gf.n || (DIM >= 2 && j >= gf.n) || (DIM >= 3 && k >= gf.n)) continue;
+      T v;
+      if (DIM >= 3) {
+        int J[4];
+        float w[4];
+        const int t = interp_taps_raw(order, k, J, w);
+        v = T(0);
+        for (int u = 0; u < t; ++u) v += T(w[u]) * Src[((J[u] - cz0) * TY + y) * ITX + x];
+      } else {
+        v = Src[y * ITX + x];
+      }
+      dst[((long long)(DIM >= 3 ? k : 0) * gf.ny + (DIM >= 2 ? j : 0)) * gf.pitch + i] += (double)v;
+    }
+    __syncthreads();
   }
 }
 
@@ -416,6 +453,81 @@ __global__ void colloc_residual_kernel(Grid g, ResCoef cf, const double *__restr
         }
       }
     warp_max_atomic(mx, out + b);
+  }
+}
+
+// End-of-iteration pass of the fine level (fixed V-cycle counts): from U alone,
+//   F_j = nu Lap_h U_j at every node (not stored),
+//   P_m = sum_j dtQ[m][j] F_j,
+//   collocation residual r_m = U_0 + P_m - U_m (Eq. resid), max-reduced per slice,
+//   q_m = P_{m+1} - P_m - U_{m+1}: u_m + q_m is the initial residual of sub-step m
+//   of the next sweep (Eq. SDCcompactLIII with initial guess u^k_{m+1}).
+template <int DIM>
+__global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, double nu, const double *__restrict__ U, long long stride,
+                                         double *__restrict__ q, long long sq, int batch, unsigned long long *res) {
+  const double a = nu * g.ih2;
+  for (int zb = blockIdx.z; zb < g.nz * batch; zb += gridDim.z) {
+    const int k = zb % g.nz, b = zb / g.nz;
+    double mx = 0.0;
+    for (int j = blockIdx.y * blockDim.y + threadIdx.y; j < g.ny; j += gridDim.y * blockDim.y)
+      for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+        const long long off = ((long long)k * g.ny + j) * g.pitch + i;
+        const double *Ub = U + b * stride;
+        double Uv[kMaxNodes], Fv[kMaxNodes];
+        for (int jn = 0; jn < cf.s; ++jn) {
+          const double *Uj = Ub + jn * g.slab;
+          Uv[jn] = Uj[off];
+          Fv[jn] = a * (nbsum<DIM>(Uj, g, i, j, k, off) - 2.0 * DIM * Uv[jn]);
+        }
+        double Pprev = 0.0;
+        for (int m = 1; m < cf.s; ++m) {
+          double P = 0.0;
+          for (int jn = 0; jn < cf.s; ++jn) P += cf.dtQ[m][jn] * Fv[jn];
+          const double r = fabs(Uv[0] + P - Uv[m]);
+          if (!(r <= mx)) mx = r;
+          q[b * sq + (m - 1) * g.slab + off] = (P - Pprev) - Uv[m];
+          Pprev = P;
+        }
+      }
+    if (res) warp_max_atomic(mx, res + b);
+  }
+}
+
+// FAS restriction with the fine F evaluated from U_f at the coarse points only
+template <int DIM>
+__global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double *__restrict__ Uf, long long sfine,
+                                      double *__restrict__ Uc, double *__restrict__ Fc, double *__restrict__ tau,
+                                      double *__restrict__ Uc0, long long scoarse, int batch) {
+  const double ac = cf.nu * gc.ih2, af = cf.nu * gf.ih2;
+  const long long plf = (long long)gf.ny * gf.pitch;
+  PMG_FOR_POINTS(gc, batch) {
+    PMG_POINT(gc);
+    const int fi = 2 * i + 1, fj = DIM >= 2 ? 2 * j + 1 : 0, fk = DIM >= 3 ? 2 * k + 1 : 0;
+    const long long fo = ((long long)fk * gf.ny + fj) * gf.pitch + fi;
+    double Fcv[kMaxNodes], Ffv[kMaxNodes];
+    for (int in = 0; in < cf.sf; ++in) {
+      const double *U = Uf + b * sfine + in * gf.slab;
+      Ffv[in] = af * (nbsum<DIM>(U, gf, fi, fj, fk, fo) - 2.0 * DIM * U[fo]);
+    }
+    for (int jn = 0; jn < cf.sc; ++jn) {
+      const double *U = Uf + b * sfine + cf.map[jn] * gf.slab;
+      const double uc = U[fo];
+      double s = (i > 0 ? U[fo - 2] : 0.0) + (i < gc.n - 1 ? U[fo + 2] : 0.0);
+      if (DIM >= 2) s += (j > 0 ? U[fo - 2 * gf.pitch] : 0.0) + (j < gc.n - 1 ? U[fo + 2 * gf.pitch] : 0.0);
+      if (DIM >= 3) s += (k > 0 ? U[fo - 2 * plf] : 0.0) + (k < gc.n - 1 ? U[fo + 2 * plf] : 0.0);
+      Fcv[jn] = ac * (s - 2.0 * DIM * uc);
+      const long long co = b * scoarse + jn * gc.slab + off;
+      Uc[co] = uc;
+      Uc0[co] = uc;
+      Fc[co] = Fcv[jn];
+    }
+    for (int jn = 0; jn < cf.sc; ++jn) {
+      double If = 0.0;
+      for (int in = 0; in < cf.sf; ++in) If += cf.dtQf[jn][in] * Ffv[in];
+      double Ic = 0.0;
+      for (int in = 0; in < cf.sc; ++in) Ic += cf.dtQc[jn][in] * Fcv[in];
+      tau[b * scoarse + jn * gc.slab + off] = If - Ic;
+    }
   }
 }
 
@@ -574,12 +686,24 @@ cudaError_t k_apply_A(const Launch &L, const Grid &g, double nu, const double *u
   return sc.done();
 }
 
-cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const double *F, long long sF,
+cudaError_t k_resid_pt(const Launch &L, const Grid &g, Prec pr, const double *um, long long sum, const double *qm,
+                       long long sq, void *f, int batch) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_RESID_PT, g, batch, pr);
+  if (pr == F64)
+    resid_pt_kernel<double><<<gr, bl, 0, L.stream>>>(g, um, sum, qm, sq, (double *)f, batch);
+  else
+    resid_pt_kernel<float><<<gr, bl, 0, L.stream>>>(g, um, sum, qm, sq, (float *)f, batch);
+  return sc.done();
+}
+
+cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const double *F, const double *U, long long sF,
                      const double *tau, long long stau, double *q, long long sq, int batch) {
   dim3 gr, bl;
   config(g, batch, gr, bl);
   Scope sc(L, K_SF_RHS, g, batch, 0);
-  sf_rhs_kernel<<<gr, bl, 0, L.stream>>>(g, cf, F, sF, tau, stau, q, sq, batch);
+  sf_rhs_kernel<<<gr, bl, 0, L.stream>>>(g, cf, F, U, sF, tau, stau, q, sq, batch);
   return sc.done();
 }
 
@@ -594,13 +718,42 @@ cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, cons
   return sc.done();
 }
 
-cudaError_t k_interp_correction(const Launch &L, const Grid &gf, const Grid &gc, const InterpCoef &cf, double *Uf,
-                                long long sfine, const double *Uc, const double *Uc0, long long scoarse, int batch) {
+cudaError_t k_interp_time(const Launch &L, const Grid &gc, const InterpCoef &cf, Prec pr, const double *Uc,
+                          const double *Uc0, long long scoarse, void *dU, int batch) {
   dim3 gr, bl;
-  config(gf, batch, gr, bl);
-  Scope sc(L, K_INTERP, gf, batch, 0);
-  PMG_DIM_SWITCH(gf.dim, (interp_correction_kernel<D><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Uc0,
-                                                                                  scoarse, batch)))
+  config(gc, batch, gr, bl);
+  Scope sc(L, K_INTERP_T, gc, batch, pr);
+  if (pr == F64)
+    interp_time_kernel<double><<<gr, bl, 0, L.stream>>>(gc, cf, Uc, Uc0, scoarse, (double *)dU, batch);
+  else
+    interp_time_kernel<float><<<gr, bl, 0, L.stream>>>(gc, cf, Uc, Uc0, scoarse, (float *)dU, batch);
+  return sc.done();
+}
+
+template <int D, typename T>
+cudaError_t launch_interp_space(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, const void *dU,
+                                double *Uf, long long sfine, int batch) {
+  constexpr int TY = D >= 2 ? ITY : 1, TZ = D >= 3 ? ITZ : 1;
+  constexpr int CX = ITX / 2 + 4, CY = D >= 2 ? ITY / 2 + 4 : 1, CZ = D >= 3 ? ITZ / 2 + 4 : 1;
+  const size_t smem = sizeof(T) * (CZ * CY * CX + CZ * CY * ITX + CZ * TY * ITX);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(interp_space_kernel<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int ntx = (gf.n + ITX - 1) / ITX, nty = (gf.ny + TY - 1) / TY, ntz = (gf.nz + TZ - 1) / TZ;
+  dim3 gr(ntx, nty, ntz * batch);
+  interp_space_kernel<D, T><<<gr, 256, smem, L.stream>>>(gf, gc, order, sf, (const T *)dU, Uf, sfine, ntz);
+  return cudaSuccess;
+}
+
+cudaError_t k_interp_space_add(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, Prec pr,
+                               const void *dU, double *Uf, long long sfine, int batch) {
+  Scope sc(L, K_INTERP, gf, batch * sf, pr);
+  if (pr == F64)
+    PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, double>(L, gf, gc, order, sf, dU, Uf, sfine, batch)))
+  else
+    PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, float>(L, gf, gc, order, sf, dU, Uf, sfine, batch)))
   return sc.done();
 }
 
@@ -610,6 +763,26 @@ cudaError_t k_colloc_residual(const Launch &L, const Grid &g, const ResCoef &cf,
   config(g, batch, gr, bl);
   Scope sc(L, K_COLLOC, g, batch, 0);
   colloc_residual_kernel<<<gr, bl, 0, L.stream>>>(g, cf, U, F, stride, batch, out);
+  return sc.done();
+}
+
+cudaError_t k_fine_rhs_residual(const Launch &L, const Grid &g, const ResCoef &cf, double nu, const double *U,
+                                long long stride, double *q, long long sq, int batch, unsigned long long *res) {
+  dim3 gr, bl;
+  config(g, batch, gr, bl);
+  Scope sc(L, K_FINE_RHS, g, batch, 0);
+  PMG_DIM_SWITCH(g.dim, (fine_rhs_residual_kernel<D><<<gr, bl, 0, L.stream>>>(g, cf, nu, U, stride, q, sq, batch, res)))
+  return sc.done();
+}
+
+cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
+                             long long sfine, double *Uc, double *Fc, double *tau, double *Uc0, long long scoarse,
+                             int batch) {
+  dim3 gr, bl;
+  config(gc, batch, gr, bl);
+  Scope sc(L, K_FAS, gc, batch, 0);
+  PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Fc, tau, Uc0,
+                                                                               scoarse, batch)))
   return sc.done();
 }
 

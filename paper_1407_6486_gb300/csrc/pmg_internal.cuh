@@ -43,22 +43,33 @@ inline Grid make_grid(int dim, int n) {
 // kernel identifiers for launch accounting and the event profiler
 enum KernelId {
   K_RESIDUAL0 = 0, K_JACOBI, K_RBGS, K_RESRESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_ZERO,
-  K_APPLY_A, K_SF_RHS, K_FAS, K_INTERP, K_COLLOC, K_COPY, K_PACK, K_UNPACK, K_COUNT
+  K_APPLY_A, K_SF_RHS, K_FAS, K_INTERP, K_COLLOC, K_COPY, K_PACK, K_UNPACK, K_INTERP_T,
+  K_RBGS3D, K_RESRESTRICT3D, K_PROLONG3D, K_RESID_PT, K_FINE_RHS, K_RBGS3D_ZERO, K_RBGS3D_UPD, K_COUNT
 };
 
 // CUDA-event timing of individual launches on the launching stream (only launches
-// that cover at least min_points grid points are recorded)
+// that cover at least min_points grid points are recorded).  Eager launches get an
+// event pair from a recycled pool; launches recorded while a stream is captured into
+// a graph get persistent events recorded by event nodes of the graph, harvested after
+// every replay.
 struct ProfRec {
   int kid, n, prec;
   long long pts;
   cudaEvent_t a, b;
 };
+struct ProfDone {
+  int kid, n, prec;
+  long long pts;
+  double ms;
+};
 struct Profiler {
   bool on = false;
   long long min_points = 0;
-  std::vector<cudaEvent_t> pool;
+  std::vector<cudaEvent_t> pool, persist;
   size_t used = 0;
-  std::vector<ProfRec> recs;
+  std::vector<ProfRec> recs;              // pending eager records
+  std::vector<ProfRec> *capture = nullptr;  // set while capturing a graph
+  std::vector<ProfDone> done;
   cudaEvent_t take() {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -67,8 +78,15 @@ struct Profiler {
     }
     return pool[used++];
   }
+  cudaEvent_t take_persistent() {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    persist.push_back(e);
+    return e;
+  }
   ~Profiler() {
     for (auto e : pool) cudaEventDestroy(e);
+    for (auto e : persist) cudaEventDestroy(e);
   }
 };
 
@@ -78,10 +96,57 @@ struct Launch {
   Profiler *prof;      // may be null
 };
 
-// sub-step right-hand side coefficients: q_m = sum_j W[m][j] F_j (+ tau_{m+1} - tau_m)
+// records a start event before a launch and the matching end event after it
+struct Scope {
+  const Launch &L;
+  ProfRec rec;
+  bool active = false, graph = false;
+  Scope(const Launch &L_, KernelId kid, const Grid &g, int batch, int prec) : L(L_) {
+    const long long pts = (long long)g.n * g.ny * g.nz * batch;
+    if (L.prof && L.prof->on && pts >= L.prof->min_points) {
+      rec.kid = kid;
+      rec.n = g.n;
+      rec.prec = prec;
+      rec.pts = pts;
+      graph = L.prof->capture != nullptr;
+      if (graph) {
+        rec.a = L.prof->take_persistent();
+        rec.b = L.prof->take_persistent();
+        cudaEventRecordWithFlags(rec.a, L.stream, cudaEventRecordExternal);
+      } else {
+        rec.a = L.prof->take();
+        rec.b = L.prof->take();
+        cudaEventRecord(rec.a, L.stream);
+      }
+      active = true;
+    }
+  }
+  cudaError_t done() {
+    if (L.counter) ++*L.counter;
+    cudaError_t e = cudaGetLastError();
+    if (active) {
+      if (graph) {
+        cudaEventRecordWithFlags(rec.b, L.stream, cudaEventRecordExternal);
+        L.prof->capture->push_back(rec);
+      } else {
+        cudaEventRecord(rec.b, L.stream);
+        L.prof->recs.push_back(rec);
+      }
+    }
+    return e;
+  }
+};
+
+// sub-step right-hand side coefficients:
+//   q_m = sum_j W[m][j] F_j (+ tau_{m+1} - tau_m) (- U_{m+1} when sub_next)
+// Full solves: W = dt (Q[m+1][j] - Q[m][j]) - [j == m+1] dt_m and sub_next = 0, so that
+// u_m + q_m is the right-hand side of the sub-step equation.  Fixed V-cycle counts:
+// W = dt (Q[m+1][j] - Q[m][j]) and sub_next = 1, so that u_m + q_m is directly the
+// initial residual b - (I - dt_m A) u^k_{m+1} (using F_{m+1} = A u^k_{m+1}).
 struct SFCoef {
   int s;                                 // nodes
-  double W[kMaxNodes - 1][kMaxNodes];    // dt (Q[m+1][j] - Q[m][j]) - [j == m+1] dt_m
+  int sub_next;
+  double W[kMaxNodes - 1][kMaxNodes];
 };
 
 // collocation residual coefficients: r_m = U_0 + sum_i dtQ[m][i] F_i - U_m
@@ -122,16 +187,37 @@ cudaError_t k_update_u(const Launch &L, const Grid &g, Prec pr, double *u, long 
                        const int *active);
 cudaError_t k_zero(const Launch &L, const Grid &g, Prec pr, void *e, int batch);
 
+// tiled 3D kernels for large batched grids (stencil3d.cu)
+constexpr int kTiled3dMinN = 63;
+cudaError_t k_rbgs_sweep3d(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
+                           void *eout, const void *f, double *u, long long su, int batch, bool zero, bool update_u);
+cudaError_t k_resrestrict3d(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
+                            const void *f, void *fc, int batch);
+cudaError_t k_prolong3d(const Launch &L, const Grid &gf, const Grid &gc, Prec pr, const void *ec, void *e, int batch);
+
 // ---- SDC / PFASST kernels (FP64) ----
 cudaError_t k_apply_A(const Launch &L, const Grid &g, double nu, const double *u, long long su, double *F,
                       long long sF, int batch);
-cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const double *F, long long sF,
+cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const double *F, const double *U, long long sF,
                      const double *tau, long long stau, double *q, long long sq, int batch);
+// pointwise initial residual f = (T)(u_m + q_m) of the sub-step equation
+cudaError_t k_resid_pt(const Launch &L, const Grid &g, Prec pr, const double *um, long long sum, const double *qm,
+                       long long sq, void *f, int batch);
 cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
                            const double *Ff, long long sfine, double *Uc, double *Fc, double *tau, double *Uc0,
                            long long scoarse, int batch);
-cudaError_t k_interp_correction(const Launch &L, const Grid &gf, const Grid &gc, const InterpCoef &cf, double *Uf,
-                                long long sfine, const double *Uc, const double *Uc0, long long scoarse, int batch);
+// coarse-correction interpolation in two steps: in time on the coarse grid (dU in the
+// precision pr), then in space onto every fine node, added to U_f
+cudaError_t k_interp_time(const Launch &L, const Grid &gc, const InterpCoef &cf, Prec pr, const double *Uc,
+                          const double *Uc0, long long scoarse, void *dU, int batch);
+cudaError_t k_interp_space_add(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, Prec pr,
+                               const void *dU, double *Uf, long long sfine, int batch);
+// fine level without stored F (fixed V-cycle counts): residual + next right-hand sides
+cudaError_t k_fine_rhs_residual(const Launch &L, const Grid &g, const ResCoef &cf, double nu, const double *U,
+                                long long stride, double *q, long long sq, int batch, unsigned long long *res);
+cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
+                             long long sfine, double *Uc, double *Fc, double *tau, double *Uc0, long long scoarse,
+                             int batch);
 cudaError_t k_colloc_residual(const Launch &L, const Grid &g, const ResCoef &cf, const double *U, const double *F,
                               long long stride, int batch, unsigned long long *out);
 cudaError_t k_copy(const Launch &L, const Grid &g, const double *src, long long ss, double *dst, long long sd,

@@ -42,12 +42,14 @@ def omega(sm):
 
 # ---------------------------------------------------------------- multigrid alone
 
-@pytest.mark.parametrize("dim,n,sm,vc", [
-    (1, 3, 0, 1), (1, 63, 0, 2), (1, 1023, 1, 2), (2, 31, 0, 1), (2, 255, 1, 2), (2, 127, 0, 3),
-    (3, 7, 1, 1), (3, 15, 0, 2), (3, 31, 1, 2), (3, 63, 0, 1),
+@pytest.mark.parametrize("dim,n,sm,vc,batch", [
+    (1, 3, 0, 1, 3), (1, 63, 0, 2, 3), (1, 1023, 1, 2, 3), (2, 31, 0, 1, 3), (2, 255, 1, 2, 3), (2, 127, 0, 3, 3),
+    (3, 7, 1, 1, 3), (3, 15, 0, 2, 3), (3, 31, 1, 2, 3), (3, 63, 0, 1, 3), (3, 63, 1, 2, 3), (3, 127, 1, 1, 3),
+    # 127^3 x 9 grids: large enough for the tiled z-marching kernels (partial tiles in x, y and z)
+    (3, 127, 1, 2, 9),
 ])
-def test_vcycles_fp64_match_oracle(dim, n, sm, vc):
-    batch, c = 3, 0.37 / (n + 1) ** 2 * 4
+def test_vcycles_fp64_match_oracle(dim, n, sm, vc, batch):
+    c = 0.37 / (n + 1) ** 2 * 4
     rng = np.random.default_rng(dim * 1000 + n)
     b = rng.standard_normal((batch, n ** dim))
     u = rng.standard_normal((batch, n ** dim))
@@ -75,11 +77,11 @@ def test_full_solve_matches_oracle(dim, n, sm):
     assert rel(ut.cpu().numpy(), np.stack([o[0] for o in outs])) < 1e-11
 
 
-@pytest.mark.parametrize("dim,n,sm", [(2, 127, 0), (3, 31, 1)])
-def test_mixed_vcycle_and_refinement(dim, n, sm):
+@pytest.mark.parametrize("dim,n,sm,batch", [(2, 127, 0, 2), (3, 31, 1, 2), (3, 127, 1, 9)])
+def test_mixed_vcycle_and_refinement(dim, n, sm, batch):
     """FP32 V-cycles: one cycle matches the FP64 oracle to FP32 accuracy; the full solve
     (FP64 residual, FP32 correction) refines to the FP64 solution."""
-    batch, c = 2, 0.02
+    c = 0.02
     rng = np.random.default_rng(11)
     b = rng.standard_normal((batch, n ** dim))
     g = pmg.pmg_grid(dim, n)
