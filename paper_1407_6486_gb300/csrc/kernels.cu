@@ -265,11 +265,17 @@ __global__ void sf_rhs_kernel(Grid g, SFCoef cf, const double *__restrict__ F, c
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
     double Fv[kMaxNodes];
-    for (int jn = 0; jn < cf.s; ++jn) Fv[jn] = F[b * sF + jn * g.slab + off];
+#pragma unroll
+    for (int jn = 0; jn < kMaxNodes; ++jn)
+      if (jn < cf.s) Fv[jn] = F[b * sF + jn * g.slab + off];
     double tprev = tau ? tau[b * stau + off] : 0.0;
-    for (int m = 0; m < cf.s - 1; ++m) {
+#pragma unroll
+    for (int m = 0; m < kMaxNodes - 1; ++m) {
+      if (m >= cf.s - 1) break;
       double acc = 0.0;
-      for (int jn = 0; jn < cf.s; ++jn) acc += cf.W[m][jn] * Fv[jn];
+#pragma unroll
+      for (int jn = 0; jn < kMaxNodes; ++jn)
+        if (jn < cf.s) acc += cf.W[m][jn] * Fv[jn];
       if (tau) {
         const double tnext = tau[b * stau + (m + 1) * g.slab + off];
         acc += tnext - tprev;
@@ -325,13 +331,17 @@ __global__ void interp_time_kernel(Grid gc, InterpCoef cf, const double *__restr
   PMG_FOR_POINTS(gc, batch) {
     PMG_POINT(gc);
     double d[kMaxNodes];
-    for (int jn = 0; jn < cf.sc; ++jn) {
+#pragma unroll
+    for (int jn = 0; jn < kMaxNodes; ++jn) {
+      if (jn >= cf.sc) break;
       const long long co = b * scoarse + jn * gc.slab + off;
       d[jn] = Uc[co] - Uc0[co];
     }
     for (int m = 0; m < cf.sf; ++m) {
       double acc = 0.0;
-      for (int jn = 0; jn < cf.sc; ++jn) acc += cf.T[m][jn] * d[jn];
+#pragma unroll
+      for (int jn = 0; jn < kMaxNodes; ++jn)
+        if (jn < cf.sc) acc += cf.T[m][jn] * d[jn];
       dU[((long long)b * cf.sf + m) * gc.slab + off] = (T)acc;
     }
   }
@@ -462,10 +472,11 @@ __global__ void colloc_residual_kernel(Grid g, ResCoef cf, const double *__restr
 //   collocation residual r_m = U_0 + P_m - U_m (Eq. resid), max-reduced per slice,
 //   q_m = P_{m+1} - P_m - U_{m+1}: u_m + q_m is the initial residual of sub-step m
 //   of the next sweep (Eq. SDCcompactLIII with initial guess u^k_{m+1}).
-template <int DIM>
-__global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, double nu, const double *__restrict__ U, long long stride,
+// cf.dtQ holds (nu / h^2) dt Q here (scaled by the launcher).  S = number of nodes,
+// a compile-time constant so that no predicated-off FP64 work is issued.
+template <int DIM, int S>
+__global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, const double *__restrict__ U, long long stride,
                                          double *__restrict__ q, long long sq, int batch, unsigned long long *res) {
-  const double a = nu * g.ih2;
   for (int zb = blockIdx.z; zb < g.nz * batch; zb += gridDim.z) {
     const int k = zb % g.nz, b = zb / g.nz;
     double mx = 0.0;
@@ -473,16 +484,20 @@ __global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, double nu, const do
       for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
         const long long off = ((long long)k * g.ny + j) * g.pitch + i;
         const double *Ub = U + b * stride;
-        double Uv[kMaxNodes], Fv[kMaxNodes];
-        for (int jn = 0; jn < cf.s; ++jn) {
+        // G_j = h^2 Lap_h U_j; the factor nu / h^2 is folded into the weights (aQ = a dtQ)
+        double Uv[S], Gv[S];
+#pragma unroll
+        for (int jn = 0; jn < S; ++jn) {
           const double *Uj = Ub + jn * g.slab;
           Uv[jn] = Uj[off];
-          Fv[jn] = a * (nbsum<DIM>(Uj, g, i, j, k, off) - 2.0 * DIM * Uv[jn]);
+          Gv[jn] = nbsum<DIM>(Uj, g, i, j, k, off) - 2.0 * DIM * Uv[jn];
         }
         double Pprev = 0.0;
-        for (int m = 1; m < cf.s; ++m) {
+#pragma unroll
+        for (int m = 1; m < S; ++m) {
           double P = 0.0;
-          for (int jn = 0; jn < cf.s; ++jn) P += cf.dtQ[m][jn] * Fv[jn];
+#pragma unroll
+          for (int jn = 0; jn < S; ++jn) P += cf.dtQ[m][jn] * Gv[jn];
           const double r = fabs(Uv[0] + P - Uv[m]);
           if (!(r <= mx)) mx = r;
           q[b * sq + (m - 1) * g.slab + off] = (P - Pprev) - Uv[m];
@@ -494,7 +509,7 @@ __global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, double nu, const do
 }
 
 // FAS restriction with the fine F evaluated from U_f at the coarse points only
-template <int DIM>
+template <int DIM, int SF, int SC>
 __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double *__restrict__ Uf, long long sfine,
                                       double *__restrict__ Uc, double *__restrict__ Fc, double *__restrict__ tau,
                                       double *__restrict__ Uc0, long long scoarse, int batch) {
@@ -504,12 +519,17 @@ __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double
     PMG_POINT(gc);
     const int fi = 2 * i + 1, fj = DIM >= 2 ? 2 * j + 1 : 0, fk = DIM >= 3 ? 2 * k + 1 : 0;
     const long long fo = ((long long)fk * gf.ny + fj) * gf.pitch + fi;
-    double Fcv[kMaxNodes], Ffv[kMaxNodes];
-    for (int in = 0; in < cf.sf; ++in) {
+    constexpr int NF = SF ? SF : kMaxNodes, NC = SC ? SC : kMaxNodes;  // 0: counts known at run time
+    double Fcv[NC], Ffv[NF];
+#pragma unroll
+    for (int in = 0; in < NF; ++in) {
+      if (SF == 0 && in >= cf.sf) break;
       const double *U = Uf + b * sfine + in * gf.slab;
       Ffv[in] = af * (nbsum<DIM>(U, gf, fi, fj, fk, fo) - 2.0 * DIM * U[fo]);
     }
-    for (int jn = 0; jn < cf.sc; ++jn) {
+#pragma unroll
+    for (int jn = 0; jn < NC; ++jn) {
+      if (SC == 0 && jn >= cf.sc) break;
       const double *U = Uf + b * sfine + cf.map[jn] * gf.slab;
       const double uc = U[fo];
       double s = (i > 0 ? U[fo - 2] : 0.0) + (i < gc.n - 1 ? U[fo + 2] : 0.0);
@@ -521,11 +541,17 @@ __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double
       Uc0[co] = uc;
       Fc[co] = Fcv[jn];
     }
-    for (int jn = 0; jn < cf.sc; ++jn) {
+#pragma unroll
+    for (int jn = 0; jn < NC; ++jn) {
+      if (SC == 0 && jn >= cf.sc) break;
       double If = 0.0;
-      for (int in = 0; in < cf.sf; ++in) If += cf.dtQf[jn][in] * Ffv[in];
+#pragma unroll
+      for (int in = 0; in < NF; ++in)
+        if (SF != 0 || in < cf.sf) If += cf.dtQf[jn][in] * Ffv[in];
       double Ic = 0.0;
-      for (int in = 0; in < cf.sc; ++in) Ic += cf.dtQc[jn][in] * Fcv[in];
+#pragma unroll
+      for (int in = 0; in < NC; ++in)
+        if (SC != 0 || in < cf.sc) Ic += cf.dtQc[jn][in] * Fcv[in];
       tau[b * scoarse + jn * gc.slab + off] = If - Ic;
     }
   }
@@ -771,7 +797,19 @@ cudaError_t k_fine_rhs_residual(const Launch &L, const Grid &g, const ResCoef &c
   dim3 gr, bl;
   config(g, batch, gr, bl);
   Scope sc(L, K_FINE_RHS, g, batch, 0);
-  PMG_DIM_SWITCH(g.dim, (fine_rhs_residual_kernel<D><<<gr, bl, 0, L.stream>>>(g, cf, nu, U, stride, q, sq, batch, res)))
+  ResCoef scaled = cf;
+  for (int m = 0; m < cf.s; ++m)
+    for (int jn = 0; jn < cf.s; ++jn) scaled.dtQ[m][jn] = nu * g.ih2 * cf.dtQ[m][jn];
+#define PMG_FRR(S_)                                                                                          \
+  case S_:                                                                                                   \
+    PMG_DIM_SWITCH(g.dim, (fine_rhs_residual_kernel<D, S_><<<gr, bl, 0, L.stream>>>(g, scaled, U, stride, q, sq, \
+                                                                                     batch, res)));          \
+    break;
+  switch (cf.s) {
+    PMG_FRR(2) PMG_FRR(3) PMG_FRR(4) PMG_FRR(5) PMG_FRR(6) PMG_FRR(7) PMG_FRR(8) PMG_FRR(9)
+    default: break;
+  }
+#undef PMG_FRR
   return sc.done();
 }
 
@@ -781,8 +819,17 @@ cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, co
   dim3 gr, bl;
   config(gc, batch, gr, bl);
   Scope sc(L, K_FAS, gc, batch, 0);
-  PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Fc, tau, Uc0,
-                                                                               scoarse, batch)))
+  // node counts as compile-time constants: coarse nodes are a subset of the fine ones
+#define PMG_FAS(SF_, SC_)                                                                                        \
+  if (cf.sf == SF_ && cf.sc == SC_) {                                                                            \
+    PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D, SF_, SC_><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Fc, \
+                                                                                         tau, Uc0, scoarse, batch))); \
+    return sc.done();                                                                                          \
+  }
+  PMG_FAS(5, 3) PMG_FAS(3, 2) PMG_FAS(5, 2) PMG_FAS(9, 3)
+#undef PMG_FAS
+  PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D, 0, 0><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Fc, tau,
+                                                                                    Uc0, scoarse, batch)))
   return sc.done();
 }
 

@@ -163,6 +163,175 @@ __global__ void __launch_bounds__(256, 4) rbgs_sweep3d_kernel(Grid g, T a, T D, 
   }
 }
 
+// Full-row variant for n + 1 = NX in {64, 128, 256}: a tile spans the whole padded
+// x row (the pad column is the zero wall), so no x ring is needed and no red point is
+// computed twice in x.  Threads own x-pairs (one red, one black point each) across
+// several rows; x neighbours come from the neighbouring lanes by warp shuffles.
+constexpr int FTY = 8;               // output rows per tile
+constexpr int FEY = FTY + 4;         // e_in rows (two-row ring)
+constexpr int FMY = FTY + 2;         // red / f rows (one-row ring)
+
+template <typename T, int NX, bool ZERO, bool UPD>
+__global__ void __launch_bounds__(256, 2) rbgs_rows3d_kernel(Grid g, T a, T iD, T omega, const T *__restrict__ ein,
+                                                             T *__restrict__ eout, const T *__restrict__ f,
+                                                             double *__restrict__ u, long long su, int nzc) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  constexpr int NP = NX / 2;                  // pairs per row
+  constexpr int RS = 256 / NP;                // rows covered per round of 256 threads
+  constexpr int PE = (FEY + RS - 1) / RS, PF = (FMY + RS - 1) / RS, PB = (FTY + RS - 1) / RS;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T2(*E)[FEY][NP] = (T2(*)[FEY][NP])sm_raw;                                         // [4][FEY][NP]
+  T2(*M)[FMY][NP] = (T2(*)[FMY][NP])(sm_raw + sizeof(T2) * 4 * FEY * NP);             // [3][FMY][NP]
+  T2(*Fs)[FMY][NP] = (T2(*)[FMY][NP])(sm_raw + sizeof(T2) * (4 * FEY + 3 * FMY) * NP);  // [3][FMY][NP]
+  const int n = g.n, tid = threadIdx.x, px = tid % NP, ry = tid / NP, lane = tid & 31;
+  const int y0 = blockIdx.y * FTY;
+  const int zc = blockIdx.z % nzc, b = blockIdx.z / nzc;
+  const int z0 = zc * RZC, z1 = min(z0 + RZC, n);
+  const long long plane = (long long)g.ny * g.pitch;
+  const T *Eb = ein + b * g.slab + 2 * px;
+  const T *Fb = f + b * g.slab + 2 * px;
+  const unsigned full = 0xffffffffu;
+
+  T2 pe[PE], pf[PF];
+  auto fetch = [&](const T *base, int k, int row0, int nrows, T2 *dst, int cnt) {
+#pragma unroll
+    for (int h = 0; h < cnt; ++h) {
+      const int r = ry + RS * h, y = row0 + r;
+      T2 v;
+      v.x = T(0);
+      v.y = T(0);
+      if (r < nrows && k >= 0 && k < n && y >= 0 && y < n) v = *(const T2 *)(base + k * plane + (long long)y * g.pitch);
+      dst[h] = v;
+    }
+  };
+  auto store = [&](T2(*S)[NP], int nrows, const T2 *src, int cnt) {
+#pragma unroll
+    for (int h = 0; h < cnt; ++h) {
+      const int r = ry + RS * h;
+      if (r < nrows) S[r][px] = src[h];
+    }
+  };
+  // x neighbours of the pair (c.x, c.y) in smem row `row`: left of c.x and right of
+  // c.y, from the neighbouring lanes, or from shared memory at a warp edge (a row may
+  // span several warps), or zero at the walls
+  auto xnb = [&](T2 c, const T2 *row, T &left, T &right) {
+    const T l = __shfl_up_sync(full, c.y, 1), r = __shfl_down_sync(full, c.x, 1);
+    left = lane != 0 ? l : (px > 0 ? row[px - 1].y : T(0));
+    right = lane != 31 ? r : (px < NP - 1 ? row[px + 1].x : T(0));
+  };
+
+  if (!ZERO) {
+    fetch(Eb, z0 - 2, y0 - 2, FEY, pe, PE);
+    store(E[(z0 + 2) & 3], FEY, pe, PE);
+    fetch(Eb, z0 - 1, y0 - 2, FEY, pe, PE);
+    store(E[(z0 + 3) & 3], FEY, pe, PE);
+    fetch(Eb, z0, y0 - 2, FEY, pe, PE);
+  }
+  fetch(Fb, z0 - 1, y0 - 1, FMY, pf, PF);
+  for (int k = z0 - 1; k <= z1; ++k) {
+    if (!ZERO) store(E[(k + 5) & 3], FEY, pe, PE);
+    store(Fs[(k + 3) % 3], FMY, pf, PF);
+    if (k < z1) {
+      if (!ZERO) fetch(Eb, k + 2, y0 - 2, FEY, pe, PE);
+      fetch(Fb, k + 1, y0 - 1, FMY, pf, PF);
+    }
+    __syncthreads();
+    {  // red half-sweep on plane k, rows y0-1 .. y0+FTY
+      const int se = (k + 4) & 3, sl = (k + 3) & 3, sh = (k + 5) & 3, s3 = (k + 3) % 3;
+      const bool kin = k >= 0 && k < n;
+#pragma unroll
+      for (int h = 0; h < PF; ++h) {
+        const int r = ry + RS * h;
+        if (r >= FMY) break;  // uniform per warp (a warp lies in one row)
+        const int y = y0 - 1 + r;
+        T2 out;
+        out.x = T(0);
+        out.y = T(0);
+        const bool yin = kin && y >= 0 && y < n;
+        if (ZERO) {
+          const T2 fv = Fs[s3][r][px];
+          const int ro = ((y + k) & 1) ? 0 : 1;   // red: x + y + k odd
+          const int xr = 2 * px + ro;
+          const T v = (yin && xr < n) ? omega * ((ro ? fv.y : fv.x) * iD) : T(0);
+          if (ro) out.y = v; else out.x = v;
+        } else {
+          const T2 c = E[se][r + 1][px];
+          T left, right;
+          xnb(c, E[se][r + 1], left, right);
+          if (yin) {
+            const T2 up = E[se][r][px], dn = E[se][r + 2][px], zl = E[sl][r + 1][px], zh = E[sh][r + 1][px];
+            const T2 fv = Fs[s3][r][px];
+            const int ro = ((y + k) & 1) ? 0 : 1;
+            out = c;
+            const int xr = 2 * px + ro;
+            if (xr < n) {
+              T nb, fr, old;
+              if (ro == 0) {
+                nb = left + c.y + up.x + dn.x + zl.x + zh.x;
+                fr = fv.x;
+                old = c.x;
+              } else {
+                nb = c.x + right + up.y + dn.y + zl.y + zh.y;
+                fr = fv.y;
+                old = c.y;
+              }
+              const T gs = (fr + a * nb) * iD;
+              const T v = omega == T(1) ? gs : old + omega * (gs - old);
+              if (ro) out.y = v; else out.x = v;
+            }
+          }
+        }
+        M[s3][r][px] = out;
+      }
+    }
+    __syncthreads();
+    const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+FTY-1
+    if (kb >= z0 && kb < z1) {
+      const int s0 = (kb + 3) % 3, sl = (kb + 2) % 3, sh = (kb + 4) % 3, se = (kb + 4) & 3;
+#pragma unroll
+      for (int h = 0; h < PB; ++h) {
+        const int r = ry + RS * h;
+        if (r >= FTY) break;
+        const int y = y0 + r;
+        const T2 c = M[s0][r + 1][px];
+        T left, right;
+        xnb(c, M[s0][r + 1], left, right);
+        if (y >= n) continue;
+        const T2 up = M[s0][r][px], dn = M[s0][r + 2][px], zl = M[sl][r + 1][px], zh = M[sh][r + 1][px];
+        const T2 fv = Fs[s0][r + 1][px];
+        const int bo = ((y + kb) & 1) ? 1 : 0;    // black: x + y + kb even
+        T2 out = c;
+        const int xb = 2 * px + bo;
+        if (xb < n) {
+          T nb, fr, old;
+          if (bo == 0) {
+            nb = left + c.y + up.x + dn.x + zl.x + zh.x;
+            fr = fv.x;
+            old = ZERO ? T(0) : E[se][r + 2][px].x;
+          } else {
+            nb = c.x + right + up.y + dn.y + zl.y + zh.y;
+            fr = fv.y;
+            old = ZERO ? T(0) : E[se][r + 2][px].y;
+          }
+          const T gs = (fr + a * nb) * iD;
+          const T v = omega == T(1) ? gs : old + omega * (gs - old);
+          if (bo) out.y = v; else out.x = v;
+        }
+        const long long o = kb * plane + (long long)y * g.pitch + 2 * px;
+        if (UPD) {
+          double2 *up2 = (double2 *)(u + b * su + o);
+          double2 w = *up2;
+          w.x += (double)out.x;
+          w.y += (double)out.y;
+          *up2 = w;
+        } else {
+          *(T2 *)(eout + b * g.slab + o) = out;
+        }
+      }
+    }
+  }
+}
+
 // residual + full weighting: coarse tile CTX x CTY, coarse z chunk CZC.  Fine smem
 // column c <-> x = 2*I0 - 2 + c; the residual is needed on x in [2I0, 2I0+64] (c 2..66),
 // e on x in [2I0-1, 2I0+65] (c 1..67); rows likewise with y.
@@ -326,10 +495,30 @@ __global__ void prolong3d_kernel(Grid gf, Grid gc, const T *__restrict__ ec, T *
   }
 }
 
+template <typename T, int NX, bool ZERO, bool UPD>
+void launch_rows(const Launch &L, const Grid &g, T a, T D, T omega, const void *ein, void *eout, const void *f,
+                 double *u, long long su, int batch) {
+  const T iD = T(1) / D;
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  const size_t smem = sizeof(T2) * (4 * FEY + 6 * FMY) * (NX / 2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(rbgs_rows3d_kernel<T, NX, ZERO, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int nty = (g.n + FTY - 1) / FTY, nzc = (g.n + RZC - 1) / RZC;
+  dim3 gr(1, nty, nzc * batch);
+  rbgs_rows3d_kernel<T, NX, ZERO, UPD><<<gr, 256, smem, L.stream>>>(g, a, iD, omega, (const T *)ein, (T *)eout,
+                                                                     (const T *)f, u, su, nzc);
+}
+
 template <typename T, bool ZERO, bool UPD>
 void launch_sweep(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout, const void *f,
                   double *u, long long su, int batch) {
   const T a = (T)(c * g.ih2), D = T(1) + T(6) * a;
+  if (g.pitch == 256) return launch_rows<T, 256, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch);
+  if (g.pitch == 128) return launch_rows<T, 128, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch);
+  if (g.pitch == 64) return launch_rows<T, 64, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch);
   const int ntx = (g.n + RTX - 1) / RTX, nty = (g.n + RTY - 1) / RTY, nzc = (g.n + RZC - 1) / RZC;
   const size_t smem = sizeof(T) * (4 * EY + 6 * MY) * SX;
   static bool attr = false;

@@ -45,8 +45,8 @@ def omega(sm):
 @pytest.mark.parametrize("dim,n,sm,vc,batch", [
     (1, 3, 0, 1, 3), (1, 63, 0, 2, 3), (1, 1023, 1, 2, 3), (2, 31, 0, 1, 3), (2, 255, 1, 2, 3), (2, 127, 0, 3, 3),
     (3, 7, 1, 1, 3), (3, 15, 0, 2, 3), (3, 31, 1, 2, 3), (3, 63, 0, 1, 3), (3, 63, 1, 2, 3), (3, 127, 1, 1, 3),
-    # 127^3 x 9 grids: large enough for the tiled z-marching kernels (partial tiles in x, y and z)
-    (3, 127, 1, 2, 9),
+    # large enough batches for the tiled z-marching kernels (partial tiles in y and z)
+    (3, 127, 1, 2, 9), (3, 63, 1, 2, 70),
 ])
 def test_vcycles_fp64_match_oracle(dim, n, sm, vc, batch):
     c = 0.37 / (n + 1) ** 2 * 4
