@@ -79,12 +79,15 @@ typedef struct {
     int    precision;     /* PMG_PREC_*                                              */
     int    interp_order;  /* spatial interpolation between PFASST levels: 2 or 4    */
     int    use_graphs;    /* 1: replay each PFASST iteration as a captured CUDA graph */
+    int    autotune;      /* 1: at creation, time the smoother variants of every multigrid
+                             level (threads per block; fused 3D sweep z chunk) and keep
+                             the fastest; 0: built-in size rules                          */
 } pmg_options;
 
 typedef struct pmg_ctx *pmg_handle;
 
 /* Defaults: Jacobi omega 2/3, V(2,1), 2 V-cycles, tol 1e-12, stall 0.75, cap 50,
- * FP64, 4th-order interpolation, graphs on. */
+ * FP64, 4th-order interpolation, graphs on, autotuning on. */
 void pfasst_mg_default_options(pmg_options *opt);
 
 /* Bytes of device workspace pfasst_mg_create needs for this problem.
@@ -179,6 +182,40 @@ int pfasst_mg_destroy(pmg_handle h);
 
 /* Message of the last error on h (or of the last failed create when h is NULL). */
 const char *pfasst_mg_last_error(pmg_handle h);
+
+/* ---- uneven batch of independent problems ------------------------------------ */
+
+/* One problem of an uneven batch: its own grid, Gauss-Lobatto node count, nu and dt. */
+typedef struct {
+    pmg_grid grid;
+    int      nodes;
+    double   nu, dt;
+} pmg_problem_desc;
+
+/* Bytes of workspace pfasst_mg_create_batch needs.  Errors as pfasst_mg_create;
+ * PMG_ERR_UNSUPPORTED if opt->vcycles == 0 (batches run fixed V-cycle counts). */
+int pfasst_mg_batch_workspace_bytes(int nprob, const pmg_problem_desc *probs, const pmg_options *opt,
+                                    size_t *bytes);
+
+/* Create a solver for nprob independent heat problems of different sizes, each
+ * integrated by single-level SDC (Sec. 2.2) with multigrid sub-step solves, one time
+ * step of length dt at a time.  All problems advance together: pfasst_mg_batch_run
+ * replays one CUDA graph per time step in which every problem is an independent
+ * branch.  Arguments and ownership as pfasst_mg_create; probs is copied. */
+int pfasst_mg_create_batch(int nprob, const pmg_problem_desc *probs, const pmg_options *opt, void *stream,
+                           void *workspace, size_t workspace_bytes, pmg_handle *out);
+
+/* Initial value of problem `prob` (its own n^d doubles, dense layout). */
+int pfasst_mg_batch_set_initial(pmg_handle h, int prob, const double *u0, int on_device);
+
+/* Advance every problem by `steps` time steps of `sweeps` SDC sweeps each
+ * (Eq. sdc-be with V-cycle sub-step solves); residuals (host, nprob doubles, may be
+ * NULL) receives each problem's collocation residual (Eq. resid) after its last sweep.
+ * Synchronises the stream. */
+int pfasst_mg_batch_run(pmg_handle h, int steps, int sweeps, double *residuals);
+
+/* Current value of problem `prob` (after batch_run: the end of its last time step). */
+int pfasst_mg_batch_get_solution(pmg_handle h, int prob, double *out, int on_device);
 
 /* ---- standalone multigrid solve ------------------------------------------ */
 

@@ -34,7 +34,8 @@ EXPORTS = [
     "pfasst_mg_residual", "pfasst_mg_get_solution", "pfasst_mg_get_state", "pfasst_mg_advance",
     "pfasst_mg_launch_count", "pfasst_mg_destroy", "pfasst_mg_last_error",
     "pfasst_mg_helmholtz_solve", "pfasst_mg_profile", "pfasst_mg_profile_read", "pfasst_mg_kernel_name",
-    "pfasst_mg_helmholtz_solve_noalloc",
+    "pfasst_mg_helmholtz_solve_noalloc", "pfasst_mg_batch_workspace_bytes", "pfasst_mg_create_batch",
+    "pfasst_mg_batch_set_initial", "pfasst_mg_batch_run", "pfasst_mg_batch_get_solution",
 ]
 
 
@@ -55,7 +56,11 @@ class pmg_options(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("vcycles", ctypes.c_int), ("mg_tol", ctypes.c_double),
                 ("mg_stall", ctypes.c_double), ("mg_maxcycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("interp_order", ctypes.c_int),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class pmg_problem_desc(ctypes.Structure):
+    _fields_ = [("grid", pmg_grid), ("nodes", ctypes.c_int), ("nu", ctypes.c_double), ("dt", ctypes.c_double)]
 
 
 class pmg_kernel_stat(ctypes.Structure):
@@ -109,6 +114,13 @@ def load() -> ctypes.CDLL:
                                             ctypes.POINTER(pmg_options), _P, ctypes.POINTER(_I)]
     L.pfasst_mg_helmholtz_solve_noalloc.argtypes = [ctypes.POINTER(pmg_grid), _D, _I, _P, _P,
                                                     ctypes.POINTER(pmg_options), _P, ctypes.POINTER(_I)]
+    L.pfasst_mg_batch_workspace_bytes.argtypes = [_I, ctypes.POINTER(pmg_problem_desc), ctypes.POINTER(pmg_options),
+                                                  ctypes.POINTER(ctypes.c_size_t)]
+    L.pfasst_mg_create_batch.argtypes = [_I, ctypes.POINTER(pmg_problem_desc), ctypes.POINTER(pmg_options), _P, _P,
+                                         ctypes.c_size_t, ctypes.POINTER(_P)]
+    L.pfasst_mg_batch_set_initial.argtypes = [_P, _I, _P, _I]
+    L.pfasst_mg_batch_run.argtypes = [_P, _I, _I, _P]
+    L.pfasst_mg_batch_get_solution.argtypes = [_P, _I, _P, _I]
     L.pfasst_mg_profile.argtypes = [_P, _I, ctypes.c_longlong]
     L.pfasst_mg_profile_read.argtypes = [_P, ctypes.POINTER(pmg_kernel_stat), _I, ctypes.POINTER(_I)]
     L.pfasst_mg_kernel_name.argtypes = [_I]
@@ -273,6 +285,86 @@ def pfasst_mg_profile_read(h):
 
 def pfasst_mg_kernel_name(k) -> str:
     return load().pfasst_mg_kernel_name(k).decode()
+
+
+def pfasst_mg_batch_workspace_bytes(probs, opt) -> int:
+    arr = (pmg_problem_desc * len(probs))(*probs)
+    nb = ctypes.c_size_t(0)
+    _check(load().pfasst_mg_batch_workspace_bytes(len(probs), arr, ctypes.byref(opt), ctypes.byref(nb)))
+    return nb.value
+
+
+def pfasst_mg_create_batch(probs, opt, stream=None, workspace=None):
+    """Returns (handle, workspace tensor) for a list of pmg_problem_desc."""
+    import torch
+    arr = (pmg_problem_desc * len(probs))(*probs)
+    nbytes = pfasst_mg_batch_workspace_bytes(probs, opt)
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p()
+    _check(load().pfasst_mg_create_batch(len(probs), arr, ctypes.byref(opt), _stream_ptr(stream),
+                                         ctypes.c_void_p(workspace.data_ptr()), nbytes, ctypes.byref(h)))
+    return h, workspace
+
+
+def pfasst_mg_batch_set_initial(h, prob, u0):
+    import numpy as np
+    if hasattr(u0, "is_cuda"):
+        _check(load().pfasst_mg_batch_set_initial(h, prob, _dev_ptr(u0), 1), h)
+    else:
+        a = np.ascontiguousarray(u0, dtype=np.float64)
+        _check(load().pfasst_mg_batch_set_initial(h, prob, a.ctypes.data_as(ctypes.c_void_p), 0), h)
+
+
+def pfasst_mg_batch_run(h, steps, sweeps, nprob):
+    import numpy as np
+    res = np.zeros(nprob)
+    _check(load().pfasst_mg_batch_run(h, steps, sweeps, res.ctypes.data_as(ctypes.c_void_p)), h)
+    return res
+
+
+def pfasst_mg_batch_get_solution(h, prob, out):
+    if hasattr(out, "is_cuda"):
+        _check(load().pfasst_mg_batch_get_solution(h, prob, _dev_ptr(out), 1), h)
+    else:
+        _check(load().pfasst_mg_batch_get_solution(h, prob, out.ctypes.data_as(ctypes.c_void_p), 0), h)
+    return out
+
+
+class BatchSolver:
+    """Owns an uneven-batch handle (independent single-level SDC problems)."""
+
+    def __init__(self, problems, stream=None, **opts):
+        """problems: list of (dim, n, nodes, nu, dt)."""
+        self.problems = list(problems)
+        self.opt = pfasst_mg_default_options(**opts)
+        descs = [pmg_problem_desc(pmg_grid(d, n), m, nu, dt) for (d, n, m, nu, dt) in self.problems]
+        self.h, self.workspace = pfasst_mg_create_batch(descs, self.opt, stream)
+
+    def set_initial(self, prob, u0):
+        pfasst_mg_batch_set_initial(self.h, prob, u0)
+
+    def run(self, steps, sweeps):
+        return pfasst_mg_batch_run(self.h, steps, sweeps, len(self.problems))
+
+    def solution(self, prob):
+        import numpy as np
+        d, n = self.problems[prob][0], self.problems[prob][1]
+        return pfasst_mg_batch_get_solution(self.h, prob, np.zeros(n ** d))
+
+    def launches(self):
+        return pfasst_mg_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            pfasst_mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience handle

@@ -134,12 +134,22 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ----------------------------------------------------------------- hierarchy
 
+// Smoother choice of one level: the fused red-black z-marching sweep (param = z chunk,
+// 0 = default) or the one-point-per-thread kernels (param = threads per block).
+struct Tune {
+  int fused = 0;
+  int param = 256;
+};
+
 struct Hier {
   int L = 0;
   Grid lev[kMaxLevels];
   void *e[kMaxLevels] = {}, *e2[kMaxLevels] = {}, *f[kMaxLevels] = {};
   Prec pr = F64;
   size_t tsize = 8;
+  int batch = 1;                  // grids per level the buffers hold
+  Tune tune[kMaxLevels][2];       // [level][0: wide batches, 1: narrow (a single grid)]
+  const Tune &tune_for(int l, int B) const { return tune[l][2 * B >= batch ? 0 : 1]; }
 };
 
 int mg_levels(int n) {
@@ -201,6 +211,14 @@ struct pmg_ctx {
     std::vector<ProfRec> recs;
   } g_pred, g_iter;
   cudaStream_t cap_stream = nullptr;
+  // uneven batch: one single-level solver per problem, run as branches of one graph
+  std::vector<pmg_ctx *> kids;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t bexec = nullptr;
+  int bsweeps = -1;
+  long long bkernels = 0;
   std::string err;
 
   Launch L() { return Launch{stream, &launches, &prof}; }
@@ -253,19 +271,31 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
   return PMG_OK;
 }
 
+// the z-marching tiled kernels pay off on large batched 3D grids; small or batch-1
+// grids (coarse levels, the serial coarse chain) keep the one-thread-per-point kernels
+bool tiled3d(const Grid &g, int B) {
+  return g.dim == 3 && g.n >= kTiled3dMinN && (long long)g.n * g.n * g.n * B >= (1LL << 24);
+}
+
 // multigrid hierarchy for `batch` grids of size n (levels n, (n-1)/2, ..., 3)
 void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smoother) {
   H.L = mg_levels(n);
   H.pr = pr;
   H.tsize = pr == F64 ? 8 : 4;
+  H.batch = batch;
   int nl = n;
   for (int l = 0; l < H.L; ++l) {
     H.lev[l] = make_grid(dim, nl);
+    for (int cls = 0; cls < 2; ++cls) {  // default choice; the autotuner may replace it
+      Tune &t = H.tune[l][cls];
+      t.fused = smoother == PMG_SMOOTHER_RBGS && tiled3d(H.lev[l], cls == 0 ? batch : 1);
+      t.param = t.fused ? 0 : 256;
+    }
     size_t bytes = (size_t)H.lev[l].slab * batch * H.tsize;
     pl.add(&H.e[l], bytes);
     pl.add(&H.f[l], bytes);
-    // second correction buffer: Jacobi ping-pong, or the out-of-place tiled 3D sweep
-    if (smoother == PMG_SMOOTHER_JACOBI || (dim == 3 && nl >= kTiled3dMinN)) pl.add(&H.e2[l], bytes);
+    // second correction buffer: Jacobi ping-pong, or the out-of-place fused 3D sweep
+    if (smoother == PMG_SMOOTHER_JACOBI || dim == 3) pl.add(&H.e2[l], bytes);
     nl = (nl - 1) / 2;
   }
 }
@@ -307,31 +337,31 @@ struct MGCtx {
   cudaStream_t stream;
 };
 
-// the z-marching tiled kernels pay off on large batched 3D grids; small or batch-1
-// grids (coarse levels, the serial coarse chain) keep the one-thread-per-point kernels
-bool tiled3d(const Grid &g, int B) {
-  return g.dim == 3 && g.n >= kTiled3dMinN && (long long)g.n * g.n * g.n * B >= (1LL << 24);
-}
-
-// one smoothing sweep on level l; with the tiled 3D red-black kernel and a non-null
-// u_upd the sweep's result is added to u_upd (stride su) instead of being stored
-int smooth(MGCtx &M, int l, int B, double c, void *&cur, bool first, double *u_upd = nullptr, long long su = 0) {
+// one smoothing sweep on level l with the smoother variant t; with the fused 3D
+// red-black kernel and a non-null u_upd the sweep's result is added to u_upd (stride
+// su) instead of being stored
+int smooth_with(MGCtx &M, const Tune &t, int l, int B, double c, void *&cur, bool first, double *u_upd = nullptr,
+                long long su = 0) {
   Hier &H = *M.H;
   const pmg_options &o = *M.o;
   if (o.smoother == PMG_SMOOTHER_JACOBI) {
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
-    PMG_CUDA(M.h, k_smooth_jacobi(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], B, first));
+    PMG_CUDA(M.h, k_smooth_jacobi(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], B, first, t.param));
     cur = out;
-  } else if (tiled3d(H.lev[l], B)) {
+  } else if (t.fused) {
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
     PMG_CUDA(M.h, k_rbgs_sweep3d(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], u_upd, su, B, first,
-                                 u_upd != nullptr));
+                                 u_upd != nullptr, t.param));
     cur = out;
   } else {
-    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 0, first));
-    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 1, false));
+    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 0, first, t.param));
+    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 1, false, t.param));
   }
   return PMG_OK;
+}
+
+int smooth(MGCtx &M, int l, int B, double c, void *&cur, bool first, double *u_upd = nullptr, long long su = 0) {
+  return smooth_with(M, M.H->tune_for(l, B), l, B, c, cur, first, u_upd, su);
 }
 
 // one V(nu1,nu2)-cycle for (I - c Lap) e = f[l0] on levels l0..L-1, starting from
@@ -364,7 +394,7 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, vo
       PMG_CUDA(M.h, k_prolong_add(M.L, H.lev[l], H.lev[l + 1], H.pr, cur[l + 1], cur[l], B));
     for (int s = 0; s < o.nu2; ++s) {
       const bool last = l == l0 && s == o.nu2 - 1;
-      const bool fuse = last && u_upd && o.smoother == PMG_SMOOTHER_RBGS && tiled3d(H.lev[l], B);
+      const bool fuse = last && u_upd && o.smoother == PMG_SMOOTHER_RBGS && H.tune_for(l, B).fused;
       PMG_RET(smooth(M, l, B, c, cur[l], false, fuse ? u_upd : nullptr, su));
       if (fuse && fused) *fused = true;
     }
@@ -450,6 +480,61 @@ int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const dou
 MGCtx mgctx(pmg_ctx *h) {
   MGCtx M{h->L(), &h->H, &h->opt, h->red, h->active, h->hred, h->hactive, h, h->stream};
   return M;
+}
+
+// ----------------------------------------------------------------- autotuner
+//
+// For every multigrid level (except the exact coarsest one) and both batch classes,
+// time the candidate smoother variants -- one-point-per-thread kernels with 128, 256
+// or 512 threads per block, and for 3D red-black Gauss-Seidel the fused z-marching
+// sweep with z chunks of 8, 16 or 32 planes -- on the level's own buffers and keep the
+// fastest.  Runs once at creation (it synchronises the stream).
+int autotune(MGCtx &M, int l0, int Bwide, double c) {
+  Hier &H = *M.H;
+  cudaEvent_t e0, e1;
+  PMG_CUDA(M.h, cudaEventCreate(&e0));
+  PMG_CUDA(M.h, cudaEventCreate(&e1));
+  int rc = PMG_OK;
+  for (int l = l0; l < H.L - 1 && rc == PMG_OK; ++l)
+    for (int cls = 0; cls < 2 && rc == PMG_OK; ++cls) {
+      const int B = cls == 0 ? Bwide : 1;
+      if (cls == 1 && Bwide == 1) { H.tune[l][1] = H.tune[l][0]; continue; }
+      std::vector<Tune> cand;
+      for (int th : {128, 256, 512}) cand.push_back(Tune{0, th});
+      const Grid &g = H.lev[l];
+      if (M.o->smoother == PMG_SMOOTHER_RBGS && g.dim == 3 && g.n >= 15)
+        for (int zc : {8, 16, 32})
+          if (zc <= g.n) cand.push_back(Tune{1, zc});
+      float best = 1e30f;
+      Tune pick = H.tune[l][cls];
+      for (const Tune &t : cand) {
+        void *cur = H.e[l];
+        float ms = 0.f;
+        for (int rep = 0; rep < 4 && rc == PMG_OK; ++rep) {
+          if (rep == 1 && cudaEventRecord(e0, M.stream) != cudaSuccess) rc = PMG_ERR_CUDA;
+          if (rc == PMG_OK) rc = smooth_with(M, t, l, B, c, cur, rep == 0);
+        }
+        if (rc != PMG_OK) break;
+        if (cudaEventRecord(e1, M.stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = fail(M.h, PMG_ERR_CUDA, "autotune timing failed");
+          break;
+        }
+        if (ms < best) { best = ms; pick = t; }
+      }
+      H.tune[l][cls] = pick;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the timing sweeps left arbitrary values in the correction buffers; they are always
+  // re-initialised before use, but clear them so the state is reproducible
+  for (int l = l0; l < H.L && rc == PMG_OK; ++l) {
+    const size_t bytes = (size_t)H.lev[l].slab * H.batch * H.tsize;
+    if (cudaMemsetAsync(H.e[l], 0, bytes, M.stream) != cudaSuccess ||
+        (H.e2[l] && cudaMemsetAsync(H.e2[l], 0, bytes, M.stream) != cudaSuccess))
+      rc = fail(M.h, PMG_ERR_CUDA, "autotune clear failed");
+  }
+  return rc;
 }
 
 // ----------------------------------------------------------------- SDC / PFASST schedule
@@ -631,10 +716,12 @@ double bits_to_double(unsigned long long v) {
 }
 
 int spread(pmg_ctx *h) {
-  // F = A u0 once, then copy u0 and F to every node of every slice
-  PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->u0, 0, h->dense, 0, 1));
+  // copy u0 to every node of every slice; with a stored F, also F = A u0 everywhere
+  if (!ffree(h)) {
+    PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->u0, 0, h->dense, 0, 1));
+    PMG_CUDA(h, k_copy(h->L(), h->gf, h->dense, 0, h->Ff, h->gf.slab, h->P * h->sf));
+  }
   PMG_CUDA(h, k_copy(h->L(), h->gf, h->u0, 0, h->Uf, h->gf.slab, h->P * h->sf));
-  PMG_CUDA(h, k_copy(h->L(), h->gf, h->dense, 0, h->Ff, h->gf.slab, h->P * h->sf));
   h->predicted = false;
   h->q_valid = false;
   return PMG_OK;
@@ -743,6 +830,7 @@ void pfasst_mg_default_options(pmg_options *o) {
   o->precision = PMG_PREC_FP64;
   o->interp_order = 4;
   o->use_graphs = 1;
+  o->autotune = 1;
 }
 
 int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,
@@ -812,11 +900,16 @@ int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_l
   cudaError_t e = cudaMemsetAsync(h->ws, 0, pl.total, h->stream);
   if (e != cudaSuccess) return bail(PMG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   if (upload_minv(h) != PMG_OK) return bail(PMG_ERR_CUDA, h->err);
+  if (h->opt.autotune) {
+    MGCtx M = mgctx(h);
+    if (autotune(M, 0, h->P, h->cf_sub[0]) != PMG_OK) return bail(PMG_ERR_CUDA, h->err);
+  }
   *out = h;
   return PMG_OK;
 }
 
 int pfasst_mg_set_initial(pmg_handle h, const double *u0, int on_device) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h || !u0) return fail(h, PMG_ERR_INVALID_ARG, "null argument");
   const size_t N = (size_t)h->gf.nz * h->gf.ny * h->gf.n;
   const double *src = u0;
@@ -831,11 +924,13 @@ int pfasst_mg_set_initial(pmg_handle h, const double *u0, int on_device) {
 }
 
 int pfasst_mg_predict(pmg_handle h) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
   return predict(h);
 }
 
 int pfasst_mg_sweep(pmg_handle h, int level) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
   if (level == 0) {
     if (ffree(h) && !h->q_valid) PMG_RET(fine_residual(h));
@@ -853,6 +948,7 @@ int pfasst_mg_sweep(pmg_handle h, int level) {
 }
 
 int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, double *final_res) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h || max_iter < 0) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
   if (iters_done) *iters_done = 0;
   if (!h->predicted) PMG_RET(predict(h));
@@ -878,6 +974,7 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
 }
 
 int pfasst_mg_residual(pmg_handle h, double *res) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h || !res) return fail(h, PMG_ERR_INVALID_ARG, "null argument");
   PMG_RET(fine_residual(h));
   h->q_valid = ffree(h);
@@ -887,6 +984,7 @@ int pfasst_mg_residual(pmg_handle h, double *res) {
 }
 
 int pfasst_mg_get_solution(pmg_handle h, int slice, int node, double *out, int on_device) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h || !out || slice < 0 || slice >= h->P || node < 0 || node >= h->sf)
     return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
   const size_t N = (size_t)h->gf.nz * h->gf.ny * h->gf.n;
@@ -899,6 +997,7 @@ int pfasst_mg_get_solution(pmg_handle h, int slice, int node, double *out, int o
 }
 
 int pfasst_mg_get_state(pmg_handle h, int level, double *out) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h || !out || level < 0 || level > 1 || (level == 1 && h->nlevels < 2))
     return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
   const Grid &g = level ? h->gc : h->gf;
@@ -915,6 +1014,7 @@ int pfasst_mg_get_state(pmg_handle h, int level, double *out) {
 }
 
 int pfasst_mg_advance(pmg_handle h) {
+  if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
   const long long last = ((long long)(h->P - 1) * h->sf + (h->sf - 1)) * h->gf.slab;
   PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + last, 0, h->u0, 0, 1));
@@ -969,6 +1069,17 @@ const char *pfasst_mg_kernel_name(int kernel) {
 int pfasst_mg_destroy(pmg_handle h) {
   if (!h) return PMG_OK;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  for (pmg_ctx *k : h->kids) {
+    drop_graph(k->g_pred);
+    drop_graph(k->g_iter);
+    if (k->hred) cudaFreeHost(k->hred);
+    if (k->hactive) cudaFreeHost(k->hactive);
+    delete k;
+  }
+  for (cudaStream_t b : h->branch) cudaStreamDestroy(b);
+  for (cudaEvent_t e : h->join) cudaEventDestroy(e);
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->bexec) cudaGraphExecDestroy(h->bexec);
   drop_graph(h->g_pred);
   drop_graph(h->g_iter);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1053,6 +1164,240 @@ int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const d
   if (hactive) cudaFreeHost(hactive);
   if (result == PMG_OK && e != cudaSuccess) result = fail(nullptr, PMG_ERR_CUDA, cudaGetErrorString(e));
   return result;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- uneven batch
+//
+// Independent heat problems of different grids, node counts, nu and dt: each is a
+// single-level SDC solver (one time slice) with its own multigrid hierarchy carved
+// from one workspace.  A time step of every problem -- right-hand sides, `sweeps` SDC
+// sweeps, residual, advance to the step's end value -- is captured once into a CUDA
+// graph in which every problem is its own branch, so the small problems fill the GPU
+// side by side; the graph is replayed once per time step.
+
+namespace {
+
+int validate_problem(const pmg_problem_desc &d, const pmg_options *o, std::string &why) {
+  pmg_nodes_desc fn{d.nodes, 0};
+  pmg_levels lv{1, {0, 0}};
+  int rc = validate(&d.grid, &fn, &lv, 1, o, why);
+  if (rc != PMG_OK) return rc;
+  if (!(d.nu > 0) || !(d.dt > 0) || !std::isfinite(d.nu) || !std::isfinite(d.dt)) {
+    why = "nu and dt must be positive and finite";
+    return PMG_ERR_INVALID_ARG;
+  }
+  return PMG_OK;
+}
+
+pmg_ctx *make_kid(const pmg_problem_desc &d, const pmg_options &o) {
+  pmg_nodes_desc fn{d.nodes, 0};
+  pmg_levels lv{1, {0, 0}};
+  return make_ctx(&d.grid, &fn, &lv, d.nu, d.dt, 1, &o);
+}
+
+// one time step of one problem (captured into the batch graph)
+int batch_step_body(pmg_ctx *k, int sweeps) {
+  PMG_RET(fine_residual(k));
+  for (int i = 0; i < sweeps; ++i) PMG_RET(iteration(k));
+  const long long last = (long long)(k->sf - 1) * k->gf.slab;
+  PMG_CUDA(k, k_copy(k->L(), k->gf, k->Uf + last, 0, k->u0, 0, 1));
+  return spread(k);
+}
+
+bool is_batch(const pmg_ctx *h) { return h && !h->kids.empty(); }
+
+}  // namespace
+
+extern "C" {
+
+int pfasst_mg_batch_workspace_bytes(int nprob, const pmg_problem_desc *probs, const pmg_options *opt,
+                                    size_t *bytes) {
+  if (nprob < 1 || nprob > 4096 || !probs || !bytes) return fail(nullptr, PMG_ERR_INVALID_ARG, "bad argument");
+  pmg_options o;
+  if (opt) o = *opt; else pfasst_mg_default_options(&o);
+  if (o.vcycles < 1) return fail(nullptr, PMG_ERR_UNSUPPORTED, "batches run a fixed number of V-cycles (vcycles >= 1)");
+  size_t total = 0;
+  for (int i = 0; i < nprob; ++i) {
+    std::string why;
+    int rc = validate_problem(probs[i], &o, why);
+    if (rc != PMG_OK) return fail(nullptr, rc, "problem " + std::to_string(i) + ": " + why);
+    pmg_ctx *k = make_kid(probs[i], o);
+    if (!k) return fail(nullptr, PMG_ERR_OOM, "host allocation failed");
+    Plan pl;
+    plan_ctx(pl, k);
+    total += pl.total;
+    delete k;
+  }
+  *bytes = total;
+  return PMG_OK;
+}
+
+int pfasst_mg_create_batch(int nprob, const pmg_problem_desc *probs, const pmg_options *opt, void *stream,
+                           void *workspace, size_t workspace_bytes, pmg_handle *out) {
+  if (!out) return fail(nullptr, PMG_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = pfasst_mg_batch_workspace_bytes(nprob, probs, opt, &need);
+  if (rc != PMG_OK) return rc;
+  pmg_options o;
+  if (opt) o = *opt; else pfasst_mg_default_options(&o);
+  pmg_ctx *h = new (std::nothrow) pmg_ctx();
+  if (!h) return fail(nullptr, PMG_ERR_OOM, "host allocation failed");
+  h->opt = o;
+  h->stream = (cudaStream_t)stream;
+  if (workspace) {
+    if (workspace_bytes < need || ((uintptr_t)workspace & 255)) {
+      delete h;
+      return fail(nullptr, PMG_ERR_OOM, "workspace too small or not 256-byte aligned");
+    }
+    h->ws = workspace;
+  } else {
+    cudaError_t e = cudaMalloc(&h->ws, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return fail(nullptr, PMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->ws_owned = true;
+  }
+  std::string why;
+  char *base = (char *)h->ws;
+  rc = PMG_OK;
+  for (int i = 0; i < nprob && rc == PMG_OK; ++i) {
+    pmg_ctx *k = make_kid(probs[i], o);
+    if (!k) { rc = PMG_ERR_OOM; why = "host allocation failed"; break; }
+    h->kids.push_back(k);
+    k->stream = h->stream;
+    fill_coefficients(k);
+    Plan pl;
+    plan_ctx(pl, k);
+    pl.carve(base);
+    base += pl.total;
+    if (cudaMallocHost(&k->hred, sizeof(unsigned long long) * 3) != cudaSuccess ||
+        cudaMallocHost(&k->hactive, sizeof(int)) != cudaSuccess) {
+      rc = PMG_ERR_OOM;
+      why = "pinned host allocation failed";
+      break;
+    }
+    if (cudaMemsetAsync(k->ws ? k->ws : (void *)(base - pl.total), 0, pl.total, h->stream) != cudaSuccess ||
+        upload_minv(k) != PMG_OK) {
+      rc = PMG_ERR_CUDA;
+      why = "set-up of problem " + std::to_string(i) + " failed";
+      break;
+    }
+    if (o.autotune) {
+      MGCtx M = mgctx(k);
+      if (autotune(M, 0, 1, k->cf_sub[0]) != PMG_OK) { rc = PMG_ERR_CUDA; why = k->err; break; }
+    }
+  }
+  if (rc == PMG_OK) {
+    const int nb = nprob < 32 ? nprob : 32;
+    h->branch.resize(nb, nullptr);
+    h->join.resize(nb, nullptr);
+    for (int b = 0; b < nb && rc == PMG_OK; ++b)
+      if (cudaStreamCreateWithFlags(&h->branch[b], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->join[b], cudaEventDisableTiming) != cudaSuccess) {
+        rc = PMG_ERR_CUDA;
+        why = "stream creation failed";
+      }
+    if (rc == PMG_OK && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
+      rc = PMG_ERR_CUDA;
+      why = "event creation failed";
+    }
+  }
+  if (rc != PMG_OK) {
+    std::string msg = why;
+    pfasst_mg_destroy(h);
+    return fail(nullptr, rc, msg);
+  }
+  *out = h;
+  return PMG_OK;
+}
+
+int pfasst_mg_batch_set_initial(pmg_handle h, int prob, const double *u0, int on_device) {
+  if (!is_batch(h) || prob < 0 || prob >= (int)h->kids.size()) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  int rc = pfasst_mg_set_initial(h->kids[prob], u0, on_device);
+  if (rc != PMG_OK) return fail(h, rc, h->kids[prob]->err);
+  return PMG_OK;
+}
+
+int pfasst_mg_batch_run(pmg_handle h, int steps, int sweeps, double *residuals) {
+  if (!is_batch(h) || steps < 0 || sweeps < 1) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  const int np = (int)h->kids.size(), nb = (int)h->branch.size();
+  if (!h->opt.use_graphs) {  // eager: the problems one after the other on the handle's stream
+    for (int st = 0; st < steps; ++st)
+      for (pmg_ctx *k : h->kids) {
+        const long long before = k->launches;
+        int rc = batch_step_body(k, sweeps);
+        h->launches += k->launches - before;
+        if (rc != PMG_OK) return fail(h, rc, k->err);
+      }
+  } else {
+    if (h->bexec && h->bsweeps != sweeps) {
+      cudaGraphExecDestroy(h->bexec);
+      h->bexec = nullptr;
+    }
+    if (!h->bexec) {
+      if (!h->cap_stream) PMG_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      PMG_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int rc = cudaEventRecord(h->fork, h->cap_stream) == cudaSuccess ? PMG_OK : PMG_ERR_CUDA;
+      for (int b = 0; b < nb && rc == PMG_OK; ++b)
+        if (cudaStreamWaitEvent(h->branch[b], h->fork, 0) != cudaSuccess) rc = PMG_ERR_CUDA;
+      long long kernels = 0;
+      std::string why;
+      for (int i = 0; i < np && rc == PMG_OK; ++i) {
+        pmg_ctx *k = h->kids[i];
+        const long long before = k->launches;
+        k->stream = h->branch[i % nb];
+        rc = batch_step_body(k, sweeps);
+        k->stream = h->stream;
+        kernels += k->launches - before;
+        k->launches = before;
+        if (rc != PMG_OK) why = k->err;
+      }
+      for (int b = 0; b < nb && rc == PMG_OK; ++b)
+        if (cudaEventRecord(h->join[b], h->branch[b]) != cudaSuccess ||
+            cudaStreamWaitEvent(h->cap_stream, h->join[b], 0) != cudaSuccess)
+          rc = PMG_ERR_CUDA;
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (rc != PMG_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(h, rc != PMG_OK ? rc : PMG_ERR_CUDA,
+                    "batch capture failed: " + (why.empty() ? std::string(cudaGetErrorString(e)) : why));
+      }
+      e = cudaGraphInstantiate(&h->bexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        h->bexec = nullptr;
+        return fail(h, PMG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+      h->bsweeps = sweeps;
+      h->bkernels = kernels;
+    }
+    for (int st = 0; st < steps; ++st) {
+      PMG_CUDA(h, cudaGraphLaunch(h->bexec, h->stream));
+      h->launches += h->bkernels;
+    }
+  }
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (residuals)
+    for (int i = 0; i < np; ++i) residuals[i] = bits_to_double(h->kids[i]->hred[2]);
+  return PMG_OK;
+}
+
+int pfasst_mg_batch_get_solution(pmg_handle h, int prob, double *out, int on_device) {
+  if (!is_batch(h) || !out || prob < 0 || prob >= (int)h->kids.size())
+    return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  pmg_ctx *k = h->kids[prob];
+  const size_t N = (size_t)k->gf.nz * k->gf.ny * k->gf.n;
+  double *dst = on_device ? out : k->dense;
+  PMG_CUDA(h, k_unpack(k->L(), k->gf, k->u0, 0, dst, 0, 1));
+  if (!on_device) PMG_CUDA(h, cudaMemcpyAsync(out, k->dense, N * 8, cudaMemcpyDeviceToHost, k->stream));
+  PMG_CUDA(h, cudaStreamSynchronize(k->stream));
+  return PMG_OK;
 }
 
 }  // extern "C"

@@ -27,11 +27,11 @@ namespace {
   const int b = zb / (g).nz;         \
   const long long off = ((long long)k * (g).ny + j) * (g).pitch + i
 
-void config(const Grid &g, int batch, dim3 &grid, dim3 &block) {
-  // 256 threads per block always, so every warp is full (the reductions use
-  // full-warp shuffles); small grids simply leave rows idle
-  int bx = g.pitch < 256 ? g.pitch : 256;
-  int by = 256 / bx;
+void config(const Grid &g, int batch, dim3 &grid, dim3 &block, int threads = 256) {
+  // a multiple of 32 threads per block always, so every warp is full (the reductions
+  // use full-warp shuffles); small grids simply leave rows idle
+  int bx = g.pitch < threads ? g.pitch : threads;
+  int by = threads / bx;
   block = dim3(bx, by, 1);
   int gy = (g.ny + by - 1) / by;
   long long gz = (long long)g.nz * batch;
@@ -610,9 +610,9 @@ cudaError_t k_residual0(const Launch &L, const Grid &g, double c, Prec pr, const
 }
 
 cudaError_t k_smooth_jacobi(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
-                            void *eout, const void *f, int batch, bool first) {
+                            void *eout, const void *f, int batch, bool first, int threads) {
   dim3 gr, bl;
-  config(g, batch, gr, bl);
+  config(g, batch, gr, bl, threads);
   Scope sc(L, K_JACOBI, g, batch, pr);
   if (pr == F64)
     PMG_DIM_SWITCH(g.dim, (jacobi_kernel<D, double><<<gr, bl, 0, L.stream>>>(
@@ -625,9 +625,9 @@ cudaError_t k_smooth_jacobi(const Launch &L, const Grid &g, double c, double ome
 }
 
 cudaError_t k_smooth_rbgs(const Launch &L, const Grid &g, double c, double omega, Prec pr, void *e, const void *f,
-                          int batch, int colour, bool first) {
+                          int batch, int colour, bool first, int threads) {
   dim3 gr, bl;
-  config(g, batch, gr, bl);
+  config(g, batch, gr, bl, threads);
   Scope sc(L, K_RBGS, g, batch, pr);
   if (pr == F64)
     PMG_DIM_SWITCH(g.dim, (rbgs_kernel<D, double><<<gr, bl, 0, L.stream>>>(g, c, omega, (double *)e,

@@ -174,10 +174,11 @@ struct InterpCoef {
 cudaError_t k_residual0(const Launch &L, const Grid &g, double c, Prec pr, const double *um, long long sum,
                         const double *qm, long long sq, const double *u1, long long s1, void *f, int batch,
                         unsigned long long *rnorm, unsigned long long *bnorm);
+// threads: block size of the one-point-per-thread smoothers (128, 256, 512, ...)
 cudaError_t k_smooth_jacobi(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
-                            void *eout, const void *f, int batch, bool first);
+                            void *eout, const void *f, int batch, bool first, int threads = 256);
 cudaError_t k_smooth_rbgs(const Launch &L, const Grid &g, double c, double omega, Prec pr, void *e, const void *f,
-                          int batch, int colour, bool first);
+                          int batch, int colour, bool first, int threads = 256);
 cudaError_t k_residual_restrict(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
                                 const void *f, void *fc, int batch);
 cudaError_t k_prolong_add(const Launch &L, const Grid &gf, const Grid &gc, Prec pr, const void *ec, void *e, int batch);
@@ -189,8 +190,11 @@ cudaError_t k_zero(const Launch &L, const Grid &g, Prec pr, void *e, int batch);
 
 // tiled 3D kernels for large batched grids (stencil3d.cu)
 constexpr int kTiled3dMinN = 63;
+// zchunk: z planes per CTA of the fused sweep (0 = default)
 cudaError_t k_rbgs_sweep3d(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
-                           void *eout, const void *f, double *u, long long su, int batch, bool zero, bool update_u);
+                           void *eout, const void *f, double *u, long long su, int batch, bool zero, bool update_u,
+                           int zchunk = 0);
+bool rbgs_rows_supported(const Grid &g);
 cudaError_t k_resrestrict3d(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
                             const void *f, void *fc, int batch);
 cudaError_t k_prolong3d(const Launch &L, const Grid &gf, const Grid &gc, Prec pr, const void *ec, void *e, int batch);

@@ -174,7 +174,7 @@ constexpr int FMY = FTY + 2;         // red / f rows (one-row ring)
 template <typename T, int NX, bool ZERO, bool UPD>
 __global__ void __launch_bounds__(256, 2) rbgs_rows3d_kernel(Grid g, T a, T iD, T omega, const T *__restrict__ ein,
                                                              T *__restrict__ eout, const T *__restrict__ f,
-                                                             double *__restrict__ u, long long su, int nzc) {
+                                                             double *__restrict__ u, long long su, int nzc, int zchunk) {
   using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   constexpr int NP = NX / 2;                  // pairs per row
   constexpr int RS = 256 / NP;                // rows covered per round of 256 threads
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256, 2) rbgs_rows3d_kernel(Grid g, T a, T iD, 
   const int n = g.n, tid = threadIdx.x, px = tid % NP, ry = tid / NP, lane = tid & 31;
   const int y0 = blockIdx.y * FTY;
   const int zc = blockIdx.z % nzc, b = blockIdx.z / nzc;
-  const int z0 = zc * RZC, z1 = min(z0 + RZC, n);
+  const int z0 = zc * zchunk, z1 = min(z0 + zchunk, n);
   const long long plane = (long long)g.ny * g.pitch;
   const T *Eb = ein + b * g.slab + 2 * px;
   const T *Fb = f + b * g.slab + 2 * px;
@@ -497,7 +497,7 @@ __global__ void prolong3d_kernel(Grid gf, Grid gc, const T *__restrict__ ec, T *
 
 template <typename T, int NX, bool ZERO, bool UPD>
 void launch_rows(const Launch &L, const Grid &g, T a, T D, T omega, const void *ein, void *eout, const void *f,
-                 double *u, long long su, int batch) {
+                 double *u, long long su, int batch, int zchunk) {
   const T iD = T(1) / D;
   using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   const size_t smem = sizeof(T2) * (4 * FEY + 6 * FMY) * (NX / 2);
@@ -506,19 +506,20 @@ void launch_rows(const Launch &L, const Grid &g, T a, T D, T omega, const void *
     cudaFuncSetAttribute(rbgs_rows3d_kernel<T, NX, ZERO, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  const int nty = (g.n + FTY - 1) / FTY, nzc = (g.n + RZC - 1) / RZC;
+  if (zchunk <= 0) zchunk = RZC;
+  const int nty = (g.n + FTY - 1) / FTY, nzc = (g.n + zchunk - 1) / zchunk;
   dim3 gr(1, nty, nzc * batch);
   rbgs_rows3d_kernel<T, NX, ZERO, UPD><<<gr, 256, smem, L.stream>>>(g, a, iD, omega, (const T *)ein, (T *)eout,
-                                                                     (const T *)f, u, su, nzc);
+                                                                     (const T *)f, u, su, nzc, zchunk);
 }
 
 template <typename T, bool ZERO, bool UPD>
 void launch_sweep(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout, const void *f,
-                  double *u, long long su, int batch) {
+                  double *u, long long su, int batch, int zchunk) {
   const T a = (T)(c * g.ih2), D = T(1) + T(6) * a;
-  if (g.pitch == 256) return launch_rows<T, 256, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch);
-  if (g.pitch == 128) return launch_rows<T, 128, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch);
-  if (g.pitch == 64) return launch_rows<T, 64, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch);
+  if (g.pitch == 256) return launch_rows<T, 256, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
+  if (g.pitch == 128) return launch_rows<T, 128, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
+  if (g.pitch == 64) return launch_rows<T, 64, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
   const int ntx = (g.n + RTX - 1) / RTX, nty = (g.n + RTY - 1) / RTY, nzc = (g.n + RZC - 1) / RZC;
   const size_t smem = sizeof(T) * (4 * EY + 6 * MY) * SX;
   static bool attr = false;
@@ -533,19 +534,24 @@ void launch_sweep(const Launch &L, const Grid &g, double c, double omega, const 
 
 }  // namespace
 
+bool rbgs_rows_supported(const Grid &g) {
+  return g.dim == 3 && (g.pitch == 256 || g.pitch == 128 || g.pitch == 64);
+}
+
 cudaError_t k_rbgs_sweep3d(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
-                           void *eout, const void *f, double *u, long long su, int batch, bool zero, bool update_u) {
+                           void *eout, const void *f, double *u, long long su, int batch, bool zero, bool update_u,
+                           int zchunk) {
   Scope sc(L, zero ? K_RBGS3D_ZERO : (update_u ? K_RBGS3D_UPD : K_RBGS3D), g, batch, pr);
   if (pr == F32) {
-    if (zero && update_u) launch_sweep<float, true, true>(L, g, c, omega, ein, eout, f, u, su, batch);
-    else if (zero) launch_sweep<float, true, false>(L, g, c, omega, ein, eout, f, u, su, batch);
-    else if (update_u) launch_sweep<float, false, true>(L, g, c, omega, ein, eout, f, u, su, batch);
-    else launch_sweep<float, false, false>(L, g, c, omega, ein, eout, f, u, su, batch);
+    if (zero && update_u) launch_sweep<float, true, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    else if (zero) launch_sweep<float, true, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    else if (update_u) launch_sweep<float, false, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    else launch_sweep<float, false, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
   } else {
-    if (zero && update_u) launch_sweep<double, true, true>(L, g, c, omega, ein, eout, f, u, su, batch);
-    else if (zero) launch_sweep<double, true, false>(L, g, c, omega, ein, eout, f, u, su, batch);
-    else if (update_u) launch_sweep<double, false, true>(L, g, c, omega, ein, eout, f, u, su, batch);
-    else launch_sweep<double, false, false>(L, g, c, omega, ein, eout, f, u, su, batch);
+    if (zero && update_u) launch_sweep<double, true, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    else if (zero) launch_sweep<double, true, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    else if (update_u) launch_sweep<double, false, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    else launch_sweep<double, false, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
   }
   return sc.done();
 }

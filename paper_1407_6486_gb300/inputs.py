@@ -97,3 +97,44 @@ def heat3d_c3(n: int = 255, slices: int = 32, precision: int = 1, iterations: in
     modes, amps = random_modes(3, 16, 8, 6486, radius=8.0)
     return Workload(f"heat3d_n{n}_pfasst5x3_P{slices}", 3, n, 0.5, 0.002, slices, 5, 3, 2, 1, 2, precision,
                     iterations, modes=modes, amps=list(amps))
+
+
+@dataclass
+class Problem:
+    """One member of an uneven batch (single-level SDC, one time step per run step)."""
+    dim: int
+    n: int
+    nodes: int
+    nu: float
+    dt: float
+    modes: list
+    amps: list
+
+    def u0(self) -> np.ndarray:
+        return sine_sum(self.dim, self.n, self.modes, self.amps)
+
+    @property
+    def dofs(self):
+        return self.n ** self.dim
+
+
+def heat_uneven_c4(seed: int = 64, n2d=(63, 127, 255, 511), n3d=(31, 63, 127), count2d: int = 32,
+                   count3d: int = 32):
+    """Uneven batch: independent heat problems, 2D sizes drawn from n2d and 3D sizes from
+    n3d, nu ~ U[0.1, 2], dt ~ U[1e-3, 1e-2], 3 or 5 Gauss-Lobatto nodes, u0 = 4 sine
+    modes with k <= min(8, n/4) and N(0,1) amplitudes; fixed seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for dim, sizes, count in ((2, n2d, count2d), (3, n3d, count3d)):
+        for _ in range(count):
+            n = int(rng.choice(sizes))
+            nodes = int(rng.choice([3, 5]))
+            nu = float(rng.uniform(0.1, 2.0))
+            dt = float(rng.uniform(1e-3, 1e-2))
+            kmax = max(2, min(8, n // 4))
+            grid = np.stack(np.meshgrid(*[np.arange(1, kmax + 1)] * dim, indexing="ij"), -1).reshape(-1, dim)
+            pick = rng.choice(len(grid), size=min(4, len(grid)), replace=False)
+            modes = [tuple(int(v) for v in grid[p]) + (1,) * (3 - dim) for p in pick]
+            amps = list(rng.standard_normal(len(modes)))
+            out.append(Problem(dim, n, nodes, nu, dt, modes, amps))
+    return out

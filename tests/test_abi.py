@@ -106,3 +106,25 @@ def test_create_rejects_nested_nodes_that_do_not_nest(lib):
                               ctypes.byref(o), None, None, 0, ctypes.byref(h))
     assert rc == pmg.PMG_ERR_INVALID_ARG and not h.value
     assert "subset" in pmg.pfasst_mg_last_error()
+
+
+def test_batch_validation_reports_the_bad_problem(lib):
+    good = pmg.pmg_problem_desc(pmg.pmg_grid(2, 31), 3, 1.0, 0.01)
+    bad = pmg.pmg_problem_desc(pmg.pmg_grid(2, 30), 3, 1.0, 0.01)
+    o = pmg.pfasst_mg_default_options()
+    assert pmg.pfasst_mg_batch_workspace_bytes([good, good], o) > 0
+    with pytest.raises(pmg.PMGError) as ei:
+        pmg.pfasst_mg_batch_workspace_bytes([good, bad], o)
+    assert "problem 1" in str(ei.value)
+    with pytest.raises(pmg.PMGError) as ei:
+        pmg.pfasst_mg_batch_workspace_bytes([good], pmg.pfasst_mg_default_options(vcycles=0))
+    assert ei.value.code == pmg.PMG_ERR_UNSUPPORTED
+
+
+def test_uneven_workload_recipe():
+    from paper_1407_6486_gb300 import inputs
+    probs = inputs.heat_uneven_c4()
+    assert len(probs) == 64 and sum(p.dim == 2 for p in probs) == 32
+    assert {p.n for p in probs if p.dim == 2} <= {63, 127, 255, 511}
+    assert {p.n for p in probs if p.dim == 3} <= {31, 63, 127}
+    assert all(0.1 <= p.nu <= 2 and 1e-3 <= p.dt <= 1e-2 and p.nodes in (3, 5) for p in probs)
