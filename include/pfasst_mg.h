@@ -153,6 +153,12 @@ int pfasst_mg_advance(pmg_handle h);
 /* Number of kernel launches this handle has issued so far (for launch accounting). */
 long long pfasst_mg_launch_count(pmg_handle h);
 
+/* Smoother chosen for multigrid level `level` (0 = finest) of the handle's hierarchy,
+ * for wide batches (narrow = 0) or a single grid (narrow = 1): *fused = 1 for the fused
+ * 3D red-black sweep (then *param = z chunk, 0 = default, and *threads per CTA), 0 for
+ * the one-point-per-thread kernels (*param = threads per block). */
+int pfasst_mg_tuning(pmg_handle h, int level, int narrow, int *fused, int *param, int *threads);
+
 /* ---- launch profiling ------------------------------------------------------ */
 
 /* Per-kernel aggregate of CUDA-event timings taken on the handle's stream. */

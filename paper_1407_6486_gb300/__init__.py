@@ -35,7 +35,7 @@ EXPORTS = [
     "pfasst_mg_launch_count", "pfasst_mg_destroy", "pfasst_mg_last_error",
     "pfasst_mg_helmholtz_solve", "pfasst_mg_profile", "pfasst_mg_profile_read", "pfasst_mg_kernel_name",
     "pfasst_mg_helmholtz_solve_noalloc", "pfasst_mg_batch_workspace_bytes", "pfasst_mg_create_batch",
-    "pfasst_mg_batch_set_initial", "pfasst_mg_batch_run", "pfasst_mg_batch_get_solution",
+    "pfasst_mg_batch_set_initial", "pfasst_mg_batch_run", "pfasst_mg_batch_get_solution", "pfasst_mg_tuning",
 ]
 
 
@@ -121,6 +121,7 @@ def load() -> ctypes.CDLL:
     L.pfasst_mg_batch_set_initial.argtypes = [_P, _I, _P, _I]
     L.pfasst_mg_batch_run.argtypes = [_P, _I, _I, _P]
     L.pfasst_mg_batch_get_solution.argtypes = [_P, _I, _P, _I]
+    L.pfasst_mg_tuning.argtypes = [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
     L.pfasst_mg_profile.argtypes = [_P, _I, ctypes.c_longlong]
     L.pfasst_mg_profile_read.argtypes = [_P, ctypes.POINTER(pmg_kernel_stat), _I, ctypes.POINTER(_I)]
     L.pfasst_mg_kernel_name.argtypes = [_I]
@@ -267,6 +268,13 @@ def pfasst_mg_helmholtz_solve_noalloc(grid, c, batch, b, u, opt, stream=None) ->
     _check(load().pfasst_mg_helmholtz_solve_noalloc(ctypes.byref(grid), c, batch, _dev_ptr(b), _dev_ptr(u),
                                                     ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(cyc)))
     return cyc.value
+
+
+def pfasst_mg_tuning(h, level, narrow=0):
+    """(fused, param, threads) chosen for a multigrid level."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().pfasst_mg_tuning(h, level, narrow, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
+    return a.value, b.value, c.value
 
 
 def pfasst_mg_profile(h, enable, min_points=0):

@@ -138,7 +138,8 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // 0 = default) or the one-point-per-thread kernels (param = threads per block).
 struct Tune {
   int fused = 0;
-  int param = 256;
+  int param = 256;    // per-point kernels: threads per block; fused sweep: z chunk (0 = default)
+  int threads = 256;  // fused sweep: threads per CTA
 };
 
 struct Hier {
@@ -351,7 +352,7 @@ int smooth_with(MGCtx &M, const Tune &t, int l, int B, double c, void *&cur, boo
   } else if (t.fused) {
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
     PMG_CUDA(M.h, k_rbgs_sweep3d(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], u_upd, su, B, first,
-                                 u_upd != nullptr, t.param));
+                                 u_upd != nullptr, t.param, t.threads));
     cur = out;
   } else {
     PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 0, first, t.param));
@@ -500,11 +501,14 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
       const int B = cls == 0 ? Bwide : 1;
       if (cls == 1 && Bwide == 1) { H.tune[l][1] = H.tune[l][0]; continue; }
       std::vector<Tune> cand;
-      for (int th : {128, 256, 512}) cand.push_back(Tune{0, th});
+      for (int th : {128, 256, 512}) cand.push_back(Tune{0, th, 256});
       const Grid &g = H.lev[l];
       if (M.o->smoother == PMG_SMOOTHER_RBGS && g.dim == 3 && g.n >= 15)
         for (int zc : {8, 16, 32})
-          if (zc <= g.n) cand.push_back(Tune{1, zc});
+          if (zc <= g.n) {
+            cand.push_back(Tune{1, zc, 256});
+            if (g.pitch >= 128) cand.push_back(Tune{1, zc, 512});
+          }
       float best = 1e30f;
       Tune pick = H.tune[l][cls];
       for (const Tune &t : cand) {
@@ -1022,6 +1026,16 @@ int pfasst_mg_advance(pmg_handle h) {
 }
 
 long long pfasst_mg_launch_count(pmg_handle h) { return h ? h->launches : -1; }
+
+int pfasst_mg_tuning(pmg_handle h, int level, int narrow, int *fused, int *param, int *threads) {
+  if (!h || !h->kids.empty() || level < 0 || level >= h->H.L || !fused || !param || !threads)
+    return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  const Tune &t = h->H.tune[level][narrow ? 1 : 0];
+  *fused = t.fused;
+  *param = t.param;
+  *threads = t.threads;
+  return PMG_OK;
+}
 
 int pfasst_mg_profile(pmg_handle h, int enable, long long min_points) {
   if (!h || min_points < 0) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");

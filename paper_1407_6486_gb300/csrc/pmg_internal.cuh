@@ -190,10 +190,11 @@ cudaError_t k_zero(const Launch &L, const Grid &g, Prec pr, void *e, int batch);
 
 // tiled 3D kernels for large batched grids (stencil3d.cu)
 constexpr int kTiled3dMinN = 63;
-// zchunk: z planes per CTA of the fused sweep (0 = default)
+// zchunk: z planes per CTA of the fused sweep (0 = default); threads: 256 or 512
+// threads per CTA for the full-row variant
 cudaError_t k_rbgs_sweep3d(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
                            void *eout, const void *f, double *u, long long su, int batch, bool zero, bool update_u,
-                           int zchunk = 0);
+                           int zchunk = 0, int threads = 256);
 bool rbgs_rows_supported(const Grid &g);
 cudaError_t k_resrestrict3d(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
                             const void *f, void *fc, int batch);

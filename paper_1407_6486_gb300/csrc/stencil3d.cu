@@ -171,13 +171,13 @@ constexpr int FTY = 8;               // output rows per tile
 constexpr int FEY = FTY + 4;         // e_in rows (two-row ring)
 constexpr int FMY = FTY + 2;         // red / f rows (one-row ring)
 
-template <typename T, int NX, bool ZERO, bool UPD>
-__global__ void __launch_bounds__(256, 2) rbgs_rows3d_kernel(Grid g, T a, T iD, T omega, const T *__restrict__ ein,
+template <typename T, int NX, bool ZERO, bool UPD, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT * 2 > 4 ? 4 : 512 / NT * 2) rbgs_rows3d_kernel(Grid g, T a, T iD, T omega, const T *__restrict__ ein,
                                                              T *__restrict__ eout, const T *__restrict__ f,
                                                              double *__restrict__ u, long long su, int nzc, int zchunk) {
   using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   constexpr int NP = NX / 2;                  // pairs per row
-  constexpr int RS = 256 / NP;                // rows covered per round of 256 threads
+  constexpr int RS = NT / NP;                 // rows covered per round of NT threads
   constexpr int PE = (FEY + RS - 1) / RS, PF = (FMY + RS - 1) / RS, PB = (FTY + RS - 1) / RS;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T2(*E)[FEY][NP] = (T2(*)[FEY][NP])sm_raw;                                         // [4][FEY][NP]
@@ -495,7 +495,7 @@ __global__ void prolong3d_kernel(Grid gf, Grid gc, const T *__restrict__ ec, T *
   }
 }
 
-template <typename T, int NX, bool ZERO, bool UPD>
+template <typename T, int NX, bool ZERO, bool UPD, int NT>
 void launch_rows(const Launch &L, const Grid &g, T a, T D, T omega, const void *ein, void *eout, const void *f,
                  double *u, long long su, int batch, int zchunk) {
   const T iD = T(1) / D;
@@ -503,23 +503,30 @@ void launch_rows(const Launch &L, const Grid &g, T a, T D, T omega, const void *
   const size_t smem = sizeof(T2) * (4 * FEY + 6 * FMY) * (NX / 2);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(rbgs_rows3d_kernel<T, NX, ZERO, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(rbgs_rows3d_kernel<T, NX, ZERO, UPD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   if (zchunk <= 0) zchunk = RZC;
   const int nty = (g.n + FTY - 1) / FTY, nzc = (g.n + zchunk - 1) / zchunk;
   dim3 gr(1, nty, nzc * batch);
-  rbgs_rows3d_kernel<T, NX, ZERO, UPD><<<gr, 256, smem, L.stream>>>(g, a, iD, omega, (const T *)ein, (T *)eout,
-                                                                     (const T *)f, u, su, nzc, zchunk);
+  rbgs_rows3d_kernel<T, NX, ZERO, UPD, NT><<<gr, NT, smem, L.stream>>>(g, a, iD, omega, (const T *)ein, (T *)eout,
+                                                                        (const T *)f, u, su, nzc, zchunk);
 }
 
 template <typename T, bool ZERO, bool UPD>
 void launch_sweep(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout, const void *f,
-                  double *u, long long su, int batch, int zchunk) {
+                  double *u, long long su, int batch, int zchunk, int threads) {
   const T a = (T)(c * g.ih2), D = T(1) + T(6) * a;
-  if (g.pitch == 256) return launch_rows<T, 256, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
-  if (g.pitch == 128) return launch_rows<T, 128, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
-  if (g.pitch == 64) return launch_rows<T, 64, ZERO, UPD>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
+  const bool wide = threads >= 512;
+  if (g.pitch == 256) {
+    if (wide) return launch_rows<T, 256, ZERO, UPD, 512>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
+    return launch_rows<T, 256, ZERO, UPD, 256>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
+  }
+  if (g.pitch == 128) {
+    if (wide) return launch_rows<T, 128, ZERO, UPD, 512>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
+    return launch_rows<T, 128, ZERO, UPD, 256>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
+  }
+  if (g.pitch == 64) return launch_rows<T, 64, ZERO, UPD, 256>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
   const int ntx = (g.n + RTX - 1) / RTX, nty = (g.n + RTY - 1) / RTY, nzc = (g.n + RZC - 1) / RZC;
   const size_t smem = sizeof(T) * (4 * EY + 6 * MY) * SX;
   static bool attr = false;
@@ -540,18 +547,18 @@ bool rbgs_rows_supported(const Grid &g) {
 
 cudaError_t k_rbgs_sweep3d(const Launch &L, const Grid &g, double c, double omega, Prec pr, const void *ein,
                            void *eout, const void *f, double *u, long long su, int batch, bool zero, bool update_u,
-                           int zchunk) {
+                           int zchunk, int threads) {
   Scope sc(L, zero ? K_RBGS3D_ZERO : (update_u ? K_RBGS3D_UPD : K_RBGS3D), g, batch, pr);
   if (pr == F32) {
-    if (zero && update_u) launch_sweep<float, true, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
-    else if (zero) launch_sweep<float, true, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
-    else if (update_u) launch_sweep<float, false, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
-    else launch_sweep<float, false, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    if (zero && update_u) launch_sweep<float, true, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
+    else if (zero) launch_sweep<float, true, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
+    else if (update_u) launch_sweep<float, false, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
+    else launch_sweep<float, false, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
   } else {
-    if (zero && update_u) launch_sweep<double, true, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
-    else if (zero) launch_sweep<double, true, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
-    else if (update_u) launch_sweep<double, false, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
-    else launch_sweep<double, false, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk);
+    if (zero && update_u) launch_sweep<double, true, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
+    else if (zero) launch_sweep<double, true, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
+    else if (update_u) launch_sweep<double, false, true>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
+    else launch_sweep<double, false, false>(L, g, c, omega, ein, eout, f, u, su, batch, zchunk, threads);
   }
   return sc.done();
 }
