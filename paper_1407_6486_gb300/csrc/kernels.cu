@@ -479,7 +479,7 @@ __global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, const double *__res
                                          double *__restrict__ q, long long sq, int batch, unsigned long long *res) {
   for (int zb = blockIdx.z; zb < g.nz * batch; zb += gridDim.z) {
     const int k = zb % g.nz, b = zb / g.nz;
-    double mx = 0.0;
+    unsigned long long mxb = 0ULL;
     for (int j = blockIdx.y * blockDim.y + threadIdx.y; j < g.ny; j += gridDim.y * blockDim.y)
       for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
         const long long off = ((long long)k * g.ny + j) * g.pitch + i;
@@ -498,13 +498,22 @@ __global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, const double *__res
           double P = 0.0;
 #pragma unroll
           for (int jn = 0; jn < S; ++jn) P += cf.dtQ[m][jn] * Gv[jn];
-          const double r = fabs(Uv[0] + P - Uv[m]);
-          if (!(r <= mx)) mx = r;
-          q[b * sq + (m - 1) * g.slab + off] = (P - Pprev) - Uv[m];
+          const double d = P - Uv[m];
+          // |r| as a bit pattern: for non-negative doubles (and NaN above Inf) the
+          // unsigned integer order is the numeric order, so no FP64 compare is issued
+          const unsigned long long rb = (unsigned long long)__double_as_longlong(Uv[0] + d) & 0x7fffffffffffffffULL;
+          mxb = rb > mxb ? rb : mxb;
+          q[b * sq + (m - 1) * g.slab + off] = d - Pprev;
           Pprev = P;
         }
       }
-    if (res) warp_max_atomic(mx, res + b);
+    if (res) {
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, mxb, o);
+        mxb = w > mxb ? w : mxb;
+      }
+      if ((threadIdx.x & 31) == 0 && mxb != 0ULL) atomicMax(res + b, mxb);
+    }
   }
 }
 
