@@ -1,0 +1,95 @@
+"""Pins of the FP64 network oracle (learned multigrid correction): finite-difference
+gradients, delta-kernel identities, a brute-force loop on a tiny grid, BF16 rounding."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import learned as N
+
+
+def small_params(seed=1, ch=3):
+    p = N.init_params(seed, ch=ch)
+    rng = np.random.default_rng(seed + 10)
+    for k in ("b1", "b2", "b3"):
+        p[k] = 0.1 * rng.standard_normal(p[k].shape)
+    return p
+
+
+def test_single_layer_equals_brute_force_loops():
+    n = 4
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((2, n, n, n))
+    W = rng.standard_normal((3, 27, 2))
+    b = rng.standard_normal(3)
+    got = N.conv(a, W, b)
+    want = np.zeros((3, n, n, n))
+    for o, z, y, x in itertools.product(range(3), range(n), range(n), range(n)):
+        acc = b[o]
+        for t, (dz, dy, dx) in enumerate(N.TAPS):
+            zz, yy, xx = z + dz, y + dy, x + dx
+            if 0 <= zz < n and 0 <= yy < n and 0 <= xx < n:
+                acc += sum(W[o, t, c] * a[c, zz, yy, xx] for c in range(2))
+        want[o, z, y, x] = acc
+    np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_delta_kernels_reduce_the_network_to_relu():
+    n, ch = 5, 4
+    p = {k: np.zeros_like(v) for k, v in N.init_params(0, ch=ch).items()}
+    c = N.TAPS.index((0, 0, 0))
+    p["W1"][0, c, 0] = 1.0
+    p["W2"][0, c, 0] = 1.0
+    p["W3"][0, c, 0] = 2.0
+    x = np.random.default_rng(3).standard_normal((n, n, n))
+    y, _ = N.forward(p, x)
+    np.testing.assert_allclose(y, 2.0 * np.maximum(x, 0.0), atol=0)
+
+
+def test_zero_padding_on_a_constant_field():
+    n = 4
+    a = np.ones((1, n, n, n))
+    W = np.ones((1, 27, 1))
+    out = N.conv(a, W, np.zeros(1))[0]
+    # each output counts the in-grid neighbours: 27 inside, 8 at a corner, 12 on an edge
+    assert out[1, 1, 1] == 27 and out[0, 0, 0] == 8 and out[0, 0, 1] == 12 and out[0, 1, 1] == 18
+
+
+def test_input_gradient_is_the_adjoint():
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal((2, 5, 5, 5))
+    g = rng.standard_normal((3, 5, 5, 5))
+    W = rng.standard_normal((3, 27, 2))
+    lhs = float((g * N.conv(a, W, np.zeros(3))).sum())
+    rhs = float((N.conv_input_grad(g, W) * a).sum())
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_parameter_gradients_match_central_differences():
+    p = small_params()
+    rng = np.random.default_rng(7)
+    xs = [rng.standard_normal((5, 5, 5)) for _ in range(2)]
+    ts = [rng.standard_normal((5, 5, 5)) for _ in range(2)]
+    L0, g = N.loss_and_grads(p, xs, ts)
+    eps = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        idx = rng.choice(flat.size, size=min(6, flat.size), replace=False)
+        for i in idx:
+            old = flat[i]
+            flat[i] = old + eps
+            Lp, _ = N.loss_and_grads(p, xs, ts)
+            flat[i] = old - eps
+            Lm, _ = N.loss_and_grads(p, xs, ts)
+            flat[i] = old
+            fd = (Lp - Lm) / (2 * eps)
+            an = g[k].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 * max(1e-3, abs(an)) + 1e-9, (k, i, fd, an)
+
+
+def test_bf16_rounding():
+    v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7, -3.14159265, 1e-30, 0.0])
+    r = N.bf16_round(v)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7      # ties to even
+    assert abs(r[3] - (-3.140625)) < 1e-12 and r[5] == 0.0
+    assert np.all(np.abs(r - v) <= 2 ** -8 * np.abs(v) + 1e-38)
