@@ -7,8 +7,12 @@ library.  Plain numpy, FP64, written from the definition:
   where `*` is a 3x3x3 convolution with zero padding (the zero Dirichlet wall) on the
   interior grid, channels 1 -> 16 -> 16 -> 1.  Input x = D^-1 r, the residual of the
   sub-step operator (I - c Lap_h) scaled by its diagonal D = 1 + 6 c / h^2; output y is
-  added to the multigrid correction e.  Loss 0.5 * mean((y - target)^2) with target the
-  exact error e* - e (from a full multigrid solve).
+  added to the multigrid correction e; target t = e* - e, the exact remaining error.
+
+  Loss, per sample with its own kappa: 0.5 * mean((Ahat (y - t))^2), where
+  Ahat = D^-1 (I - c Lap_h) = I - kappa N, N the sum over the 6 face neighbours (zero
+  walls) and kappa = (c/h^2) / (1 + 6 c/h^2).  Since Ahat t = x, this is the scaled
+  residual left after adding y; kappa = 0 gives the plain error norm 0.5 mean((y - t)^2).
 
 Array conventions: grid functions [z][y][x]; activations [C][z][y][x]; weights
 W[c_out][tap][c_in] with tap = (dz+1)*9 + (dy+1)*3 + (dx+1), offsets in {-1, 0, 1}.
@@ -59,6 +63,14 @@ def conv_weight_grad(g: np.ndarray, a: np.ndarray) -> np.ndarray:
     return Wg
 
 
+def apply_ahat(v: np.ndarray, kappa: float) -> np.ndarray:
+    """Ahat v = v - kappa * (sum of the 6 face neighbours of v), zero outside the grid."""
+    nb = np.zeros_like(v)
+    for d in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+        nb += shift(v, d)
+    return v - kappa * nb
+
+
 def init_params(seed: int = 5, ch: int = CH) -> dict:
     """He-scaled random weights, zero biases."""
     rng = np.random.default_rng(seed)
@@ -83,16 +95,19 @@ def forward(p: dict, x: np.ndarray):
     return y, (x4, z1, a1, z2, a2)
 
 
-def loss_and_grads(p: dict, xs, ts):
-    """Mean over all points of all samples of 0.5 (y - t)^2, and its parameter gradients."""
+def loss_and_grads(p: dict, xs, ts, kappas=None):
+    """Mean over all points of all samples of 0.5 (Ahat_kappa (y - t))^2 (kappa = 0 for
+    every sample when kappas is None), and its parameter gradients."""
     npts = sum(x.size for x in xs)
+    if kappas is None:
+        kappas = [0.0] * len(xs)
     L = 0.0
     g = {k: np.zeros_like(v) for k, v in p.items()}
-    for x, t in zip(xs, ts):
+    for x, t, kap in zip(xs, ts, kappas):
         y, (x4, z1, a1, z2, a2) = forward(p, x)
-        d = y - t
-        L += 0.5 * float((d * d).sum()) / npts
-        gy = (d / npts)[None]
+        w = apply_ahat(y - t, kap)
+        L += 0.5 * float((w * w).sum()) / npts
+        gy = (apply_ahat(w, kap) / npts)[None]  # Ahat is symmetric
         g["W3"] += conv_weight_grad(gy, a2)
         g["b3"] += gy.sum(axis=(1, 2, 3))
         gz2 = conv_input_grad(gy, p["W3"]) * (z2 > 0)

@@ -93,3 +93,57 @@ def test_bf16_rounding():
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7      # ties to even
     assert abs(r[3] - (-3.140625)) < 1e-12 and r[5] == 0.0
     assert np.all(np.abs(r - v) <= 2 ** -8 * np.abs(v) + 1e-38)
+
+
+def test_ahat_on_a_sine_mode_is_its_eigenvalue():
+    n, kap = 9, 0.13
+    h = 1.0 / (n + 1)
+    k = (1, 3, 2)
+    i = np.arange(1, n + 1) * h
+    v = (np.sin(k[0] * np.pi * i)[:, None, None] * np.sin(k[1] * np.pi * i)[None, :, None]
+         * np.sin(k[2] * np.pi * i)[None, None, :])
+    lam = 1.0 - 2.0 * kap * sum(np.cos(kk * np.pi * h) for kk in k)
+    np.testing.assert_allclose(N.apply_ahat(v, kap), lam * v, atol=1e-13)
+
+
+def test_ahat_is_symmetric():
+    rng = np.random.default_rng(8)
+    a, b = rng.standard_normal((2, 6, 6, 6))
+    lhs = float((b * N.apply_ahat(a, 0.15)).sum())
+    rhs = float((N.apply_ahat(b, 0.15) * a).sum())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_operator_norm_loss_gradients_match_central_differences():
+    p = small_params(seed=2)
+    rng = np.random.default_rng(9)
+    xs = [rng.standard_normal((5, 5, 5)) for _ in range(2)]
+    ts = [rng.standard_normal((5, 5, 5)) for _ in range(2)]
+    kaps = [0.1, 1.0 / 6.0]
+    _, g = N.loss_and_grads(p, xs, ts, kaps)
+    eps = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for i in rng.choice(flat.size, size=min(5, flat.size), replace=False):
+            old = flat[i]
+            flat[i] = old + eps
+            Lp, _ = N.loss_and_grads(p, xs, ts, kaps)
+            flat[i] = old - eps
+            Lm, _ = N.loss_and_grads(p, xs, ts, kaps)
+            flat[i] = old
+            fd = (Lp - Lm) / (2 * eps)
+            an = g[k].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 * max(1e-3, abs(an)) + 1e-9, (k, i, fd, an)
+
+
+def test_operator_norm_loss_is_the_scaled_residual_after_the_correction():
+    # with x = Ahat t the loss equals 0.5 mean((x - Ahat y)^2): the residual left by y
+    p = small_params(seed=3)
+    rng = np.random.default_rng(10)
+    t = rng.standard_normal((5, 5, 5))
+    kap = 0.12
+    x = N.apply_ahat(t, kap)
+    L, _ = N.loss_and_grads(p, [x], [t], [kap])
+    y, _ = N.forward(p, x)
+    r = x - N.apply_ahat(y, kap)
+    assert abs(L - 0.5 * float((r * r).mean())) < 1e-13
