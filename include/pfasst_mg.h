@@ -223,6 +223,110 @@ int pfasst_mg_batch_run(pmg_handle h, int steps, int sweeps, double *residuals);
 /* Current value of problem `prob` (after batch_run: the end of its last time step). */
 int pfasst_mg_batch_get_solution(pmg_handle h, int prob, double *out, int on_device);
 
+/* ---- learned multigrid correction network ----------------------------------- */
+/*
+ * A small convolutional network that stands in for the second pre-smoothing sweep
+ * of the V-cycles (the paper has no learned component; this extends its sub-step
+ * solver of Sec. 4.1.1):
+ *   y = W3 * relu(W2 * relu(W1 * x + b1) + b2) + b3,
+ * three 3x3x3 convolutions with zero padding, channels 1 -> 16 -> 16 -> 1.  On a
+ * level with operator I - c Lap_h and diagonal D = 1 + 6 c / h^2 the input is the
+ * scaled residual x = D^-1 (f - (I - c Lap_h) e) and y is added to e.
+ * Parameters: one float vector of pfasst_mg_net_param_count() = 7809 values,
+ *   W1[16][27], b1[16], W2[16 out][27][16 in], b2[16], W3[27][16 in], b3[1],
+ *   tap index (dz+1)*9 + (dy+1)*3 + (dx+1).
+ * The 16 -> 16 layer runs on the tensor cores with BF16 weights and activations and
+ * FP32 accumulation; the other layers and all gradients accumulate in FP32.
+ * Training loss, per grid b with its own kappa_b in [0, 1/6], for a power p in 0..3:
+ *   0.5 * mean over points of (Ahat_b^p (y - t))^2,  Ahat_b v = v - kappa_b * (sum of
+ *   the 6 face neighbours of v), kappa = (c/h^2) / (1 + 6 c/h^2),
+ * with t the exact remaining error: p = 0 the plain mean squared error, p = 1 the
+ * scaled residual left after adding y, p = 2 the error weighted by the squared
+ * eigenvalue of Ahat, which ignores the smooth modes that the coarse-grid correction
+ * removes.  Grid arrays of a pmg_net handle are dense float [batch][n][n][n], x fastest.
+ */
+typedef struct pmg_net *pmg_net_handle;
+
+/* Number of parameters (7809). */
+int pfasst_mg_net_param_count(void);
+
+/* He-scaled normal weights from a counter-based generator, zero biases, into params
+ * (host, 7809 floats). */
+int pfasst_mg_net_init(float *params, unsigned long long seed);
+
+/* Create a trainer for batches of `batch` grids of n^3 points (3 <= n <= 255,
+ * batch * n^3 <= 2^28); allocates its device memory with cudaMalloc; the parameters
+ * start as pfasst_mg_net_init(seed 5).  Errors: INVALID_ARG, OOM. */
+int pfasst_mg_net_create(int batch, int n, void *stream, pmg_net_handle *out);
+
+/* Copy parameters in (host, 7809 floats; also resets the Adam state) or out. */
+int pfasst_mg_net_set_params(pmg_net_handle h, const float *params);
+int pfasst_mg_net_get_params(pmg_net_handle h, float *params);
+
+/* y = net(x) for the handle's batch; x, y dense [batch][n^3] floats, device memory if
+ * on_device, else host.  Synchronises. */
+int pfasst_mg_net_forward(pmg_net_handle h, const float *x, float *y, int on_device);
+
+/* Loss (power p) of the inputs x and targets t (layout as above) with kappa (host,
+ * batch floats) and its gradient with respect to the 7809 parameters, into grad
+ * (host) and *loss (may be NULL).  Synchronises. */
+int pfasst_mg_net_gradients(pmg_net_handle h, const float *x, const float *t, const float *kappa, int power,
+                            int on_device, float *grad, double *loss);
+
+/* Synthetic training pairs: kappa_b uniform in [kappa_lo, kappa_hi]; an error u_b:
+ * uniform noise in [-1, 1] (vcycles_max = 0), or (vcycles_max = K in 1..8, n = 2^p - 1)
+ * that noise after k_b V(2,1) red-black cycles, k_b uniform in 0..K, of
+ * (I - c_b Lap_h) u = 0 with c_b / h^2 = kappa_b / (1 - 6 kappa_b) -- the errors the
+ * multigrid iteration leaves -- scaled to max |u_b| = 1; then t = u_b after one
+ * red-black Gauss-Seidel sweep of Ahat t = 0 (red = even 1-based index sum first),
+ * i.e. the error a first pre-smoothing sweep leaves, and x = Ahat t.  Noise, kappa
+ * and k_b come from counter-based generators of `seed`.  Outputs x, t (layout as
+ * above) and kappa (host, batch floats).  Errors: INVALID_ARG. */
+int pfasst_mg_net_sample(pmg_net_handle h, unsigned long long seed, double kappa_lo, double kappa_hi,
+                         int vcycles_max, float *x, float *t, float *kappa, int on_device);
+
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the loss of
+ * power p, each on a fresh batch from pfasst_mg_net_sample(seed + k * golden,
+ * kappa_lo, kappa_hi, vcycles_max).  train_bias = 0 keeps the
+ * biases fixed (at zero from the default init: the network is then positively
+ * homogeneous, net(a x) = a net(x) for a > 0, as residuals shrink by orders of
+ * magnitude over an iteration).  loss_history (host, steps doubles, may be NULL)
+ * gets every step's loss.  Errors: INVALID_ARG (steps outside 1..4096, lr <= 0, bad
+ * kappa range or vcycles_max, power outside 0..3), DIVERGED (non-finite loss).
+ * Synchronises. */
+int pfasst_mg_net_train(pmg_net_handle h, int steps, double lr, unsigned long long seed, double kappa_lo,
+                        double kappa_hi, int vcycles_max, int power, int train_bias, double *loss_history);
+
+/* One Adam step (as pfasst_mg_net_train) on a caller-supplied batch: inputs x, targets
+ * t (layout as above, device memory if on_device), kappa (host, batch floats in
+ * [0, 1/6]); *loss (may be NULL) gets the batch loss before the step.  Use it to train
+ * on error / residual pairs produced elsewhere, e.g. by another multigrid code.
+ * Errors: INVALID_ARG, DIVERGED.  Synchronises. */
+int pfasst_mg_net_step(pmg_net_handle h, const float *x, const float *t, const float *kappa, int power, double lr,
+                       int train_bias, int on_device, double *loss);
+
+/* Kernel launches issued by the trainer so far. */
+long long pfasst_mg_net_launch_count(pmg_net_handle h);
+
+int pfasst_mg_net_destroy(pmg_net_handle h);
+const char *pfasst_mg_net_last_error(pmg_net_handle h);
+
+/* Deploy a network (params, host, 7809 floats; copied) in the V-cycles of h: on
+ * multigrid levels with n >= min_n (and n >= 7, never the exact coarsest level) the
+ * second pre-smoothing sweep becomes e += net(D^-1 r).  calibrate = 1: measure the
+ * V-cycle contraction rho on the fine level (uniform noise, f = 0, the max-norm ratio
+ * over V-cycles 2..4, worst over the fine sub-step operators) without the network
+ * (*rho_plain) and then add levels finest first, keeping a level only when rho drops
+ * (*rho_net = the final rho); levels that do not help keep the plain sweep, and with
+ * no level kept the handle runs exactly as before.  calibrate = 0: use every
+ * eligible level (*rho_plain and *rho_net are still measured).  *level_mask gets bit l set for level l (0 =
+ * finest).  params = NULL removes a deployed network.  The correction allocates up to
+ * about 1 GiB of scratch (cudaMalloc; grids of a batch are processed in chunks).
+ * Errors: UNSUPPORTED unless dim = 3, red-black Gauss-Seidel and nu1 >= 2, and on
+ * batch handles; INVALID_ARG if no level qualifies; OOM.  Synchronises. */
+int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int calibrate, double *rho_plain,
+                               double *rho_net, int *level_mask);
+
 /* ---- standalone multigrid solve ------------------------------------------ */
 
 /* Solve (I - c Lap_h) u = b (the sub-step operator of Eq. SDCcompactLIII with

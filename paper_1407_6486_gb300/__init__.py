@@ -36,7 +36,13 @@ EXPORTS = [
     "pfasst_mg_helmholtz_solve", "pfasst_mg_profile", "pfasst_mg_profile_read", "pfasst_mg_kernel_name",
     "pfasst_mg_helmholtz_solve_noalloc", "pfasst_mg_batch_workspace_bytes", "pfasst_mg_create_batch",
     "pfasst_mg_batch_set_initial", "pfasst_mg_batch_run", "pfasst_mg_batch_get_solution", "pfasst_mg_tuning",
+    "pfasst_mg_net_param_count", "pfasst_mg_net_init", "pfasst_mg_net_create", "pfasst_mg_net_set_params",
+    "pfasst_mg_net_get_params", "pfasst_mg_net_forward", "pfasst_mg_net_gradients", "pfasst_mg_net_sample",
+    "pfasst_mg_net_train", "pfasst_mg_net_launch_count", "pfasst_mg_net_destroy", "pfasst_mg_net_last_error",
+    "pfasst_mg_set_smoother_net", "pfasst_mg_net_step",
 ]
+
+NET_PARAMS = 7809  # W1[16][27], b1[16], W2[16][27][16], b2[16], W3[27][16], b3
 
 
 class pmg_grid(ctypes.Structure):
@@ -126,9 +132,27 @@ def load() -> ctypes.CDLL:
     L.pfasst_mg_profile_read.argtypes = [_P, ctypes.POINTER(pmg_kernel_stat), _I, ctypes.POINTER(_I)]
     L.pfasst_mg_kernel_name.argtypes = [_I]
     L.pfasst_mg_kernel_name.restype = ctypes.c_char_p
+    _U64 = ctypes.c_ulonglong
+    L.pfasst_mg_net_param_count.argtypes = []
+    L.pfasst_mg_net_init.argtypes = [_P, _U64]
+    L.pfasst_mg_net_create.argtypes = [_I, _I, _P, ctypes.POINTER(_P)]
+    L.pfasst_mg_net_set_params.argtypes = [_P, _P]
+    L.pfasst_mg_net_get_params.argtypes = [_P, _P]
+    L.pfasst_mg_net_forward.argtypes = [_P, _P, _P, _I]
+    L.pfasst_mg_net_gradients.argtypes = [_P, _P, _P, _P, _I, _I, _P, ctypes.POINTER(_D)]
+    L.pfasst_mg_net_sample.argtypes = [_P, _U64, _D, _D, _I, _P, _P, _P, _I]
+    L.pfasst_mg_net_train.argtypes = [_P, _I, _D, _U64, _D, _D, _I, _I, _I, _P]
+    L.pfasst_mg_net_step.argtypes = [_P, _P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(_D)]
+    L.pfasst_mg_net_launch_count.argtypes = [_P]
+    L.pfasst_mg_net_launch_count.restype = ctypes.c_longlong
+    L.pfasst_mg_net_destroy.argtypes = [_P]
+    L.pfasst_mg_net_last_error.argtypes = [_P]
+    L.pfasst_mg_net_last_error.restype = ctypes.c_char_p
+    L.pfasst_mg_set_smoother_net.argtypes = [_P, _P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                             ctypes.POINTER(_I)]
     for name in EXPORTS:
         if name not in ("pfasst_mg_default_options", "pfasst_mg_launch_count", "pfasst_mg_last_error",
-                        "pfasst_mg_kernel_name"):
+                        "pfasst_mg_kernel_name", "pfasst_mg_net_launch_count", "pfasst_mg_net_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -377,6 +401,176 @@ class BatchSolver:
 
 # ---------------------------------------------------------------- convenience handle
 
+# ---------------------------------------------------------------- learned correction network
+
+def _ncheck(rc, h=None):
+    if rc != PMG_OK:
+        msg = load().pfasst_mg_net_last_error(h)
+        raise PMGError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _f32(a, size):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    assert a.size == size, (a.size, size)
+    return a
+
+
+def pfasst_mg_net_param_count() -> int:
+    return load().pfasst_mg_net_param_count()
+
+
+def pfasst_mg_net_init(seed):
+    import numpy as np
+    p = np.zeros(NET_PARAMS, dtype=np.float32)
+    _ncheck(load().pfasst_mg_net_init(p.ctypes.data_as(ctypes.c_void_p), seed))
+    return p
+
+
+def pfasst_mg_net_create(batch, n, stream=None):
+    h = ctypes.c_void_p()
+    _ncheck(load().pfasst_mg_net_create(batch, n, _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def pfasst_mg_net_set_params(h, params):
+    p = _f32(params, NET_PARAMS)
+    _ncheck(load().pfasst_mg_net_set_params(h, p.ctypes.data_as(ctypes.c_void_p)), h)
+
+
+def pfasst_mg_net_get_params(h):
+    import numpy as np
+    p = np.zeros(NET_PARAMS, dtype=np.float32)
+    _ncheck(load().pfasst_mg_net_get_params(h, p.ctypes.data_as(ctypes.c_void_p)), h)
+    return p
+
+
+def pfasst_mg_net_forward(h, x, npts):
+    """x: host float array of npts = batch * n^3 values; returns y (host)."""
+    import numpy as np
+    xa = _f32(x, npts)
+    y = np.zeros(npts, dtype=np.float32)
+    _ncheck(load().pfasst_mg_net_forward(h, xa.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p),
+                                         0), h)
+    return y
+
+
+def pfasst_mg_net_gradients(h, x, t, kappa, npts, power=1):
+    """Host arrays; returns (loss, grad[7809])."""
+    import numpy as np
+    xa, ta = _f32(x, npts), _f32(t, npts)
+    ka = np.ascontiguousarray(kappa, dtype=np.float32)
+    g = np.zeros(NET_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double(0.0)
+    _ncheck(load().pfasst_mg_net_gradients(h, xa.ctypes.data_as(ctypes.c_void_p), ta.ctypes.data_as(ctypes.c_void_p),
+                                           ka.ctypes.data_as(ctypes.c_void_p), power, 0,
+                                           g.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.byref(loss)), h)
+    return loss.value, g
+
+
+def pfasst_mg_net_sample(h, seed, kappa_lo, kappa_hi, batch, npts, vcycles_max=0):
+    """Returns host arrays (x, t, kappa)."""
+    import numpy as np
+    x = np.zeros(npts, dtype=np.float32)
+    t = np.zeros(npts, dtype=np.float32)
+    k = np.zeros(batch, dtype=np.float32)
+    _ncheck(load().pfasst_mg_net_sample(h, seed, kappa_lo, kappa_hi, vcycles_max, x.ctypes.data_as(ctypes.c_void_p),
+                                        t.ctypes.data_as(ctypes.c_void_p), k.ctypes.data_as(ctypes.c_void_p), 0), h)
+    return x, t, k
+
+
+def pfasst_mg_net_train(h, steps, lr, seed, kappa_lo, kappa_hi, vcycles_max=0, power=2, train_bias=0):
+    """Returns the loss of every step (host)."""
+    import numpy as np
+    hist = np.zeros(steps)
+    _ncheck(load().pfasst_mg_net_train(h, steps, lr, seed, kappa_lo, kappa_hi, vcycles_max, power, train_bias,
+                                       hist.ctypes.data_as(ctypes.c_void_p)), h)
+    return hist
+
+
+def pfasst_mg_net_step(h, x, t, kappa, npts, power=1, lr=1e-3, train_bias=0):
+    """One Adam step on host arrays x, t (npts floats) and kappa; returns the loss."""
+    import numpy as np
+    xa, ta = _f32(x, npts), _f32(t, npts)
+    ka = np.ascontiguousarray(kappa, dtype=np.float32)
+    loss = ctypes.c_double(0.0)
+    _ncheck(load().pfasst_mg_net_step(h, xa.ctypes.data_as(ctypes.c_void_p), ta.ctypes.data_as(ctypes.c_void_p),
+                                      ka.ctypes.data_as(ctypes.c_void_p), power, lr, train_bias, 0,
+                                      ctypes.byref(loss)), h)
+    return loss.value
+
+
+def pfasst_mg_net_launch_count(h) -> int:
+    return load().pfasst_mg_net_launch_count(h)
+
+
+def pfasst_mg_net_destroy(h):
+    _ncheck(load().pfasst_mg_net_destroy(h))
+
+
+def pfasst_mg_net_last_error(h=None) -> str:
+    m = load().pfasst_mg_net_last_error(h)
+    return m.decode() if m else ""
+
+
+def pfasst_mg_set_smoother_net(h, params, min_n=15, calibrate=1):
+    """Deploy params (or remove with None); returns (rho_plain, rho_net, level_mask)."""
+    rp, rn, mask = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int(0)
+    ptr = None
+    if params is not None:
+        p = _f32(params, NET_PARAMS)
+        ptr = p.ctypes.data_as(ctypes.c_void_p)
+    _check(load().pfasst_mg_set_smoother_net(h, ptr, min_n, calibrate, ctypes.byref(rp), ctypes.byref(rn),
+                                             ctypes.byref(mask)), h)
+    return rp.value, rn.value, mask.value
+
+
+class NetTrainer:
+    """Owns a pmg_net trainer handle (batch of n^3 grids); methods call the C ABI."""
+
+    def __init__(self, batch, n, stream=None):
+        self.batch, self.n = batch, n
+        self.npts = batch * n ** 3
+        self.h = pfasst_mg_net_create(batch, n, stream)
+
+    def set_params(self, p):
+        pfasst_mg_net_set_params(self.h, p)
+
+    def params(self):
+        return pfasst_mg_net_get_params(self.h)
+
+    def forward(self, x):
+        return pfasst_mg_net_forward(self.h, x, self.npts)
+
+    def gradients(self, x, t, kappa, power=1):
+        return pfasst_mg_net_gradients(self.h, x, t, kappa, self.npts, power)
+
+    def sample(self, seed, kappa_lo, kappa_hi, vcycles_max=0):
+        return pfasst_mg_net_sample(self.h, seed, kappa_lo, kappa_hi, self.batch, self.npts, vcycles_max)
+
+    def train(self, steps, lr, seed, kappa_lo, kappa_hi, vcycles_max=0, power=2, train_bias=0):
+        return pfasst_mg_net_train(self.h, steps, lr, seed, kappa_lo, kappa_hi, vcycles_max, power, train_bias)
+
+    def step(self, x, t, kappa, power=1, lr=1e-3, train_bias=0):
+        return pfasst_mg_net_step(self.h, x, t, kappa, self.npts, power, lr, train_bias)
+
+    def launches(self):
+        return pfasst_mg_net_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            pfasst_mg_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class PFASSTSolver:
     """Owns a pfasst_mg handle and its torch workspace; methods call the C ABI."""
 
@@ -420,6 +614,9 @@ class PFASSTSolver:
 
     def advance(self):
         pfasst_mg_advance(self.h)
+
+    def set_smoother_net(self, params, min_n=15, calibrate=1):
+        return pfasst_mg_set_smoother_net(self.h, params, min_n, calibrate)
 
     def launches(self):
         return pfasst_mg_launch_count(self.h)

@@ -174,6 +174,16 @@ struct Plan {
 
 // ----------------------------------------------------------------- handle
 
+// learned correction network deployed in the V-cycles of a handle: on every level
+// with on[l], the second pre-smoothing sweep is replaced by e += net(D^-1 r)
+struct NetDeploy {
+  void *mem = nullptr;  // parameters + scratch, one cudaMalloc
+  float *prm = nullptr;
+  NetScratch s;
+  int chunk = 1;        // grids per correction launch (bounds the scratch)
+  bool on[kMaxLevels] = {};
+};
+
 struct pmg_ctx {
   int dim = 0, nf = 0, nc = 0, sf = 0, sc = 0, P = 0, nlevels = 1;
   double nu = 0, dt = 0;
@@ -220,6 +230,7 @@ struct pmg_ctx {
   cudaGraphExec_t bexec = nullptr;
   int bsweeps = -1;
   long long bkernels = 0;
+  NetDeploy *net = nullptr;
   std::string err;
 
   Launch L() { return Launch{stream, &launches, &prof}; }
@@ -336,6 +347,7 @@ struct MGCtx {
   int *hactive;
   pmg_ctx *h;               // for error messages (may be null)
   cudaStream_t stream;
+  const NetDeploy *net = nullptr;  // learned correction (may be null)
 };
 
 // one smoothing sweep on level l with the smoother variant t; with the fused 3D
@@ -365,6 +377,20 @@ int smooth(MGCtx &M, int l, int B, double c, void *&cur, bool first, double *u_u
   return smooth_with(M, M.H->tune_for(l, B), l, B, c, cur, first, u_upd, su);
 }
 
+// learned correction on level l: e += net(D^-1 (f - (I - c Lap) e)), in chunks of
+// net->chunk grids so that the activations fit the scratch
+int net_correct(MGCtx &M, int l, int B, double c, void *e) {
+  Hier &H = *M.H;
+  const Grid &g = H.lev[l];
+  const size_t gb = (size_t)g.slab * H.tsize;
+  for (int b0 = 0; b0 < B; b0 += M.net->chunk) {
+    const int nb = B - b0 < M.net->chunk ? B - b0 : M.net->chunk;
+    PMG_CUDA(M.h, k_net_correct(M.L, g, c, H.pr, (char *)e + b0 * gb, (const char *)H.f[l] + b0 * gb, nb,
+                                M.net->prm, M.net->s));
+  }
+  return PMG_OK;
+}
+
 // one V(nu1,nu2)-cycle for (I - c Lap) e = f[l0] on levels l0..L-1, starting from
 // e = 0 (e_init null) or from e_init (a buffer of level l0); *eout = result.
 // If u_upd is non-null and the last post-smoothing sweep on level l0 can be fused
@@ -379,7 +405,10 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, vo
     const bool zero = l > l0 || e_init == nullptr;
     cur[l] = zero ? H.e[l] : e_init;
     if (o.nu1 == 0 && zero) PMG_CUDA(M.h, k_zero(M.L, H.lev[l], H.pr, cur[l], B));
-    for (int s = 0; s < o.nu1; ++s) PMG_RET(smooth(M, l, B, c, cur[l], zero && s == 0));
+    for (int s = 0; s < o.nu1; ++s) {
+      if (s == 1 && M.net && M.net->on[l]) PMG_RET(net_correct(M, l, B, c, cur[l]));
+      else PMG_RET(smooth(M, l, B, c, cur[l], zero && s == 0));
+    }
     if (tiled3d(H.lev[l], B))
       PMG_CUDA(M.h, k_resrestrict3d(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
     else
@@ -479,7 +508,7 @@ int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const dou
 }
 
 MGCtx mgctx(pmg_ctx *h) {
-  MGCtx M{h->L(), &h->H, &h->opt, h->red, h->active, h->hred, h->hactive, h, h->stream};
+  MGCtx M{h->L(), &h->H, &h->opt, h->red, h->active, h->hred, h->hactive, h, h->stream, h->net};
   return M;
 }
 
@@ -1097,6 +1126,10 @@ int pfasst_mg_destroy(pmg_handle h) {
   drop_graph(h->g_pred);
   drop_graph(h->g_iter);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->net) {
+    if (h->net->mem) cudaFree(h->net->mem);
+    delete h->net;
+  }
   if (h->ws_owned && h->ws) cudaFree(h->ws);
   if (h->hred) cudaFreeHost(h->hred);
   if (h->hactive) cudaFreeHost(h->hactive);
@@ -1411,6 +1444,380 @@ int pfasst_mg_batch_get_solution(pmg_handle h, int prob, double *out, int on_dev
   PMG_CUDA(h, k_unpack(k->L(), k->gf, k->u0, 0, dst, 0, 1));
   if (!on_device) PMG_CUDA(h, cudaMemcpyAsync(out, k->dense, N * 8, cudaMemcpyDeviceToHost, k->stream));
   PMG_CUDA(h, cudaStreamSynchronize(k->stream));
+  return PMG_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- learned correction network
+//
+// Training: a pmg_net handle owns the parameters, the Adam moments and the scratch of
+// the forward / backward kernels for a batch of n^3 grids.  Deployment:
+// pfasst_mg_set_smoother_net copies a parameter vector into a PFASST handle, where it
+// replaces the second pre-smoothing sweep on the chosen multigrid levels; levels on
+// which the measured V-cycle contraction does not improve keep the plain sweep.
+
+struct pmg_net {
+  int batch = 0, n = 0;
+  cudaStream_t stream = nullptr;
+  void *mem = nullptr;
+  float *prm = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *xs = nullptr, *ts = nullptr;
+  double *loss = nullptr;
+  double *u64 = nullptr, *zero64 = nullptr;  // multigrid-shaped samples (FP64, dense)
+  unsigned long long *mx = nullptr;
+  NetScratch s;
+  int step = 0;
+  long long launches = 0;
+  std::string err;
+  Launch L() { return Launch{stream, &launches, nullptr}; }
+  NetGrid grid() const { return NetGrid{batch, n, n, (long long)n * n * n}; }
+  size_t pts() const { return (size_t)batch * n * n * n; }
+};
+
+namespace {
+
+int nfail(pmg_net *h, int code, const std::string &msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+#define PMG_NCUDA(h, expr)                                                                 \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return nfail(h, PMG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+// V-cycle contraction on the fine level of h with the handle's current network
+// settings: from uniform noise e with f = 0, rho = (|e_4| / |e_1|)^(1/3) in the max
+// norm after V-cycles 1 and 4, worst over the fine sub-step operators
+int net_measure(pmg_ctx *h, double *rho) {
+  MGCtx M = mgctx(h);
+  Hier &H = h->H;
+  const Grid &g = H.lev[0];
+  double worst = 0.0;
+  for (int m = 0; m < h->sf - 1; ++m) {
+    PMG_CUDA(h, k_net_noise(h->L(), g, H.pr, H.e[0], 1, 0x5eedULL + (unsigned long long)m));
+    PMG_CUDA(h, cudaMemsetAsync(H.f[0], 0, (size_t)g.slab * H.tsize, h->stream));
+    void *e = H.e[0];
+    double nrm[2] = {0.0, 0.0};
+    for (int k = 0; k < 4; ++k) {
+      PMG_RET(vcycle(M, 0, 1, h->cf_sub[m], h->minv_slot(m), e, &e));
+      if (k != 0 && k != 3) continue;
+      PMG_CUDA(h, cudaMemsetAsync(h->red, 0, sizeof(unsigned long long), h->stream));
+      PMG_CUDA(h, k_net_maxabs(h->L(), g, H.pr, e, 1, h->red));
+      PMG_CUDA(h, cudaMemcpyAsync(h->hred, h->red, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+      PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+      std::memcpy(&nrm[k == 3], h->hred, 8);
+    }
+    if (!std::isfinite(nrm[0]) || !std::isfinite(nrm[1])) { worst = INFINITY; break; }
+    const double r = nrm[0] > 0.0 ? std::pow(nrm[1] / nrm[0], 1.0 / 3.0) : 0.0;
+    worst = r > worst ? r : worst;
+  }
+  for (int l = 0; l < H.L; ++l) {
+    const size_t bytes = (size_t)H.lev[l].slab * H.batch * H.tsize;
+    PMG_CUDA(h, cudaMemsetAsync(H.e[l], 0, bytes, h->stream));
+    if (H.e2[l]) PMG_CUDA(h, cudaMemsetAsync(H.e2[l], 0, bytes, h->stream));
+  }
+  PMG_CUDA(h, cudaMemsetAsync(H.f[0], 0, (size_t)g.slab * H.batch * H.tsize, h->stream));
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  *rho = worst;
+  return PMG_OK;
+}
+
+// one batch of training pairs into h->xs, h->ts, h->s.kappa: vmax = 0, smoothed noise;
+// vmax > 0, grid b first gets k_b in 0..vmax V-cycles of (I - c_b Lap) u = 0 from
+// noise (c_b from kappa_b), so the errors have the spectrum the multigrid iteration
+// leaves, normalised to max 1
+int net_draw(pmg_net *h, unsigned long long seed, double klo, double khi, int vmax) {
+  const NetGrid g = h->grid();
+  if (vmax == 0) {
+    PMG_NCUDA(h, k_net_sample(h->L(), g, seed, (float)klo, (float)khi, h->xs, h->ts, h->s.kappa));
+    return PMG_OK;
+  }
+  std::vector<float> kap(h->batch);
+  for (int b = 0; b < h->batch; ++b) kap[b] = net_sample_kappa(seed, (float)klo, (float)khi, b);
+  PMG_NCUDA(h, cudaMemcpyAsync(h->s.kappa, kap.data(), sizeof(float) * h->batch, cudaMemcpyHostToDevice, h->stream));
+  PMG_NCUDA(h, k_net_sample_noise64(h->L(), g, seed, h->u64));
+  pmg_options o;
+  pfasst_mg_default_options(&o);
+  o.smoother = PMG_SMOOTHER_RBGS;
+  o.omega = 1.0;
+  o.use_graphs = 0;
+  o.autotune = 0;
+  const pmg_grid grid{3, h->n};
+  const double ih2 = (double)(h->n + 1) * (h->n + 1);
+  for (int b = 0; b < h->batch; ++b) {
+    o.vcycles = net_sample_vcycles(seed, vmax, b);
+    if (o.vcycles == 0) continue;
+    const double k = kap[b] < 1.0 / 6.0 - 1e-6 ? kap[b] : 1.0 / 6.0 - 1e-6;
+    const double c = k / ((1.0 - 6.0 * k) * ih2);  // kappa = (c/h^2) / (1 + 6 c/h^2)
+    const size_t off = (size_t)b * h->n * h->n * h->n;
+    const int rc = pfasst_mg_helmholtz_solve(&grid, c, 1, h->zero64 + off, h->u64 + off, &o, h->stream, nullptr);
+    if (rc != PMG_OK) return nfail(h, rc, std::string("sample V-cycles: ") + pfasst_mg_last_error(nullptr));
+  }
+  PMG_NCUDA(h, k_net_sample_finish(h->L(), g, h->u64, h->mx, h->xs, h->ts, h->s.kappa));
+  return PMG_OK;
+}
+
+int check_sample_args(pmg_net *h, double kappa_lo, double kappa_hi, int vmax) {
+  if (!(kappa_lo >= 0.0 && kappa_hi >= kappa_lo && kappa_hi <= 1.0 / 6.0))
+    return nfail(h, PMG_ERR_INVALID_ARG, "need 0 <= kappa_lo <= kappa_hi <= 1/6");
+  if (vmax < 0 || vmax > 8) return nfail(h, PMG_ERR_INVALID_ARG, "vcycles_max must be 0..8");
+  if (vmax > 0 && (h->n < 7 || ((h->n + 1) & h->n) != 0))
+    return nfail(h, PMG_ERR_INVALID_ARG, "multigrid-shaped samples need n = 2^p - 1 >= 7");
+  return PMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pfasst_mg_net_param_count(void) { return kNetParams; }
+
+int pfasst_mg_net_init(float *params, unsigned long long seed) {
+  if (!params) return nfail(nullptr, PMG_ERR_INVALID_ARG, "params is NULL");
+  net_init_params(params, seed);
+  return PMG_OK;
+}
+
+int pfasst_mg_net_create(int batch, int n, void *stream, pmg_net_handle *out) {
+  if (!out) return nfail(nullptr, PMG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (batch < 1 || n < 3 || n > 255 || (long long)batch * n * n * n > (1LL << 28))
+    return nfail(nullptr, PMG_ERR_INVALID_ARG, "need batch >= 1, 3 <= n <= 255 and batch * n^3 <= 2^28");
+  pmg_net *h = new (std::nothrow) pmg_net();
+  if (!h) return nfail(nullptr, PMG_ERR_OOM, "host allocation failed");
+  h->batch = batch;
+  h->n = n;
+  h->stream = (cudaStream_t)stream;
+  const size_t P = align256(kNetParams * sizeof(float)), X = align256(h->pts() * sizeof(float));
+  const size_t X64 = align256(h->pts() * sizeof(double));
+  const size_t bytes = 4 * P + 2 * X + 2 * X64 + align256(sizeof(double) * 4096) + align256(8 * (size_t)batch) +
+                       net_train_bytes(batch, n);
+  if (cudaMalloc(&h->mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return nfail(nullptr, PMG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  char *p = (char *)h->mem;
+  h->prm = (float *)p; p += P;
+  h->grad = (float *)p; p += P;
+  h->m = (float *)p; p += P;
+  h->v = (float *)p; p += P;
+  h->xs = (float *)p; p += X;
+  h->ts = (float *)p; p += X;
+  h->loss = (double *)p; p += align256(sizeof(double) * 4096);
+  h->u64 = (double *)p; p += X64;
+  h->zero64 = (double *)p; p += X64;
+  h->mx = (unsigned long long *)p; p += align256(8 * (size_t)batch);
+  h->s = net_train_carve(p, batch, n);
+  if (cudaMemsetAsync(h->zero64, 0, h->pts() * sizeof(double), h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    pfasst_mg_net_destroy(h);
+    return nfail(nullptr, PMG_ERR_CUDA, "cudaMemsetAsync failed");
+  }
+  std::vector<float> init(kNetParams);
+  net_init_params(init.data(), 5);
+  int rc = pfasst_mg_net_set_params(h, init.data());
+  if (rc != PMG_OK) {
+    g_create_error = h->err;
+    pfasst_mg_net_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return PMG_OK;
+}
+
+int pfasst_mg_net_set_params(pmg_net_handle h, const float *params) {
+  if (!h || !params) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or params");
+  PMG_NCUDA(h, cudaMemcpyAsync(h->prm, params, kNetParams * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  PMG_NCUDA(h, cudaMemsetAsync(h->m, 0, kNetParams * sizeof(float), h->stream));
+  PMG_NCUDA(h, cudaMemsetAsync(h->v, 0, kNetParams * sizeof(float), h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  h->step = 0;
+  return PMG_OK;
+}
+
+int pfasst_mg_net_get_params(pmg_net_handle h, float *params) {
+  if (!h || !params) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or params");
+  PMG_NCUDA(h, cudaMemcpyAsync(params, h->prm, kNetParams * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  return PMG_OK;
+}
+
+int pfasst_mg_net_forward(pmg_net_handle h, const float *x, float *y, int on_device) {
+  if (!h || !x || !y) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or array");
+  const size_t bytes = h->pts() * sizeof(float);
+  PMG_NCUDA(h, cudaMemcpyAsync(h->xs, x, bytes, kind_in(on_device), h->stream));
+  PMG_NCUDA(h, k_net_pack(h->L(), h->prm, h->s));
+  PMG_NCUDA(h, k_net_forward(h->L(), h->grid(), h->xs, h->prm, h->s, h->s.y));
+  PMG_NCUDA(h, cudaMemcpyAsync(y, h->s.y, bytes, kind_out(on_device), h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  return PMG_OK;
+}
+
+int pfasst_mg_net_gradients(pmg_net_handle h, const float *x, const float *t, const float *kappa, int power,
+                            int on_device, float *grad, double *loss) {
+  if (!h || !x || !t || !kappa || !grad) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or array");
+  if (power < 0 || power > 3) return nfail(h, PMG_ERR_INVALID_ARG, "power must be 0..3");
+  const size_t bytes = h->pts() * sizeof(float);
+  PMG_NCUDA(h, cudaMemcpyAsync(h->xs, x, bytes, kind_in(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(h->ts, t, bytes, kind_in(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(h->s.kappa, kappa, h->batch * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  PMG_NCUDA(h, cudaMemsetAsync(h->grad, 0, kNetParams * sizeof(float), h->stream));
+  PMG_NCUDA(h, cudaMemsetAsync(h->loss, 0, sizeof(double), h->stream));
+  PMG_NCUDA(h, k_net_pack(h->L(), h->prm, h->s));
+  PMG_NCUDA(h, k_net_grads(h->L(), h->grid(), h->xs, h->ts, h->s.kappa, power, h->prm, h->grad, h->s, h->loss));
+  PMG_NCUDA(h, cudaMemcpyAsync(grad, h->grad, kNetParams * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  double l = 0.0;
+  PMG_NCUDA(h, cudaMemcpyAsync(&l, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  if (loss) *loss = l;
+  return PMG_OK;
+}
+
+int pfasst_mg_net_sample(pmg_net_handle h, unsigned long long seed, double kappa_lo, double kappa_hi,
+                         int vcycles_max, float *x, float *t, float *kappa, int on_device) {
+  if (!h || !x || !t || !kappa) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or array");
+  PMG_RET(check_sample_args(h, kappa_lo, kappa_hi, vcycles_max));
+  const size_t bytes = h->pts() * sizeof(float);
+  PMG_RET(net_draw(h, seed, kappa_lo, kappa_hi, vcycles_max));
+  PMG_NCUDA(h, cudaMemcpyAsync(x, h->xs, bytes, kind_out(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(t, h->ts, bytes, kind_out(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(kappa, h->s.kappa, h->batch * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  return PMG_OK;
+}
+
+int pfasst_mg_net_train(pmg_net_handle h, int steps, double lr, unsigned long long seed, double kappa_lo,
+                        double kappa_hi, int vcycles_max, int power, int train_bias, double *loss_history) {
+  if (!h) return nfail(h, PMG_ERR_INVALID_ARG, "null handle");
+  if (power < 0 || power > 3) return nfail(h, PMG_ERR_INVALID_ARG, "power must be 0..3");
+  if (steps < 1 || steps > 4096 || !(lr > 0.0))
+    return nfail(h, PMG_ERR_INVALID_ARG, "need 1 <= steps <= 4096 and lr > 0");
+  PMG_RET(check_sample_args(h, kappa_lo, kappa_hi, vcycles_max));
+  PMG_NCUDA(h, cudaMemsetAsync(h->loss, 0, sizeof(double) * steps, h->stream));
+  for (int k = 0; k < steps; ++k) {
+    PMG_RET(net_draw(h, seed + (unsigned long long)k * 0x9e3779b97f4a7c15ULL, kappa_lo, kappa_hi, vcycles_max));
+    PMG_NCUDA(h, cudaMemsetAsync(h->grad, 0, kNetParams * sizeof(float), h->stream));
+    PMG_NCUDA(h, k_net_pack(h->L(), h->prm, h->s));
+    PMG_NCUDA(h, k_net_grads(h->L(), h->grid(), h->xs, h->ts, h->s.kappa, power, h->prm, h->grad, h->s,
+                             h->loss + k));
+    PMG_NCUDA(h, k_net_adam(h->L(), h->prm, h->m, h->v, h->grad, ++h->step, (float)lr, 0.9f, 0.999f, 1e-8f,
+                            train_bias != 0));
+  }
+  std::vector<double> hist(steps);
+  PMG_NCUDA(h, cudaMemcpyAsync(hist.data(), h->loss, sizeof(double) * steps, cudaMemcpyDeviceToHost, h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < steps; ++k)
+    if (!std::isfinite(hist[k])) return nfail(h, PMG_ERR_DIVERGED, "non-finite training loss");
+  if (loss_history) std::memcpy(loss_history, hist.data(), sizeof(double) * steps);
+  return PMG_OK;
+}
+
+int pfasst_mg_net_step(pmg_net_handle h, const float *x, const float *t, const float *kappa, int power, double lr,
+                       int train_bias, int on_device, double *loss) {
+  if (!h || !x || !t || !kappa) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or array");
+  if (power < 0 || power > 3 || !(lr > 0.0)) return nfail(h, PMG_ERR_INVALID_ARG, "need power 0..3 and lr > 0");
+  for (int b = 0; b < h->batch; ++b)
+    if (!(kappa[b] >= 0.f && kappa[b] <= 1.f / 6.f + 1e-7f))
+      return nfail(h, PMG_ERR_INVALID_ARG, "kappa must lie in [0, 1/6]");
+  const size_t bytes = h->pts() * sizeof(float);
+  PMG_NCUDA(h, cudaMemcpyAsync(h->xs, x, bytes, kind_in(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(h->ts, t, bytes, kind_in(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(h->s.kappa, kappa, h->batch * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  PMG_NCUDA(h, cudaMemsetAsync(h->grad, 0, kNetParams * sizeof(float), h->stream));
+  PMG_NCUDA(h, cudaMemsetAsync(h->loss, 0, sizeof(double), h->stream));
+  PMG_NCUDA(h, k_net_pack(h->L(), h->prm, h->s));
+  PMG_NCUDA(h, k_net_grads(h->L(), h->grid(), h->xs, h->ts, h->s.kappa, power, h->prm, h->grad, h->s, h->loss));
+  PMG_NCUDA(h, k_net_adam(h->L(), h->prm, h->m, h->v, h->grad, ++h->step, (float)lr, 0.9f, 0.999f, 1e-8f,
+                          train_bias != 0));
+  double l = 0.0;
+  PMG_NCUDA(h, cudaMemcpyAsync(&l, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  if (!std::isfinite(l)) return nfail(h, PMG_ERR_DIVERGED, "non-finite training loss");
+  if (loss) *loss = l;
+  return PMG_OK;
+}
+
+long long pfasst_mg_net_launch_count(pmg_net_handle h) { return h ? h->launches : 0; }
+
+int pfasst_mg_net_destroy(pmg_net_handle h) {
+  if (!h) return PMG_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  if (h->mem) cudaFree(h->mem);
+  delete h;
+  return PMG_OK;
+}
+
+const char *pfasst_mg_net_last_error(pmg_net_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int calibrate, double *rho_plain,
+                               double *rho_net, int *level_mask) {
+  if (!h) return fail(nullptr, PMG_ERR_INVALID_ARG, "null handle");
+  if (is_batch(h)) return fail(h, PMG_ERR_UNSUPPORTED, "the learned correction is not available on batch handles");
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h->g_pred);
+  drop_graph(h->g_iter);
+  if (h->net) {
+    if (h->net->mem) cudaFree(h->net->mem);
+    delete h->net;
+    h->net = nullptr;
+  }
+  if (level_mask) *level_mask = 0;
+  if (!params) return PMG_OK;  // plain smoothing everywhere
+  if (h->dim != 3 || h->opt.smoother != PMG_SMOOTHER_RBGS || h->opt.nu1 < 2)
+    return fail(h, PMG_ERR_UNSUPPORTED, "the learned correction needs dim 3, red-black Gauss-Seidel and nu1 >= 2");
+  Hier &H = h->H;
+  const int nmin = min_n > 7 ? min_n : 7;
+  int lfin = -1, lend = 0;  // eligible levels [lfin, lend): n >= nmin, not the coarsest
+  for (int l = 0; l < H.L - 1; ++l)
+    if (H.lev[l].n >= nmin) {
+      if (lfin < 0) lfin = l;
+      lend = l + 1;
+    }
+  if (lfin < 0) return fail(h, PMG_ERR_INVALID_ARG, "no multigrid level with n >= min_n below the coarsest");
+  NetDeploy *d = new (std::nothrow) NetDeploy();
+  if (!d) return fail(h, PMG_ERR_OOM, "host allocation failed");
+  const size_t per = net_infer_bytes(1, H.lev[lfin]), budget = size_t(1) << 30;
+  d->chunk = (int)(budget / per);
+  if (d->chunk < 1) d->chunk = 1;
+  if (d->chunk > H.batch) d->chunk = H.batch;
+  const size_t P = align256(kNetParams * sizeof(float)), bytes = P + net_infer_bytes(d->chunk, H.lev[lfin]);
+  if (cudaMalloc(&d->mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete d;
+    return fail(h, PMG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  d->prm = (float *)d->mem;
+  d->s = net_infer_carve((char *)d->mem + P, d->chunk, H.lev[lfin]);
+  h->net = d;
+  PMG_CUDA(h, cudaMemcpyAsync(d->prm, params, kNetParams * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  PMG_CUDA(h, k_net_pack(h->L(), d->prm, d->s));
+  double rp = 0.0, rb = 0.0;
+  PMG_RET(net_measure(h, &rp));
+  if (calibrate) {
+    rb = rp;
+    for (int l = lfin; l < lend; ++l) {  // finest first; keep a level only if it helps
+      d->on[l] = true;
+      double r = 0.0;
+      PMG_RET(net_measure(h, &r));
+      if (r < rb) rb = r;
+      else d->on[l] = false;
+    }
+  } else {
+    for (int l = lfin; l < lend; ++l) d->on[l] = true;
+    PMG_RET(net_measure(h, &rb));
+  }
+  int mask = 0;
+  for (int l = 0; l < H.L - 1; ++l) mask |= d->on[l] ? 1 << l : 0;
+  if (rho_plain) *rho_plain = rp;
+  if (rho_net) *rho_net = rb;
+  if (level_mask) *level_mask = mask;
   return PMG_OK;
 }
 

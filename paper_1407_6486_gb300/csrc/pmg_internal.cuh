@@ -7,6 +7,7 @@
 // A batch of grid functions is addressed as ptr + b * stride.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -44,7 +45,9 @@ inline Grid make_grid(int dim, int n) {
 enum KernelId {
   K_RESIDUAL0 = 0, K_JACOBI, K_RBGS, K_RESRESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_ZERO,
   K_APPLY_A, K_SF_RHS, K_FAS, K_INTERP, K_COLLOC, K_COPY, K_PACK, K_UNPACK, K_INTERP_T,
-  K_RBGS3D, K_RESRESTRICT3D, K_PROLONG3D, K_RESID_PT, K_FINE_RHS, K_RBGS3D_ZERO, K_RBGS3D_UPD, K_COUNT
+  K_RBGS3D, K_RESRESTRICT3D, K_PROLONG3D, K_RESID_PT, K_FINE_RHS, K_RBGS3D_ZERO, K_RBGS3D_UPD,
+  K_NET_RESID, K_NET_L1, K_NET_L2, K_NET_L3, K_NET_LOSS, K_NET_L3BWD, K_NET_L2BWD, K_NET_WGRAD, K_NET_ADAM,
+  K_NET_SAMPLE, K_COUNT
 };
 
 // CUDA-event timing of individual launches on the launching stream (only launches
@@ -231,5 +234,63 @@ cudaError_t k_pack(const Launch &L, const Grid &g, const double *dense, long lon
                    int batch);
 cudaError_t k_unpack(const Launch &L, const Grid &g, const double *pad, long long spad, double *dense,
                      long long sdense, int batch);
+
+
+// ---- learned correction network (learned.cu) ----
+// Flat FP32 parameter vector: W1[16][27], b1[16], W2[16][27][16] ([out][tap][in]),
+// b2[16], W3[27][16] ([tap][in]), b3; tap = (dz+1)*9 + (dy+1)*3 + (dx+1).
+constexpr int kNetC = 16;
+constexpr int kNetW1 = 0, kNetB1 = kNetW1 + kNetC * 27, kNetW2 = kNetB1 + kNetC,
+              kNetB2 = kNetW2 + kNetC * 27 * kNetC, kNetW3 = kNetB2 + kNetC, kNetB3 = kNetW3 + 27 * kNetC,
+              kNetParams = kNetB3 + 1;
+
+// batch of n^3 grids; the network input and output grid functions are addressed as
+// b * slab + (z * n + y) * pitch + x (dense: pitch = n, slab = n^3; the padded level
+// layout: pitch = n + 1); hidden activations are dense [b][z][y][x][16] BF16.
+struct NetGrid {
+  int batch, n, pitch;
+  long long slab;
+};
+
+struct NetScratch {
+  __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *gz2b = nullptr, *w2f = nullptr, *w2t = nullptr;
+  float *gz2 = nullptr, *gz1 = nullptr, *y = nullptr, *w = nullptr, *gy = nullptr, *x = nullptr, *tmp = nullptr;
+  float *kappa = nullptr;
+};
+
+// scratch of the training kernels (batch dense n^3 grids) / of the correction step
+size_t net_train_bytes(int batch, int n);
+NetScratch net_train_carve(void *base, int batch, int n);
+size_t net_infer_bytes(int batch, const Grid &g);
+NetScratch net_infer_carve(void *base, int batch, const Grid &g);
+
+void net_init_params(float *prm, unsigned long long seed);  // host, He-scaled normals, zero biases
+cudaError_t k_net_pack(const Launch &L, const float *prm, const NetScratch &s);
+cudaError_t k_net_forward(const Launch &L, const NetGrid &g, const float *x, const float *prm, const NetScratch &s,
+                          float *y);
+// loss 0.5 mean((Ahat_kappa_b^power (y - t))^2) and its gradient, added to grad / *loss
+cudaError_t k_net_grads(const Launch &L, const NetGrid &g, const float *x, const float *t, const float *kappa,
+                        int power, const float *prm, float *grad, const NetScratch &s, double *loss);
+cudaError_t k_net_adam(const Launch &L, float *prm, float *m, float *v, const float *grad, int step, float lr,
+                       float b1, float b2, float eps, bool train_bias);
+// synthetic training pairs: kappa_b uniform in [lo, hi]; t = one red-black Gauss-Seidel
+// sweep of Ahat t = 0 applied to uniform noise; x = Ahat t
+cudaError_t k_net_sample(const Launch &L, const NetGrid &g, unsigned long long seed, float klo, float khi, float *x,
+                         float *t, float *kappa);
+// the kappa of grid b of a sample (as the sample kernels draw it), and its V-cycle count
+float net_sample_kappa(unsigned long long seed, float klo, float khi, int b);
+int net_sample_vcycles(unsigned long long seed, int vmax, int b);
+// multigrid-shaped training pairs, in three steps: FP64 noise u (dense); the caller runs
+// V-cycles of (I - c Lap) u = 0 on u; then t = u / max|u| per grid, one red-black sweep
+// of Ahat t = 0, x = Ahat t (mx: batch scratch words)
+cudaError_t k_net_sample_noise64(const Launch &L, const NetGrid &g, unsigned long long seed, double *u);
+cudaError_t k_net_sample_finish(const Launch &L, const NetGrid &g, const double *u, unsigned long long *mx,
+                                float *x, float *t, const float *kappa);
+// correction step on a multigrid level: x = D^-1 (f - (I - c Lap) e), e += net(x)
+cudaError_t k_net_correct(const Launch &L, const Grid &g, double c, Prec pr, void *e, const void *f, int batch,
+                          const float *prm, const NetScratch &s);
+// calibration helpers on a level: e = uniform noise in [-1, 1] (walls zero); max |e|
+cudaError_t k_net_noise(const Launch &L, const Grid &g, Prec pr, void *e, int batch, unsigned long long seed);
+cudaError_t k_net_maxabs(const Launch &L, const Grid &g, Prec pr, const void *e, int batch, unsigned long long *out);
 
 }  // namespace pmg

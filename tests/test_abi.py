@@ -128,3 +128,30 @@ def test_uneven_workload_recipe():
     assert {p.n for p in probs if p.dim == 2} <= {63, 127, 255, 511}
     assert {p.n for p in probs if p.dim == 3} <= {31, 63, 127}
     assert all(0.1 <= p.nu <= 2 and 1e-3 <= p.dt <= 1e-2 and p.nodes in (3, 5) for p in probs)
+
+
+def test_network_parameter_layout_and_host_init(lib):
+    import numpy as np
+    assert pmg.pfasst_mg_net_param_count() == pmg.NET_PARAMS == 16 * 27 + 16 + 16 * 27 * 16 + 16 + 27 * 16 + 1
+    p = pmg.pfasst_mg_net_init(5)
+    q = pmg.pfasst_mg_net_init(5)
+    assert np.array_equal(p, q) and not np.array_equal(p, pmg.pfasst_mg_net_init(6))
+    w1, b1 = p[:432], p[432:448]
+    w2, b2 = p[448:7360], p[7360:7376]
+    w3, b3 = p[7376:7808], p[7808:]
+    assert not b1.any() and not b2.any() and not b3.any()
+    # He scaling: std sqrt(2/27), sqrt(2/432), sqrt(1/432) within sampling error
+    for w, sd in ((w1, (2 / 27) ** 0.5), (w2, (2 / 432) ** 0.5), (w3, (1 / 432) ** 0.5)):
+        assert abs(w.std() / sd - 1) < 4 / len(w) ** 0.5 + 0.02 and abs(w.mean()) < 4 * sd / len(w) ** 0.5
+
+
+def test_network_argument_validation_needs_no_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.pfasst_mg_net_create(0, 16, None, ctypes.byref(h)) == pmg.PMG_ERR_INVALID_ARG
+    assert lib.pfasst_mg_net_create(1, 2, None, ctypes.byref(h)) == pmg.PMG_ERR_INVALID_ARG
+    assert lib.pfasst_mg_net_create(1, 300, None, ctypes.byref(h)) == pmg.PMG_ERR_INVALID_ARG
+    assert "n <= 255" in pmg.pfasst_mg_net_last_error(None)
+    assert lib.pfasst_mg_net_init(None, 1) == pmg.PMG_ERR_INVALID_ARG
+    assert lib.pfasst_mg_net_train(None, 1, 1e-3, 0, 0.1, 0.15, 0, 2, 0, None) == pmg.PMG_ERR_INVALID_ARG
+    assert lib.pfasst_mg_set_smoother_net(None, None, 15, 1, None, None, None) == pmg.PMG_ERR_INVALID_ARG
+    assert lib.pfasst_mg_net_destroy(None) == pmg.PMG_OK
