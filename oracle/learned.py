@@ -9,10 +9,13 @@ library.  Plain numpy, FP64, written from the definition:
   sub-step operator (I - c Lap_h) scaled by its diagonal D = 1 + 6 c / h^2; output y is
   added to the multigrid correction e; target t = e* - e, the exact remaining error.
 
-  Loss, per sample with its own kappa: 0.5 * mean((Ahat (y - t))^2), where
+  Loss, per sample with its own kappa: 0.5 * mean((Ahat^p (y - t))^2), where
   Ahat = D^-1 (I - c Lap_h) = I - kappa N, N the sum over the 6 face neighbours (zero
-  walls) and kappa = (c/h^2) / (1 + 6 c/h^2).  Since Ahat t = x, this is the scaled
-  residual left after adding y; kappa = 0 gives the plain error norm 0.5 mean((y - t)^2).
+  walls) and kappa = (c/h^2) / (1 + 6 c/h^2).  p = 0 is the plain error norm; p = 1 the
+  scaled residual left after adding y (Ahat t = x); p = 2 weights each error mode by
+  the square of its eigenvalue of Ahat, i.e. it ignores smooth modes (eigenvalues near
+  0), which the coarse-grid correction removes, and measures the oscillatory modes a
+  smoother must damp.  kappa = 0 reduces every p to the plain error norm.
 
 Array conventions: grid functions [z][y][x]; activations [C][z][y][x]; weights
 W[c_out][tap][c_in] with tap = (dz+1)*9 + (dy+1)*3 + (dx+1), offsets in {-1, 0, 1}.
@@ -95,9 +98,9 @@ def forward(p: dict, x: np.ndarray):
     return y, (x4, z1, a1, z2, a2)
 
 
-def loss_and_grads(p: dict, xs, ts, kappas=None):
-    """Mean over all points of all samples of 0.5 (Ahat_kappa (y - t))^2 (kappa = 0 for
-    every sample when kappas is None), and its parameter gradients."""
+def loss_and_grads(p: dict, xs, ts, kappas=None, power: int = 1):
+    """Mean over all points of all samples of 0.5 (Ahat_kappa^power (y - t))^2 (kappa = 0
+    for every sample when kappas is None), and its parameter gradients."""
     npts = sum(x.size for x in xs)
     if kappas is None:
         kappas = [0.0] * len(xs)
@@ -105,9 +108,14 @@ def loss_and_grads(p: dict, xs, ts, kappas=None):
     g = {k: np.zeros_like(v) for k, v in p.items()}
     for x, t, kap in zip(xs, ts, kappas):
         y, (x4, z1, a1, z2, a2) = forward(p, x)
-        w = apply_ahat(y - t, kap)
+        w = y - t
+        for _ in range(power):
+            w = apply_ahat(w, kap)
         L += 0.5 * float((w * w).sum()) / npts
-        gy = (apply_ahat(w, kap) / npts)[None]  # Ahat is symmetric
+        gy = w / npts
+        for _ in range(power):  # Ahat is symmetric
+            gy = apply_ahat(gy, kap)
+        gy = gy[None]
         g["W3"] += conv_weight_grad(gy, a2)
         g["b3"] += gy.sum(axis=(1, 2, 3))
         gz2 = conv_input_grad(gy, p["W3"]) * (z2 > 0)

@@ -147,3 +147,42 @@ def test_operator_norm_loss_is_the_scaled_residual_after_the_correction():
     y, _ = N.forward(p, x)
     r = x - N.apply_ahat(y, kap)
     assert abs(L - 0.5 * float((r * r).mean())) < 1e-13
+
+
+@pytest.mark.parametrize("power", [0, 2, 3])
+def test_loss_powers_match_central_differences(power):
+    p = small_params(seed=4)
+    rng = np.random.default_rng(11)
+    xs = [rng.standard_normal((5, 5, 5))]
+    ts = [rng.standard_normal((5, 5, 5))]
+    kaps = [0.14]
+    _, g = N.loss_and_grads(p, xs, ts, kaps, power)
+    eps = 1e-6
+    for k in ("W1", "W2", "b3"):
+        flat = p[k].reshape(-1)
+        for i in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+            old = flat[i]
+            flat[i] = old + eps
+            Lp, _ = N.loss_and_grads(p, xs, ts, kaps, power)
+            flat[i] = old - eps
+            Lm, _ = N.loss_and_grads(p, xs, ts, kaps, power)
+            flat[i] = old
+            fd = (Lp - Lm) / (2 * eps)
+            an = g[k].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 * max(1e-3, abs(an)) + 1e-9, (k, i, fd, an)
+
+
+def test_loss_power_two_weights_a_mode_by_its_squared_eigenvalue():
+    # a single sine mode as the error y - t (y = 0 with zero weights): the loss is
+    # 0.5 lambda^(2p) mean(t^2), lambda the mode's eigenvalue of Ahat
+    n, kap = 7, 0.15
+    h = 1.0 / (n + 1)
+    i = np.arange(1, n + 1) * h
+    k = (5, 6, 7)
+    t = (np.sin(k[0] * np.pi * i)[:, None, None] * np.sin(k[1] * np.pi * i)[None, :, None]
+         * np.sin(k[2] * np.pi * i)[None, None, :])
+    lam = 1.0 - 2.0 * kap * sum(np.cos(kk * np.pi * h) for kk in k)
+    p = {kk: np.zeros_like(v) for kk, v in N.init_params(0).items()}
+    for power in (0, 1, 2):
+        L, _ = N.loss_and_grads(p, [np.zeros_like(t)], [t], [kap], power)
+        assert abs(L - 0.5 * lam ** (2 * power) * float((t * t).mean())) < 1e-14
