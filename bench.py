@@ -292,6 +292,96 @@ def run_uneven(args):
         print(json.dumps(line), flush=True)
 
 
+NET_LAYER2_FLOPS = 2 * 27 * 16 * 16  # one point of the 16 -> 16 layer (tensor cores)
+NET_FLOPS_FWD = 2 * 27 * (1 * 16 + 16 * 16 + 16 * 1)  # one point, three layers
+
+
+def run_learned(args):
+    """Training of the learned multigrid correction network: one step = one Adam step on
+    a fresh batch of 16 grids of 63^3 points drawn by the library's sampler (noise after
+    one red-black sweep, loss power 2): sampling, forward, loss, backward, weight
+    gradients, Adam -- all library kernels.  value = grid points through forward and
+    backward per second.  Roofline: the 16 -> 16 tensor-core layer (forward)."""
+    import torch
+    import paper_1407_6486_gb300 as pmg
+    from paper_1407_6486_gb300 import _build
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    pmg.load()
+    B, n = 16, 63
+    pts = B * n ** 3
+    tr = pmg.NetTrainer(B, n)
+    tr.train(max(args.warmup, 3), 2e-3, 7, 0.08, 1.0 / 6.0, 0, 2)
+    torch.cuda.synchronize()
+    tr.profile(1, 0)
+    l0 = tr.launches()
+    clk_p, clk_f = sample_clocks_start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    hist = tr.train(args.steps, 2e-3, 1000, 0.08, 1.0 / 6.0, 0, 2)
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sample_clocks_stop(clk_p, clk_f, local)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = tr.launches() - l0
+    stats = tr.profile_read()
+    tr.profile(0, 0)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, peak_src = float(json.load(fh)["bf16_tflops"]), "measured bf16_tflops (burst)"
+    except Exception:
+        peak, peak_src = 1900.0, "fallback"
+    by = {st["kernel"]: st for st in stats}
+    l2 = by.get("net_layer2_mma")
+    roof = None
+    if l2 and l2["launches"]:
+        avg_ms = l2["ms"] / l2["launches"]
+        ach = NET_LAYER2_FLOPS * (l2["points"] / l2["launches"]) / (avg_ms / 1000.0) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "net_layer2_mma", "launches": l2["launches"], "avg_launch_ms": avg_ms,
+                "algo_flops_per_point": NET_LAYER2_FLOPS, "peak_source": peak_src}
+    kernels = sorted(({"kernel": st["kernel"], "ms_per_step": st["ms"] / args.steps,
+                       "launches_per_step": st["launches"] / args.steps} for st in stats),
+                     key=lambda d: -d["ms_per_step"])
+    # end to end through the public API: host batch in (x, t, kappa), loss out
+    x, t, k = tr.sample(4242, 0.08, 1.0 / 6.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        tr.step(x, t, k, power=2, lr=2e-3)
+    e2e_ms = 1000 * (time.perf_counter() - t0) / args.steps
+    tr.close()
+    line = {"metric": "network training points/s", "value": pts / (ms / 1000.0), "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": "learned_train_16x63^3", "batch": B, "grid": f"{n}^3",
+                       "network": "3x3x3 conv 1->16->16->1, ReLU", "loss_power": 2,
+                       "flops_per_point_fwd": NET_FLOPS_FWD, "final_loss": float(hist[-1]),
+                       "l2": "activations 16 x 4.0M points x 2 B = 128 MB per layer, at the L2 size; no flush"},
+            "roofline": roof, "kernels": kernels,
+            "e2e": {"value": pts / (e2e_ms / 1000.0), "unit": "points/s", "h2d_bytes_per_step": 2 * pts * 4 + B * 4,
+                    "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
+        from oracle import learned as N
+        rng = np.random.default_rng(3)
+        nn = 24
+        xs, ts = rng.standard_normal((nn, nn, nn)), rng.standard_normal((nn, nn, nn))
+        prm = N.init_params(5)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0:
+            N.loss_and_grads(prm, [xs], [ts], [0.15], 2)
+            reps += 1
+        sec = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": reps * nn ** 3 / sec, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{reps} FP64 numpy forward+backward passes on one {nn}^3 grid"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import paper_1407_6486_gb300 as pmg
@@ -491,7 +581,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d",
-                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven"])
+                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train"])
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
                          "no CPU baseline")
@@ -507,6 +597,8 @@ def main():
         run_reference(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "learned-train":
+        run_learned(args)
     else:
         run_ours(args)
 

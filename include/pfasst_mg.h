@@ -308,6 +308,11 @@ int pfasst_mg_net_step(pmg_net_handle h, const float *x, const float *t, const f
 /* Kernel launches issued by the trainer so far. */
 long long pfasst_mg_net_launch_count(pmg_net_handle h);
 
+/* CUDA-event timing of the trainer's launches, as pfasst_mg_profile /
+ * pfasst_mg_profile_read for a solver handle. */
+int pfasst_mg_net_profile(pmg_net_handle h, int enable, long long min_points);
+int pfasst_mg_net_profile_read(pmg_net_handle h, pmg_kernel_stat *out, int capacity, int *count);
+
 int pfasst_mg_net_destroy(pmg_net_handle h);
 const char *pfasst_mg_net_last_error(pmg_net_handle h);
 

@@ -39,7 +39,7 @@ EXPORTS = [
     "pfasst_mg_net_param_count", "pfasst_mg_net_init", "pfasst_mg_net_create", "pfasst_mg_net_set_params",
     "pfasst_mg_net_get_params", "pfasst_mg_net_forward", "pfasst_mg_net_gradients", "pfasst_mg_net_sample",
     "pfasst_mg_net_train", "pfasst_mg_net_launch_count", "pfasst_mg_net_destroy", "pfasst_mg_net_last_error",
-    "pfasst_mg_set_smoother_net", "pfasst_mg_net_step",
+    "pfasst_mg_set_smoother_net", "pfasst_mg_net_step", "pfasst_mg_net_profile", "pfasst_mg_net_profile_read",
 ]
 
 NET_PARAMS = 7809  # W1[16][27], b1[16], W2[16][27][16], b2[16], W3[27][16], b3
@@ -143,6 +143,8 @@ def load() -> ctypes.CDLL:
     L.pfasst_mg_net_sample.argtypes = [_P, _U64, _D, _D, _I, _P, _P, _P, _I]
     L.pfasst_mg_net_train.argtypes = [_P, _I, _D, _U64, _D, _D, _I, _I, _I, _P]
     L.pfasst_mg_net_step.argtypes = [_P, _P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(_D)]
+    L.pfasst_mg_net_profile.argtypes = [_P, _I, ctypes.c_longlong]
+    L.pfasst_mg_net_profile_read.argtypes = [_P, ctypes.POINTER(pmg_kernel_stat), _I, ctypes.POINTER(_I)]
     L.pfasst_mg_net_launch_count.argtypes = [_P]
     L.pfasst_mg_net_launch_count.restype = ctypes.c_longlong
     L.pfasst_mg_net_destroy.argtypes = [_P]
@@ -502,6 +504,20 @@ def pfasst_mg_net_step(h, x, t, kappa, npts, power=1, lr=1e-3, train_bias=0):
     return loss.value
 
 
+def pfasst_mg_net_profile(h, enable, min_points=0):
+    _ncheck(load().pfasst_mg_net_profile(h, enable, min_points), h)
+
+
+def pfasst_mg_net_profile_read(h):
+    """Returns a list of dicts {kernel, n, precision, launches, points, ms}."""
+    cap = 64
+    arr = (pmg_kernel_stat * cap)()
+    cnt = ctypes.c_int(0)
+    _ncheck(load().pfasst_mg_net_profile_read(h, arr, cap, ctypes.byref(cnt)), h)
+    return [dict(kernel=pfasst_mg_kernel_name(a.kernel), n=a.n, precision=a.precision, launches=a.launches,
+                 points=a.points, ms=a.ms) for a in arr[:min(cnt.value, cap)]]
+
+
 def pfasst_mg_net_launch_count(h) -> int:
     return load().pfasst_mg_net_launch_count(h)
 
@@ -552,6 +568,12 @@ class NetTrainer:
 
     def train(self, steps, lr, seed, kappa_lo, kappa_hi, vcycles_max=0, power=2, train_bias=0):
         return pfasst_mg_net_train(self.h, steps, lr, seed, kappa_lo, kappa_hi, vcycles_max, power, train_bias)
+
+    def profile(self, enable, min_points=0):
+        pfasst_mg_net_profile(self.h, enable, min_points)
+
+    def profile_read(self):
+        return pfasst_mg_net_profile_read(self.h)
 
     def step(self, x, t, kappa, power=1, lr=1e-3, train_bias=0):
         return pfasst_mg_net_step(self.h, x, t, kappa, self.npts, power, lr, train_bias)

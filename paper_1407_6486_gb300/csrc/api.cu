@@ -1073,18 +1073,22 @@ int pfasst_mg_profile(pmg_handle h, int enable, long long min_points) {
   return PMG_OK;
 }
 
-int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int *count) {
-  if (!h || !count || capacity < 0 || (capacity > 0 && !out)) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
-  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
-  for (const ProfRec &r : h->prof.recs) {
+}  // extern "C"
+
+namespace {
+
+// resolve the pending event pairs of a profiler and aggregate per (kernel, n, precision)
+cudaError_t prof_aggregate(Profiler &P, pmg_kernel_stat *out, int capacity, int *count) {
+  for (const ProfRec &r : P.recs) {
     float ms = 0.f;
-    PMG_CUDA(h, cudaEventElapsedTime(&ms, r.a, r.b));
-    h->prof.done.push_back(ProfDone{r.kid, r.n, r.prec, r.pts, ms});
+    cudaError_t e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return e;
+    P.done.push_back(ProfDone{r.kid, r.n, r.prec, r.pts, ms});
   }
-  h->prof.recs.clear();
-  h->prof.used = 0;
+  P.recs.clear();
+  P.used = 0;
   std::vector<pmg_kernel_stat> agg;
-  for (const ProfDone &r : h->prof.done) {
+  for (const ProfDone &r : P.done) {
     size_t q = 0;
     for (; q < agg.size(); ++q)
       if (agg[q].kernel == r.kid && agg[q].n == r.n && agg[q].precision == r.prec) break;
@@ -1093,9 +1097,20 @@ int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int
     agg[q].points += r.pts;
     agg[q].ms += r.ms;
   }
-  h->prof.done.clear();
+  P.done.clear();
   *count = (int)agg.size();
   for (int q = 0; q < capacity && q < (int)agg.size(); ++q) out[q] = agg[q];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int *count) {
+  if (!h || !count || capacity < 0 || (capacity > 0 && !out)) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  PMG_CUDA(h, prof_aggregate(h->prof, out, capacity, count));
   return PMG_OK;
 }
 
@@ -1105,7 +1120,9 @@ const char *pfasst_mg_kernel_name(int kernel) {
                                        "fas_restrict", "interp_space", "colloc_residual", "copy", "pack",
                                        "unpack", "interp_time", "rbgs_sweep3d", "resrestrict3d", "prolong3d",
                                        "resid_pt", "fine_rhs_residual", "rbgs_sweep3d_zero",
-                                       "rbgs_sweep3d_upd"};
+                                       "rbgs_sweep3d_upd", "net_resid", "net_layer1", "net_layer2_mma",
+                                       "net_layer3", "net_loss", "net_layer3_bwd", "net_layer2_mma_bwd",
+                                       "net_wgrad", "net_adam", "net_sample"};
   return kernel >= 0 && kernel < K_COUNT ? names[kernel] : "unknown";
 }
 
@@ -1468,8 +1485,9 @@ struct pmg_net {
   NetScratch s;
   int step = 0;
   long long launches = 0;
+  Profiler prof;
   std::string err;
-  Launch L() { return Launch{stream, &launches, nullptr}; }
+  Launch L() { return Launch{stream, &launches, &prof}; }
   NetGrid grid() const { return NetGrid{batch, n, n, (long long)n * n * n}; }
   size_t pts() const { return (size_t)batch * n * n * n; }
 };
@@ -1745,6 +1763,20 @@ int pfasst_mg_net_step(pmg_net_handle h, const float *x, const float *t, const f
 }
 
 long long pfasst_mg_net_launch_count(pmg_net_handle h) { return h ? h->launches : 0; }
+
+int pfasst_mg_net_profile(pmg_net_handle h, int enable, long long min_points) {
+  if (!h || min_points < 0) return nfail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  h->prof.on = enable != 0;
+  h->prof.min_points = min_points;
+  return PMG_OK;
+}
+
+int pfasst_mg_net_profile_read(pmg_net_handle h, pmg_kernel_stat *out, int capacity, int *count) {
+  if (!h || !count || capacity < 0 || (capacity > 0 && !out)) return nfail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  PMG_NCUDA(h, prof_aggregate(h->prof, out, capacity, count));
+  return PMG_OK;
+}
 
 int pfasst_mg_net_destroy(pmg_net_handle h) {
   if (!h) return PMG_OK;

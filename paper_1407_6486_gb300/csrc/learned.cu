@@ -351,6 +351,89 @@ __global__ void __launch_bounds__(256) wgrad_kernel(NetGrid g, const float *__re
   if (threadIdx.x < CO) atomicAdd(db + threadIdx.x, bacc);
 }
 
+// 16 -> 16 weight gradient on the tensor cores: for every tap t,
+//   dW[o][t][c] += sum_p G[p][o] act[p + off_t][c]
+// is a GEMM with M = o (16), N = c (two 8-wide tiles) and K = grid points.  A CTA walks
+// 32-point row segments: it stages G transposed (Gt[o][x], BF16) and the 3 x 3 rows x
+// 34 points neighbourhood of the activations transposed (At[row][c][x], BF16) in shared
+// memory, so that both mma operands have their K (point) pairs adjacent; warp w owns
+// the taps w, w + 8, w + 16, w + 24 and keeps their 16 x 16 sums in registers (FP32),
+// added to dW once per CTA.  db[o] += sum_p G[p][o] in FP32.
+__global__ void __launch_bounds__(256) wgrad_mma_kernel(NetGrid g, const float *__restrict__ G,
+                                                        const __nv_bfloat16 *__restrict__ act, float *__restrict__ dW,
+                                                        float *__restrict__ db) {
+  constexpr int XS = 40;  // row pitch (elements) of the staged tiles: 34 used, padded against bank conflicts
+  __shared__ __align__(16) __nv_bfloat16 Gt[NC][XS];
+  __shared__ __align__(16) __nv_bfloat16 At[9][NC][XS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t4 = lane & 3;
+  float acc[4][2][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[j][nt][q] = 0.f;
+  float bacc = 0.f;  // bias sum of channel threadIdx.x % 16
+  const int segs = (g.n + 31) / 32;
+  const long long nseg = (long long)g.batch * g.n * g.n * segs;
+  for (long long s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const int seg = (int)(s % segs);
+    const long long row = s / segs;
+    const int y = (int)(row % g.n), z = (int)((row / g.n) % g.n), b = (int)(row / ((long long)g.n * g.n));
+    const int x0 = seg * 32;
+    __syncthreads();  // the previous segment's reads are done
+    for (int i = threadIdx.x; i < 32 * NC; i += blockDim.x) {
+      const int xi = i / NC, o = i % NC, x = x0 + xi;
+      const float v = x < g.n ? G[dense_index(b, z, y, x, g.n) * NC + o] : 0.f;
+      bacc += v;
+      Gt[o][xi] = __float2bfloat16_rn(v);
+    }
+    for (int i = threadIdx.x; i < 9 * 34 * NC; i += blockDim.x) {
+      const int c = i % NC, xi = (i / NC) % 34, r = i / (NC * 34);
+      const int zz = z + r / 3 - 1, yy = y + r % 3 - 1, xx = x0 + xi - 1;
+      At[r][c][xi] = inside(zz, yy, xx, g.n) ? act[dense_index(b, zz, yy, xx, g.n) * NC + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = warp + 8 * j;
+      if (t >= 27) break;
+      const int r = t / 3, dx = t % 3;  // (dz, dy) row of the tile and x offset + 1
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const int k0 = ks * 16 + 2 * t4;
+        unsigned a[4];
+        a[0] = *(const unsigned *)&Gt[gq][k0];
+        a[1] = *(const unsigned *)&Gt[gq + 8][k0];
+        a[2] = *(const unsigned *)&Gt[gq][k0 + 8];
+        a[3] = *(const unsigned *)&Gt[gq + 8][k0 + 8];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const __nv_bfloat16 *src = &At[r][nt * 8 + gq][k0 + dx];
+          const unsigned short s0 = __bfloat16_as_ushort(src[0]), s1 = __bfloat16_as_ushort(src[1]);
+          const unsigned short s8 = __bfloat16_as_ushort(src[8]), s9 = __bfloat16_as_ushort(src[9]);
+          const unsigned bb[2] = {(unsigned)s0 | ((unsigned)s1 << 16), (unsigned)s8 | ((unsigned)s9 << 16)};
+          mma_bf16(acc[j][nt], a, bb);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int t = warp + 8 * j;
+    if (t >= 27) break;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int o = gq + 8 * h, c = nt * 8 + 2 * t4;
+        atomicAdd(dW + (o * 27 + t) * NC + c, acc[j][nt][2 * h]);
+        atomicAdd(dW + (o * 27 + t) * NC + c + 1, acc[j][nt][2 * h + 1]);
+      }
+  }
+  atomicAdd(db + (threadIdx.x % NC), bacc);
+}
+
 __device__ __forceinline__ bool is_bias(int i) {
   return (i >= kNetB1 && i < kNetB1 + NC) || (i >= kNetB2 && i < kNetB2 + NC) || i == kNetB3;
 }
@@ -635,8 +718,7 @@ cudaError_t k_net_grads(const Launch &L, const NetGrid &g, const float *x, const
                                                                             grad + kNetB3)));
   PMG_NET_STEP(K_NET_L3BWD, (l3_bwd_data_kernel<<<nb, 256, 0, L.stream>>>(g, s.gy, s.a2, prm, s.gz2, s.gz2b)));
   PMG_NET_STEP(K_NET_WGRAD,
-               (wgrad_kernel<NC, NC, __nv_bfloat16><<<wb, 256, 0, L.stream>>>(g, s.gz2, s.a1, grad + kNetW2,
-                                                                             grad + kNetB2)));
+               (wgrad_mma_kernel<<<wb, 256, 0, L.stream>>>(g, s.gz2, s.a1, grad + kNetW2, grad + kNetB2)));
   const long long nwarps = (long long)g.batch * g.n * g.n * ((g.n + 15) / 16);
   PMG_NET_STEP(K_NET_L2BWD, (l2_mma_kernel<1><<<grid_blocks(nwarps * 32, 256), 256, 0, L.stream>>>(
                                 g, s.gz2b, s.w2t, nullptr, s.a1, nullptr, s.gz1)));

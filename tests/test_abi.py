@@ -155,3 +155,18 @@ def test_network_argument_validation_needs_no_gpu(lib):
     assert lib.pfasst_mg_net_train(None, 1, 1e-3, 0, 0.1, 0.15, 0, 2, 0, None) == pmg.PMG_ERR_INVALID_ARG
     assert lib.pfasst_mg_set_smoother_net(None, None, 15, 1, None, None, None) == pmg.PMG_ERR_INVALID_ARG
     assert lib.pfasst_mg_net_destroy(None) == pmg.PMG_OK
+
+
+def test_every_kernel_identifier_has_a_name(lib):
+    names = []
+    k = 0
+    while True:
+        raw = lib.pfasst_mg_kernel_name(k)
+        assert raw is not None, k
+        if raw.decode() == "unknown":
+            break
+        names.append(raw.decode())
+        k += 1
+    assert len(names) == len(set(names)) and len(names) >= 30
+    assert {"net_layer2_mma", "net_layer2_mma_bwd", "net_wgrad", "fine_rhs_residual"} <= set(names)
+    assert lib.pfasst_mg_kernel_name(-1).decode() == "unknown"
