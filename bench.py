@@ -53,7 +53,7 @@ def algo_bytes_per_point(kernel: str, tsize: int, sf: int = 5, sc: int = 3) -> f
         "prolong3d": 2 * t + t / 8,
         "resid_pt": 16 + t,                    # read u_m, q_m (FP64), write f
         "fine_rhs_residual": 8 * sf + 8 * (sf - 1),  # read U at all nodes, write q per sub-step
-        "interp_space": 16 * sf + t * sf / 8.0,
+        "interp_space": 16 + t / 8.0,          # per fine node-point: read/write U, read the coarse correction
     }.get(kernel, 0.0)
 
 
@@ -382,6 +382,9 @@ def run_learned(args):
         print(json.dumps(line), flush=True)
 
 
+RES_TOL = 0.01  # relative tolerance on the FP64 path's residual (the bench's "fixed residual")
+
+
 def run_ours(args):
     import torch
     import paper_1407_6486_gb300 as pmg
@@ -410,6 +413,7 @@ def run_ours(args):
     common = dict(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, interp_order=4)
 
     fp64_ms = None
+    r_ref = None
     if args.quick:
         k_ref, target = wl.iterations, 0.0
     else:
@@ -418,18 +422,19 @@ def run_ours(args):
                                nlevels=wl.nlevels, precision=0, **common)
         ref.set_initial(u0_dev)
         _, k_ref, r_ref = ref.iterate(wl.iterations, 0.0)
-        target = float(f"{r_ref * 1.0001:.3e}")
-        # one timed step of the plain FP64 path (same schedule, residual target, graphs)
-        fp64_ms = None
-        if wl.precision != 0:
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            ref.set_initial(u0_dev)
-            ref.iterate(4 * wl.iterations, target)
-            f1.record(stream)
-            torch.cuda.synchronize()
-            fp64_ms = f0.elapsed_time(f1)
+        # the same residual to RES_TOL: FP32 V-cycles perturb U at the FP32 rounding level
+        # (~1e-7 |U|), which moves a residual of ~1e-4 |U| by ~0.1 %
+        target = float(f"{r_ref * (1.0 + RES_TOL):.4e}")
+        # one timed step of the plain FP64 path to that target (same schedule, graphs); its
+        # iteration count is K_ref
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ref.set_initial(u0_dev)
+        _, k_ref, _ = ref.iterate(4 * wl.iterations, target)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = f0.elapsed_time(f1) if wl.precision != 0 else None
         ref.close()
         del ref
         torch.cuda.empty_cache()
@@ -454,7 +459,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    pmg.pfasst_mg_profile(s.h, True, 0 if args.profile_all else wl.dofs * wl.slices)
+    # record every launch on the fine grid (whole batch or a slice group), or every launch
+    pmg.pfasst_mg_profile(s.h, True, 0 if args.profile_all else wl.dofs)
     launches0 = s.launches()
     # inputs larger than L2 (the 3D workload) need no flush; otherwise a 512 MB buffer is
     # rewritten between timed steps, outside the timed intervals
@@ -482,7 +488,7 @@ def run_ours(args):
         for d in sorted(stats, key=lambda d: -d["ms"]):
             print(f"{d['kernel']:>18} n={d['n']:>4} prec={d['precision']} launches/step={d['launches'] / args.steps:8.0f} "
                   f"ms/step={d['ms'] / args.steps:9.2f} share={d['ms'] / tot:6.1%}", file=sys.stderr)
-        stats = [d for d in stats if d["n"] == wl.n and d["points"] >= wl.dofs * wl.slices * d["launches"]]
+    stats = [d for d in stats if d["n"] == wl.n]
     ms = ms_total / args.steps
     t = torch.tensor([ms], device="cuda")
     if world > 1:
@@ -545,7 +551,8 @@ def run_ours(args):
                    "slices": wl.slices, "nodes": f"{wl.fine_nodes}/{wl.coarse_nodes} Gauss-Lobatto",
                    "smoother": "V(2,1) " + ("red-black Gauss-Seidel" if wl.smoother == 1 else "Jacobi 2/3"),
                    "vcycles": wl.vcycles, "precision": "FP32 V-cycles, FP64 SDC/FAS" if wl.precision else "FP64",
-                   "K_ref": k_ref, "residual_target": target, "iterations": [it for _, it, _ in iters],
+                   "K_ref": k_ref, "residual_target": target, "residual_tolerance": RES_TOL,
+                   "fp64_residual_at_K_ref": r_ref, "iterations": [it for _, it, _ in iters],
                    "final_residual": iters[-1][2], "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "working set > 60 GB, far above the 129 MB L2; no flush" if flush is None
                    else "L2 flushed (512 MB write) before every timed step, outside the timed interval",

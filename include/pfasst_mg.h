@@ -82,12 +82,23 @@ typedef struct {
     int    autotune;      /* 1: at creation, time the smoother variants of every multigrid
                              level (threads per block; fused 3D sweep z chunk) and keep
                              the fastest; 0: built-in size rules                          */
+    int    slice_groups;  /* two-level PFASST with fixed V-cycle counts: the slices of an
+                             iteration are processed in this many groups so that the serial
+                             coarse chain of group g overlaps the fine sweeps of groups
+                             > g (same results); 1 = no overlap, 0 = automatic (2 groups
+                             from 4 slices on), at most 8                                   */
+    int    vcycle_tail;   /* 1: for single grids (the serial coarse chain) the coarsest
+                             multigrid levels (from the first level whose whole remaining
+                             V-cycle fits one CTA's shared memory: 15^3 in 3D, 63^2 in 2D)
+                             run as one kernel launch per V-cycle; 0: one launch per
+                             smoothing sweep, restriction and prolongation                */
 } pmg_options;
 
 typedef struct pmg_ctx *pmg_handle;
 
 /* Defaults: Jacobi omega 2/3, V(2,1), 2 V-cycles, tol 1e-12, stall 0.75, cap 50,
- * FP64, 4th-order interpolation, graphs on, autotuning on. */
+ * FP64, 4th-order interpolation, graphs on, autotuning on, automatic slice groups,
+ * V-cycle tail on. */
 void pfasst_mg_default_options(pmg_options *opt);
 
 /* Bytes of device workspace pfasst_mg_create needs for this problem.

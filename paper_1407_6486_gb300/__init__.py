@@ -62,7 +62,8 @@ class pmg_options(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("vcycles", ctypes.c_int), ("mg_tol", ctypes.c_double),
                 ("mg_stall", ctypes.c_double), ("mg_maxcycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("interp_order", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("slice_groups", ctypes.c_int),
+                ("vcycle_tail", ctypes.c_int)]
 
 
 class pmg_problem_desc(ctypes.Structure):

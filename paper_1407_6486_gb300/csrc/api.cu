@@ -150,7 +150,10 @@ struct Hier {
   size_t tsize = 8;
   int batch = 1;                  // grids per level the buffers hold
   Tune tune[kMaxLevels][2];       // [level][0: wide batches, 1: narrow (a single grid)]
-  const Tune &tune_for(int l, int B) const { return tune[l][2 * B >= batch ? 0 : 1]; }
+  int tail = -1;                  // first level of the one-launch V-cycle bottom (-1: none)
+  VTailDesc td;                   // its shared-memory plan
+  // wide tuning for batches of a few grids or more (slice groups), narrow for single grids
+  const Tune &tune_for(int l, int B) const { return tune[l][(2 * B >= batch || B >= 4) ? 0 : 1]; }
 };
 
 int mg_levels(int n) {
@@ -173,6 +176,8 @@ struct Plan {
 }  // namespace
 
 // ----------------------------------------------------------------- handle
+
+constexpr int kMaxGroups = 8;  // slice groups of the pipelined PFASST iteration
 
 // learned correction network deployed in the V-cycles of a handle: on every level
 // with on[l], the second pre-smoothing sweep is replaced by e += net(D^-1 r)
@@ -199,7 +204,8 @@ struct pmg_ctx {
   // device state
   double *Uf = nullptr, *Ff = nullptr, *qf = nullptr, *u0 = nullptr, *dense = nullptr;
   double *Uc = nullptr, *Fc = nullptr, *qc = nullptr, *tau = nullptr, *Uc0 = nullptr;
-  void *dU = nullptr;  // time-interpolated coarse correction [slice][fine node][coarse grid], MG precision
+  // time-interpolated coarse correction [slice][fine node][coarse grid], MG precision
+  void *dU = nullptr;
   Hier H;
   void *minv = nullptr;  // (sf-1 + sc-1) slots of N3*N3 in MG precision
   int n3 = 3;
@@ -231,6 +237,16 @@ struct pmg_ctx {
   int bsweeps = -1;
   long long bkernels = 0;
   NetDeploy *net = nullptr;
+  // slice-group pipeline of a PFASST iteration: the coarse chain of group g runs on
+  // s_chain (high priority, own multigrid scratch Hc) while the fine sweeps of later
+  // groups run on the main stream; interpolation, send-forward and residual of group g
+  // follow on s_post
+  int groups = 1;
+  Hier Hc;
+  Hier *mgH = nullptr;  // hierarchy the multigrid schedule uses (null: H)
+  cudaStream_t s_chain = nullptr, s_post = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_chain_end = nullptr, ev_post_end = nullptr;
+  cudaEvent_t ev_fas[kMaxGroups] = {}, ev_chain[kMaxGroups] = {};
   std::string err;
 
   Launch L() { return Launch{stream, &launches, &prof}; }
@@ -278,6 +294,11 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
     if (o->vcycles == 0 && (o->mg_maxcycles < 1 || !(o->mg_tol > 0))) { why = "bad full-solve settings"; return PMG_ERR_INVALID_ARG; }
     if (o->precision != PMG_PREC_FP64 && o->precision != PMG_PREC_MIXED) { why = "bad precision"; return PMG_ERR_INVALID_ARG; }
     if (o->interp_order != 2 && o->interp_order != 4) { why = "interp_order must be 2 or 4"; return PMG_ERR_INVALID_ARG; }
+    if (o->vcycle_tail != 0 && o->vcycle_tail != 1) { why = "vcycle_tail must be 0 or 1"; return PMG_ERR_INVALID_ARG; }
+    if (o->slice_groups < 0 || o->slice_groups > kMaxGroups) {
+      why = "slice_groups must be 0 (automatic) .. 8";
+      return PMG_ERR_INVALID_ARG;
+    }
     if (!(o->omega > 0) || o->omega > 2) { why = "omega must be in (0, 2]"; return PMG_ERR_INVALID_ARG; }
   }
   return PMG_OK;
@@ -290,7 +311,8 @@ bool tiled3d(const Grid &g, int B) {
 }
 
 // multigrid hierarchy for `batch` grids of size n (levels n, (n-1)/2, ..., 3)
-void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smoother) {
+// buffers of levels >= first (the levels a V-cycle from `first` touches)
+void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smoother, int first = 0) {
   H.L = mg_levels(n);
   H.pr = pr;
   H.tsize = pr == F64 ? 8 : 4;
@@ -304,11 +326,24 @@ void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smooth
       t.param = t.fused ? 0 : 256;
     }
     size_t bytes = (size_t)H.lev[l].slab * batch * H.tsize;
-    pl.add(&H.e[l], bytes);
-    pl.add(&H.f[l], bytes);
-    // second correction buffer: Jacobi ping-pong, or the out-of-place fused 3D sweep
-    if (smoother == PMG_SMOOTHER_JACOBI || dim == 3) pl.add(&H.e2[l], bytes);
+    if (l >= first) {
+      pl.add(&H.e[l], bytes);
+      pl.add(&H.f[l], bytes);
+      // second correction buffer: Jacobi ping-pong, or the out-of-place fused 3D sweep
+      if (smoother == PMG_SMOOTHER_JACOBI || dim == 3) pl.add(&H.e2[l], bytes);
+    }
     nl = (nl - 1) / 2;
+  }
+  // the finest level from which the rest of the V-cycle fits one CTA's shared memory
+  // (at least two levels, so that the tail replaces several launches)
+  H.tail = -1;
+  for (int l = 0; l + 1 < H.L; ++l) {
+    VTailDesc d;
+    if (vtail_plan(dim, H.lev[l].n, H.L - l, smoother == PMG_SMOOTHER_JACOBI ? 0 : 1, H.tsize, d) <= kVTailMaxSmem) {
+      H.tail = l;
+      H.td = d;
+      break;
+    }
   }
 }
 
@@ -327,7 +362,9 @@ void plan_ctx(Plan &pl, pmg_ctx *h) {
     pl.add((void **)&h->Uc0, sc * h->P * h->sc);
     pl.add((void **)&h->qc, sc * h->P * (h->sc - 1));
   }
-  plan_hier(pl, h->H, h->dim, h->nf, h->P, h->opt.precision == PMG_PREC_MIXED ? F32 : F64, h->opt.smoother);
+  const Prec pr = h->opt.precision == PMG_PREC_MIXED ? F32 : F64;
+  plan_hier(pl, h->H, h->dim, h->nf, h->P, pr, h->opt.smoother);
+  if (h->groups > 1) plan_hier(pl, h->Hc, h->dim, h->nf, 1, pr, h->opt.smoother, 1);  // coarse chain scratch
   if (h->nlevels == 2) pl.add(&h->dU, (size_t)h->gc.slab * h->P * h->sf * h->H.tsize);
   const int slots = (h->sf - 1) + (h->nlevels == 2 ? h->sc - 1 : 0);
   pl.add(&h->minv, (size_t)slots * h->n3 * h->n3 * h->H.tsize);
@@ -401,7 +438,17 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, vo
   const pmg_options &o = *M.o;
   void *cur[kMaxLevels];
   if (fused) *fused = false;
-  for (int l = l0; l < H.L - 1; ++l) {
+  // levels from lb down run in one launch for single grids (one CTA per grid: wide
+  // batches keep the per-level kernels, which spread each level over many CTAs), unless
+  // a learned correction acts there
+  int lb = H.L;
+  if (o.vcycle_tail && H.tail >= l0 && B <= 2) {
+    lb = H.tail;
+    if (M.net)
+      for (int l = H.tail; l < H.L; ++l)
+        if (M.net->on[l]) lb = H.L;
+  }
+  for (int l = l0; l < H.L - 1 && l < lb; ++l) {
     const bool zero = l > l0 || e_init == nullptr;
     cur[l] = zero ? H.e[l] : e_init;
     if (o.nu1 == 0 && zero) PMG_CUDA(M.h, k_zero(M.L, H.lev[l], H.pr, cur[l], B));
@@ -414,10 +461,23 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, vo
     else
       PMG_CUDA(M.h, k_residual_restrict(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
   }
-  const int lc = H.L - 1;
-  PMG_CUDA(M.h, k_coarse_solve(M.L, H.lev[lc], H.pr, minv, H.f[lc], H.e[lc], B));
-  cur[lc] = H.e[lc];
-  for (int l = lc - 1; l >= l0; --l) {
+  int ltop = H.L - 1;
+  if (lb < H.L) {
+    VTailDesc d = H.td;
+    d.c = c;
+    d.omega = o.omega;
+    d.smoother = o.smoother == PMG_SMOOTHER_JACOBI ? 0 : 1;
+    d.nu1 = o.nu1;
+    d.nu2 = o.nu2;
+    const void *ein = (lb == l0 && e_init) ? e_init : nullptr;
+    PMG_CUDA(M.h, k_vcycle_tail(M.L, H.lev[lb], d, H.pr, minv, H.f[lb], ein, H.e[lb], B));
+    cur[lb] = H.e[lb];
+    ltop = lb;
+  } else {
+    PMG_CUDA(M.h, k_coarse_solve(M.L, H.lev[ltop], H.pr, minv, H.f[ltop], H.e[ltop], B));
+    cur[ltop] = H.e[ltop];
+  }
+  for (int l = ltop - 1; l >= l0; --l) {
     if (H.lev[l].dim == 3 && H.lev[l].n >= 15)
       PMG_CUDA(M.h, k_prolong3d(M.L, H.lev[l], H.lev[l + 1], H.pr, cur[l + 1], cur[l], B));
     else
@@ -508,7 +568,7 @@ int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const dou
 }
 
 MGCtx mgctx(pmg_ctx *h) {
-  MGCtx M{h->L(), &h->H, &h->opt, h->red, h->active, h->hred, h->hactive, h, h->stream, h->net};
+  MGCtx M{h->L(), h->mgH ? h->mgH : &h->H, &h->opt, h->red, h->active, h->hred, h->hactive, h, h->stream, h->net};
   return M;
 }
 
@@ -683,7 +743,8 @@ int run_graph(pmg_ctx *h, pmg_ctx::Captured &G, int (*body)(pmg_ctx *)) {
     h->launches = before;
     if (rc != PMG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
     if (e2 != cudaSuccess) return fail(h, PMG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e2));
-    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    // per-node priorities: the coarse-chain kernels keep the high priority of their stream
+    e = cudaGraphInstantiate(&G.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) { G.exec = nullptr; return fail(h, PMG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)); }
     G.with_prof = h->prof.on;
@@ -723,8 +784,107 @@ int predict(pmg_ctx *h) {
   return PMG_OK;
 }
 
+// ---- pieces of one PFASST iteration on the slices [p0, p0+B)
+
+int fas_part(pmg_ctx *h, int p0, int B) {
+  const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
+  PMG_CUDA(h, k_fas_restrict_u(h->L(), h->gf, h->gc, h->fas, h->Uf + p0 * sfs, sfs, h->Uc + p0 * scs,
+                               h->Fc + p0 * scs, h->tau + p0 * scs, h->Uc0 + p0 * scs, scs, B));
+  return PMG_OK;
+}
+
+int interp_part(pmg_ctx *h, int p0, int B) {
+  const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
+  void *dU = (char *)h->dU + (size_t)p0 * h->sf * h->gc.slab * h->H.tsize;
+  PMG_CUDA(h, k_interp_time(h->L(), h->gc, h->interp, h->H.pr, h->Uc + p0 * scs, h->Uc0 + p0 * scs, scs, dU, B));
+  PMG_CUDA(h, k_interp_space_add(h->L(), h->gf, h->gc, h->opt.interp_order, h->sf, h->H.pr, dU, h->Uf + p0 * sfs,
+                                 sfs, B));
+  return PMG_OK;
+}
+
+// U_f[p][0] <- U_f[p-1][M_f] for p in [max(p0,1), p0+B)
+int send_forward_part(pmg_ctx *h, int p0, int B) {
+  const long long sfs = (long long)h->sf * h->gf.slab;
+  const int first = p0 > 1 ? p0 : 1, cnt = p0 + B - first;
+  if (cnt > 0)
+    PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + (first - 1) * sfs + (h->sf - 1) * h->gf.slab, sfs,
+                       h->Uf + first * sfs, sfs, cnt));
+  return PMG_OK;
+}
+
+// F-free fine level: collocation residual and next right-hand sides of [p0, p0+B)
+int fine_residual_part(pmg_ctx *h, int p0, int B) {
+  const long long sfs = (long long)h->sf * h->gf.slab, sq = (long long)(h->sf - 1) * h->gf.slab;
+  PMG_CUDA(h, k_fine_rhs_residual(h->L(), h->gf, h->resf, h->nu, h->Uf + p0 * sfs, sfs, h->qf + p0 * sq, sq, B,
+                                  h->red + 2 * h->P + p0));
+  return PMG_OK;
+}
+
+// One PFASST iteration with the slices in `groups` groups (Sec. 2.4 schedule, same
+// operations on the same data as iteration_serial, so the results are identical):
+//   main stream:  fine sweep + FAS restriction of group 0, 1, ...
+//   chain stream: as soon as group g is restricted, the coarse sweeps of its slices in
+//                 order (slice p receives the coarse end value of p-1) -- the serial
+//                 part, overlapped with the fine sweeps of the later groups
+//   post stream:  as soon as the chain has passed group g, its interpolation,
+//                 send-forward and collocation residual / next right-hand sides
+int iteration_pipe(pmg_ctx *h) {
+  const int P = h->P, G = h->groups, per = (P + G - 1) / G;
+  cudaStream_t main = h->stream;
+  PMG_CUDA(h, cudaMemsetAsync(h->red + 2 * P, 0, sizeof(unsigned long long) * P, main));
+  PMG_CUDA(h, cudaEventRecord(h->ev_fork, main));
+  PMG_CUDA(h, cudaStreamWaitEvent(h->s_chain, h->ev_fork, 0));
+  PMG_CUDA(h, cudaStreamWaitEvent(h->s_post, h->ev_fork, 0));
+  auto group = [&](int g, int &p0, int &B) {
+    p0 = g * per;
+    B = P - p0 < per ? P - p0 : per;
+    return B > 0;
+  };
+  int rc = PMG_OK;
+  int p0 = 0, B = 0;
+  for (int g = 0; g < G && rc == PMG_OK && group(g, p0, B); ++g) {
+    rc = sweep(h, 0, p0, B);
+    if (rc == PMG_OK) rc = fas_part(h, p0, B);
+    if (rc == PMG_OK && cudaEventRecord(h->ev_fas[g], h->stream) != cudaSuccess)
+      rc = fail(h, PMG_ERR_CUDA, "event record failed");
+  }
+  h->stream = h->s_chain;
+  h->mgH = &h->Hc;
+  for (int g = 0; g < G && rc == PMG_OK && group(g, p0, B); ++g) {
+    if (cudaStreamWaitEvent(h->stream, h->ev_fas[g], 0) != cudaSuccess) rc = fail(h, PMG_ERR_CUDA, "wait failed");
+    for (int p = p0; p < p0 + B && rc == PMG_OK; ++p) {
+      if (p > 0) rc = coarse_receive(h, p, 1);
+      if (rc == PMG_OK) rc = sweep(h, 1, p, 1);
+    }
+    if (rc == PMG_OK && cudaEventRecord(h->ev_chain[g], h->stream) != cudaSuccess)
+      rc = fail(h, PMG_ERR_CUDA, "event record failed");
+  }
+  h->mgH = nullptr;
+  if (rc == PMG_OK && cudaEventRecord(h->ev_chain_end, h->stream) != cudaSuccess)
+    rc = fail(h, PMG_ERR_CUDA, "event record failed");
+  h->stream = h->s_post;
+  for (int g = 0; g < G && rc == PMG_OK && group(g, p0, B); ++g) {
+    if (cudaStreamWaitEvent(h->stream, h->ev_chain[g], 0) != cudaSuccess) rc = fail(h, PMG_ERR_CUDA, "wait failed");
+    if (rc == PMG_OK) rc = interp_part(h, p0, B);
+    if (rc == PMG_OK) rc = send_forward_part(h, p0, B);
+    if (rc == PMG_OK) rc = fine_residual_part(h, p0, B);
+  }
+  if (rc == PMG_OK && cudaEventRecord(h->ev_post_end, h->stream) != cudaSuccess)
+    rc = fail(h, PMG_ERR_CUDA, "event record failed");
+  h->stream = main;
+  // join both side streams (also required to end a stream capture)
+  PMG_CUDA(h, cudaStreamWaitEvent(main, h->ev_chain_end, 0));
+  PMG_CUDA(h, cudaStreamWaitEvent(main, h->ev_post_end, 0));
+  if (rc != PMG_OK) return rc;
+  PMG_CUDA(h, cudaMemcpyAsync(h->hred + 2 * P, h->red + 2 * P, sizeof(unsigned long long) * P,
+                              cudaMemcpyDeviceToHost, main));
+  return PMG_OK;
+}
+
 // one PFASST iteration (Sec. 2.4), residual copied to hred[2P..3P) asynchronously
 int iteration(pmg_ctx *h) {
+  // (a deployed network shares one scratch between all V-cycles: no overlap then)
+  if (h->groups > 1 && !h->net) return iteration_pipe(h);
   const long long sfs = (long long)h->sf * h->gf.slab;
   PMG_RET(sweep(h, 0, 0, h->P));
   if (h->nlevels == 2) {
@@ -841,6 +1001,11 @@ pmg_ctx *make_ctx(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_leve
   h->gf = make_grid(h->dim, h->nf);
   if (h->nlevels == 2) h->gc = make_grid(h->dim, h->nc);
   h->n3 = h->dim == 1 ? 3 : (h->dim == 2 ? 9 : 27);
+  // slice groups: only two-level PFASST with fixed V-cycle counts pipelines
+  int G = h->opt.slice_groups;
+  if (G == 0) G = slices >= 4 ? 2 : 1;  // measured best on the 3D workload (2 > 4 > 8 groups)
+  if (G > slices) G = slices;
+  h->groups = (h->nlevels == 2 && h->opt.vcycles > 0 && G > 1) ? G : 1;
   return h;
 }
 
@@ -864,6 +1029,8 @@ void pfasst_mg_default_options(pmg_options *o) {
   o->interp_order = 4;
   o->use_graphs = 1;
   o->autotune = 1;
+  o->slice_groups = 0;
+  o->vcycle_tail = 1;
 }
 
 int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,
@@ -936,6 +1103,27 @@ int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_l
   if (h->opt.autotune) {
     MGCtx M = mgctx(h);
     if (autotune(M, 0, h->P, h->cf_sub[0]) != PMG_OK) return bail(PMG_ERR_CUDA, h->err);
+  }
+  if (h->groups > 1) {
+    // the coarse chain runs single grids: it takes the narrow tuning of every level
+    for (int l = 0; l < h->H.L; ++l) h->Hc.tune[l][0] = h->Hc.tune[l][1] = h->H.tune[l][1];
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&h->s_chain, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&h->s_post, cudaStreamNonBlocking, least) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->ev_chain_end, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->ev_post_end, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; ok && g < h->groups; ++g)
+      ok = cudaEventCreateWithFlags(&h->ev_fas[g], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_chain[g], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      *out = h;  // let destroy release what was created
+      pfasst_mg_destroy(h);
+      *out = nullptr;
+      return fail(nullptr, PMG_ERR_CUDA, "creating the pipeline streams failed");
+    }
   }
   *out = h;
   return PMG_OK;
@@ -1122,7 +1310,7 @@ const char *pfasst_mg_kernel_name(int kernel) {
                                        "resid_pt", "fine_rhs_residual", "rbgs_sweep3d_zero",
                                        "rbgs_sweep3d_upd", "net_resid", "net_layer1", "net_layer2_mma",
                                        "net_layer3", "net_loss", "net_layer3_bwd", "net_layer2_mma_bwd",
-                                       "net_wgrad", "net_adam", "net_sample"};
+                                       "net_wgrad", "net_adam", "net_sample", "vcycle_tail"};
   return kernel >= 0 && kernel < K_COUNT ? names[kernel] : "unknown";
 }
 
@@ -1143,6 +1331,14 @@ int pfasst_mg_destroy(pmg_handle h) {
   drop_graph(h->g_pred);
   drop_graph(h->g_iter);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->s_chain) cudaStreamDestroy(h->s_chain);
+  if (h->s_post) cudaStreamDestroy(h->s_post);
+  for (cudaEvent_t e : {h->ev_fork, h->ev_chain_end, h->ev_post_end})
+    if (e) cudaEventDestroy(e);
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (h->ev_fas[g]) cudaEventDestroy(h->ev_fas[g]);
+    if (h->ev_chain[g]) cudaEventDestroy(h->ev_chain[g]);
+  }
   if (h->net) {
     if (h->net->mem) cudaFree(h->net->mem);
     delete h->net;
@@ -1850,6 +2046,11 @@ int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int
   if (rho_plain) *rho_plain = rp;
   if (rho_net) *rho_net = rb;
   if (level_mask) *level_mask = mask;
+  if (mask == 0) {  // no level kept: run exactly as without a network
+    cudaFree(d->mem);
+    delete d;
+    h->net = nullptr;
+  }
   return PMG_OK;
 }
 

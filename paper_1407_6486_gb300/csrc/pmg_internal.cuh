@@ -47,7 +47,7 @@ enum KernelId {
   K_APPLY_A, K_SF_RHS, K_FAS, K_INTERP, K_COLLOC, K_COPY, K_PACK, K_UNPACK, K_INTERP_T,
   K_RBGS3D, K_RESRESTRICT3D, K_PROLONG3D, K_RESID_PT, K_FINE_RHS, K_RBGS3D_ZERO, K_RBGS3D_UPD,
   K_NET_RESID, K_NET_L1, K_NET_L2, K_NET_L3, K_NET_LOSS, K_NET_L3BWD, K_NET_L2BWD, K_NET_WGRAD, K_NET_ADAM,
-  K_NET_SAMPLE, K_COUNT
+  K_NET_SAMPLE, K_VTAIL, K_COUNT
 };
 
 // CUDA-event timing of individual launches on the launching stream (only launches
@@ -235,6 +235,25 @@ cudaError_t k_pack(const Launch &L, const Grid &g, const double *dense, long lon
 cudaError_t k_unpack(const Launch &L, const Grid &g, const double *pad, long long spad, double *dense,
                      long long sdense, int batch);
 
+
+// ---- bottom of a V-cycle in one launch (tail.cu) ----
+// levels top .. 3^d of one grid per CTA in shared memory: offsets (elements) of the
+// dense e, e2 (Jacobi), f and residual arrays of every tail level
+constexpr size_t kVTailMaxSmem = 200 * 1024;
+struct VTailDesc {
+  int nlev = 0;
+  int n[kMaxLevels] = {};
+  int off_e[kMaxLevels] = {}, off_e2[kMaxLevels] = {}, off_f[kMaxLevels] = {}, off_r[kMaxLevels] = {};
+  size_t smem_elems = 0;
+  double c = 0, omega = 1;
+  int smoother = 1, nu1 = 2, nu2 = 1;  // smoother 0 = weighted Jacobi, 1 = red-black Gauss-Seidel
+};
+// fills d for nlev levels from n_top; returns the shared-memory bytes
+size_t vtail_plan(int dim, int n_top, int nlev, int smoother, size_t tsize, VTailDesc &d);
+// e (top level, padded layout) = V-cycle correction for right-hand side f, starting
+// from e_in (may equal e) or from zero (e_in null)
+cudaError_t k_vcycle_tail(const Launch &L, const Grid &g_top, const VTailDesc &d, Prec pr, const void *minv,
+                          const void *f, const void *e_in, void *e, int batch);
 
 // ---- learned correction network (learned.cu) ----
 // Flat FP32 parameter vector: W1[16][27], b1[16], W2[16][27][16] ([out][tap][in]),

@@ -170,3 +170,19 @@ def test_every_kernel_identifier_has_a_name(lib):
     assert len(names) == len(set(names)) and len(names) >= 30
     assert {"net_layer2_mma", "net_layer2_mma_bwd", "net_wgrad", "fine_rhs_residual"} <= set(names)
     assert lib.pfasst_mg_kernel_name(-1).decode() == "unknown"
+
+
+def test_slice_groups_option_is_validated(lib):
+    o = pmg.pfasst_mg_default_options(slice_groups=9)
+    nb = ctypes.c_size_t(0)
+    g, fnodes, lv = pmg.pmg_grid(3, 31), pmg.pmg_nodes_desc(5, 0), pmg.pmg_levels(2, pmg.pmg_nodes_desc(3, 0))
+    assert lib.pfasst_mg_workspace_bytes(ctypes.byref(g), ctypes.byref(fnodes), ctypes.byref(lv), 8,
+                                         ctypes.byref(o), ctypes.byref(nb)) == pmg.PMG_ERR_INVALID_ARG
+    sizes = []
+    for G in (1, 0, 4):
+        o = pmg.pfasst_mg_default_options(slice_groups=G, vcycles=2)
+        assert lib.pfasst_mg_workspace_bytes(ctypes.byref(g), ctypes.byref(fnodes), ctypes.byref(lv), 8,
+                                             ctypes.byref(o), ctypes.byref(nb)) == pmg.PMG_OK
+        sizes.append(nb.value)
+    # the pipelined iteration adds a single-grid multigrid scratch for the coarse chain
+    assert sizes[0] < sizes[1] == sizes[2]

@@ -293,3 +293,24 @@ def test_heat3d_workload_full_size_first_slices_match_oracle(precision, tol):
     o.predict()
     o.iteration()
     assert rel(gpu, o.Uf) < tol
+
+
+@pytest.mark.parametrize("precision,graphs,groups,autotune,n", [
+    (1, 1, 2, 1, 63), (0, 1, 2, 1, 63), (1, 0, 2, 1, 63), (1, 1, 4, 0, 31), (0, 0, 4, 0, 31)])
+def test_slice_group_pipeline_gives_identical_iterates(precision, graphs, groups, autotune, n):
+    """The pipelined iteration (coarse chain of group g overlapping the fine sweeps of
+    later groups on other streams) runs the same operations on the same data as the
+    serial schedule: every iterate is bit-identical."""
+    wl = inputs.heat3d_c3(n=n, slices=8)
+    states = []
+    for G in (1, groups):
+        s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                             smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, precision=precision,
+                             use_graphs=graphs, autotune=autotune, slice_groups=G)
+        s.set_initial(wl.u0())
+        rc, it, res = s.iterate(3, 0.0)
+        states.append((s.state(0), s.state(1), s.residual()))
+        s.close()
+    assert np.array_equal(states[0][0], states[1][0])
+    assert np.array_equal(states[0][1], states[1][1])
+    assert np.array_equal(states[0][2], states[1][2])
