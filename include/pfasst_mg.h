@@ -85,8 +85,9 @@ typedef struct {
     int    slice_groups;  /* two-level PFASST with fixed V-cycle counts: the slices of an
                              iteration are processed in this many groups so that the serial
                              coarse chain of group g overlaps the fine sweeps of groups
-                             > g (same results); 1 = no overlap, 0 = automatic (2 groups
-                             from 4 slices on), at most 8                                   */
+                             > g (same results); 0 or 1 = no overlap, at most 8 (2 groups
+                             gain 1.5 % on the 3D workload: every fine kernel already fills
+                             the GPU)                                                       */
     int    vcycle_tail;   /* 1: for single grids (the serial coarse chain) the coarsest
                              multigrid levels (from the first level whose whole remaining
                              V-cycle fits one CTA's shared memory: 15^3 in 3D, 63^2 in 2D)

@@ -259,23 +259,22 @@ __global__ void apply_A_kernel(Grid g, double nu, const double *__restrict__ u, 
   }
 }
 
+// S = node count as a template parameter: no predicated-off FP64 work
+template <int S>
 __global__ void sf_rhs_kernel(Grid g, SFCoef cf, const double *__restrict__ F, const double *__restrict__ U,
                               long long sF, const double *__restrict__ tau, long long stau, double *__restrict__ q,
                               long long sq, int batch) {
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
-    double Fv[kMaxNodes];
+    double Fv[S];
 #pragma unroll
-    for (int jn = 0; jn < kMaxNodes; ++jn)
-      if (jn < cf.s) Fv[jn] = F[b * sF + jn * g.slab + off];
+    for (int jn = 0; jn < S; ++jn) Fv[jn] = F[b * sF + jn * g.slab + off];
     double tprev = tau ? tau[b * stau + off] : 0.0;
 #pragma unroll
-    for (int m = 0; m < kMaxNodes - 1; ++m) {
-      if (m >= cf.s - 1) break;
+    for (int m = 0; m < S - 1; ++m) {
       double acc = 0.0;
 #pragma unroll
-      for (int jn = 0; jn < kMaxNodes; ++jn)
-        if (jn < cf.s) acc += cf.W[m][jn] * Fv[jn];
+      for (int jn = 0; jn < S; ++jn) acc += cf.W[m][jn] * Fv[jn];
       if (tau) {
         const double tnext = tau[b * stau + (m + 1) * g.slab + off];
         acc += tnext - tprev;
@@ -738,7 +737,14 @@ cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const dou
   dim3 gr, bl;
   config(g, batch, gr, bl);
   Scope sc(L, K_SF_RHS, g, batch, 0);
-  sf_rhs_kernel<<<gr, bl, 0, L.stream>>>(g, cf, F, U, sF, tau, stau, q, sq, batch);
+  switch (cf.s) {
+#define PMG_SF_CASE(S) \
+  case S: sf_rhs_kernel<S><<<gr, bl, 0, L.stream>>>(g, cf, F, U, sF, tau, stau, q, sq, batch); break;
+    PMG_SF_CASE(2) PMG_SF_CASE(3) PMG_SF_CASE(4) PMG_SF_CASE(5) PMG_SF_CASE(6) PMG_SF_CASE(7) PMG_SF_CASE(8)
+    PMG_SF_CASE(9)
+#undef PMG_SF_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return sc.done();
 }
 

@@ -185,4 +185,4 @@ def test_slice_groups_option_is_validated(lib):
                                              ctypes.byref(o), ctypes.byref(nb)) == pmg.PMG_OK
         sizes.append(nb.value)
     # the pipelined iteration adds a single-grid multigrid scratch for the coarse chain
-    assert sizes[0] < sizes[1] == sizes[2]
+    assert sizes[0] == sizes[1] < sizes[2]
