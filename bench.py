@@ -446,7 +446,8 @@ def run_ours(args):
     for lev in range(8):
         try:
             fz, prm, thr = pmg.pfasst_mg_tuning(s.h, lev, 0)
-            tuning.append(f"L{lev}:{'fused z' + str(prm or 32) + ' x' + str(thr) if fz else 'point x' + str(prm)}")
+            kind = {0: f"point x{prm}", 1: f"fused z{prm or 32} x{thr}", 2: f"tma z{prm}"}.get(fz, "?")
+            tuning.append(f"L{lev}:{kind}")
         except pmg.PMGError:
             break
 

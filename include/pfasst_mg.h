@@ -167,9 +167,15 @@ long long pfasst_mg_launch_count(pmg_handle h);
 
 /* Smoother chosen for multigrid level `level` (0 = finest) of the handle's hierarchy,
  * for wide batches (narrow = 0) or a single grid (narrow = 1): *fused = 1 for the fused
- * 3D red-black sweep (then *param = z chunk, 0 = default, and *threads per CTA), 0 for
- * the one-point-per-thread kernels (*param = threads per block). */
+ * 3D red-black sweep (then *param = z chunk, 0 = default, and *threads per CTA), 2 for
+ * its variant with TMA-staged planes (FP32), 0 for the one-point-per-thread kernels
+ * (*param = threads per block). */
 int pfasst_mg_tuning(pmg_handle h, int level, int narrow, int *fused, int *param, int *threads);
+
+/* Pin the smoother variant of a level (same encoding as pfasst_mg_tuning; the exact
+ * coarsest level has none).  Later iterations use it (captured graphs are rebuilt).
+ * Errors: INVALID_ARG, UNSUPPORTED (a variant the level or precision cannot run). */
+int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int param, int threads);
 
 /* ---- launch profiling ------------------------------------------------------ */
 

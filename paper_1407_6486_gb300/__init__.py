@@ -129,6 +129,7 @@ def load() -> ctypes.CDLL:
     L.pfasst_mg_batch_run.argtypes = [_P, _I, _I, _P]
     L.pfasst_mg_batch_get_solution.argtypes = [_P, _I, _P, _I]
     L.pfasst_mg_tuning.argtypes = [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
+    L.pfasst_mg_set_tuning.argtypes = [_P, _I, _I, _I, _I, _I]
     L.pfasst_mg_profile.argtypes = [_P, _I, ctypes.c_longlong]
     L.pfasst_mg_profile_read.argtypes = [_P, ctypes.POINTER(pmg_kernel_stat), _I, ctypes.POINTER(_I)]
     L.pfasst_mg_kernel_name.argtypes = [_I]
@@ -302,6 +303,10 @@ def pfasst_mg_tuning(h, level, narrow=0):
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().pfasst_mg_tuning(h, level, narrow, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
     return a.value, b.value, c.value
+
+
+def pfasst_mg_set_tuning(h, level, narrow, fused, param, threads=256):
+    _check(load().pfasst_mg_set_tuning(h, level, narrow, fused, param, threads), h)
 
 
 def pfasst_mg_profile(h, enable, min_points=0):

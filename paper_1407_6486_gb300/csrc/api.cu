@@ -134,8 +134,9 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ----------------------------------------------------------------- hierarchy
 
-// Smoother choice of one level: the fused red-black z-marching sweep (param = z chunk,
-// 0 = default) or the one-point-per-thread kernels (param = threads per block).
+// Smoother choice of one level: the fused red-black z-marching sweep (fused = 1; param =
+// z chunk, 0 = default), its TMA-staged variant (fused = 2, FP32), or the
+// one-point-per-thread kernels (fused = 0; param = threads per block).
 struct Tune {
   int fused = 0;
   int param = 256;    // per-point kernels: threads per block; fused sweep: z chunk (0 = default)
@@ -398,6 +399,11 @@ int smooth_with(MGCtx &M, const Tune &t, int l, int B, double c, void *&cur, boo
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
     PMG_CUDA(M.h, k_smooth_jacobi(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], B, first, t.param));
     cur = out;
+  } else if (t.fused == 2) {
+    void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
+    PMG_CUDA(M.h, k_rbgs_sweep3d_tma(M.L, H.lev[l], c, o.omega, cur, out, H.f[l], u_upd, su, B, first,
+                                     u_upd != nullptr, t.param));
+    cur = out;
   } else if (t.fused) {
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
     PMG_CUDA(M.h, k_rbgs_sweep3d(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], u_upd, su, B, first,
@@ -598,6 +604,9 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
             cand.push_back(Tune{1, zc, 256});
             if (g.pitch >= 128) cand.push_back(Tune{1, zc, 512});
           }
+      if (M.o->smoother == PMG_SMOOTHER_RBGS && rbgs_tma_supported(g, H.pr))
+        for (int zc : {16, 32, 64})
+          if (zc <= g.n) cand.push_back(Tune{2, zc, 512});
       float best = 1e30f;
       Tune pick = H.tune[l][cls];
       for (const Tune &t : cand) {
@@ -1182,6 +1191,7 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
     else PMG_RET(iteration(h));
     h->q_valid = ffree(h);
     PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (sweep_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a TMA-staged sweep timed out waiting for its loads");
     if (!h->g_iter.recs.empty() && use_graphs(h)) PMG_RET(harvest(h, h->g_iter));
     res = 0.0;
     for (int p = 0; p < h->P; ++p) {
@@ -1253,6 +1263,29 @@ int pfasst_mg_tuning(pmg_handle h, int level, int narrow, int *fused, int *param
   *fused = t.fused;
   *param = t.param;
   *threads = t.threads;
+  return PMG_OK;
+}
+
+int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int param, int threads) {
+  if (!h || !h->kids.empty() || level < 0 || level >= h->H.L - 1 || fused < 0 || fused > 2)
+    return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  const Grid &g = h->H.lev[level];
+  Tune t{fused, param, threads};
+  if (fused == 0 && (param < 32 || param > 1024 || param % 32)) return fail(h, PMG_ERR_INVALID_ARG, "threads per block");
+  if (fused >= 1) {
+    if (h->opt.smoother != PMG_SMOOTHER_RBGS || g.dim != 3 || g.n < 15 || param < 0 || param > g.n)
+      return fail(h, PMG_ERR_UNSUPPORTED, "the fused sweep needs 3D red-black Gauss-Seidel, n >= 15, 0 <= z chunk <= n");
+    if (fused == 1 && threads != 256 && !(threads == 512 && g.pitch >= 128))
+      return fail(h, PMG_ERR_INVALID_ARG, "fused sweep threads: 256, or 512 for rows of >= 128");
+    if (fused == 2 && !rbgs_tma_supported(g, h->H.pr))
+      return fail(h, PMG_ERR_UNSUPPORTED, "the TMA-staged sweep needs FP32 (mixed precision) and n = 127 or 255");
+    if (fused == 2) t.threads = 512;
+  }
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h->g_pred);
+  drop_graph(h->g_iter);
+  h->H.tune[level][narrow ? 1 : 0] = t;
+  if (h->groups > 1 && narrow) h->Hc.tune[level][0] = h->Hc.tune[level][1] = t;
   return PMG_OK;
 }
 

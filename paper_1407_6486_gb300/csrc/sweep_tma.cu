@@ -1,0 +1,336 @@
+// sweep_tma.cu -- red-black Gauss-Seidel sweep of (I - c Lap_h) e = f on batched 3D
+// grids with TMA-staged planes (FP32, rows of 128 or 256 elements).
+//
+// The same sweep as rbgs_rows3d_kernel in stencil3d.cu (one pass: the red half-sweep
+// on plane k, then the black half-sweep on plane k-1, marching along z; out of place
+// e_in -> e_out, from e = 0, or fused with u += e), but the planes are not fetched by
+// the threads: one elected thread streams each z-plane tile of e_in (rows y0-2 ..
+// y0+FTY+1) and of f (rows y0-1 .. y0+FTY) into a ring of shared-memory slots with
+// cp.async.bulk.tensor, DEPTH planes ahead of the computation, completing on one
+// mbarrier per slot.  The tensor-map box covers whole rows (x = 0, 16-byte aligned); rows and
+// planes outside the grid arrive as zeros (the Dirichlet wall).  The threads only
+// compute, which keeps their register count low and the loads deep.
+//
+// Every wait on an mbarrier is bounded (about 2 s of SM clock); on a timeout the
+// kernel records the fact in a device flag, stops at the end of the current plane and
+// returns; the host turns the flag into PMG_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "pmg_internal.cuh"
+
+namespace pmg {
+namespace {
+
+constexpr int TTY = 8;             // output rows per tile
+constexpr int TEY = TTY + 4;       // e_in rows staged per plane (y0-2 .. y0+TTY+1)
+constexpr int TMY = TTY + 2;       // red / f rows (y0-1 .. y0+TTY)
+constexpr int DEPTH = 1;           // planes in flight ahead of the computation
+constexpr int NE = 3 + DEPTH;      // e_in slots: planes k-1, k, k+1 in use, DEPTH more in flight
+constexpr int NF = 2 + DEPTH;      // f slots: planes k-1, k in use, DEPTH more in flight
+constexpr int TNT = 512;           // threads per CTA (two CTAs per SM: ~108 KB of ring each)
+constexpr int TZC = 32;            // default z planes per CTA
+
+__device__ int g_sweep_timeout;    // set by a timed-out mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait for the completion of phase `parity` of a barrier
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (clock64() - t0 > 4000000000LL) return false;  // ~2 s at 2 GHz
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// 4D tiled TMA load (x, y, z, batch) of one box into shared memory, completing on bar
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int NX, bool ZERO, bool UPD>
+__global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant__ CUtensorMap tme,
+                                                          const __grid_constant__ CUtensorMap tmf, Grid g, float a,
+                                                          float iD, float omega, float *__restrict__ eout,
+                                                          double *__restrict__ u, long long su, int nzc, int zchunk) {
+  constexpr int NP = NX / 2;          // x-pairs per row
+  constexpr int RS = TNT / NP;        // rows per round of the CTA
+  constexpr int PF = (TMY + RS - 1) / RS, PB = (TTY + RS - 1) / RS;
+  constexpr uint32_t EB = TEY * NX * 4, FB = TMY * NX * 4;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float2(*E)[TEY][NP] = (float2(*)[TEY][NP])sm;                                   // [NE]
+  float2(*Fs)[TMY][NP] = (float2(*)[TMY][NP])(sm + NE * EB);                       // [NF]
+  float2(*M)[TMY][NP] = (float2(*)[TMY][NP])(sm + NE * EB + NF * FB);              // [3]
+  uint64_t *bar = (uint64_t *)(sm + NE * EB + NF * FB + 3 * FB);                   // [NE + NF]
+  __shared__ int s_bad;
+  const int n = g.n, tid = threadIdx.x, px = tid % NP, ry = tid / NP, lane = tid & 31;
+  const int y0 = blockIdx.y * TTY;
+  const int zc = blockIdx.z % nzc, b = blockIdx.z / nzc;
+  const int z0 = zc * zchunk, z1 = min(z0 + zchunk, n);
+  const long long plane = (long long)g.ny * g.pitch;
+  const unsigned full = 0xffffffffu;
+  // ring positions: e plane p in slot (p - z0 + 2) % NE, f plane p in slot (p - z0 + 1) % NF;
+  // the j-th use of a slot completes phase j of its barrier
+  auto eslot = [&](int p) { return (p - z0 + 2) % NE; };
+  auto fslot = [&](int p) { return (p - z0 + 1) % NF; };
+  auto issue_e = [&](int p) {
+    const int s = eslot(p);
+    mbar_expect_tx(&bar[s], EB);
+    tma_load_4d(&E[s][0][0], &tme, 0, y0 - 2, p, b, &bar[s]);
+  };
+  auto issue_f = [&](int p) {
+    const int s = fslot(p);
+    mbar_expect_tx(&bar[NE + s], FB);
+    tma_load_4d(&Fs[s][0][0], &tmf, 0, y0 - 1, p, b, &bar[NE + s]);
+  };
+  auto wait_e = [&](int p) { return mbar_wait(&bar[eslot(p)], ((p - z0 + 2) / NE) & 1); };
+  auto wait_f = [&](int p) { return mbar_wait(&bar[NE + fslot(p)], ((p - z0 + 1) / NF) & 1); };
+  // x neighbours of the pair c in smem row `row` (lanes, or smem at a warp edge, or 0)
+  auto xnb = [&](float2 c, const float2 *row, float &left, float &right) {
+    const float l = __shfl_up_sync(full, c.y, 1), r = __shfl_down_sync(full, c.x, 1);
+    left = lane != 0 ? l : (px > 0 ? row[px - 1].y : 0.f);
+    right = lane != 31 ? r : (px < NP - 1 ? row[px + 1].x : 0.f);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < NE + NF; ++i) mbar_init(&bar[i]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_bad = 0;
+    if (!ZERO)
+      for (int p = z0 - 2; p <= min(z0 - 1 + DEPTH, z1 + 1); ++p) issue_e(p);
+    for (int p = z0 - 1; p <= min(z0 - 2 + DEPTH, z1); ++p) issue_f(p);
+  }
+  __syncthreads();
+  bool ok = true;
+  if (!ZERO) ok = wait_e(z0 - 2) && wait_e(z0 - 1);
+  for (int k = z0 - 1; k <= z1; ++k) {
+    if (tid == 0) {  // refill the slots the previous plane released
+      if (!ZERO && k + 1 + DEPTH <= z1 + 1) issue_e(k + 1 + DEPTH);
+      if (k + DEPTH <= z1) issue_f(k + DEPTH);
+    }
+    if (ok && !ZERO) ok = wait_e(k + 1);
+    if (ok) ok = wait_f(k);
+    if (!ok) s_bad = 1;
+    {  // red half-sweep on plane k, rows y0-1 .. y0+TTY
+      const int se = eslot(k), sl = eslot(k - 1), sh = eslot(k + 1), sf = fslot(k), s3 = (k + 3) % 3;
+      const bool kin = k >= 0 && k < n;
+#pragma unroll
+      for (int h = 0; h < PF; ++h) {
+        const int r = ry + RS * h;
+        if (r >= TMY) break;  // uniform per warp (a warp lies in one row)
+        const int y = y0 - 1 + r;
+        float2 out = make_float2(0.f, 0.f);
+        const bool yin = kin && y >= 0 && y < n;
+        const float2 fv = Fs[sf][r][px];
+        const int ro = ((y + k) & 1) ? 0 : 1;  // red: x + y + k odd
+        const int xr = 2 * px + ro;
+        if (ZERO) {
+          const float v = (yin && xr < n) ? omega * ((ro ? fv.y : fv.x) * iD) : 0.f;
+          if (ro) out.y = v; else out.x = v;
+        } else {
+          const float2 c = E[se][r + 1][px];
+          float left, right;
+          xnb(c, E[se][r + 1], left, right);
+          if (yin) {
+            const float2 up = E[se][r][px], dn = E[se][r + 2][px], zl = E[sl][r + 1][px], zh = E[sh][r + 1][px];
+            out = c;
+            if (xr < n) {
+              float nb, fr, old;
+              if (ro == 0) {
+                nb = left + c.y + up.x + dn.x + zl.x + zh.x;
+                fr = fv.x;
+                old = c.x;
+              } else {
+                nb = c.x + right + up.y + dn.y + zl.y + zh.y;
+                fr = fv.y;
+                old = c.y;
+              }
+              const float gs = (fr + a * nb) * iD;
+              const float v = omega == 1.f ? gs : old + omega * (gs - old);
+              if (ro) out.y = v; else out.x = v;
+            }
+          }
+        }
+        M[s3][r][px] = out;
+      }
+    }
+    __syncthreads();
+    const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+TTY-1
+    if (kb >= z0 && kb < z1) {
+      const int s0 = (kb + 3) % 3, sl = (kb + 2) % 3, sh = (kb + 4) % 3, se = eslot(kb), sf = fslot(kb);
+#pragma unroll
+      for (int h = 0; h < PB; ++h) {
+        const int r = ry + RS * h;
+        if (r >= TTY) break;
+        const int y = y0 + r;
+        const float2 c = M[s0][r + 1][px];
+        float left, right;
+        xnb(c, M[s0][r + 1], left, right);
+        if (y >= n) continue;
+        const float2 up = M[s0][r][px], dn = M[s0][r + 2][px], zl = M[sl][r + 1][px], zh = M[sh][r + 1][px];
+        const float2 fv = Fs[sf][r + 1][px];
+        const int bo = ((y + kb) & 1) ? 1 : 0;  // black: x + y + kb even
+        float2 out = c;
+        const int xb = 2 * px + bo;
+        if (xb < n) {
+          float nb, fr, old;
+          if (bo == 0) {
+            nb = left + c.y + up.x + dn.x + zl.x + zh.x;
+            fr = fv.x;
+            old = ZERO ? 0.f : E[se][r + 2][px].x;
+          } else {
+            nb = c.x + right + up.y + dn.y + zl.y + zh.y;
+            fr = fv.y;
+            old = ZERO ? 0.f : E[se][r + 2][px].y;
+          }
+          const float gs = (fr + a * nb) * iD;
+          const float v = omega == 1.f ? gs : old + omega * (gs - old);
+          if (bo) out.y = v; else out.x = v;
+        }
+        const long long o = kb * plane + (long long)y * g.pitch + 2 * px;
+        if (UPD) {
+          double2 *up2 = (double2 *)(u + b * su + o);
+          double2 w = *up2;
+          w.x += (double)out.x;
+          w.y += (double)out.y;
+          *up2 = w;
+        } else {
+          *(float2 *)(eout + b * g.slab + o) = out;
+        }
+      }
+    }
+    __syncthreads();  // slots of plane k-1 may be refilled now
+    if (s_bad) break;  // uniform: read after the barrier
+  }
+  if (s_bad && tid == 0) {
+    atomicExch(&g_sweep_timeout, 1);
+    // let loads still in flight land before the CTA's shared memory is released
+    for (int i = 0; i < NE + NF; ++i) {
+      const long long t0 = clock64();
+      while (clock64() - t0 < 200000) __nanosleep(64);
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// tensor map of a batch of padded grid functions: dims (pitch, n, n, batch), box of
+// `rows` whole rows of one plane
+bool make_map(CUtensorMap *m, const void *base, const Grid &g, int batch, int rows) {
+  auto enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.ny * g.pitch * 4, (cuuint64_t)g.slab * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)g.pitch, (cuuint32_t)rows, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NX, bool ZERO, bool UPD>
+cudaError_t launch_tma(const Launch &L, const Grid &g, float a, float iD, float omega, const void *ein, void *eout,
+                       const void *f, double *u, long long su, int batch, int zchunk) {
+  constexpr uint32_t EB = TEY * NX * 4, FB = TMY * NX * 4;
+  const size_t smem = NE * EB + NF * FB + 3 * FB + (NE + NF) * 8;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(rbgs_tma_kernel<NX, ZERO, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap me, mf;
+  if (!make_map(&mf, f, g, batch, TMY)) return cudaErrorInvalidValue;
+  if (!make_map(&me, ZERO ? f : ein, g, batch, TEY)) return cudaErrorInvalidValue;  // unused when ZERO
+  if (zchunk <= 0) zchunk = TZC;
+  const int nty = (g.n + TTY - 1) / TTY, nzc = (g.n + zchunk - 1) / zchunk;
+  dim3 gr(1, nty, nzc * batch);
+  rbgs_tma_kernel<NX, ZERO, UPD><<<gr, TNT, smem, L.stream>>>(me, mf, g, a, iD, omega, (float *)eout, u, su, nzc,
+                                                               zchunk);
+  return cudaGetLastError();
+}
+
+template <bool ZERO, bool UPD>
+cudaError_t launch_tma_pitch(const Launch &L, const Grid &g, float a, float iD, float omega, const void *ein,
+                             void *eout, const void *f, double *u, long long su, int batch, int zchunk) {
+  if (g.pitch == 256) return launch_tma<256, ZERO, UPD>(L, g, a, iD, omega, ein, eout, f, u, su, batch, zchunk);
+  return launch_tma<128, ZERO, UPD>(L, g, a, iD, omega, ein, eout, f, u, su, batch, zchunk);
+}
+
+}  // namespace
+
+bool rbgs_tma_supported(const Grid &g, Prec pr) {
+  return pr == F32 && g.dim == 3 && (g.pitch == 128 || g.pitch == 256) && encoder() != nullptr;
+}
+
+cudaError_t k_rbgs_sweep3d_tma(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout,
+                               const void *f, double *u, long long su, int batch, bool zero, bool update_u,
+                               int zchunk) {
+  Scope sc(L, zero ? K_RBGS3D_ZERO : (update_u ? K_RBGS3D_UPD : K_RBGS3D), g, batch, F32);
+  const float a = (float)(c * g.ih2), D = 1.f + 6.f * a, iD = 1.f / D, w = (float)omega;
+  cudaError_t e;
+  if (zero && update_u) e = launch_tma_pitch<true, true>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+  else if (zero) e = launch_tma_pitch<true, false>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+  else if (update_u) e = launch_tma_pitch<false, true>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+  else e = launch_tma_pitch<false, false>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+  cudaError_t e2 = sc.done();
+  return e != cudaSuccess ? e : e2;
+}
+
+int sweep_timeouts() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_sweep_timeout, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_sweep_timeout, &zero, sizeof(int));
+  }
+  return v;
+}
+
+}  // namespace pmg

@@ -335,3 +335,24 @@ def test_vcycle_tail_matches_per_level_kernels(dim, n, precision):
         s.close()
     rel = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0])
     assert rel <= (1e-12 if precision == 0 else 1e-5), rel
+
+
+@pytest.mark.parametrize("n,level,zchunk", [(127, 0, 32), (255, 1, 16), (127, 0, 7)])
+def test_tma_staged_sweep_matches_the_fused_sweep(n, level, zchunk):
+    """The TMA-staged sweep (planes streamed by cp.async.bulk.tensor into a shared-memory
+    ring) computes the same red-black sweep as the register-prefetch fused kernel: PFASST
+    iterates agree to FP32 rounding."""
+    wl = inputs.heat3d_c3(n=n, slices=2)
+    out = []
+    for fused, param, threads in ((1, zchunk, 256), (2, zchunk, 512)):
+        s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                             smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, precision=1, autotune=0)
+        for narrow in (0, 1):
+            pmg.pfasst_mg_set_tuning(s.h, level, narrow, fused, param, threads)
+        assert pmg.pfasst_mg_tuning(s.h, level, 0) == (fused, param, threads)
+        s.set_initial(wl.u0())
+        s.iterate(2, 0.0)
+        out.append(s.state(0))
+        s.close()
+    rel = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0])
+    assert rel <= 1e-6, rel
