@@ -606,7 +606,7 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
           }
       if (M.o->smoother == PMG_SMOOTHER_RBGS && rbgs_tma_supported(g, H.pr))
         for (int zc : {16, 32, 64})
-          if (zc <= g.n) cand.push_back(Tune{2, zc, 512});
+          if (zc <= g.n) cand.push_back(Tune{2, zc, rbgs_tma_threads()});
       float best = 1e30f;
       Tune pick = H.tune[l][cls];
       for (const Tune &t : cand) {
@@ -1279,7 +1279,7 @@ int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int par
       return fail(h, PMG_ERR_INVALID_ARG, "fused sweep threads: 256, or 512 for rows of >= 128");
     if (fused == 2 && !rbgs_tma_supported(g, h->H.pr))
       return fail(h, PMG_ERR_UNSUPPORTED, "the TMA-staged sweep needs FP32 (mixed precision) and n = 127 or 255");
-    if (fused == 2) t.threads = 512;
+    if (fused == 2) t.threads = rbgs_tma_threads();
   }
   PMG_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graph(h->g_pred);

@@ -201,6 +201,7 @@ cudaError_t k_rbgs_sweep3d(const Launch &L, const Grid &g, double c, double omeg
 bool rbgs_rows_supported(const Grid &g);
 // the same fused sweep with TMA-staged planes (sweep_tma.cu): FP32, pitch 128 or 256
 bool rbgs_tma_supported(const Grid &g, Prec pr);
+int rbgs_tma_threads();
 cudaError_t k_rbgs_sweep3d_tma(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout,
                                const void *f, double *u, long long su, int batch, bool zero, bool update_u,
                                int zchunk);

@@ -349,7 +349,7 @@ def test_tma_staged_sweep_matches_the_fused_sweep(n, level, zchunk):
                              smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, precision=1, autotune=0)
         for narrow in (0, 1):
             pmg.pfasst_mg_set_tuning(s.h, level, narrow, fused, param, threads)
-        assert pmg.pfasst_mg_tuning(s.h, level, 0) == (fused, param, threads)
+        assert pmg.pfasst_mg_tuning(s.h, level, 0)[:2] == (fused, param)
         s.set_initial(wl.u0())
         s.iterate(2, 0.0)
         out.append(s.state(0))
