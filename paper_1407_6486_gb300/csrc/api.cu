@@ -707,10 +707,14 @@ int coarse_receive(pmg_ctx *h, int p0, int B) {
   return PMG_OK;
 }
 
-int interp_all(pmg_ctx *h) {
+// m0 = 1 inside an iteration: the send-forward that follows overwrites node 0 of slices
+// p >= 1, and for slice 0 the coarse correction at node 0 is exactly zero (its coarse
+// node 0 is the restricted initial value, which no sweep changes)
+int interp_all(pmg_ctx *h, int m0 = 0) {
   const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
-  PMG_CUDA(h, k_interp_time(h->L(), h->gc, h->interp, h->H.pr, h->Uc, h->Uc0, scs, h->dU, h->P));
-  PMG_CUDA(h, k_interp_space_add(h->L(), h->gf, h->gc, h->opt.interp_order, h->sf, h->H.pr, h->dU, h->Uf, sfs, h->P));
+  PMG_CUDA(h, k_interp_time(h->L(), h->gc, h->interp, h->H.pr, h->Uc, h->Uc0, scs, h->dU, h->P, m0));
+  PMG_CUDA(h, k_interp_space_add(h->L(), h->gf, h->gc, h->opt.interp_order, h->sf, h->H.pr, h->dU, h->Uf, sfs, h->P,
+                                 m0));
   if (!ffree(h)) PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf, h->gf.slab, h->Ff, h->gf.slab, h->P * h->sf));
   return PMG_OK;
 }
@@ -805,9 +809,9 @@ int fas_part(pmg_ctx *h, int p0, int B) {
 int interp_part(pmg_ctx *h, int p0, int B) {
   const long long sfs = (long long)h->sf * h->gf.slab, scs = (long long)h->sc * h->gc.slab;
   void *dU = (char *)h->dU + (size_t)p0 * h->sf * h->gc.slab * h->H.tsize;
-  PMG_CUDA(h, k_interp_time(h->L(), h->gc, h->interp, h->H.pr, h->Uc + p0 * scs, h->Uc0 + p0 * scs, scs, dU, B));
+  PMG_CUDA(h, k_interp_time(h->L(), h->gc, h->interp, h->H.pr, h->Uc + p0 * scs, h->Uc0 + p0 * scs, scs, dU, B, 1));
   PMG_CUDA(h, k_interp_space_add(h->L(), h->gf, h->gc, h->opt.interp_order, h->sf, h->H.pr, dU, h->Uf + p0 * sfs,
-                                 sfs, B));
+                                 sfs, B, 1));
   return PMG_OK;
 }
 
@@ -902,7 +906,7 @@ int iteration(pmg_ctx *h) {
       if (p > 0) PMG_RET(coarse_receive(h, p, 1));
       PMG_RET(sweep(h, 1, p, 1));
     }
-    PMG_RET(interp_all(h));
+    PMG_RET(interp_all(h, 1));
   }
   if (h->P > 1) {  // send forward: U_f[p][0] <- U_f[p-1][M_f]
     PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + (h->sf - 1) * h->gf.slab, sfs, h->Uf + sfs, sfs, h->P - 1));

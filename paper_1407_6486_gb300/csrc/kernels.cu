@@ -326,7 +326,8 @@ __global__ void fas_restrict_kernel(Grid gf, Grid gc, FASCoef cf, const double *
 // dU_m = sum_j T[m][j] (U_c,j - U_c0,j) for every fine node m (stored as T)
 template <typename T>
 __global__ void interp_time_kernel(Grid gc, InterpCoef cf, const double *__restrict__ Uc,
-                                   const double *__restrict__ Uc0, long long scoarse, T *__restrict__ dU, int batch) {
+                                   const double *__restrict__ Uc0, long long scoarse, T *__restrict__ dU, int batch,
+                                   int m0) {
   PMG_FOR_POINTS(gc, batch) {
     PMG_POINT(gc);
     double d[kMaxNodes];
@@ -336,7 +337,7 @@ __global__ void interp_time_kernel(Grid gc, InterpCoef cf, const double *__restr
       const long long co = b * scoarse + jn * gc.slab + off;
       d[jn] = Uc[co] - Uc0[co];
     }
-    for (int m = 0; m < cf.sf; ++m) {
+    for (int m = m0; m < cf.sf; ++m) {
       double acc = 0.0;
 #pragma unroll
       for (int jn = 0; jn < kMaxNodes; ++jn)
@@ -375,7 +376,7 @@ __device__ __forceinline__ int interp_taps_raw(int order, int i, int *J, float *
 constexpr int ITX = 32, ITY = 8, ITZ = 8;
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256) interp_space_kernel(Grid gf, Grid gc, int order, int sf, const T *__restrict__ dU,
-                                                           double *__restrict__ Uf, long long sfine, int ntz) {
+                                                           double *__restrict__ Uf, long long sfine, int ntz, int m0) {
   constexpr int TY = DIM >= 2 ? ITY : 1, TZ = DIM >= 3 ? ITZ : 1;
   constexpr int CX = ITX / 2 + 4, CY = DIM >= 2 ? ITY / 2 + 4 : 1, CZ = DIM >= 3 ? ITZ / 2 + 4 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(256) interp_space_kernel(Grid gf, Grid gc, int
   const int zt = blockIdx.z % ntz, b = blockIdx.z / ntz, z0 = zt * TZ;
   const int cx0 = x0 / 2 - 1, cy0 = DIM >= 2 ? y0 / 2 - 1 : 1, cz0 = DIM >= 3 ? z0 / 2 - 1 : 1;
   const int nc = gc.n, tid = threadIdx.x;
-  for (int m = 0; m < sf; ++m) {
+  for (int m = m0; m < sf; ++m) {
     const T *src = dU + ((long long)b * sf + m) * gc.slab;
     for (int q = tid; q < CZ * CY * CX; q += blockDim.x) {
       const int a = q % CX, bb = (q / CX) % CY, cc = q / (CX * CY);
@@ -760,20 +761,20 @@ cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, cons
 }
 
 cudaError_t k_interp_time(const Launch &L, const Grid &gc, const InterpCoef &cf, Prec pr, const double *Uc,
-                          const double *Uc0, long long scoarse, void *dU, int batch) {
+                          const double *Uc0, long long scoarse, void *dU, int batch, int m0) {
   dim3 gr, bl;
   config(gc, batch, gr, bl);
   Scope sc(L, K_INTERP_T, gc, batch, pr);
   if (pr == F64)
-    interp_time_kernel<double><<<gr, bl, 0, L.stream>>>(gc, cf, Uc, Uc0, scoarse, (double *)dU, batch);
+    interp_time_kernel<double><<<gr, bl, 0, L.stream>>>(gc, cf, Uc, Uc0, scoarse, (double *)dU, batch, m0);
   else
-    interp_time_kernel<float><<<gr, bl, 0, L.stream>>>(gc, cf, Uc, Uc0, scoarse, (float *)dU, batch);
+    interp_time_kernel<float><<<gr, bl, 0, L.stream>>>(gc, cf, Uc, Uc0, scoarse, (float *)dU, batch, m0);
   return sc.done();
 }
 
 template <int D, typename T>
 cudaError_t launch_interp_space(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, const void *dU,
-                                double *Uf, long long sfine, int batch) {
+                                double *Uf, long long sfine, int batch, int m0) {
   constexpr int TY = D >= 2 ? ITY : 1, TZ = D >= 3 ? ITZ : 1;
   constexpr int CX = ITX / 2 + 4, CY = D >= 2 ? ITY / 2 + 4 : 1, CZ = D >= 3 ? ITZ / 2 + 4 : 1;
   const size_t smem = sizeof(T) * (CZ * CY * CX + CZ * CY * ITX + CZ * TY * ITX);
@@ -784,17 +785,17 @@ cudaError_t launch_interp_space(const Launch &L, const Grid &gf, const Grid &gc,
   }
   const int ntx = (gf.n + ITX - 1) / ITX, nty = (gf.ny + TY - 1) / TY, ntz = (gf.nz + TZ - 1) / TZ;
   dim3 gr(ntx, nty, ntz * batch);
-  interp_space_kernel<D, T><<<gr, 256, smem, L.stream>>>(gf, gc, order, sf, (const T *)dU, Uf, sfine, ntz);
+  interp_space_kernel<D, T><<<gr, 256, smem, L.stream>>>(gf, gc, order, sf, (const T *)dU, Uf, sfine, ntz, m0);
   return cudaSuccess;
 }
 
 cudaError_t k_interp_space_add(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, Prec pr,
-                               const void *dU, double *Uf, long long sfine, int batch) {
-  Scope sc(L, K_INTERP, gf, batch * sf, pr);
+                               const void *dU, double *Uf, long long sfine, int batch, int m0) {
+  Scope sc(L, K_INTERP, gf, batch * (sf - m0), pr);
   if (pr == F64)
-    PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, double>(L, gf, gc, order, sf, dU, Uf, sfine, batch)))
+    PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, double>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0)))
   else
-    PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, float>(L, gf, gc, order, sf, dU, Uf, sfine, batch)))
+    PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, float>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0)))
   return sc.done();
 }
 

@@ -223,11 +223,12 @@ cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, cons
                            const double *Ff, long long sfine, double *Uc, double *Fc, double *tau, double *Uc0,
                            long long scoarse, int batch);
 // coarse-correction interpolation in two steps: in time on the coarse grid (dU in the
-// precision pr), then in space onto every fine node, added to U_f
+// precision pr), then in space onto every fine node m >= m0, added to U_f (m0 = 1 when
+// the fine node 0 is overwritten by the send-forward right after)
 cudaError_t k_interp_time(const Launch &L, const Grid &gc, const InterpCoef &cf, Prec pr, const double *Uc,
-                          const double *Uc0, long long scoarse, void *dU, int batch);
+                          const double *Uc0, long long scoarse, void *dU, int batch, int m0 = 0);
 cudaError_t k_interp_space_add(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, Prec pr,
-                               const void *dU, double *Uf, long long sfine, int batch);
+                               const void *dU, double *Uf, long long sfine, int batch, int m0 = 0);
 // fine level without stored F (fixed V-cycle counts): residual + next right-hand sides
 cudaError_t k_fine_rhs_residual(const Launch &L, const Grid &g, const ResCoef &cf, double nu, const double *U,
                                 long long stride, double *q, long long sq, int batch, unsigned long long *res);
