@@ -650,13 +650,13 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
 bool ffree(const pmg_ctx *h) { return h->opt.vcycles > 0; }
 
 // collocation residual of the fine level into red[2P..3P) (+ next right-hand sides
-// when F-free), copied to hred asynchronously
-int fine_residual(pmg_ctx *h) {
+// when F-free), copied to hred asynchronously; `chained` right after a send-forward
+int fine_residual(pmg_ctx *h, bool chained = false) {
   const long long sfs = (long long)h->sf * h->gf.slab;
   PMG_CUDA(h, cudaMemsetAsync(h->red + 2 * h->P, 0, sizeof(unsigned long long) * h->P, h->stream));
   if (ffree(h))
     PMG_CUDA(h, k_fine_rhs_residual(h->L(), h->gf, h->resf, h->nu, h->Uf, sfs, h->qf, (long long)(h->sf - 1) * h->gf.slab,
-                                    h->P, h->red + 2 * h->P));
+                                    h->P, h->red + 2 * h->P, chained));
   else
     PMG_CUDA(h, k_colloc_residual(h->L(), h->gf, h->resf, h->Uf, h->Ff, sfs, h->P, h->red + 2 * h->P));
   PMG_CUDA(h, cudaMemcpyAsync(h->hred + 2 * h->P, h->red + 2 * h->P, sizeof(unsigned long long) * h->P,
@@ -829,7 +829,7 @@ int send_forward_part(pmg_ctx *h, int p0, int B) {
 int fine_residual_part(pmg_ctx *h, int p0, int B) {
   const long long sfs = (long long)h->sf * h->gf.slab, sq = (long long)(h->sf - 1) * h->gf.slab;
   PMG_CUDA(h, k_fine_rhs_residual(h->L(), h->gf, h->resf, h->nu, h->Uf + p0 * sfs, sfs, h->qf + p0 * sq, sq, B,
-                                  h->red + 2 * h->P + p0));
+                                  h->red + 2 * h->P + p0, true));
   return PMG_OK;
 }
 
@@ -912,7 +912,7 @@ int iteration(pmg_ctx *h) {
     PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + (h->sf - 1) * h->gf.slab, sfs, h->Uf + sfs, sfs, h->P - 1));
     if (!ffree(h)) PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf + sfs, sfs, h->Ff + sfs, sfs, h->P - 1));
   }
-  return fine_residual(h);
+  return fine_residual(h, true);
 }
 
 double bits_to_double(unsigned long long v) {

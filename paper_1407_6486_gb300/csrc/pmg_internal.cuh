@@ -230,8 +230,11 @@ cudaError_t k_interp_time(const Launch &L, const Grid &gc, const InterpCoef &cf,
 cudaError_t k_interp_space_add(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, Prec pr,
                                const void *dU, double *Uf, long long sfine, int batch, int m0 = 0);
 // fine level without stored F (fixed V-cycle counts): residual + next right-hand sides
+// chained: U[b][0] is a copy of U[b-1][S-1] for b >= 1 (after the send-forward); node 0's
+// Laplacian is then taken over from the previous slice (same results)
 cudaError_t k_fine_rhs_residual(const Launch &L, const Grid &g, const ResCoef &cf, double nu, const double *U,
-                                long long stride, double *q, long long sq, int batch, unsigned long long *res);
+                                long long stride, double *q, long long sq, int batch, unsigned long long *res,
+                                bool chained = false);
 cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
                              long long sfine, double *Uc, double *Fc, double *tau, double *Uc0, long long scoarse,
                              int batch);
