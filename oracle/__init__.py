@@ -43,14 +43,14 @@ class _MG(ctypes.Structure):
 
 class _Level(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("s", ctypes.c_int),
-                ("nu", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("family", ctypes.c_int)]
 
 
 class _PFASST(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n_f", ctypes.c_int), ("s_f", ctypes.c_int),
                 ("s_c", ctypes.c_int), ("slices", ctypes.c_int), ("nlevels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("nu", ctypes.c_double),
-                ("dt", ctypes.c_double), ("mg", _MG)]
+                ("dt", ctypes.c_double), ("mg", _MG), ("fam_f", ctypes.c_int), ("fam_c", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -113,10 +113,17 @@ def gauss_lobatto(s: int) -> np.ndarray:
     return t
 
 
-def qmatrix(s: int) -> np.ndarray:
-    t = gauss_lobatto(s)
+def nodes(s: int, family: int = 0) -> np.ndarray:
+    """family 0: Gauss-Lobatto; 1: uniform m/M, quadrature without the left endpoint."""
+    t = np.zeros(s)
+    assert lib().orc_nodes(s, family, _p(t)) == 0
+    return t
+
+
+def qmatrix(s: int, family: int = 0) -> np.ndarray:
+    t = nodes(s, family)
     Q = np.zeros((s, s))
-    assert lib().orc_qmatrix(s, _p(t), _p(Q)) == 0
+    assert lib().orc_qmatrix_family(s, family, _p(t), _p(Q)) == 0
     return Q
 
 
@@ -178,18 +185,18 @@ def mg_solve(mg: MGParams, dim: int, n: int, c: float, b: np.ndarray, u: np.ndar
     return u, cyc
 
 
-def sweep(dim, n, s, nu, dt, mg: MGParams, U, F, fas=None):
+def sweep(dim, n, s, nu, dt, mg: MGParams, U, F, fas=None, family=0):
     """One SDC sweep on one slice, in place on copies; returns (U, F, V-cycles)."""
     U = np.ascontiguousarray(U, dtype=np.float64).copy()
     F = np.ascontiguousarray(F, dtype=np.float64).copy()
-    L = _Level(dim, n, s, nu, dt)
+    L = _Level(dim, n, s, nu, dt, family)
     m = mg.c()
     cyc = lib().orc_sweep(ctypes.byref(L), ctypes.byref(m), _p(U), _p(F), _p(fas))
     return U, F, cyc
 
 
-def residual(dim, n, s, nu, dt, U, F, fas=None) -> float:
-    L = _Level(dim, n, s, nu, dt)
+def residual(dim, n, s, nu, dt, U, F, fas=None, family=0) -> float:
+    L = _Level(dim, n, s, nu, dt, family)
     return lib().orc_residual(ctypes.byref(L), _p(np.ascontiguousarray(U)), _p(np.ascontiguousarray(F)), _p(fas))
 
 
@@ -214,18 +221,21 @@ class PFASST:
     (slices, s_c, n_c^dim).  ``nlevels == 1`` gives (parallel) single-level SDC.
     """
 
-    def __init__(self, dim, n, s_f, s_c, slices, nu, dt, mg: MGParams, nlevels=2, interp_order=4):
+    def __init__(self, dim, n, s_f, s_c, slices, nu, dt, mg: MGParams, nlevels=2, interp_order=4, family=0,
+                 coarse_family=None):
         self.dim, self.n, self.s_f, self.s_c = dim, n, s_f, s_c
         self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
         self.mg = mg
+        fam_c = family if coarse_family is None else coarse_family
+        self.family, self.coarse_family = family, fam_c
         if nlevels > 1:
-            tf, tc = gauss_lobatto(s_f), gauss_lobatto(s_c)
+            tf, tc = nodes(s_f, family), nodes(s_c, fam_c)
             if not all(np.min(np.abs(tf - t)) < 1e-14 for t in tc):
                 raise ValueError("coarse nodes must be a subset of the fine nodes")
             if n < 7:
                 raise ValueError("two levels need n >= 7")
         self._c = _PFASST(dim, n, s_f, s_c if nlevels > 1 else 2, slices, nlevels,
-                          interp_order, nu, dt, mg.c())
+                          interp_order, nu, dt, mg.c(), family, fam_c)
         Nf = n ** dim
         nc = (n - 1) // 2
         Nc = max(nc, 1) ** dim

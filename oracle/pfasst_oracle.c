@@ -77,18 +77,33 @@ int orc_gauss_lobatto(int s, double *tau)
     return 0;
 }
 
-/* Q[m][j] = integral from 0 to tau_m of the Lagrange basis polynomial l_j
- * (Sec. 2.1: q_{m,i} chosen for the highest order; first row is zero).
- * The basis polynomial is expanded in monomials and integrated exactly. */
-int orc_qmatrix(int s, const double *tau, double *Q)
+/* Node families: 0 = Gauss-Lobatto (the workloads'), 1 = uniform nodes tau_m = m/M whose
+ * quadrature rule does not use the left endpoint (Sec. 3: the paper's second- and
+ * fourth-order methods; M = 1 is backward Euler). */
+int orc_nodes(int s, int family, double *tau)
 {
     if (s < 2 || s > ORC_MAXS) return -1;
-    for (int j = 0; j < s; ++j) {
+    if (family == 0) return orc_gauss_lobatto(s, tau);
+    if (family != 1) return -1;
+    for (int m = 0; m < s; ++m) tau[m] = (double)m / (double)(s - 1);
+    return 0;
+}
+
+/* Q[m][j] = integral from 0 to tau_m of the Lagrange basis polynomial l_j
+ * (Sec. 2.1: q_{m,i} chosen for the highest order; first row is zero).
+ * The basis polynomial is expanded in monomials and integrated exactly.  With
+ * first = 1 the interpolation nodes are tau_1..tau_{s-1} (the rule without the left
+ * endpoint) and column 0 is zero. */
+static int qmatrix_from(int s, int first, const double *tau, double *Q)
+{
+    if (s < 2 || s > ORC_MAXS) return -1;
+    for (int m = 0; m < s; ++m) Q[m * s] = 0.0;
+    for (int j = first; j < s; ++j) {
         long double c[ORC_MAXS + 1];
         memset(c, 0, sizeof c);
         c[0] = 1.0L;
         int deg = 0;
-        for (int i = 0; i < s; ++i) {
+        for (int i = first; i < s; ++i) {
             if (i == j) continue;
             long double den = (long double)tau[j] - (long double)tau[i];
             /* multiply c(x) by (x - tau_i)/den */
@@ -107,6 +122,14 @@ int orc_qmatrix(int s, const double *tau, double *Q)
         }
     }
     return 0;
+}
+
+int orc_qmatrix(int s, const double *tau, double *Q) { return qmatrix_from(s, 0, tau, Q); }
+
+int orc_qmatrix_family(int s, int family, const double *tau, double *Q)
+{
+    if (family != 0 && family != 1) return -1;
+    return qmatrix_from(s, family == 1 ? 1 : 0, tau, Q);
 }
 
 /* Lagrange interpolation weights from nodes tc[0..sc) to the point t. */
@@ -427,14 +450,15 @@ void orc_apply_L(int dim, int n, double c, const double *e, double *out) { apply
 
 typedef struct {
     int dim, n;        /* spatial grid of this level             */
-    int s;             /* number of Gauss-Lobatto nodes (M + 1)  */
+    int s;             /* number of nodes (M + 1)                */
     double nu, dt;     /* diffusion coefficient, slice length    */
+    int family;        /* 0 Gauss-Lobatto, 1 uniform (see orc_nodes) */
 } orc_level;
 
 static void level_nodes(const orc_level *L, double *tau, double *Q)
 {
-    orc_gauss_lobatto(L->s, tau);
-    orc_qmatrix(L->s, tau, Q);
+    orc_nodes(L->s, L->family, tau);
+    orc_qmatrix_family(L->s, L->family, tau, Q);
 }
 
 /* One SDC sweep with implicit-Euler sub-steps, Eq. (sdc-be) in the form (SDCcompactLIII):
@@ -576,14 +600,16 @@ typedef struct {
     int dim, n_f, s_f, s_c, slices, nlevels, interp_order;
     double nu, dt;
     orc_mg mg;
+    int fam_f, fam_c;  /* node families of the fine and coarse level */
 } orc_pfasst;
 
 /* coarse node j coincides with fine node map[j] (coarse nodes are a subset) */
-static int node_map(int sf, int sc, int *map)
+static int node_map(const orc_pfasst *P, int *map)
 {
+    int sf = P->s_f, sc = P->s_c;
     double tf[ORC_MAXS], tc[ORC_MAXS];
-    orc_gauss_lobatto(sf, tf);
-    orc_gauss_lobatto(sc, tc);
+    orc_nodes(sf, P->fam_f, tf);
+    orc_nodes(sc, P->fam_c, tc);
     for (int j = 0; j < sc; ++j) {
         map[j] = -1;
         for (int m = 0; m < sf; ++m)
@@ -604,9 +630,9 @@ static void fas_restrict(const orc_pfasst *P, const double *Uf, const double *Ff
     size_t Nf = npts(dim, nf), Nc = npts(dim, nc);
     double tf[ORC_MAXS], tc[ORC_MAXS], Qf[ORC_MAXS * ORC_MAXS], Qc[ORC_MAXS * ORC_MAXS];
     int map[ORC_MAXS];
-    orc_gauss_lobatto(sf, tf); orc_qmatrix(sf, tf, Qf);
-    orc_gauss_lobatto(sc, tc); orc_qmatrix(sc, tc, Qc);
-    node_map(sf, sc, map);
+    orc_nodes(sf, P->fam_f, tf); orc_qmatrix_family(sf, P->fam_f, tf, Qf);
+    orc_nodes(sc, P->fam_c, tc); orc_qmatrix_family(sc, P->fam_c, tc, Qc);
+    node_map(P, map);
     double *tmpf = malloc(sizeof(double) * Nf), *tmpc = malloc(sizeof(double) * Nc);
     for (int j = 0; j < sc; ++j) {
         orc_inject(dim, nf, Uf + (size_t)map[j] * Nf, Uc + j * Nc);
@@ -637,8 +663,8 @@ static void interp_correction(const orc_pfasst *P, double *Uf, double *Ff, const
     int dim = P->dim, nf = P->n_f, nc = (nf - 1) / 2, sf = P->s_f, sc = P->s_c;
     size_t Nf = npts(dim, nf), Nc = npts(dim, nc);
     double tf[ORC_MAXS], tc[ORC_MAXS], w[ORC_MAXS];
-    orc_gauss_lobatto(sf, tf);
-    orc_gauss_lobatto(sc, tc);
+    orc_nodes(sf, P->fam_f, tf);
+    orc_nodes(sc, P->fam_c, tc);
     double *d = malloc(sizeof(double) * Nc);
     for (int j = 0; j < sc; ++j) {
         for (size_t p = 0; p < Nc; ++p) d[p] = Uc[j * Nc + p] - Uc0[j * Nc + p];
@@ -653,12 +679,12 @@ static void interp_correction(const orc_pfasst *P, double *Uf, double *Ff, const
 
 static orc_level fine_level(const orc_pfasst *P)
 {
-    orc_level L = {P->dim, P->n_f, P->s_f, P->nu, P->dt};
+    orc_level L = {P->dim, P->n_f, P->s_f, P->nu, P->dt, P->fam_f};
     return L;
 }
 static orc_level coarse_level(const orc_pfasst *P)
 {
-    orc_level L = {P->dim, (P->n_f - 1) / 2, P->s_c, P->nu, P->dt};
+    orc_level L = {P->dim, (P->n_f - 1) / 2, P->s_c, P->nu, P->dt, P->fam_c};
     return L;
 }
 

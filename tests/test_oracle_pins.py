@@ -516,3 +516,96 @@ def test_predictor_does_p_plus_one_coarse_sweeps():
         for p in range(stage, P):
             Uc[p], Fc[p], _ = O.sweep(dim, nc, s_c, nu, dt, FULL, Uc[p], Fc[p], np.ascontiguousarray(fas[p]))
     np.testing.assert_allclose(pf.Uc, Uc, atol=1e-15)
+
+
+# ---------------------------------------------------------------- uniform nodes (Sec. 3)
+# The paper's node family: tau_m = m/M, quadrature rule without the left endpoint
+# (interpolation through tau_1..tau_M); M = 1 is backward Euler, M = 2 the midpoint +
+# right-endpoint rule, M = 4 the fourth-order method.
+
+def test_uniform_nodes_and_closed_form_q():
+    for s in (2, 3, 4, 5):
+        np.testing.assert_array_equal(O.nodes(s, 1), np.arange(s) / (s - 1))
+    np.testing.assert_allclose(O.qmatrix(2, 1), [[0, 0], [0, 1]], atol=1e-16)
+    # M = 2: l_1 = 2(1 - t), l_2 = 2t - 1 on {1/2, 1}; integrals from 0 to 1/2 and to 1
+    np.testing.assert_allclose(O.qmatrix(3, 1), [[0, 0, 0], [0, 0.75, -0.25], [0, 1, 0]], atol=1e-15)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5, 6])
+def test_uniform_q_structure_and_exactness(s):
+    """Column and row 0 vanish; the rule through M = s-1 nodes integrates polynomials of
+    degree <= M-1 exactly on every [0, tau_m] and is not exact for degree M."""
+    Q = O.qmatrix(s, 1)
+    t = O.nodes(s, 1)
+    M = s - 1
+    assert np.all(Q[:, 0] == 0) and np.all(Q[0] == 0)
+    for k in range(M):
+        np.testing.assert_allclose(Q @ t ** k, t ** (k + 1) / (k + 1), atol=1e-14)
+    assert np.max(np.abs(Q @ t ** M - t ** (M + 1) / (M + 1))) > 1e-6
+
+
+def _r_midpoint_right(z):
+    """Stability function of the M = 2 uniform rule, from its two collocation equations
+    u_h = u0 + z (3/4 u_h - 1/4 u_1), u_1 = u0 + z u_h:  (1 + z/4) / (1 - 3z/4 + z^2/4)."""
+    return (1 + z / 4) / (1 - 3 * z / 4 + z * z / 4)
+
+
+def test_uniform_one_sweep_of_backward_euler_is_exact():
+    """M = 1: one SDC sweep with exact sub-step solves is backward Euler, whatever the
+    initial iterate (the sub-step rhs no longer depends on it)."""
+    n, nu, dt = 31, 1.0, 0.1
+    A = nu * _lap(1, n)
+    u0 = np.random.default_rng(1).standard_normal(n)
+    U = np.stack([u0, np.random.default_rng(2).standard_normal(n)])
+    F = U @ A.T
+    U1, _, _ = O.sweep(1, n, 2, nu, dt, FULL, U, F, family=1)
+    np.testing.assert_allclose(U1[1], np.linalg.solve(np.eye(n) - dt * A, u0), atol=1e-12)
+
+
+def test_uniform_collocation_fixed_point_closed_form():
+    """Serial SDC on the M = 2 uniform rule converges on an eigenmode to R(lambda dt) per
+    step, R the closed form above (second order: R = 1 + z + z^2/2 + O(z^3))."""
+    n, s, nu, dt = 31, 3, 1.0, 0.05
+    mode = _sine_mode(1, n, (2,))
+    lam = nu * _d(2, n)
+    pf = O.PFASST(1, n, s, 2, 1, nu, dt, FULL, nlevels=1, family=1)
+    pf.set_initial(mode)
+    pf.run(60, 1e-14)
+    np.testing.assert_allclose(pf.end_value(), _r_midpoint_right(lam * dt) * mode, atol=1e-13)
+    z = 1e-3
+    assert abs(_r_midpoint_right(z) - (1 + z + z * z / 2)) < 1e-9
+
+
+def test_uniform_rule_order_is_M():
+    """Collocation on M uniform nodes without the left endpoint has order M: halving dt
+    divides the end-value error on an eigenmode by about 2^M (M = 2 and 4)."""
+    n, nu = 15, 0.25  # lambda dt = -0.05, -0.025: the asymptotic range
+    mode = _sine_mode(1, n, (1,))
+    lam = nu * _d(1, n)
+    for s, order in ((3, 2), (5, 4)):
+        errs = []
+        for dt in (0.02, 0.01):
+            pf = O.PFASST(1, n, s, 2, 1, nu, dt, FULL, nlevels=1, family=1)
+            pf.set_initial(mode)
+            pf.run(80, 1e-15)
+            errs.append(abs(pf.end_value()[7] - math.exp(lam * dt) * mode[7]))
+        rate = math.log2(errs[0] / errs[1])
+        assert abs(rate - (order + 1)) < 0.15, (s, rate)  # local (one-step) error: order + 1
+
+
+def test_uniform_pfasst_limit_is_serial_collocation():
+    """Two-level PFASST with uniform nodes (fine M = 4, coarse M = 2: {0,1/2,1} within
+    {0,1/4,...,1}) converges to the serial fine collocation solution slice by slice."""
+    dim, n, s_f, s_c, P, nu, dt = 1, 31, 5, 3, 4, 1.0, 0.02
+    mode = _sine_mode(dim, n, (3,))
+    pf = O.PFASST(dim, n, s_f, s_c, P, nu, dt, FULL, family=1)
+    pf.set_initial(mode)
+    pf.run(80, 1e-13)
+    # serial reference: ISDC step by step with the same rule
+    u = mode.copy()
+    for p in range(P):
+        sr = O.PFASST(dim, n, s_f, 2, 1, nu, dt, FULL, nlevels=1, family=1)
+        sr.set_initial(u)
+        sr.run(80, 1e-15)
+        u = sr.end_value()
+        np.testing.assert_allclose(pf.Uf[p, -1], u, atol=1e-11)
