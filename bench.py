@@ -61,8 +61,9 @@ def algo_bytes_per_point(kernel: str, tsize: int, sf: int = 5, sc: int = 3) -> f
 def algo_fp64_flops_per_point(kernel: str, sf: int = 5, sc: int = 3) -> float:
     stencil = 7  # 6 neighbour/centre terms: 5 adds + 1 FMA
     return {
-        # G_j = Lap U_j at every node, P_m = sum_j w_mj G_j, residual and next rhs per sub-step
-        "fine_rhs_residual": stencil * sf + 2 * sf * (sf - 1) + 4 * (sf - 1),
+        # G_j = Lap U_j at nodes 1..M (node 0's is the previous slice's node M after the
+        # send-forward), P_m = sum_j w_mj G_j, residual and next rhs per sub-step
+        "fine_rhs_residual": stencil * (sf - 1) + 2 * sf * (sf - 1) + 4 * (sf - 1),
         # at each coarse point (1/8 of the fine points): fine G at every fine node, coarse F, tau
         "fas_restrict": (stencil * sf + 8 * sc + 2 * sc * sf + 2 * sc * sc + sc) / 8.0,
         "apply_A": 8.0,

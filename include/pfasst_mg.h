@@ -54,7 +54,10 @@ extern "C" {
 typedef struct { int dim; int n; } pmg_grid;
 
 /* Collocation nodes of one level: count = M + 1 nodes in [0,1] including both
- * endpoints; family 0 = Gauss-Lobatto (the only family implemented). */
+ * endpoints.  family 0 = Gauss-Lobatto (Lobatto IIIA collocation); family 1 = the
+ * paper's uniform nodes tau_m = m/M with a quadrature rule that does not use the left
+ * endpoint (Sec. 3: M = 1 backward Euler, M = 2 midpoint + right endpoint, second
+ * order; M = 4 fourth order).  Node 0 (t = 0) carries the slice's initial value. */
 typedef struct { int count; int family; } pmg_nodes_desc;
 
 /* Level hierarchy: nlevels = 1 (SDC / parallel SDC) or 2 (PFASST / MLSDC).  The

@@ -602,13 +602,14 @@ class NetTrainer:
 class PFASSTSolver:
     """Owns a pfasst_mg handle and its torch workspace; methods call the C ABI."""
 
-    def __init__(self, dim, n, fine_nodes, coarse_nodes, slices, nu, dt, nlevels=2, stream=None, **opts):
+    def __init__(self, dim, n, fine_nodes, coarse_nodes, slices, nu, dt, nlevels=2, stream=None, family=0, **opts):
+        """family: 0 Gauss-Lobatto nodes, 1 the uniform family (both levels)."""
         self.dim, self.n, self.sf, self.sc = dim, n, fine_nodes, coarse_nodes
         self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
         self.opt = pfasst_mg_default_options(**opts)
         self.grid = pmg_grid(dim, n)
-        self.fnodes = pmg_nodes_desc(fine_nodes, 0)
-        self.levels = pmg_levels(nlevels, pmg_nodes_desc(coarse_nodes if nlevels == 2 else 0, 0))
+        self.fnodes = pmg_nodes_desc(fine_nodes, family)
+        self.levels = pmg_levels(nlevels, pmg_nodes_desc(coarse_nodes if nlevels == 2 else 0, family))
         self.h, self.workspace = pfasst_mg_create(self.grid, self.fnodes, self.levels, nu, dt, slices, self.opt, stream)
 
     @property

@@ -57,25 +57,41 @@ void gauss_lobatto(int s, long double *tau) {
 
 // Q[m][j]: weights of the interpolatory rule for the integral over [0, tau_m]:
 // sum_j Q[m][j] tau_j^k = tau_m^{k+1}/(k+1), k = 0..s-1 (Gaussian elimination).
-void integration_matrix(int s, const long double *tau, long double Q[kMaxNodes][kMaxNodes]) {
+// Node positions on [0,1]: family 0 Gauss-Lobatto, family 1 uniform m/(s-1) (the
+// paper's second- and fourth-order methods, Sec. 3).
+void node_positions(int s, int family, long double *tau) {
+  if (family == 0) {
+    gauss_lobatto(s, tau);
+    return;
+  }
+  for (int m = 0; m < s; ++m) tau[m] = (long double)m / (long double)(s - 1);
+}
+
+// Integration matrix from the moment equations of the interpolatory rule: row m holds
+// the weights that integrate polynomials of degree < (number of rule nodes) exactly
+// over [0, tau_m].  Family 0 interpolates through all s nodes; family 1 through
+// tau_1..tau_{s-1} only (the rule without the left endpoint; column 0 is zero).
+void integration_matrix(int s, const long double *tau, long double Q[kMaxNodes][kMaxNodes], int family = 0) {
+  const int j0 = family == 1 ? 1 : 0, nr = s - j0;  // first rule node, rule size
   for (int m = 0; m < s; ++m) {
     long double A[kMaxNodes][kMaxNodes + 1];
-    for (int k = 0; k < s; ++k) {
-      for (int j = 0; j < s; ++j) A[k][j] = powl(tau[j], k);
-      A[k][s] = powl(tau[m], k + 1) / (k + 1);
+    for (int k = 0; k < nr; ++k) {
+      for (int j = 0; j < nr; ++j) A[k][j] = powl(tau[j0 + j], k);
+      A[k][nr] = powl(tau[m], k + 1) / (k + 1);
     }
-    for (int col = 0; col < s; ++col) {
+    for (int col = 0; col < nr; ++col) {
       int piv = col;
-      for (int r = col + 1; r < s; ++r)
+      for (int r = col + 1; r < nr; ++r)
         if (fabsl(A[r][col]) > fabsl(A[piv][col])) piv = r;
-      for (int q = 0; q <= s; ++q) { long double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
-      for (int r = 0; r < s; ++r) {
+      for (int q = 0; q <= nr; ++q) { long double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+      for (int r = 0; r < nr; ++r) {
         if (r == col) continue;
         long double f = A[r][col] / A[col][col];
-        for (int q = col; q <= s; ++q) A[r][q] -= f * A[col][q];
+        for (int q = col; q <= nr; ++q) A[r][q] -= f * A[col][q];
       }
     }
-    for (int j = 0; j < s; ++j) Q[m][j] = A[j][s] / A[j][j];
+    for (int j = 0; j < j0; ++j) Q[m][j] = 0.0L;
+    for (int j = 0; j < nr; ++j) Q[m][j0 + j] = A[j][nr] / A[j][j];
   }
 }
 
@@ -192,6 +208,7 @@ struct NetDeploy {
 
 struct pmg_ctx {
   int dim = 0, nf = 0, nc = 0, sf = 0, sc = 0, P = 0, nlevels = 1;
+  int famf = 0, famc = 0;  // node families (0 Gauss-Lobatto, 1 uniform)
   double nu = 0, dt = 0;
   pmg_options opt{};
   cudaStream_t stream = nullptr;
@@ -279,11 +296,14 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
   if (!grid || !fn || !lv) { why = "null description"; return PMG_ERR_INVALID_ARG; }
   if (grid->dim < 1 || grid->dim > 3) { why = "dim must be 1, 2 or 3"; return PMG_ERR_INVALID_ARG; }
   if (!is_pow2_minus1(grid->n) || grid->n > 1023) { why = "n must be 2^p - 1 in [3, 1023]"; return PMG_ERR_INVALID_ARG; }
-  if (fn->family != 0) { why = "only Gauss-Lobatto nodes (family 0)"; return PMG_ERR_UNSUPPORTED; }
+  if (fn->family != 0 && fn->family != 1) { why = "node family must be 0 (Gauss-Lobatto) or 1 (uniform)"; return PMG_ERR_UNSUPPORTED; }
   if (fn->count < 2 || fn->count > kMaxNodes) { why = "fine node count must be in [2, 9]"; return PMG_ERR_INVALID_ARG; }
   if (lv->nlevels != 1 && lv->nlevels != 2) { why = "nlevels must be 1 or 2"; return PMG_ERR_INVALID_ARG; }
   if (lv->nlevels == 2) {
-    if (lv->coarse_nodes.family != 0) { why = "only Gauss-Lobatto coarse nodes"; return PMG_ERR_UNSUPPORTED; }
+    if (lv->coarse_nodes.family != 0 && lv->coarse_nodes.family != 1) {
+      why = "coarse node family must be 0 (Gauss-Lobatto) or 1 (uniform)";
+      return PMG_ERR_UNSUPPORTED;
+    }
     if (lv->coarse_nodes.count < 2 || lv->coarse_nodes.count > fn->count) { why = "bad coarse node count"; return PMG_ERR_INVALID_ARG; }
     if (grid->n < 7) { why = "two levels need n >= 7"; return PMG_ERR_INVALID_ARG; }
   }
@@ -935,8 +955,8 @@ int spread(pmg_ctx *h) {
 
 void fill_coefficients(pmg_ctx *h) {
   long double Qf[kMaxNodes][kMaxNodes], Qc[kMaxNodes][kMaxNodes];
-  gauss_lobatto(h->sf, h->tauf);
-  integration_matrix(h->sf, h->tauf, Qf);
+  node_positions(h->sf, h->famf, h->tauf);
+  integration_matrix(h->sf, h->tauf, Qf, h->famf);
   auto fill_sf = [&](SFCoef &cf, int s, const long double *t, long double Q[kMaxNodes][kMaxNodes], double *csub) {
     std::memset(&cf, 0, sizeof cf);
     cf.s = s;
@@ -957,8 +977,8 @@ void fill_coefficients(pmg_ctx *h) {
   for (int m = 0; m < h->sf; ++m)
     for (int i = 0; i < h->sf; ++i) h->resf.dtQ[m][i] = (double)((long double)h->dt * Qf[m][i]);
   if (h->nlevels == 2) {
-    gauss_lobatto(h->sc, h->tauc);
-    integration_matrix(h->sc, h->tauc, Qc);
+    node_positions(h->sc, h->famc, h->tauc);
+    integration_matrix(h->sc, h->tauc, Qc, h->famc);
     fill_sf(h->sfc, h->sc, h->tauc, Qc, h->cc_sub);
     std::memset(&h->fas, 0, sizeof h->fas);
     h->fas.sf = h->sf;
@@ -1006,6 +1026,8 @@ pmg_ctx *make_ctx(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_leve
   h->nf = grid->n;
   h->nc = (grid->n - 1) / 2;
   h->sf = fn->count;
+  h->famf = fn->family;
+  h->famc = lv->nlevels == 2 ? lv->coarse_nodes.family : 0;
   h->nlevels = lv->nlevels;
   h->sc = lv->nlevels == 2 ? lv->coarse_nodes.count : 0;
   h->P = slices;

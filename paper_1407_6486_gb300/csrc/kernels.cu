@@ -524,7 +524,7 @@ __global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, const double *__res
 // reduced per warp into shared memory, then once per CTA into res.  The loop bound is
 // rounded up to whole warps so that every lane takes part in the shuffles.
 template <int DIM, int S>
-__global__ void __launch_bounds__(256) fine_rhs_chain_kernel(Grid g, ResCoef cf, const double *__restrict__ U,
+__global__ void __launch_bounds__(256, 4) fine_rhs_chain_kernel(Grid g, ResCoef cf, const double *__restrict__ U,
                                                              long long stride, double *__restrict__ q, long long sq,
                                                              int batch, unsigned long long *res) {
   extern __shared__ unsigned long long smax[];  // [batch]

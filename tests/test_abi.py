@@ -186,3 +186,17 @@ def test_slice_groups_option_is_validated(lib):
         sizes.append(nb.value)
     # the pipelined iteration adds a single-grid multigrid scratch for the coarse chain
     assert sizes[0] == sizes[1] < sizes[2]
+
+
+def test_uniform_node_family_is_accepted_and_checked(lib):
+    o = pmg.pfasst_mg_default_options()
+    nb = ctypes.c_size_t(0)
+    g = pmg.pmg_grid(2, 31)
+    ok = lib.pfasst_mg_workspace_bytes(ctypes.byref(g), ctypes.byref(pmg.pmg_nodes_desc(5, 1)),
+                                       ctypes.byref(pmg.pmg_levels(2, pmg.pmg_nodes_desc(3, 1))), 4,
+                                       ctypes.byref(o), ctypes.byref(nb))
+    assert ok == pmg.PMG_OK
+    bad = lib.pfasst_mg_workspace_bytes(ctypes.byref(g), ctypes.byref(pmg.pmg_nodes_desc(5, 2)),
+                                        ctypes.byref(pmg.pmg_levels(1, pmg.pmg_nodes_desc(0, 0))), 4,
+                                        ctypes.byref(o), ctypes.byref(nb))
+    assert bad == pmg.PMG_ERR_UNSUPPORTED

@@ -356,3 +356,57 @@ def test_tma_staged_sweep_matches_the_fused_sweep(n, level, zchunk):
         s.close()
     rel = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0])
     assert rel <= 1e-6, rel
+
+
+UNIFORM_CASES = [
+    # dim, n, sf, sc, P, nlevels, smoother, vcycles, interp  (uniform nodes, Sec. 3)
+    (1, 63, 5, 3, 3, 2, 0, 2, 4),
+    (2, 31, 3, 2, 4, 2, 0, 1, 4),    # {0, 1/2, 1} over {0, 1}: backward Euler on the coarse level
+    (3, 15, 5, 3, 2, 2, 1, 2, 4),
+    (2, 31, 5, 0, 3, 1, 0, 2, 4),
+]
+
+
+@pytest.mark.parametrize("case", UNIFORM_CASES, ids=[f"d{c[0]}n{c[1]}s{c[2]}x{c[3]}P{c[4]}" for c in UNIFORM_CASES])
+def test_uniform_nodes_match_oracle_every_iteration(case):
+    dim, n, sf, sc, P, nl, sm, vc, interp = case
+    s = pmg.PFASSTSolver(dim, n, sf, sc if nl == 2 else 0, P, 1.0, 0.01, nlevels=nl, smoother=sm, omega=omega(sm),
+                         vcycles=vc, interp_order=interp, family=1)
+    o = O.PFASST(dim, n, sf, sc if nl == 2 else 2, P, 1.0, 0.01,
+                 O.MGParams(smoother=sm, omega=omega(sm), vcycles=vc), nlevels=nl, interp_order=interp, family=1)
+    u0 = _u0(dim, n)
+    s.set_initial(u0)
+    o.set_initial(u0)
+    s.predict()
+    o.predict()
+    assert rel(s.state(0), o.Uf) < FP64_TOL
+    for k in range(3):
+        s.iterate(1, 0.0)
+        ores = o.iteration()
+        assert rel(s.state(0), o.Uf) < FP64_TOL, f"iteration {k}"
+        if nl == 2:
+            assert rel(s.state(1), o.Uc) < FP64_TOL
+        np.testing.assert_allclose(s.residual(), ores, rtol=1e-7, atol=1e-13)
+    s.close()
+
+
+def test_uniform_nodes_3d_fixed_point_is_the_midpoint_right_rule():
+    """3D heat with the paper's second-order rule (3 uniform nodes, coarse backward Euler),
+    mixed precision: PFASST converges on every sine mode to R(lambda dt)^P with
+    R(z) = (1 + z/4) / (1 - 3z/4 + z^2/4), the rule's stability function."""
+    wl = inputs.heat3d_c3(n=63, slices=4)
+    s = pmg.PFASSTSolver(3, wl.n, 3, 2, wl.slices, wl.nu, wl.dt, smoother=1, omega=1.0, vcycles=2, precision=1,
+                         family=1)
+    s.set_initial(wl.u0())
+    rc, it, res = s.iterate(200, 1e-10)
+    assert rc == pmg.PMG_OK, (it, res)
+    n, h = wl.n, 1.0 / (wl.n + 1)
+    x = np.arange(1, n + 1) * h
+    want = np.zeros((n, n, n))
+    for k, a in zip(wl.modes, wl.amps):
+        z = wl.dt * wl.nu * sum((2 * math.cos(kk * math.pi * h) - 2) / h ** 2 for kk in k)
+        want += a * ((1 + z / 4) / (1 - 3 * z / 4 + z * z / 4)) ** wl.slices * np.einsum(
+            "k,j,i->kji", np.sin(k[2] * np.pi * x), np.sin(k[1] * np.pi * x), np.sin(k[0] * np.pi * x))
+    end = s.solution(wl.slices - 1, 2).reshape(n, n, n)
+    assert np.abs(end - want).max() <= 1e-8 * np.abs(want).max()
+    s.close()
