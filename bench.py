@@ -383,6 +383,96 @@ def run_learned(args):
         print(json.dumps(line), flush=True)
 
 
+def _pade(z, s):
+    """Diagonal (s-1, s-1) Pade approximant of exp(z): the Gauss-Lobatto collocation step."""
+    import math
+    N = s - 1
+    c = [math.factorial(2 * N - j) * math.factorial(N) / (math.factorial(2 * N) * math.factorial(j)
+                                                           * math.factorial(N - j)) for j in range(N + 1)]
+    return sum(c[j] * z ** j for j in range(N + 1)) / sum(c[j] * (-z) ** j for j in range(N + 1))
+
+
+def run_compare(args):
+    """Solver comparison (a GPU analogue of the paper's full-solve PFASST / ISDC / MLSDC
+    table, Sec. 4.2.1): 3D heat nu = 0.5 on 127^3 (coarse 63^3), dt = 0.002, 16 slices,
+    16 sine modes (seed 6486), 5/3 Gauss-Lobatto nodes, red-black V(2,1).  Every variant
+    integrates the block [0, 16 dt] until the collocation residual of every slice is
+    <= 1e-9: PFASST with 2 V-cycles per sub-step (mixed and FP64) or with sub-steps solved
+    to 1e-12 (FP64), and the serial methods one slice after another: MLSDC (two levels,
+    2 V-cycles), ISDC (one level, 2 V-cycles) and ISDC with full solves.  Reported per
+    variant: time, iterations, fine sweeps, final residual, and the max error of the end
+    value against the serial collocation solution (Pade^16 per sine mode)."""
+    import math
+    import torch
+    import paper_1407_6486_gb300 as pmg
+    from paper_1407_6486_gb300 import _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    pmg.load()
+    wl = inputs.heat3d_c3(n=127, slices=16)
+    tol, maxit = 1e-9, 400
+    n, h = wl.n, 1.0 / (wl.n + 1)
+    x = np.arange(1, n + 1) * h
+    want = np.zeros((n, n, n))
+    for k, a in zip(wl.modes, wl.amps):
+        z = wl.dt * wl.nu * sum((2 * math.cos(kk * math.pi * h) - 2) / h ** 2 for kk in k)
+        want += a * _pade(z, wl.fine_nodes) ** wl.slices * np.einsum(
+            "k,j,i->kji", np.sin(k[2] * np.pi * x), np.sin(k[1] * np.pi * x), np.sin(k[0] * np.pi * x))
+    u0 = torch.tensor(wl.u0(), device="cuda")
+    variants = [("pfasst_2vc_mixed", 2, 16, dict(vcycles=2, precision=1)),
+                ("pfasst_2vc_fp64", 2, 16, dict(vcycles=2, precision=0)),
+                ("pfasst_full_fp64", 2, 16, dict(vcycles=0, precision=0, mg_tol=1e-12)),
+                ("mlsdc_2vc_mixed", 2, 1, dict(vcycles=2, precision=1)),
+                ("isdc_2vc_mixed", 1, 1, dict(vcycles=2, precision=1)),
+                ("isdc_full_fp64", 1, 1, dict(vcycles=0, precision=0, mg_tol=1e-12))]
+    rows = []
+    for name, nl, P, opts in variants:
+        s = pmg.PFASSTSolver(3, n, wl.fine_nodes, wl.coarse_nodes if nl == 2 else 0, P, wl.nu, wl.dt, nlevels=nl,
+                             smoother=1, omega=1.0, **opts)
+        out = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+
+        def solve():
+            if P == wl.slices:
+                s.set_initial(u0)
+                rc, it, res = s.iterate(maxit, tol)
+                return it, it * P, res, rc == pmg.PMG_OK
+            u, its, ok, res = u0, 0, True, 0.0
+            for _ in range(wl.slices):
+                s.set_initial(u)
+                rc, it, r = s.iterate(maxit, tol)
+                its, ok, res = its + it, ok and rc == pmg.PMG_OK, max(res, r)
+                pmg.pfasst_mg_get_solution(s.h, 0, wl.fine_nodes - 1, out)
+                u = out.clone()
+            return its, its, res, ok
+
+        solve()  # warm-up (graph capture, caches)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, sweeps, res, ok = solve()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        end = (out if P == 1 else pmg.pfasst_mg_get_solution(s.h, P - 1, wl.fine_nodes - 1, out)).cpu().numpy()
+        err = float(np.abs(end.reshape(n, n, n) - want).max() / np.abs(want).max())
+        rows.append({"variant": name, "seconds": sec, "iterations": its, "fine_sweeps": sweeps,
+                     "final_residual": res, "reached_1e-9": ok, "rel_error_vs_collocation": err})
+        s.close()
+        torch.cuda.empty_cache()
+    best = min((r for r in rows if r["reached_1e-9"]), key=lambda r: r["seconds"], default=rows[0])
+    dofs = n ** 3 * (wl.fine_nodes - 1)
+    line = {"metric": "seconds to collocation residual 1e-9", "value": best["seconds"], "unit": "s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": best["seconds"] * 1000, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "heat3d_n127_compare_P16", "grid": "127^3/63^3", "slices": wl.slices,
+                       "nodes": "5/3 Gauss-Lobatto", "best": best["variant"],
+                       "dof_sweeps_per_fine_sweep_of_one_slice": dofs, "variants": rows,
+                       "l2": "not flushed between variants (each variant's state is hundreds of MB to GB)"},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 RES_TOL = 0.01  # relative tolerance on the FP64 path's residual (the bench's "fixed residual")
 
 
@@ -598,7 +688,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d",
-                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train"])
+                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "compare"])
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
                          "no CPU baseline")
@@ -618,6 +708,8 @@ def main():
         run_uneven(args)
     elif args.workload == "learned-train":
         run_learned(args)
+    elif args.workload == "compare":
+        run_compare(args)
     else:
         run_ours(args)
 
