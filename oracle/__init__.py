@@ -274,3 +274,84 @@ class PFASST:
 
     def end_value(self) -> np.ndarray:
         return self.Uf[-1, -1].copy()
+
+
+class _ML(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n0", ctypes.c_int), ("slices", ctypes.c_int), ("nlevels", ctypes.c_int),
+                ("interp_order", ctypes.c_int), ("s", ctypes.c_int * 3), ("fam", ctypes.c_int * 3),
+                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("mg", _MG)]
+
+
+class _MLState(ctypes.Structure):
+    _fields_ = [("U", _D * 3), ("F", _D * 3), ("tau", _D * 3), ("Ur", _D * 3)]
+
+
+class MLPFASST:
+    """Serial emulation of PFASST with up to three levels (level l grid: n_l = (n_{l-1}-1)/2).
+
+    ``nodes``: node count per level, ``families``: node family per level (0 Gauss-Lobatto,
+    1 uniform).  State ``U[l], F[l], tau[l], Ur[l]`` of shape (slices, s_l, n_l^dim).
+    With two levels the schedule is the one of :class:`PFASST`.
+    """
+
+    def __init__(self, dim, n, nodes, slices, nu, dt, mg: MGParams, families=None, interp_order=4):
+        L = len(nodes)
+        assert 1 <= L <= 3
+        families = list(families) if families is not None else [0] * L
+        self.dim, self.n, self.nodes, self.families = dim, n, list(nodes), families
+        self.slices, self.nu, self.dt, self.L = slices, nu, dt, L
+        grids = [n]
+        for _ in range(1, L):
+            grids.append((grids[-1] - 1) // 2)
+        if min(grids) < 3:
+            raise ValueError("every level needs at least 3 points per axis")
+        for l in range(1, L):
+            tf, tc = globals()["nodes"](nodes[l - 1], families[l - 1]), globals()["nodes"](nodes[l], families[l])
+            if not all(np.min(np.abs(tf - t)) < 1e-14 for t in tc):
+                raise ValueError("the nodes of every level must be a subset of the finer level's")
+        self.grids = grids
+        s = (ctypes.c_int * 3)(*(list(nodes) + [2] * (3 - L)))
+        f = (ctypes.c_int * 3)(*(families + [0] * (3 - L)))
+        self._c = _ML(dim, n, slices, L, interp_order, s, f, nu, dt, mg.c())
+        self.U = [np.zeros((slices, nodes[l], grids[l] ** dim)) for l in range(L)]
+        self.F = [np.zeros_like(u) for u in self.U]
+        self.tau = [np.zeros_like(u) for u in self.U]
+        self.Ur = [np.zeros_like(u) for u in self.U]
+        self.res = np.zeros(slices)
+
+    def _state(self):
+        st = _MLState()
+        for l in range(3):
+            ll = min(l, self.L - 1)
+            st.U[l] = _p(self.U[ll])
+            st.F[l] = _p(self.F[ll])
+            st.tau[l] = _p(self.tau[ll])
+            st.Ur[l] = _p(self.Ur[ll])
+        return st
+
+    def set_initial(self, u0):
+        u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
+        st = self._state()
+        lib().orc_ml_spread(ctypes.byref(self._c), _p(u0), ctypes.byref(st))
+
+    def predict(self):
+        st = self._state()
+        lib().orc_ml_predict(ctypes.byref(self._c), ctypes.byref(st))
+
+    def iteration(self) -> np.ndarray:
+        st = self._state()
+        lib().orc_ml_iteration(ctypes.byref(self._c), ctypes.byref(st), _p(self.res))
+        return self.res.copy()
+
+    def run(self, max_iter, tol):
+        self.predict()
+        hist = []
+        for k in range(max_iter):
+            r = self.iteration()
+            hist.append(float(np.max(r)))
+            if hist[-1] <= tol:
+                return k + 1, hist
+        return max_iter, hist
+
+    def end_value(self):
+        return self.U[0][-1, -1].copy()

@@ -775,3 +775,179 @@ void orc_pfasst_iteration(const orc_pfasst *P, double *Uf, double *Ff,
     for (int p = 0; p < Pn; ++p)
         res[p] = orc_residual(&F, Uf + (size_t)p * sf * Nf, Ff + (size_t)p * sf * Nf, NULL);
 }
+
+/* ------------------------------------------------------------------------- */
+/* PFASST with up to three levels (Sec. 2.3 - 2.4, reading of the multi-level */
+/* schedule): levels l = 0 (finest) .. L-1 (coarsest), grid n_l = (n_{l-1}-1)/2 */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int dim, n0, slices, nlevels, interp_order;
+    int s[3], fam[3];          /* nodes and node family of every level        */
+    double nu, dt;
+    orc_mg mg;
+} orc_ml;
+
+/* per level: U, F (slices x s_l x N_l), tau (FAS correction, unused on level 0) and
+ * Ur (the restricted values the coarse correction is measured against) */
+typedef struct {
+    double *U[3], *F[3], *tau[3], *Ur[3];
+} orc_mlstate;
+
+static int ml_n(const orc_ml *P, int l)
+{
+    int n = P->n0;
+    for (int i = 0; i < l; ++i) n = (n - 1) / 2;
+    return n;
+}
+
+static orc_level ml_level(const orc_ml *P, int l)
+{
+    orc_level L = {P->dim, ml_n(P, l), P->s[l], P->nu, P->dt, P->fam[l]};
+    return L;
+}
+
+static size_t ml_slab(const orc_ml *P, int l) { return (size_t)P->s[l] * npts(P->dim, ml_n(P, l)); }
+
+/* FAS restriction of slice p from level l to l+1 (reading g6 applied level by level):
+ *   U_{l+1,j} = R U_{l,map j},  F_{l+1} = A U_{l+1},
+ *   tau_{l+1,j} = R( dt sum_i Q_l[map j][i] F_{l,i} + tau_{l,map j} ) - dt sum_i Q_{l+1}[j][i] F_{l+1,i},
+ * so that R U_l solves level l+1 whenever U_l solves level l. */
+static void ml_fas(const orc_ml *P, const orc_mlstate *S, int l, int p)
+{
+    int dim = P->dim, nf = ml_n(P, l), nc = ml_n(P, l + 1), sf = P->s[l], sc = P->s[l + 1];
+    size_t Nf = npts(dim, nf), Nc = npts(dim, nc);
+    double tf[ORC_MAXS], tc[ORC_MAXS], Qf[ORC_MAXS * ORC_MAXS], Qc[ORC_MAXS * ORC_MAXS];
+    int map[ORC_MAXS];
+    orc_nodes(sf, P->fam[l], tf); orc_qmatrix_family(sf, P->fam[l], tf, Qf);
+    orc_nodes(sc, P->fam[l + 1], tc); orc_qmatrix_family(sc, P->fam[l + 1], tc, Qc);
+    for (int j = 0; j < sc; ++j) {
+        map[j] = -1;
+        for (int m = 0; m < sf; ++m)
+            if (fabs(tf[m] - tc[j]) < 1e-14) map[j] = m;
+    }
+    const double *Uf = S->U[l] + p * ml_slab(P, l), *Ff = S->F[l] + p * ml_slab(P, l);
+    const double *tauf = l > 0 ? S->tau[l] + p * ml_slab(P, l) : NULL;
+    double *Uc = S->U[l + 1] + p * ml_slab(P, l + 1), *Fc = S->F[l + 1] + p * ml_slab(P, l + 1);
+    double *tauc = S->tau[l + 1] + p * ml_slab(P, l + 1), *Ur = S->Ur[l + 1] + p * ml_slab(P, l + 1);
+    double *tmpf = malloc(sizeof(double) * Nf), *tmpc = malloc(sizeof(double) * Nc);
+    for (int j = 0; j < sc; ++j) {
+        orc_inject(dim, nf, Uf + (size_t)map[j] * Nf, Uc + j * Nc);
+        orc_apply_A(dim, nc, P->nu, Uc + j * Nc, Fc + j * Nc);
+    }
+    for (int j = 0; j < sc; ++j) {
+        for (size_t q = 0; q < Nf; ++q) {
+            double I = tauf ? tauf[(size_t)map[j] * Nf + q] : 0.0;
+            for (int i = 0; i < sf; ++i) I += P->dt * Qf[map[j] * sf + i] * Ff[i * Nf + q];
+            tmpf[q] = I;
+        }
+        orc_inject(dim, nf, tmpf, tmpc);
+        for (size_t q = 0; q < Nc; ++q) {
+            double I = 0.0;
+            for (int i = 0; i < sc; ++i) I += P->dt * Qc[j * sc + i] * Fc[i * Nc + q];
+            tauc[j * Nc + q] = tmpc[q] - I;
+        }
+    }
+    memcpy(Ur, Uc, sizeof(double) * Nc * sc);
+    free(tmpf); free(tmpc);
+}
+
+/* coarse correction of slice p from level l+1 to every node of level l (Lagrange in
+ * time through the level-(l+1) nodes, I_x in space), then F_l = A U_l */
+static void ml_interp(const orc_ml *P, const orc_mlstate *S, int l, int p)
+{
+    int dim = P->dim, nf = ml_n(P, l), sf = P->s[l], sc = P->s[l + 1];
+    size_t Nf = npts(dim, nf), Nc = npts(dim, ml_n(P, l + 1));
+    double tf[ORC_MAXS], tc[ORC_MAXS], w[ORC_MAXS];
+    orc_nodes(sf, P->fam[l], tf);
+    orc_nodes(sc, P->fam[l + 1], tc);
+    double *Uf = S->U[l] + p * ml_slab(P, l), *Ff = S->F[l] + p * ml_slab(P, l);
+    const double *Uc = S->U[l + 1] + p * ml_slab(P, l + 1), *Ur = S->Ur[l + 1] + p * ml_slab(P, l + 1);
+    double *d = malloc(sizeof(double) * Nc);
+    for (int j = 0; j < sc; ++j) {
+        for (size_t q = 0; q < Nc; ++q) d[q] = Uc[j * Nc + q] - Ur[j * Nc + q];
+        for (int m = 0; m < sf; ++m) {
+            lagrange_weights(sc, tc, tf[m], w);
+            if (w[j] != 0.0) orc_interp_add(dim, nf, P->interp_order, w[j], d, Uf + (size_t)m * Nf);
+        }
+    }
+    for (int m = 0; m < sf; ++m) orc_apply_A(dim, nf, P->nu, Uf + (size_t)m * Nf, Ff + (size_t)m * Nf);
+    free(d);
+}
+
+static void ml_sweep(const orc_ml *P, const orc_mlstate *S, int l, int p)
+{
+    orc_level L = ml_level(P, l);
+    orc_sweep(&L, &P->mg, S->U[l] + p * ml_slab(P, l), S->F[l] + p * ml_slab(P, l),
+              l > 0 ? S->tau[l] + p * ml_slab(P, l) : NULL);
+}
+
+/* slice p >= 1 takes the end value of slice p-1 as its initial value on level l */
+static void ml_receive(const orc_ml *P, const orc_mlstate *S, int l, int p)
+{
+    size_t N = npts(P->dim, ml_n(P, l)), sl = ml_slab(P, l);
+    double *u0 = S->U[l] + p * sl;
+    memcpy(u0, S->U[l] + (p - 1) * sl + (size_t)(P->s[l] - 1) * N, sizeof(double) * N);
+    orc_apply_A(P->dim, ml_n(P, l), P->nu, u0, S->F[l] + p * sl);
+}
+
+void orc_ml_spread(const orc_ml *P, const double *u0, const orc_mlstate *S)
+{
+    size_t N = npts(P->dim, P->n0);
+    for (int p = 0; p < P->slices; ++p)
+        for (int m = 0; m < P->s[0]; ++m) {
+            double *u = S->U[0] + p * ml_slab(P, 0) + (size_t)m * N;
+            memcpy(u, u0, sizeof(double) * N);
+            orc_apply_A(P->dim, P->n0, P->nu, u, S->F[0] + p * ml_slab(P, 0) + (size_t)m * N);
+        }
+}
+
+/* Predictor: FAS restriction of the spread values down to the coarsest level; there,
+ * stage s = 0..P-1: slices p >= s receive the coarsest end value of p-1 (s > 0) and
+ * sweep; then the corrections are interpolated up level by level. */
+void orc_ml_predict(const orc_ml *P, const orc_mlstate *S)
+{
+    int L = P->nlevels, Pn = P->slices, lc = L - 1;
+    if (L < 2) return;
+    for (int l = 0; l < lc; ++l)
+        for (int p = 0; p < Pn; ++p) ml_fas(P, S, l, p);
+    for (int s = 0; s < Pn; ++s) {
+        if (s > 0)
+            for (int p = Pn - 1; p >= s; --p) ml_receive(P, S, lc, p);
+        for (int p = s; p < Pn; ++p) ml_sweep(P, S, lc, p);
+    }
+    for (int l = lc - 1; l >= 0; --l)
+        for (int p = 0; p < Pn; ++p) ml_interp(P, S, l, p);
+}
+
+/* One PFASST iteration with L levels (reading g7b):
+ *   1. sweep on level 0, every slice;
+ *   2. for each intermediate level l = 1..L-2: FAS restriction l-1 -> l, sweep on l;
+ *   3. FAS restriction to the coarsest level, whose sweeps run as the serial chain
+ *      (slice p first receives the coarsest end value of slice p-1);
+ *   4. interpolation of the corrections level by level up to level 0;
+ *   5. send-forward on level 0, collocation residual of every slice into res.
+ * Coarser levels are restricted afresh every iteration, so only level 0 sends forward. */
+void orc_ml_iteration(const orc_ml *P, const orc_mlstate *S, double *res)
+{
+    int L = P->nlevels, Pn = P->slices, lc = L - 1;
+    for (int p = 0; p < Pn; ++p) ml_sweep(P, S, 0, p);
+    if (L >= 2) {
+        for (int l = 1; l < lc; ++l)
+            for (int p = 0; p < Pn; ++p) {
+                ml_fas(P, S, l - 1, p);
+                ml_sweep(P, S, l, p);
+            }
+        for (int p = 0; p < Pn; ++p) ml_fas(P, S, lc - 1, p);
+        for (int p = 0; p < Pn; ++p) {
+            if (p > 0) ml_receive(P, S, lc, p);
+            ml_sweep(P, S, lc, p);
+        }
+        for (int l = lc - 1; l >= 0; --l)
+            for (int p = 0; p < Pn; ++p) ml_interp(P, S, l, p);
+    }
+    for (int p = Pn - 1; p >= 1; --p) ml_receive(P, S, 0, p);
+    orc_level F = ml_level(P, 0);
+    for (int p = 0; p < Pn; ++p)
+        res[p] = orc_residual(&F, S->U[0] + p * ml_slab(P, 0), S->F[0] + p * ml_slab(P, 0), NULL);
+}

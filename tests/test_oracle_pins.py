@@ -609,3 +609,79 @@ def test_uniform_pfasst_limit_is_serial_collocation():
         sr.run(80, 1e-15)
         u = sr.end_value()
         np.testing.assert_allclose(pf.Uf[p, -1], u, atol=1e-11)
+
+
+# ---------------------------------------------------------------- three-level PFASST (Sec. 2.4, 4.2.2)
+
+def test_multilevel_oracle_with_two_levels_is_the_two_level_oracle():
+    """The generic L-level schedule with L = 2 reproduces the two-level PFASST oracle
+    bit for bit (predictor and iterations)."""
+    mg = O.MGParams(smoother=1, omega=1.0, vcycles=2)
+    dim, n, P = 2, 31, 4
+    u0 = np.random.default_rng(0).standard_normal(n ** dim)
+    a = O.PFASST(dim, n, 5, 3, P, 1.0, 0.01, mg)
+    b = O.MLPFASST(dim, n, (5, 3), P, 1.0, 0.01, mg)
+    for s in (a, b):
+        s.set_initial(u0)
+        s.predict()
+    assert np.array_equal(a.Uf, b.U[0]) and np.array_equal(a.Uc, b.U[1])
+    for _ in range(3):
+        assert np.array_equal(a.iteration(), b.iteration())
+        assert np.array_equal(a.Uf, b.U[0])
+
+
+@pytest.mark.parametrize("nodes,fams", [((5, 3, 2), (1, 1, 1)), ((3, 3, 2), (1, 1, 1)), ((5, 3, 2), (0, 0, 0))])
+def test_three_level_pfasst_limit_is_serial_collocation(nodes, fams):
+    """With exact sub-step solves, three-level PFASST converges slice by slice to the
+    serial fine collocation solution."""
+    dim, n, P, nu, dt = 1, 31, 4, 1.0, 0.02
+    mode = _sine_mode(dim, n, (2,)) + 0.3 * _sine_mode(dim, n, (5,))
+    pf = O.MLPFASST(dim, n, nodes, P, nu, dt, FULL, families=fams)
+    pf.set_initial(mode)
+    it, hist = pf.run(150, 1e-13)
+    assert hist[-1] <= 1e-13, hist[-5:]
+    u = mode.copy()
+    for p in range(P):
+        sr = O.MLPFASST(dim, n, (nodes[0],), 1, nu, dt, FULL, families=(fams[0],))
+        sr.set_initial(u)
+        sr.run(80, 1e-15)
+        u = sr.end_value()
+        np.testing.assert_allclose(pf.U[0][p, -1], u, atol=1e-11)
+
+
+def test_three_level_iteration_keeps_the_collocation_solution():
+    """FAS consistency through both restrictions: started from the converged collocation
+    solution (exact solves), one more iteration changes nothing beyond rounding."""
+    dim, n, P, nu, dt = 2, 15, 2, 1.0, 0.02
+    u0 = _sine_mode(dim, n, (1, 2)) - 0.5 * _sine_mode(dim, n, (3, 1))
+    pf = O.MLPFASST(dim, n, (5, 3, 2), P, nu, dt, FULL, families=(1, 1, 1))
+    pf.set_initial(u0)
+    pf.run(200, 1e-14)
+    before = pf.U[0].copy()
+    pf.iteration()
+    np.testing.assert_allclose(pf.U[0], before, atol=1e-12)
+
+
+def test_three_level_weak_scaling_shape_of_the_paper():
+    """Sec. 4.2.2: 1D, k = nu = L = T = 1, N_x = N_t = 32, 64, 128 parallel steps, three
+    levels coarsened by 2 in space, 3 uniform nodes on the fine and middle level and backward
+    Euler on the coarsest, two V(2,2) Gauss-Seidel cycles per solve.  The paper reports that
+    the PDE error reaches its discretization level at iteration 5 (N = 32) and 3 (N = 64,
+    128): it does not grow with N.  Shape check: the iteration at which the PDE error of the
+    last step first comes within 1.6x of its final level stays <= 6 and does not grow."""
+    mg = O.MGParams(smoother=1, omega=1.0, nu1=2, nu2=2, vcycles=2)
+    reach = []
+    for N in (32, 64, 128):
+        n, P, dt = N - 1, N, 1.0 / N
+        x = np.arange(1, n + 1) / (n + 1)
+        pde = math.exp(-math.pi ** 2) * np.sin(np.pi * x)
+        pf = O.MLPFASST(1, n, (3, 3, 2), P, 1.0, dt, mg, families=(1, 1, 1))
+        pf.set_initial(np.sin(np.pi * x))
+        pf.predict()
+        errs = []
+        for _ in range(10):
+            pf.iteration()
+            errs.append(np.abs(pf.end_value() - pde).max())
+        floor = errs[-1]
+        reach.append(next(k + 1 for k, e in enumerate(errs) if e <= 1.6 * floor))
+    assert max(reach) <= 6 and reach[2] <= reach[0], reach
