@@ -60,11 +60,14 @@ typedef struct { int dim; int n; } pmg_grid;
  * order; M = 4 fourth order).  Node 0 (t = 0) carries the slice's initial value. */
 typedef struct { int count; int family; } pmg_nodes_desc;
 
-/* Level hierarchy: nlevels = 1 (SDC / parallel SDC) or 2 (PFASST / MLSDC).  The
- * coarse level uses coarse_nodes (a subset of the fine nodes, e.g. 3 of 5
- * Gauss-Lobatto nodes) and the grid (n-1)/2 (Sec. 2.3, spatial and temporal
- * coarsening). */
-typedef struct { int nlevels; pmg_nodes_desc coarse_nodes; } pmg_levels;
+/* Level hierarchy: nlevels = 1 (SDC / parallel SDC), 2 (PFASST / MLSDC) or 3.  Level 1
+ * uses coarse_nodes (a subset of the fine nodes, e.g. 3 of 5 Gauss-Lobatto nodes) and
+ * the grid (n-1)/2 (Sec. 2.3, spatial and temporal coarsening); with three levels,
+ * level 2 uses coarsest_nodes (a subset of coarse_nodes) and the grid (n-3)/4 (needs
+ * n >= 15), and the serial coarse chain runs on level 2 while level 1 sweeps every
+ * slice at once (multi-level PFASST, Sec. 2.4).  coarsest_nodes is ignored for fewer
+ * levels. */
+typedef struct { int nlevels; pmg_nodes_desc coarse_nodes; pmg_nodes_desc coarsest_nodes; } pmg_levels;
 
 #define PMG_SMOOTHER_JACOBI 0     /* weighted Jacobi, omega (Sec. 4.1.1)          */
 #define PMG_SMOOTHER_RBGS   1     /* red-black Gauss-Seidel (Sec. 4.1.2, 4.2.1)   */
@@ -117,8 +120,8 @@ int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fine_n
  *   slices >= 1;  stream: a cudaStream_t or NULL;
  *   workspace: device memory of >= pfasst_mg_workspace_bytes() bytes, 256-byte
  *   aligned, owned by the caller, or NULL to let the library cudaMalloc its own.
- * Errors: INVALID_ARG (bad sizes, n not 2^p-1, coarse nodes not a subset of the
- * fine nodes), UNSUPPORTED, OOM, CUDA.  *out is NULL on error. */
+ * Errors: INVALID_ARG (bad sizes, n not 2^p-1, a level's nodes not a subset of the
+ * next finer level's nodes), UNSUPPORTED, OOM, CUDA.  *out is NULL on error. */
 int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fine_nodes,
                      const pmg_levels *levels, double nu, double dt, int slices,
                      const pmg_options *opt, void *stream, void *workspace,
@@ -128,21 +131,24 @@ int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fine_nodes,
  * slice (start of the predictor, Sec. 2.4).  on_device: 1 if u0 is device memory. */
 int pfasst_mg_set_initial(pmg_handle h, const double *u0, int on_device);
 
-/* PFASST predictor (Sec. 2.4): FAS-restrict the spread values; in stage s, every
- * slice p >= s takes the coarse end value of slice p-1 and does one coarse sweep
- * (slice p does p+1 sweeps); interpolate the coarse correction.  With one level the
- * predictor is the spread alone.  pfasst_mg_iterate calls it when needed. */
+/* PFASST predictor (Sec. 2.4): FAS-restrict the spread values down to the coarsest
+ * level; there, in stage s, every slice p >= s takes the coarsest end value of slice
+ * p-1 and does one sweep (slice p does p+1 sweeps); interpolate the corrections level
+ * by level up.  With one level the predictor is the spread alone.
+ * pfasst_mg_iterate calls it when needed. */
 int pfasst_mg_predict(pmg_handle h);
 
 /* One SDC sweep (Eq. sdc-be; sub-steps Eq. SDCcompactLIII solved by V-cycles) on
- * every slice at `level` (0 = fine, batched over slices; 1 = coarse, FAS-corrected,
- * serial chain over slices where slice p first receives the coarse end value of
- * slice p-1 -- the blocking coarse communication of Sec. 2.4). */
+ * every slice at `level` (0 = fine, batched over slices; the coarsest level of a
+ * hierarchy: FAS-corrected, serial chain over slices where slice p first receives the
+ * end value of slice p-1 -- the blocking coarse communication of Sec. 2.4; level 1 of
+ * three: FAS-corrected, batched over slices). */
 int pfasst_mg_sweep(pmg_handle h, int level);
 
-/* PFASST iterations (Sec. 2.4): fine sweep on all slices, FAS restriction, coarse
- * chain, interpolation of the coarse correction, send-forward of fine end values,
- * collocation residual (Eq. resid).  Runs the predictor first if it has not run.
+/* PFASST iterations (Sec. 2.4): fine sweep on all slices, FAS restriction (with three
+ * levels: a level-1 sweep on all slices and a second FAS restriction), serial chain on
+ * the coarsest level, interpolation of the corrections level by level, send-forward
+ * of fine end values, collocation residual (Eq. resid).  Runs the predictor first if it has not run.
  * Stops after max_iter iterations or when the max-norm residual of every slice is
  * <= tol.  iters_done / final_res (max over slices) may be NULL.
  * Returns PMG_OK, PMG_NOT_CONVERGED, PMG_ERR_DIVERGED (NaN/Inf) or another error. */
@@ -157,8 +163,9 @@ int pfasst_mg_residual(pmg_handle h, double *res_per_slice);
  * node in [0, M]; node M of slice P-1 is the end of the block. */
 int pfasst_mg_get_solution(pmg_handle h, int slice, int node, double *out, int on_device);
 
-/* Copy the whole state of `level` (0 fine, 1 coarse): U as [slice][node][n^d],
- * dense, into host memory out (slices*nodes*N doubles). Synchronises. */
+/* Copy the whole state of `level` (0 fine, 1 coarse, 2 coarsest): U as
+ * [slice][node][n_l^d], dense, into host memory out (slices*nodes*N_l doubles).
+ * Synchronises. */
 int pfasst_mg_get_state(pmg_handle h, int level, double *out);
 
 /* Start the next block: the end value of the last slice becomes the new initial

@@ -338,6 +338,11 @@ class MLPFASST:
         st = self._state()
         lib().orc_ml_predict(ctypes.byref(self._c), ctypes.byref(st))
 
+    def sweep(self, level):
+        """One sweep on ``level`` of every slice (the serial chain on the coarsest level)."""
+        st = self._state()
+        lib().orc_ml_sweep_level(ctypes.byref(self._c), ctypes.byref(st), level)
+
     def iteration(self) -> np.ndarray:
         st = self._state()
         lib().orc_ml_iteration(ctypes.byref(self._c), ctypes.byref(st), _p(self.res))

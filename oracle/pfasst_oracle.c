@@ -920,6 +920,18 @@ void orc_ml_predict(const orc_ml *P, const orc_mlstate *S)
         for (int p = 0; p < Pn; ++p) ml_interp(P, S, l, p);
 }
 
+/* One sweep on level l of every slice, as a standalone step: on the coarsest level of
+ * two or more the serial chain (slice p first receives the end value of slice p-1),
+ * elsewhere every slice on its own. */
+void orc_ml_sweep_level(const orc_ml *P, const orc_mlstate *S, int l)
+{
+    int chain = P->nlevels >= 2 && l == P->nlevels - 1;
+    for (int p = 0; p < P->slices; ++p) {
+        if (chain && p > 0) ml_receive(P, S, l, p);
+        ml_sweep(P, S, l, p);
+    }
+}
+
 /* One PFASST iteration with L levels (reading g7b):
  *   1. sweep on level 0, every slice;
  *   2. for each intermediate level l = 1..L-2: FAS restriction l-1 -> l, sweep on l;

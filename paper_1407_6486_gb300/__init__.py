@@ -54,7 +54,7 @@ class pmg_nodes_desc(ctypes.Structure):
 
 
 class pmg_levels(ctypes.Structure):
-    _fields_ = [("nlevels", ctypes.c_int), ("coarse_nodes", pmg_nodes_desc)]
+    _fields_ = [("nlevels", ctypes.c_int), ("coarse_nodes", pmg_nodes_desc), ("coarsest_nodes", pmg_nodes_desc)]
 
 
 class pmg_options(ctypes.Structure):
@@ -602,14 +602,17 @@ class NetTrainer:
 class PFASSTSolver:
     """Owns a pfasst_mg handle and its torch workspace; methods call the C ABI."""
 
-    def __init__(self, dim, n, fine_nodes, coarse_nodes, slices, nu, dt, nlevels=2, stream=None, family=0, **opts):
-        """family: 0 Gauss-Lobatto nodes, 1 the uniform family (both levels)."""
-        self.dim, self.n, self.sf, self.sc = dim, n, fine_nodes, coarse_nodes
+    def __init__(self, dim, n, fine_nodes, coarse_nodes, slices, nu, dt, nlevels=2, stream=None, family=0,
+                 coarsest_nodes=0, **opts):
+        """family: 0 Gauss-Lobatto nodes, 1 the uniform family (every level);
+        coarsest_nodes: node count of level 2 when nlevels == 3."""
+        self.dim, self.n, self.sf, self.sc, self.s2 = dim, n, fine_nodes, coarse_nodes, coarsest_nodes
         self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
         self.opt = pfasst_mg_default_options(**opts)
         self.grid = pmg_grid(dim, n)
         self.fnodes = pmg_nodes_desc(fine_nodes, family)
-        self.levels = pmg_levels(nlevels, pmg_nodes_desc(coarse_nodes if nlevels == 2 else 0, family))
+        self.levels = pmg_levels(nlevels, pmg_nodes_desc(coarse_nodes if nlevels >= 2 else 0, family),
+                                 pmg_nodes_desc(coarsest_nodes if nlevels == 3 else 0, family))
         self.h, self.workspace = pfasst_mg_create(self.grid, self.fnodes, self.levels, nu, dt, slices, self.opt, stream)
 
     @property
@@ -637,8 +640,10 @@ class PFASSTSolver:
 
     def state(self, level=0):
         import numpy as np
-        s = self.sf if level == 0 else self.sc
-        n = self.n if level == 0 else (self.n - 1) // 2
+        s = (self.sf, self.sc, self.s2)[level]
+        n = self.n
+        for _ in range(level):
+            n = (n - 1) // 2
         return pfasst_mg_get_state(self.h, level, np.zeros((self.slices, s, n ** self.dim)))
 
     def advance(self):

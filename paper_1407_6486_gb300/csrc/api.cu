@@ -224,8 +224,18 @@ struct pmg_ctx {
   double *Uc = nullptr, *Fc = nullptr, *qc = nullptr, *tau = nullptr, *Uc0 = nullptr;
   // time-interpolated coarse correction [slice][fine node][coarse grid], MG precision
   void *dU = nullptr;
+  // level 2 of a three-level hierarchy: grid (n-3)/4, s2 nodes of family fam2
+  int s2 = 0, fam2 = 0;
+  Grid g2{};
+  long double tau2n[kMaxNodes] = {};
+  SFCoef sf2c{};
+  FASCoef fas2{};        // restriction level 1 -> 2
+  InterpCoef interp2{};  // correction level 2 -> 1
+  double c2_sub[kMaxNodes] = {};
+  double *U2 = nullptr, *F2 = nullptr, *q2 = nullptr, *tau2 = nullptr, *U20 = nullptr;
+  void *dU2 = nullptr;   // [slice][level-1 node][level-2 grid], MG precision
   Hier H;
-  void *minv = nullptr;  // (sf-1 + sc-1) slots of N3*N3 in MG precision
+  void *minv = nullptr;  // (sf-1) + (sc-1) + (s2-1) slots of N3*N3 in MG precision
   int n3 = 3;
   unsigned long long *red = nullptr;  // [3P]: rnorm, bnorm, colloc residual
   int *active = nullptr;
@@ -298,14 +308,25 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
   if (!is_pow2_minus1(grid->n) || grid->n > 1023) { why = "n must be 2^p - 1 in [3, 1023]"; return PMG_ERR_INVALID_ARG; }
   if (fn->family != 0 && fn->family != 1) { why = "node family must be 0 (Gauss-Lobatto) or 1 (uniform)"; return PMG_ERR_UNSUPPORTED; }
   if (fn->count < 2 || fn->count > kMaxNodes) { why = "fine node count must be in [2, 9]"; return PMG_ERR_INVALID_ARG; }
-  if (lv->nlevels != 1 && lv->nlevels != 2) { why = "nlevels must be 1 or 2"; return PMG_ERR_INVALID_ARG; }
-  if (lv->nlevels == 2) {
+  if (lv->nlevels < 1 || lv->nlevels > 3) { why = "nlevels must be 1, 2 or 3"; return PMG_ERR_INVALID_ARG; }
+  if (lv->nlevels >= 2) {
     if (lv->coarse_nodes.family != 0 && lv->coarse_nodes.family != 1) {
       why = "coarse node family must be 0 (Gauss-Lobatto) or 1 (uniform)";
       return PMG_ERR_UNSUPPORTED;
     }
     if (lv->coarse_nodes.count < 2 || lv->coarse_nodes.count > fn->count) { why = "bad coarse node count"; return PMG_ERR_INVALID_ARG; }
     if (grid->n < 7) { why = "two levels need n >= 7"; return PMG_ERR_INVALID_ARG; }
+  }
+  if (lv->nlevels == 3) {
+    if (lv->coarsest_nodes.family != 0 && lv->coarsest_nodes.family != 1) {
+      why = "coarsest node family must be 0 (Gauss-Lobatto) or 1 (uniform)";
+      return PMG_ERR_UNSUPPORTED;
+    }
+    if (lv->coarsest_nodes.count < 2 || lv->coarsest_nodes.count > lv->coarse_nodes.count) {
+      why = "bad coarsest node count";
+      return PMG_ERR_INVALID_ARG;
+    }
+    if (grid->n < 15) { why = "three levels need n >= 15"; return PMG_ERR_INVALID_ARG; }
   }
   if (slices < 1 || slices > 4096) { why = "slices must be in [1, 4096]"; return PMG_ERR_INVALID_ARG; }
   if (o) {
@@ -368,6 +389,11 @@ void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smooth
   }
 }
 
+// coarsest-grid inverses: one per sub-step of every level, finest level first
+int minv_slots(const pmg_ctx *h) {
+  return (h->sf - 1) + (h->nlevels >= 2 ? h->sc - 1 : 0) + (h->nlevels == 3 ? h->s2 - 1 : 0);
+}
+
 void plan_ctx(Plan &pl, pmg_ctx *h) {
   const size_t sf = (size_t)h->gf.slab * 8;
   pl.add((void **)&h->Uf, sf * h->P * h->sf);
@@ -375,7 +401,7 @@ void plan_ctx(Plan &pl, pmg_ctx *h) {
   pl.add((void **)&h->qf, sf * h->P * (h->sf - 1));
   pl.add((void **)&h->u0, sf);
   pl.add((void **)&h->dense, sf);
-  if (h->nlevels == 2) {
+  if (h->nlevels >= 2) {
     const size_t sc = (size_t)h->gc.slab * 8;
     pl.add((void **)&h->Uc, sc * h->P * h->sc);
     pl.add((void **)&h->Fc, sc * h->P * h->sc);
@@ -383,11 +409,20 @@ void plan_ctx(Plan &pl, pmg_ctx *h) {
     pl.add((void **)&h->Uc0, sc * h->P * h->sc);
     pl.add((void **)&h->qc, sc * h->P * (h->sc - 1));
   }
+  if (h->nlevels == 3) {
+    const size_t s2 = (size_t)h->g2.slab * 8;
+    pl.add((void **)&h->U2, s2 * h->P * h->s2);
+    pl.add((void **)&h->F2, s2 * h->P * h->s2);
+    pl.add((void **)&h->tau2, s2 * h->P * h->s2);
+    pl.add((void **)&h->U20, s2 * h->P * h->s2);
+    pl.add((void **)&h->q2, s2 * h->P * (h->s2 - 1));
+  }
   const Prec pr = h->opt.precision == PMG_PREC_MIXED ? F32 : F64;
   plan_hier(pl, h->H, h->dim, h->nf, h->P, pr, h->opt.smoother);
   if (h->groups > 1) plan_hier(pl, h->Hc, h->dim, h->nf, 1, pr, h->opt.smoother, 1);  // coarse chain scratch
-  if (h->nlevels == 2) pl.add(&h->dU, (size_t)h->gc.slab * h->P * h->sf * h->H.tsize);
-  const int slots = (h->sf - 1) + (h->nlevels == 2 ? h->sc - 1 : 0);
+  if (h->nlevels >= 2) pl.add(&h->dU, (size_t)h->gc.slab * h->P * h->sf * h->H.tsize);
+  if (h->nlevels == 3) pl.add(&h->dU2, (size_t)h->g2.slab * h->P * h->sc * h->H.tsize);
+  const int slots = minv_slots(h);
   pl.add(&h->minv, (size_t)slots * h->n3 * h->n3 * h->H.tsize);
   pl.add((void **)&h->red, sizeof(unsigned long long) * 3 * h->P);
   pl.add((void **)&h->active, sizeof(int) * h->P);
@@ -684,26 +719,41 @@ int fine_residual(pmg_ctx *h, bool chained = false) {
   return PMG_OK;
 }
 
-// One SDC sweep (Eq. sdc-be) on slices [p0, p0+B) of `level` (0 fine, 1 coarse).
-// F-free fine sweeps take q from the last fine_residual.
+// The state of one level of the hierarchy (0 fine, 1 coarse, 2 coarsest of three);
+// level l lives on multigrid level l of the hierarchy H (grid n_l = (n_{l-1}-1)/2)
+struct LevelRef {
+  const Grid *g;
+  int s;                        // nodes
+  double *U, *F, *q, *tau;      // tau: FAS correction (null on the fine level)
+  const SFCoef *cf;
+  const double *csub;           // c_m = dt_m nu per sub-step
+  int slot0;                    // coarsest-grid inverse of its first sub-step
+};
+
+LevelRef level_ref(pmg_ctx *h, int level) {
+  if (level == 0) return LevelRef{&h->gf, h->sf, h->Uf, h->Ff, h->qf, nullptr, &h->sff, h->cf_sub, 0};
+  if (level == 1) return LevelRef{&h->gc, h->sc, h->Uc, h->Fc, h->qc, h->tau, &h->sfc, h->cc_sub, h->sf - 1};
+  return LevelRef{&h->g2, h->s2, h->U2, h->F2, h->q2, h->tau2, &h->sf2c, h->c2_sub, (h->sf - 1) + (h->sc - 1)};
+}
+
+// One SDC sweep (Eq. sdc-be) on slices [p0, p0+B) of `level`.  Coarser levels keep
+// F = A U and add their FAS correction; F-free fine sweeps take q from the last
+// fine_residual.
 int sweep(pmg_ctx *h, int level, int p0, int B) {
   MGCtx M = mgctx(h);
-  const Grid &g = level ? h->gc : h->gf;
-  const int s = level ? h->sc : h->sf;
-  const long long stride = (long long)s * g.slab, sq = (long long)(s - 1) * g.slab;
-  double *U = (level ? h->Uc : h->Uf) + p0 * stride;
-  double *F = (level ? h->Fc : h->Ff) + p0 * stride;
-  double *q = (level ? h->qc : h->qf) + p0 * sq;
-  const double *tau = level ? h->tau + p0 * stride : nullptr;
-  const SFCoef &cf = level ? h->sfc : h->sff;
-  const bool keepF = level == 1 || !ffree(h);
+  const LevelRef v = level_ref(h, level);
+  const Grid &g = *v.g;
+  const long long stride = (long long)v.s * g.slab, sq = (long long)(v.s - 1) * g.slab;
+  double *U = v.U + p0 * stride;
+  double *F = v.F + p0 * stride;
+  double *q = v.q + p0 * sq;
+  const double *tau = v.tau ? v.tau + p0 * stride : nullptr;
+  const bool keepF = level > 0 || !ffree(h);
   Launch Ln = h->L();
-  if (keepF) PMG_CUDA(h, k_sf_rhs(Ln, g, cf, F, U, stride, tau, stride, q, sq, B));
-  for (int m = 0; m < s - 1; ++m) {
-    const double c = level ? h->cc_sub[m] : h->cf_sub[m];
-    const int slot = level ? (h->sf - 1) + m : m;
-    PMG_RET(solve_substep(M, level, B, c, h->minv_slot(slot), U + m * g.slab, stride, q + m * g.slab, sq,
-                          U + (m + 1) * g.slab, stride, nullptr, cf.sub_next != 0));
+  if (keepF) PMG_CUDA(h, k_sf_rhs(Ln, g, *v.cf, F, U, stride, tau, stride, q, sq, B));
+  for (int m = 0; m < v.s - 1; ++m) {
+    PMG_RET(solve_substep(M, level, B, v.csub[m], h->minv_slot(v.slot0 + m), U + m * g.slab, stride, q + m * g.slab,
+                          sq, U + (m + 1) * g.slab, stride, nullptr, v.cf->sub_next != 0));
     if (keepF) PMG_CUDA(h, k_apply_A(Ln, g, h->nu, U + (m + 1) * g.slab, stride, F + (m + 1) * g.slab, stride, B));
   }
   return PMG_OK;
@@ -719,11 +769,46 @@ int fas_restrict_all(pmg_ctx *h) {
   return PMG_OK;
 }
 
-// U_c[p][0] <- U_c[p-1][M_c] and F_c[p][0] = A_c U_c[p][0] for p in [p0, p0+B), p0 >= 1
-int coarse_receive(pmg_ctx *h, int p0, int B) {
-  const long long scs = (long long)h->sc * h->gc.slab;
-  PMG_CUDA(h, k_copy(h->L(), h->gc, h->Uc + (p0 - 1) * scs + (h->sc - 1) * h->gc.slab, scs, h->Uc + p0 * scs, scs, B));
-  PMG_CUDA(h, k_apply_A(h->L(), h->gc, h->nu, h->Uc + p0 * scs, scs, h->Fc + p0 * scs, scs, B));
+// FAS restriction level 1 -> 2 of every slice: level 1 keeps F = A U, and its own
+// FAS correction enters the integral it passes down
+int fas_restrict_12(pmg_ctx *h) {
+  const long long s1 = (long long)h->sc * h->gc.slab, s2 = (long long)h->s2 * h->g2.slab;
+  PMG_CUDA(h, k_fas_restrict(h->L(), h->gc, h->g2, h->fas2, h->Uc, h->Fc, s1, h->U2, h->F2, h->tau2, h->U20, s2, h->P,
+                             h->tau));
+  return PMG_OK;
+}
+
+// U_l[p][0] <- U_l[p-1][s_l - 1] and F_l[p][0] = A_l U_l[p][0] for p in [p0, p0+B),
+// p0 >= 1, on a coarse level l
+int receive(pmg_ctx *h, int level, int p0, int B) {
+  const LevelRef v = level_ref(h, level);
+  const long long st = (long long)v.s * v.g->slab;
+  PMG_CUDA(h, k_copy(h->L(), *v.g, v.U + (p0 - 1) * st + (v.s - 1) * v.g->slab, st, v.U + p0 * st, st, B));
+  PMG_CUDA(h, k_apply_A(h->L(), *v.g, h->nu, v.U + p0 * st, st, v.F + p0 * st, st, B));
+  return PMG_OK;
+}
+
+// the serial chain on the coarsest level: slice p receives the end value of slice p-1
+// (the blocking coarse communication of Sec. 2.4), then sweeps
+int coarse_chain(pmg_ctx *h) {
+  const int lc = h->nlevels - 1;
+  for (int p = 0; p < h->P; ++p) {
+    if (p > 0) PMG_RET(receive(h, lc, p, 1));
+    PMG_RET(sweep(h, lc, p, 1));
+  }
+  return PMG_OK;
+}
+
+// correction of level 2 interpolated onto every node of level 1.  Node 0 is included:
+// for slices p >= 1 the received coarsest initial value moves it, and through the
+// level-1 Lagrange weights it reaches fine nodes that no send-forward overwrites.
+// F_1 is left stale: nothing reads it before the next restriction from level 0
+// rewrites it.
+int interp_21(pmg_ctx *h) {
+  const long long s1 = (long long)h->sc * h->gc.slab, s2 = (long long)h->s2 * h->g2.slab;
+  PMG_CUDA(h, k_interp_time(h->L(), h->g2, h->interp2, h->H.pr, h->U2, h->U20, s2, h->dU2, h->P, 0));
+  PMG_CUDA(h, k_interp_space_add(h->L(), h->gc, h->g2, h->opt.interp_order, h->sc, h->H.pr, h->dU2, h->Uc, s1, h->P,
+                                 0));
   return PMG_OK;
 }
 
@@ -790,13 +875,18 @@ int run_graph(pmg_ctx *h, pmg_ctx::Captured &G, int (*body)(pmg_ctx *)) {
 
 bool use_graphs(const pmg_ctx *h) { return h->opt.use_graphs && h->opt.vcycles > 0; }
 
+// predictor (Sec. 2.4): restrict down to the coarsest level, P stages there (stage s
+// sweeps slices s..P-1 after they received the end values of s-1..P-2), interpolate up
 int predict_body(pmg_ctx *h) {
-  if (h->nlevels == 2) {
+  if (h->nlevels >= 2) {
+    const int lc = h->nlevels - 1;
     PMG_RET(fas_restrict_all(h));
+    if (h->nlevels == 3) PMG_RET(fas_restrict_12(h));
     for (int s = 0; s < h->P; ++s) {
-      if (s > 0) PMG_RET(coarse_receive(h, s, h->P - s));
-      PMG_RET(sweep(h, 1, s, h->P - s));
+      if (s > 0) PMG_RET(receive(h, lc, s, h->P - s));
+      PMG_RET(sweep(h, lc, s, h->P - s));
     }
+    if (h->nlevels == 3) PMG_RET(interp_21(h));
     PMG_RET(interp_all(h));
   }
   return ffree(h) ? fine_residual(h) : PMG_OK;  // right-hand sides of the first fine sweep
@@ -886,7 +976,7 @@ int iteration_pipe(pmg_ctx *h) {
   for (int g = 0; g < G && rc == PMG_OK && group(g, p0, B); ++g) {
     if (cudaStreamWaitEvent(h->stream, h->ev_fas[g], 0) != cudaSuccess) rc = fail(h, PMG_ERR_CUDA, "wait failed");
     for (int p = p0; p < p0 + B && rc == PMG_OK; ++p) {
-      if (p > 0) rc = coarse_receive(h, p, 1);
+      if (p > 0) rc = receive(h, 1, p, 1);
       if (rc == PMG_OK) rc = sweep(h, 1, p, 1);
     }
     if (rc == PMG_OK && cudaEventRecord(h->ev_chain[g], h->stream) != cudaSuccess)
@@ -914,18 +1004,22 @@ int iteration_pipe(pmg_ctx *h) {
   return PMG_OK;
 }
 
-// one PFASST iteration (Sec. 2.4), residual copied to hred[2P..3P) asynchronously
+// one PFASST iteration (Sec. 2.4), residual copied to hred[2P..3P) asynchronously.
+// With three levels: fine sweep, restriction, level-1 sweep on every slice at once,
+// restriction, serial chain on level 2, corrections interpolated level by level up
 int iteration(pmg_ctx *h) {
   // (a deployed network shares one scratch between all V-cycles: no overlap then)
   if (h->groups > 1 && !h->net) return iteration_pipe(h);
   const long long sfs = (long long)h->sf * h->gf.slab;
   PMG_RET(sweep(h, 0, 0, h->P));
-  if (h->nlevels == 2) {
+  if (h->nlevels >= 2) {
     PMG_RET(fas_restrict_all(h));
-    for (int p = 0; p < h->P; ++p) {
-      if (p > 0) PMG_RET(coarse_receive(h, p, 1));
-      PMG_RET(sweep(h, 1, p, 1));
+    if (h->nlevels == 3) {
+      PMG_RET(sweep(h, 1, 0, h->P));
+      PMG_RET(fas_restrict_12(h));
     }
+    PMG_RET(coarse_chain(h));
+    if (h->nlevels == 3) PMG_RET(interp_21(h));
     PMG_RET(interp_all(h, 1));
   }
   if (h->P > 1) {  // send forward: U_f[p][0] <- U_f[p-1][M_f]
@@ -976,35 +1070,54 @@ void fill_coefficients(pmg_ctx *h) {
   h->resf.s = h->sf;
   for (int m = 0; m < h->sf; ++m)
     for (int i = 0; i < h->sf; ++i) h->resf.dtQ[m][i] = (double)((long double)h->dt * Qf[m][i]);
-  if (h->nlevels == 2) {
+  // restriction from a level with s nodes t (integration matrix Q) to one with sc nodes
+  // tc (Qc): map[j] = the finer node at the time of coarse node j (-1: none)
+  auto fill_fas = [&](FASCoef &cf, int s, const long double *t, long double Q[kMaxNodes][kMaxNodes], int sc,
+                      const long double *tc, long double Qcc[kMaxNodes][kMaxNodes]) {
+    std::memset(&cf, 0, sizeof cf);
+    cf.sf = s;
+    cf.sc = sc;
+    cf.nu = h->nu;
+    for (int j = 0; j < sc; ++j) {
+      cf.map[j] = -1;
+      for (int m = 0; m < s; ++m)
+        if (fabsl(t[m] - tc[j]) < 1e-13L) cf.map[j] = m;
+      if (cf.map[j] < 0) continue;  // rejected at creation
+      for (int i = 0; i < s; ++i) cf.dtQf[j][i] = (double)((long double)h->dt * Q[cf.map[j]][i]);
+      for (int i = 0; i < sc; ++i) cf.dtQc[j][i] = (double)((long double)h->dt * Qcc[j][i]);
+    }
+  };
+  auto fill_interp = [&](InterpCoef &ic, int s, const long double *t, int sc, const long double *tc) {
+    std::memset(&ic, 0, sizeof ic);
+    ic.sf = s;
+    ic.sc = sc;
+    ic.order = h->opt.interp_order;
+    for (int m = 0; m < s; ++m) lagrange_row(sc, tc, t[m], ic.T[m]);
+  };
+  if (h->nlevels >= 2) {
     node_positions(h->sc, h->famc, h->tauc);
     integration_matrix(h->sc, h->tauc, Qc, h->famc);
     fill_sf(h->sfc, h->sc, h->tauc, Qc, h->cc_sub);
-    std::memset(&h->fas, 0, sizeof h->fas);
-    h->fas.sf = h->sf;
-    h->fas.sc = h->sc;
-    h->fas.nu = h->nu;
-    for (int j = 0; j < h->sc; ++j) {
-      h->fas.map[j] = -1;
-      for (int m = 0; m < h->sf; ++m)
-        if (fabsl(h->tauf[m] - h->tauc[j]) < 1e-13L) h->fas.map[j] = m;
-      for (int i = 0; i < h->sf; ++i) h->fas.dtQf[j][i] = (double)((long double)h->dt * Qf[h->fas.map[j]][i]);
-      for (int i = 0; i < h->sc; ++i) h->fas.dtQc[j][i] = (double)((long double)h->dt * Qc[j][i]);
-    }
-    std::memset(&h->interp, 0, sizeof h->interp);
-    h->interp.sf = h->sf;
-    h->interp.sc = h->sc;
-    h->interp.order = h->opt.interp_order;
-    for (int m = 0; m < h->sf; ++m) lagrange_row(h->sc, h->tauc, h->tauf[m], h->interp.T[m]);
+    fill_fas(h->fas, h->sf, h->tauf, Qf, h->sc, h->tauc, Qc);
+    fill_interp(h->interp, h->sf, h->tauf, h->sc, h->tauc);
+  }
+  if (h->nlevels == 3) {
+    long double Q2[kMaxNodes][kMaxNodes];
+    node_positions(h->s2, h->fam2, h->tau2n);
+    integration_matrix(h->s2, h->tau2n, Q2, h->fam2);
+    fill_sf(h->sf2c, h->s2, h->tau2n, Q2, h->c2_sub);
+    fill_fas(h->fas2, h->sc, h->tauc, Qc, h->s2, h->tau2n, Q2);
+    fill_interp(h->interp2, h->sc, h->tauc, h->s2, h->tau2n);
   }
 }
 
 int upload_minv(pmg_ctx *h) {
-  const int slots = (h->sf - 1) + (h->nlevels == 2 ? h->sc - 1 : 0);
+  const int slots = minv_slots(h);
   std::vector<double> M;
   std::vector<char> buf((size_t)slots * h->n3 * h->n3 * h->H.tsize);
   for (int s = 0; s < slots; ++s) {
-    const double c = s < h->sf - 1 ? h->cf_sub[s] : h->cc_sub[s - (h->sf - 1)];
+    const int s1 = h->sf - 1, s12 = s1 + (h->sc > 0 ? h->sc - 1 : 0);
+    const double c = s < s1 ? h->cf_sub[s] : (s < s12 ? h->cc_sub[s - s1] : h->c2_sub[s - s12]);
     coarsest_inverse(h->dim, c, M);
     for (size_t q = 0; q < M.size(); ++q) {
       char *dst = buf.data() + ((size_t)s * h->n3 * h->n3 + q) * h->H.tsize;
@@ -1027,16 +1140,20 @@ pmg_ctx *make_ctx(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_leve
   h->nc = (grid->n - 1) / 2;
   h->sf = fn->count;
   h->famf = fn->family;
-  h->famc = lv->nlevels == 2 ? lv->coarse_nodes.family : 0;
+  h->famc = lv->nlevels >= 2 ? lv->coarse_nodes.family : 0;
+  h->fam2 = lv->nlevels == 3 ? lv->coarsest_nodes.family : 0;
   h->nlevels = lv->nlevels;
-  h->sc = lv->nlevels == 2 ? lv->coarse_nodes.count : 0;
+  h->sc = lv->nlevels >= 2 ? lv->coarse_nodes.count : 0;
+  h->s2 = lv->nlevels == 3 ? lv->coarsest_nodes.count : 0;
   h->P = slices;
   h->nu = nu;
   h->dt = dt;
   h->gf = make_grid(h->dim, h->nf);
-  if (h->nlevels == 2) h->gc = make_grid(h->dim, h->nc);
+  if (h->nlevels >= 2) h->gc = make_grid(h->dim, h->nc);
+  if (h->nlevels == 3) h->g2 = make_grid(h->dim, (h->nc - 1) / 2);
   h->n3 = h->dim == 1 ? 3 : (h->dim == 2 ? 9 : 27);
-  // slice groups: only two-level PFASST with fixed V-cycle counts pipelines
+  // slice groups: only two-level PFASST with fixed V-cycle counts pipelines (with three
+  // levels the chain runs on level 2 after a batched level-1 sweep)
   int G = h->opt.slice_groups;
   // automatic: no overlap.  On the 3D workload 2 groups gain 1.5 % (every fine kernel
   // already fills the GPU), and overlapping kernels blur per-kernel timings.
@@ -1099,12 +1216,17 @@ int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_l
   if (!h) return fail(nullptr, PMG_ERR_OOM, "host allocation failed");
   h->stream = (cudaStream_t)stream;
   fill_coefficients(h);
-  if (h->nlevels == 2)
-    for (int j = 0; j < h->sc; ++j)
-      if (h->fas.map[j] < 0) {
-        delete h;
-        return fail(nullptr, PMG_ERR_INVALID_ARG, "coarse nodes are not a subset of the fine nodes");
-      }
+  bool nested = true;
+  for (int j = 0; j < h->sc && h->nlevels >= 2; ++j) nested = nested && h->fas.map[j] >= 0;
+  if (!nested) {
+    delete h;
+    return fail(nullptr, PMG_ERR_INVALID_ARG, "coarse nodes are not a subset of the fine nodes");
+  }
+  for (int j = 0; j < h->s2 && h->nlevels == 3; ++j) nested = nested && h->fas2.map[j] >= 0;
+  if (!nested) {
+    delete h;
+    return fail(nullptr, PMG_ERR_INVALID_ARG, "coarsest nodes are not a subset of the coarse nodes");
+  }
   Plan pl;
   plan_ctx(pl, h);
   if (workspace) {
@@ -1195,14 +1317,13 @@ int pfasst_mg_sweep(pmg_handle h, int level) {
     h->q_valid = false;
     return sweep(h, 0, 0, h->P);
   }
-  if (level == 1 && h->nlevels == 2) {
-    for (int p = 0; p < h->P; ++p) {
-      if (p > 0) PMG_RET(coarse_receive(h, p, 1));
-      PMG_RET(sweep(h, 1, p, 1));
-    }
-    return PMG_OK;
+  if (level >= 1 && level == h->nlevels - 1) return coarse_chain(h);
+  if (level == 1 && h->nlevels == 3) {
+    // the iteration leaves F_1 stale after the level-2 correction: refresh it first
+    PMG_CUDA(h, k_apply_A(h->L(), h->gc, h->nu, h->Uc, h->gc.slab, h->Fc, h->gc.slab, h->P * h->sc));
+    return sweep(h, 1, 0, h->P);
   }
-  return fail(h, PMG_ERR_INVALID_ARG, "level must be 0 or (with two levels) 1");
+  return fail(h, PMG_ERR_INVALID_ARG, "level must be in [0, nlevels)");
 }
 
 int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, double *final_res) {
@@ -1257,11 +1378,11 @@ int pfasst_mg_get_solution(pmg_handle h, int slice, int node, double *out, int o
 
 int pfasst_mg_get_state(pmg_handle h, int level, double *out) {
   if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
-  if (!h || !out || level < 0 || level > 1 || (level == 1 && h->nlevels < 2))
-    return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
-  const Grid &g = level ? h->gc : h->gf;
-  const int s = level ? h->sc : h->sf;
-  const double *U = level ? h->Uc : h->Uf;
+  if (!h || !out || level < 0 || level >= h->nlevels) return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
+  const LevelRef v = level_ref(h, level);
+  const Grid &g = *v.g;
+  const int s = v.s;
+  const double *U = v.U;
   const size_t N = (size_t)g.nz * g.ny * g.n;
   for (int p = 0; p < h->P; ++p)
     for (int m = 0; m < s; ++m) {

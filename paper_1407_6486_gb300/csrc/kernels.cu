@@ -287,12 +287,13 @@ __global__ void sf_rhs_kernel(Grid g, SFCoef cf, const double *__restrict__ F, c
 }
 
 // per coarse point: U_c,j = U_f,map j (injection), F_c,j = A_c U_c,j,
-// tau_j = inject(sum_i dtQf[j][i] F_f,i) - sum_i dtQc[j][i] F_c,i
+// tau_j = inject(tau_f,map j + sum_i dtQf[j][i] F_f,i) - sum_i dtQc[j][i] F_c,i
+// (tau_f = 0 on the finest level)
 template <int DIM>
 __global__ void fas_restrict_kernel(Grid gf, Grid gc, FASCoef cf, const double *__restrict__ Uf,
                                     const double *__restrict__ Ff, long long sfine, double *__restrict__ Uc,
                                     double *__restrict__ Fc, double *__restrict__ tau, double *__restrict__ Uc0,
-                                    long long scoarse, int batch) {
+                                    long long scoarse, int batch, const double *__restrict__ tauf) {
   const double ac = cf.nu * gc.ih2;
   const long long plf = (long long)gf.ny * gf.pitch;
   PMG_FOR_POINTS(gc, batch) {
@@ -313,7 +314,7 @@ __global__ void fas_restrict_kernel(Grid gf, Grid gc, FASCoef cf, const double *
       Fc[co] = Fcv[jn];
     }
     for (int jn = 0; jn < cf.sc; ++jn) {
-      double If = 0.0;
+      double If = tauf ? tauf[b * sfine + cf.map[jn] * gf.slab + fo] : 0.0;
       for (int in = 0; in < cf.sf; ++in) If += cf.dtQf[jn][in] * Ff[b * sfine + in * gf.slab + fo];
       double Ic = 0.0;
       for (int in = 0; in < cf.sc; ++in) Ic += cf.dtQc[jn][in] * Fcv[in];
@@ -822,12 +823,12 @@ cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const dou
 
 cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
                            const double *Ff, long long sfine, double *Uc, double *Fc, double *tau, double *Uc0,
-                           long long scoarse, int batch) {
+                           long long scoarse, int batch, const double *tauf) {
   dim3 gr, bl;
   config(gc, batch, gr, bl);
   Scope sc(L, K_FAS, gc, batch, 0);
   PMG_DIM_SWITCH(gf.dim, (fas_restrict_kernel<D><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, Ff, sfine, Uc, Fc, tau,
-                                                                             Uc0, scoarse, batch)))
+                                                                             Uc0, scoarse, batch, tauf)))
   return sc.done();
 }
 

@@ -219,9 +219,12 @@ cudaError_t k_sf_rhs(const Launch &L, const Grid &g, const SFCoef &cf, const dou
 // pointwise initial residual f = (T)(u_m + q_m) of the sub-step equation
 cudaError_t k_resid_pt(const Launch &L, const Grid &g, Prec pr, const double *um, long long sum, const double *qm,
                        long long sq, void *f, int batch);
+// FAS restriction with a stored fine F; tauf (stride sfine, may be null) is the fine
+// level's own FAS correction, added to its integral when the fine level is itself a
+// coarse level of a deeper hierarchy
 cudaError_t k_fas_restrict(const Launch &L, const Grid &gf, const Grid &gc, const FASCoef &cf, const double *Uf,
                            const double *Ff, long long sfine, double *Uc, double *Fc, double *tau, double *Uc0,
-                           long long scoarse, int batch);
+                           long long scoarse, int batch, const double *tauf = nullptr);
 // coarse-correction interpolation in two steps: in time on the coarse grid (dU in the
 // precision pr), then in space onto every fine node m >= m0, added to U_f (m0 = 1 when
 // the fine node 0 is overwritten by the send-forward right after)

@@ -200,3 +200,40 @@ def test_uniform_node_family_is_accepted_and_checked(lib):
                                         ctypes.byref(pmg.pmg_levels(1, pmg.pmg_nodes_desc(0, 0))), 4,
                                         ctypes.byref(o), ctypes.byref(nb))
     assert bad == pmg.PMG_ERR_UNSUPPORTED
+
+
+def _ws3(lib, g, fnodes, lv, P=4, **kw):
+    nb = ctypes.c_size_t(0)
+    o = pmg.pfasst_mg_default_options(**kw)
+    rc = lib.pfasst_mg_workspace_bytes(ctypes.byref(g), ctypes.byref(fnodes), ctypes.byref(lv), P, ctypes.byref(o),
+                                       ctypes.byref(nb))
+    return rc, nb.value
+
+
+def test_three_level_hierarchy_is_validated(lib):
+    D = pmg.pmg_nodes_desc
+    g = pmg.pmg_grid(3, 31)
+    rc2, b2 = _ws3(lib, g, D(5, 0), pmg.pmg_levels(2, D(3, 0)))
+    rc3, b3 = _ws3(lib, g, D(5, 0), pmg.pmg_levels(3, D(3, 0), D(2, 0)))
+    assert rc2 == rc3 == pmg.PMG_OK and b3 > b2  # level-2 state, its correction and its inverses
+    assert _ws3(lib, pmg.pmg_grid(2, 7), D(5, 0), pmg.pmg_levels(3, D(3, 0), D(2, 0)))[0] == pmg.PMG_ERR_INVALID_ARG
+    assert _ws3(lib, pmg.pmg_grid(2, 15), D(5, 0), pmg.pmg_levels(3, D(3, 0), D(2, 0)))[0] == pmg.PMG_OK
+    assert _ws3(lib, g, D(5, 0), pmg.pmg_levels(3, D(3, 0), D(4, 0)))[0] == pmg.PMG_ERR_INVALID_ARG
+    assert _ws3(lib, g, D(5, 0), pmg.pmg_levels(3, D(3, 0), D(1, 0)))[0] == pmg.PMG_ERR_INVALID_ARG
+    assert _ws3(lib, g, D(5, 0), pmg.pmg_levels(3, D(3, 0), D(2, 2)))[0] == pmg.PMG_ERR_UNSUPPORTED
+    assert _ws3(lib, g, D(5, 0), pmg.pmg_levels(4, D(3, 0), D(2, 0)))[0] == pmg.PMG_ERR_INVALID_ARG
+    # with two levels the coarsest description is ignored
+    assert _ws3(lib, g, D(5, 0), pmg.pmg_levels(2, D(3, 0), D(7, 5)))[0] == pmg.PMG_OK
+
+
+def test_create_rejects_coarsest_nodes_that_do_not_nest(lib):
+    """Uniform nodes: {0, 1/2, 1} is not a subset of {0, 1/3, 2/3, 1} (which is one of
+    {0, 1/6, ..., 1}); the check runs before any device allocation."""
+    D = pmg.pmg_nodes_desc
+    h = ctypes.c_void_p()
+    o = pmg.pfasst_mg_default_options()
+    rc = lib.pfasst_mg_create(ctypes.byref(pmg.pmg_grid(1, 63)), ctypes.byref(D(7, 1)),
+                              ctypes.byref(pmg.pmg_levels(3, D(4, 1), D(3, 1))), 1.0, 0.01, 2,
+                              ctypes.byref(o), None, None, 0, ctypes.byref(h))
+    assert rc == pmg.PMG_ERR_INVALID_ARG and not h.value
+    assert "coarsest nodes are not a subset" in pmg.pfasst_mg_last_error()

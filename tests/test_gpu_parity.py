@@ -410,3 +410,82 @@ def test_uniform_nodes_3d_fixed_point_is_the_midpoint_right_rule():
     end = s.solution(wl.slices - 1, 2).reshape(n, n, n)
     assert np.abs(end - want).max() <= 1e-8 * np.abs(want).max()
     s.close()
+
+
+# ---------------------------------------------------------------- three levels
+
+THREE_CASES = [
+    # dim, n, (s0, s1, s2), family, P, smoother, vcycles, interp
+    (1, 63, (5, 3, 2), 0, 4, 0, 2, 4),
+    (2, 31, (5, 3, 2), 1, 3, 1, 1, 4),     # uniform nodes: level 2 is backward Euler
+    (3, 15, (5, 3, 2), 0, 3, 1, 2, 4),     # level 2 on the 3^3 grid: exact sub-step solves
+    (3, 31, (9, 5, 3), 1, 2, 1, 2, 2),     # uniform M = 8, 4, 2
+    (2, 63, (7, 4, 2), 1, 5, 0, 1, 4),     # uniform M = 6, 3, 1
+    (2, 31, (7, 3, 2), 0, 4, 1, 2, 4),     # Gauss-Lobatto: 3 nodes nest in any odd count
+]
+
+
+@pytest.mark.parametrize("case", THREE_CASES,
+                         ids=[f"d{c[0]}n{c[1]}s{'-'.join(map(str, c[2]))}f{c[3]}P{c[4]}" for c in THREE_CASES])
+def test_three_levels_match_oracle_every_iteration(case):
+    """Multi-level PFASST (Sec. 2.4; a level-1 sweep on every slice between the two
+    restrictions, the serial chain on level 2): predictor and each iteration against
+    the oracle's three-level schedule, on all three levels."""
+    dim, n, nodes, fam, P, sm, vc, interp = case
+    s = pmg.PFASSTSolver(dim, n, nodes[0], nodes[1], P, 1.0, 0.01, nlevels=3, coarsest_nodes=nodes[2], family=fam,
+                         smoother=sm, omega=omega(sm), vcycles=vc, interp_order=interp)
+    o = O.MLPFASST(dim, n, list(nodes), P, 1.0, 0.01, O.MGParams(smoother=sm, omega=omega(sm), vcycles=vc),
+                   families=[fam] * 3, interp_order=interp)
+    u0 = _u0(dim, n)
+    s.set_initial(u0)
+    o.set_initial(u0)
+    s.predict()
+    o.predict()
+    for l in range(3):
+        assert rel(s.state(l), o.U[l]) < FP64_TOL, f"predictor, level {l}"
+    for k in range(3):
+        s.iterate(1, 0.0)
+        ores = o.iteration()
+        for l in range(3):
+            assert rel(s.state(l), o.U[l]) < FP64_TOL, f"iteration {k}, level {l}"
+        np.testing.assert_allclose(s.residual(), ores, rtol=1e-7, atol=1e-13)
+    s.close()
+
+
+def test_three_levels_converge_to_the_two_level_fixed_point_mixed():
+    """3D heat, mixed precision: both hierarchies converge to the fine collocation
+    solution (the fixed point does not depend on the coarse levels)."""
+    wl = inputs.heat3d_c3(n=63, slices=4)
+    out = []
+    for nl in (2, 3):
+        s = pmg.PFASSTSolver(3, wl.n, 5, 3, wl.slices, wl.nu, wl.dt, nlevels=nl, coarsest_nodes=2 if nl == 3 else 0,
+                             smoother=1, omega=1.0, vcycles=2, precision=1)
+        s.set_initial(wl.u0())
+        rc, it, res = s.iterate(60, 1e-12)
+        assert rc == pmg.PMG_OK, (nl, it, res)
+        out.append(s.state(0))
+        s.close()
+    assert rel(out[1], out[0]) < MIXED_TOL
+
+
+def test_three_level_standalone_sweeps_match_oracle():
+    """pfasst_mg_sweep on each level of three after two iterations: level 1 (every
+    slice; F_1 = A U_1 refreshed first, as the oracle keeps it), level 2 (the serial
+    chain), level 0."""
+    dim, n, P, nodes = 2, 31, 3, (5, 3, 2)
+    s = pmg.PFASSTSolver(dim, n, nodes[0], nodes[1], P, 1.0, 0.01, nlevels=3, coarsest_nodes=nodes[2], smoother=1,
+                         omega=1.0, vcycles=2)
+    o = O.MLPFASST(dim, n, list(nodes), P, 1.0, 0.01, O.MGParams(smoother=1, omega=1.0, vcycles=2))
+    u0 = _u0(dim, n)
+    s.set_initial(u0)
+    o.set_initial(u0)
+    s.iterate(2, 0.0)
+    o.predict()
+    o.iteration()
+    o.iteration()
+    for level in (1, 2, 0):
+        s.sweep(level)
+        o.sweep(level)
+        for l in range(3):
+            assert rel(s.state(l), o.U[l]) < FP64_TOL, (level, l)
+    s.close()
