@@ -473,6 +473,82 @@ def run_compare(args):
         print(json.dumps(line), flush=True)
 
 
+def run_weak3(args):
+    """Three-level PFASST (Sec. 2.4 with a middle level).  Part 1, the weak-scaling runs
+    of Sec. 4.2.2 on the GPU: 1D heat, k = nu = T = 1, N_x = N_t = N parallel steps
+    (N = 32 .. 1024), 3 uniform nodes on levels 0 and 1, backward Euler on level 2,
+    two V(2,2) Gauss-Seidel cycles, FP64; per N the iteration at which the PDE error of
+    the last step first comes within 1.6x of its level after 20 iterations, and the time
+    per iteration.  Part 2: the 3D workload (255^3, 32 slices, 5/3 Gauss-Lobatto nodes,
+    mixed precision) with two levels against three (5/3/2, level 2 on 63^3): time and
+    iterations to the collocation residual that two levels reach in 10 iterations."""
+    import math
+    import torch
+    import paper_1407_6486_gb300 as pmg
+    from paper_1407_6486_gb300 import _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    pmg.load()
+    weak = []
+    for N in (32, 64, 128, 256, 512, 1024):
+        n, P, dt = N - 1, N, 1.0 / N
+        x = np.arange(1, n + 1) / (n + 1)
+        pde = math.exp(-math.pi ** 2) * np.sin(np.pi * x)
+        s = pmg.PFASSTSolver(1, n, 3, 3, P, 1.0, dt, nlevels=3, coarsest_nodes=2, family=1, smoother=1, omega=1.0,
+                             nu1=2, nu2=2, vcycles=2)
+        u0 = torch.tensor(np.sin(np.pi * x), device="cuda")
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        s.set_initial(u0)
+        s.iterate(1, 0.0)  # warm-up: graph capture
+        s.set_initial(u0)
+        errs, secs = [], 0.0
+        for _ in range(20):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.iterate(1, 0.0)
+            torch.cuda.synchronize()
+            secs += time.perf_counter() - t0
+            pmg.pfasst_mg_get_solution(s.h, P - 1, 2, out)
+            errs.append(float(np.abs(out.cpu().numpy() - pde).max()))
+        reach = next(k + 1 for k, e in enumerate(errs) if e <= 1.6 * errs[-1])
+        weak.append({"N": N, "slices": P, "iterations_to_error_level": reach, "error_level": errs[-1],
+                     "ms_per_iteration": secs / 20 * 1000})
+        s.close()
+    wl = inputs.heat3d_c3()
+    u0 = torch.tensor(wl.u0(), device="cuda")
+    three, target = [], None
+    for nl in (2, 3):
+        s = pmg.PFASSTSolver(3, wl.n, 5, 3, wl.slices, wl.nu, wl.dt, nlevels=nl, coarsest_nodes=2 if nl == 3 else 0,
+                             smoother=1, omega=1.0, vcycles=2, precision=1)
+        s.set_initial(u0)
+        _, _, r10 = s.iterate(10, 0.0)  # warm-up; two levels fix the target
+        if target is None:
+            target = 1.01 * r10
+        s.set_initial(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, it, res = s.iterate(60, target)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        three.append({"levels": nl, "nodes": "5/3" if nl == 2 else "5/3/2", "seconds": sec, "iterations": it,
+                      "final_residual": res, "target": target, "reached": rc == pmg.PMG_OK})
+        s.close()
+        torch.cuda.empty_cache()
+    best = min(three, key=lambda r: r["seconds"])
+    line = {"metric": "seconds to the two-level 10-iteration residual", "value": best["seconds"], "unit": "s",
+            "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": best["seconds"] * 1000, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "heat3d_n255_P32_two_vs_three_levels", "best_levels": best["levels"],
+                       "three_vs_two": three, "weak_scaling_1d_three_levels": weak,
+                       "l2": "not flushed (state of GBs per solve)"},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 RES_TOL = 0.01  # relative tolerance on the FP64 path's residual (the bench's "fixed residual")
 
 
@@ -688,7 +764,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d",
-                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "compare"])
+                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "compare",
+                             "weak3"])
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
                          "no CPU baseline")
@@ -710,6 +787,8 @@ def main():
         run_learned(args)
     elif args.workload == "compare":
         run_compare(args)
+    elif args.workload == "weak3":
+        run_weak3(args)
     else:
         run_ours(args)
 

@@ -489,3 +489,33 @@ def test_three_level_standalone_sweeps_match_oracle():
         for l in range(3):
             assert rel(s.state(l), o.U[l]) < FP64_TOL, (level, l)
     s.close()
+
+
+def test_three_level_weak_scaling_shape_of_the_paper():
+    """Sec. 4.2.2 through the C ABI: 1D, k = nu = L = T = 1, N_x = N_t = N parallel steps,
+    three levels (3 uniform nodes on levels 0 and 1, backward Euler on level 2), two
+    V(2,2) Gauss-Seidel cycles per solve.  The PDE error of the last step reaches its
+    floor at an iteration that stays <= 6 and does not grow with N (the paper: 5, 3, 3),
+    and every iteration's error equals the oracle's."""
+    reach = []
+    for N in (32, 64, 128):
+        n, P, dt = N - 1, N, 1.0 / N
+        x = np.arange(1, n + 1) / (n + 1)
+        pde = math.exp(-math.pi ** 2) * np.sin(np.pi * x)
+        s = pmg.PFASSTSolver(1, n, 3, 3, P, 1.0, dt, nlevels=3, coarsest_nodes=2, family=1, smoother=1, omega=1.0,
+                             nu1=2, nu2=2, vcycles=2)
+        o = O.MLPFASST(1, n, (3, 3, 2), P, 1.0, dt, O.MGParams(smoother=1, omega=1.0, nu1=2, nu2=2, vcycles=2),
+                       families=(1, 1, 1))
+        s.set_initial(np.sin(np.pi * x))
+        o.set_initial(np.sin(np.pi * x))
+        o.predict()
+        errs = []
+        for _ in range(10):
+            s.iterate(1, 0.0)
+            o.iteration()
+            end = s.solution(P - 1, 2)
+            assert np.abs(end - o.end_value()).max() <= 1e-12
+            errs.append(np.abs(end - pde).max())
+        s.close()
+        reach.append(next(k + 1 for k, e in enumerate(errs) if e <= 1.6 * errs[-1]))
+    assert max(reach) <= 6 and reach[2] <= reach[0], reach
