@@ -43,14 +43,15 @@ class _MG(ctypes.Structure):
 
 class _Level(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("s", ctypes.c_int),
-                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("family", ctypes.c_int)]
+                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("family", ctypes.c_int), ("order", ctypes.c_int)]
 
 
 class _PFASST(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n_f", ctypes.c_int), ("s_f", ctypes.c_int),
                 ("s_c", ctypes.c_int), ("slices", ctypes.c_int), ("nlevels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("nu", ctypes.c_double),
-                ("dt", ctypes.c_double), ("mg", _MG), ("fam_f", ctypes.c_int), ("fam_c", ctypes.c_int)]
+                ("dt", ctypes.c_double), ("mg", _MG), ("fam_f", ctypes.c_int), ("fam_c", ctypes.c_int),
+                ("order_f", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -65,12 +66,19 @@ def lib():
         L.orc_qmatrix.argtypes = [ctypes.c_int, _D, _D]
         L.orc_lagrange_weights.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D]
         L.orc_apply_A.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+        L.orc_apply_A_o.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
         L.orc_apply_L.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+        L.orc_apply_L_o.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
         L.orc_smooth.argtypes = [ctypes.POINTER(_MG), ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+        L.orc_smooth_o.argtypes = [ctypes.POINTER(_MG), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   _D, _D]
         L.orc_restrict_fw.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
         L.orc_prolong_add.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
         L.orc_mg_solve.argtypes = [ctypes.POINTER(_MG), ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
         L.orc_mg_solve.restype = ctypes.c_int
+        L.orc_mg_solve_o.argtypes = [ctypes.POINTER(_MG), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     _D, _D]
+        L.orc_mg_solve_o.restype = ctypes.c_int
         L.orc_sweep.argtypes = [ctypes.POINTER(_Level), ctypes.POINTER(_MG), _D, _D, _D]
         L.orc_sweep.restype = ctypes.c_int
         L.orc_residual.argtypes = [ctypes.POINTER(_Level), _D, _D, _D]
@@ -140,25 +148,36 @@ def _grid(u, dim, n):
     return u
 
 
-def apply_A(dim: int, n: int, nu: float, u: np.ndarray) -> np.ndarray:
+def apply_A(dim: int, n: int, nu: float, u: np.ndarray, order: int = 2) -> np.ndarray:
+    """nu Lap_h u with the 2nd-order (Sec. 4.1) or 4th-order (Sec. 4.2) stencil."""
     u = _grid(u, dim, n)
     out = np.empty_like(u)
-    lib().orc_apply_A(dim, n, nu, _p(u), _p(out))
+    if order == 2:
+        lib().orc_apply_A(dim, n, nu, _p(u), _p(out))
+    else:
+        lib().orc_apply_A_o(dim, n, order, nu, _p(u), _p(out))
     return out
 
 
-def apply_L(dim: int, n: int, c: float, e: np.ndarray) -> np.ndarray:
+def apply_L(dim: int, n: int, c: float, e: np.ndarray, order: int = 2) -> np.ndarray:
     e = _grid(e, dim, n)
     out = np.empty_like(e)
-    lib().orc_apply_L(dim, n, c, _p(e), _p(out))
+    if order == 2:
+        lib().orc_apply_L(dim, n, c, _p(e), _p(out))
+    else:
+        lib().orc_apply_L_o(dim, n, order, c, _p(e), _p(out))
     return out
 
 
-def smooth(mg: MGParams, dim: int, n: int, c: float, f: np.ndarray, e: np.ndarray) -> np.ndarray:
+def smooth(mg: MGParams, dim: int, n: int, c: float, f: np.ndarray, e: np.ndarray, order: int = 2) -> np.ndarray:
+    """One sweep; with order 4 Gauss-Seidel runs in three colours (I+J+K) mod 3."""
     f = _grid(f, dim, n)
     e = _grid(e, dim, n).copy()
     m = mg.c()
-    lib().orc_smooth(ctypes.byref(m), dim, n, c, _p(f), _p(e))
+    if order == 2:
+        lib().orc_smooth(ctypes.byref(m), dim, n, c, _p(f), _p(e))
+    else:
+        lib().orc_smooth_o(ctypes.byref(m), dim, n, order, c, _p(f), _p(e))
     return e
 
 
@@ -176,27 +195,31 @@ def prolong_add(dim: int, n: int, ec: np.ndarray, e: np.ndarray) -> np.ndarray:
     return e
 
 
-def mg_solve(mg: MGParams, dim: int, n: int, c: float, b: np.ndarray, u: np.ndarray):
-    """Returns (u_new, V-cycles used)."""
+def mg_solve(mg: MGParams, dim: int, n: int, c: float, b: np.ndarray, u: np.ndarray, order: int = 2):
+    """Returns (u_new, V-cycles used); `order` is the finest grid's Laplacian order
+    (coarser grids are 2nd order)."""
     b = _grid(b, dim, n)
     u = _grid(u, dim, n).copy()
     m = mg.c()
-    cyc = lib().orc_mg_solve(ctypes.byref(m), dim, n, c, _p(b), _p(u))
+    if order == 2:
+        cyc = lib().orc_mg_solve(ctypes.byref(m), dim, n, c, _p(b), _p(u))
+    else:
+        cyc = lib().orc_mg_solve_o(ctypes.byref(m), dim, n, order, c, _p(b), _p(u))
     return u, cyc
 
 
-def sweep(dim, n, s, nu, dt, mg: MGParams, U, F, fas=None, family=0):
+def sweep(dim, n, s, nu, dt, mg: MGParams, U, F, fas=None, family=0, order=2):
     """One SDC sweep on one slice, in place on copies; returns (U, F, V-cycles)."""
     U = np.ascontiguousarray(U, dtype=np.float64).copy()
     F = np.ascontiguousarray(F, dtype=np.float64).copy()
-    L = _Level(dim, n, s, nu, dt, family)
+    L = _Level(dim, n, s, nu, dt, family, order)
     m = mg.c()
     cyc = lib().orc_sweep(ctypes.byref(L), ctypes.byref(m), _p(U), _p(F), _p(fas))
     return U, F, cyc
 
 
 def residual(dim, n, s, nu, dt, U, F, fas=None, family=0) -> float:
-    L = _Level(dim, n, s, nu, dt, family)
+    L = _Level(dim, n, s, nu, dt, family, 2)
     return lib().orc_residual(ctypes.byref(L), _p(np.ascontiguousarray(U)), _p(np.ascontiguousarray(F)), _p(fas))
 
 
@@ -222,7 +245,8 @@ class PFASST:
     """
 
     def __init__(self, dim, n, s_f, s_c, slices, nu, dt, mg: MGParams, nlevels=2, interp_order=4, family=0,
-                 coarse_family=None):
+                 coarse_family=None, order=2):
+        """order: Laplacian order of the fine level (2 or 4); the coarse level is 2nd order."""
         self.dim, self.n, self.s_f, self.s_c = dim, n, s_f, s_c
         self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
         self.mg = mg
@@ -234,8 +258,10 @@ class PFASST:
                 raise ValueError("coarse nodes must be a subset of the fine nodes")
             if n < 7:
                 raise ValueError("two levels need n >= 7")
+        if order == 4 and n < 7:
+            raise ValueError("the fourth-order stencil needs n >= 7")
         self._c = _PFASST(dim, n, s_f, s_c if nlevels > 1 else 2, slices, nlevels,
-                          interp_order, nu, dt, mg.c(), family, fam_c)
+                          interp_order, nu, dt, mg.c(), family, fam_c, order)
         Nf = n ** dim
         nc = (n - 1) // 2
         Nc = max(nc, 1) ** dim
@@ -279,7 +305,7 @@ class PFASST:
 class _ML(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n0", ctypes.c_int), ("slices", ctypes.c_int), ("nlevels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("s", ctypes.c_int * 3), ("fam", ctypes.c_int * 3),
-                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("mg", _MG)]
+                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("mg", _MG), ("order0", ctypes.c_int)]
 
 
 class _MLState(ctypes.Structure):
@@ -294,7 +320,7 @@ class MLPFASST:
     With two levels the schedule is the one of :class:`PFASST`.
     """
 
-    def __init__(self, dim, n, nodes, slices, nu, dt, mg: MGParams, families=None, interp_order=4):
+    def __init__(self, dim, n, nodes, slices, nu, dt, mg: MGParams, families=None, interp_order=4, order=2):
         L = len(nodes)
         assert 1 <= L <= 3
         families = list(families) if families is not None else [0] * L
@@ -312,7 +338,7 @@ class MLPFASST:
         self.grids = grids
         s = (ctypes.c_int * 3)(*(list(nodes) + [2] * (3 - L)))
         f = (ctypes.c_int * 3)(*(families + [0] * (3 - L)))
-        self._c = _ML(dim, n, slices, L, interp_order, s, f, nu, dt, mg.c())
+        self._c = _ML(dim, n, slices, L, interp_order, s, f, nu, dt, mg.c(), order)
         self.U = [np.zeros((slices, nodes[l], grids[l] ** dim)) for l in range(L)]
         self.F = [np.zeros_like(u) for u in self.U]
         self.tau = [np.zeros_like(u) for u in self.U]

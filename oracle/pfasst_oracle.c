@@ -178,8 +178,53 @@ static double nbsum(const double *u, int dim, int n, int i, int j, int k)
     return s;
 }
 
-/* out = nu * Lap_h u : nu (u_{i-1} - 2u_i + u_{i+1}) / dx^2 summed over axes */
-void orc_apply_A(int dim, int n, double nu, const double *u, double *out)
+/* Fourth-order Laplacian (Sec. 4.2 uses a fourth-order stencil; reading g23): per axis
+ * (-u_{i-2} + 16 u_{i-1} - 30 u_i + 16 u_{i+1} - u_{i+2}) / (12 dx^2).  The wall value is
+ * 0, and the one point beyond it that the stencil reaches takes the odd reflection
+ * -u of its mirror image (0-based index -2 mirrors 0, index n+1 mirrors n-1), which
+ * keeps every sine mode an eigenvector. */
+static double at_odd(const double *u, int dim, int n, int a, int i, int j, int k, int q)
+{
+    int len = ext(dim, n, a), sign = 1;
+    if (q == -1 || q == len) return 0.0;
+    if (q < -1) { q = -2 - q; sign = -1; }
+    if (q > len) { q = 2 * len - q; sign = -1; }
+    if (a == 0) return sign * at(u, dim, n, q, j, k);
+    if (a == 1) return sign * at(u, dim, n, i, q, k);
+    return sign * at(u, dim, n, i, j, q);
+}
+
+/* h^2 Lap_h u at (i,j,k) for the spatial order `order` (2 or 4) */
+static double lap_h2(const double *u, int dim, int n, int order, int i, int j, int k)
+{
+    double up = at(u, dim, n, i, j, k);
+    if (order != 4) return nbsum(u, dim, n, i, j, k) - 2.0 * dim * up;
+    double acc = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        int c = a == 0 ? i : (a == 1 ? j : k);
+        acc += (-at_odd(u, dim, n, a, i, j, k, c - 2) + 16.0 * at_odd(u, dim, n, a, i, j, k, c - 1) - 30.0 * up
+                + 16.0 * at_odd(u, dim, n, a, i, j, k, c + 1) - at_odd(u, dim, n, a, i, j, k, c + 2)) / 12.0;
+    }
+    return acc;
+}
+
+/* -h^2 times the diagonal entry of Lap_h at (i,j,k): 2 d for order 2; for order 4,
+ * 30/12 per axis, 29/12 on an axis where the point is first or last (the reflected
+ * value beyond the wall is -u at the point itself) */
+static double lap_diag_h2(int dim, int n, int order, int i, int j, int k)
+{
+    if (order != 4) return 2.0 * dim;
+    double d = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        int c = a == 0 ? i : (a == 1 ? j : k);
+        d += (c == 0 || c == n - 1) ? 29.0 / 12.0 : 30.0 / 12.0;
+    }
+    return d;
+}
+
+/* out = nu * Lap_h u with the Laplacian of the given order (2: nu (u_{i-1} - 2u_i +
+ * u_{i+1}) / dx^2 summed over axes, Sec. 4.1; 4: see lap_h2) */
+void orc_apply_A_o(int dim, int n, int order, double nu, const double *u, double *out)
 {
     double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
     int nx = ext(dim, n, 0), ny = ext(dim, n, 1), nz = ext(dim, n, 2);
@@ -188,12 +233,14 @@ void orc_apply_A(int dim, int n, double nu, const double *u, double *out)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 size_t p = ((size_t)k * ny + j) * nx + i;
-                out[p] = nu * (nbsum(u, dim, n, i, j, k) - 2.0 * dim * u[p]) * ih2;
+                out[p] = nu * lap_h2(u, dim, n, order, i, j, k) * ih2;
             }
 }
 
+void orc_apply_A(int dim, int n, double nu, const double *u, double *out) { orc_apply_A_o(dim, n, 2, nu, u, out); }
+
 /* out = (I - c Lap_h) e : the sub-step operator of Eq. (SDCcompactLIII) with c = dt_m * nu */
-static void apply_L(int dim, int n, double c, const double *e, double *out)
+static void apply_L(int dim, int n, int order, double c, const double *e, double *out)
 {
     double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
     int nx = ext(dim, n, 0), ny = ext(dim, n, 1), nz = ext(dim, n, 2);
@@ -202,8 +249,7 @@ static void apply_L(int dim, int n, double c, const double *e, double *out)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 size_t p = ((size_t)k * ny + j) * nx + i;
-                double lap = (nbsum(e, dim, n, i, j, k) - 2.0 * dim * e[p]) * ih2;
-                out[p] = e[p] - c * lap;
+                out[p] = e[p] - c * lap_h2(e, dim, n, order, i, j, k) * ih2;
             }
 }
 
@@ -232,13 +278,44 @@ typedef struct {
     int mg_maxcycles;  /* cap on V-cycles in full-solve mode              */
 } orc_mg;
 
-/* one weighted-Jacobi sweep: e <- e + omega D^{-1} (f - L e), D = 1 + 2 d c/h^2 */
-static void smooth_jacobi(int dim, int n, double c, double omega, const double *f, double *e, double *tmp)
+/* one weighted-Jacobi sweep: e <- e + omega D^{-1} (f - L e), D = diag(L) (1 + 2 d c/h^2
+ * for order 2) */
+static void smooth_jacobi(int dim, int n, int order, double c, double omega, const double *f, double *e,
+                          double *tmp)
 {
-    size_t N = npts(dim, n);
-    double h = 1.0 / (n + 1), D = 1.0 + 2.0 * dim * c / (h * h);
-    apply_L(dim, n, c, e, tmp);
-    for (size_t p = 0; p < N; ++p) e[p] += omega * (f[p] - tmp[p]) / D;
+    double h = 1.0 / (n + 1), a = c / (h * h);
+    int nx = ext(dim, n, 0), ny = ext(dim, n, 1), nz = ext(dim, n, 2);
+    apply_L(dim, n, order, c, e, tmp);
+#pragma omp parallel for if (nz * ny > 64)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t p = ((size_t)k * ny + j) * nx + i;
+                e[p] += omega * (f[p] - tmp[p]) / (1.0 + a * lap_diag_h2(dim, n, order, i, j, k));
+            }
+}
+
+/* one multicolour Gauss-Seidel sweep for the fourth-order operator (reading g24): colour
+ * (I+J+K) mod 3 of the 1-based indices, colours 0, 1, 2 in turn; points of one colour
+ * are at least 3 apart on every axis line, so none reads another of its colour, and
+ * each solves its own row with the latest values of the other colours. */
+static void smooth_gs3(int dim, int n, double c, double omega, const double *f, double *e)
+{
+    double h = 1.0 / (n + 1), a = c / (h * h);
+    int nx = ext(dim, n, 0), ny = ext(dim, n, 1), nz = ext(dim, n, 2);
+    for (int colour = 0; colour < 3; ++colour) {
+#pragma omp parallel for if (nz * ny > 64)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int s1 = (i + 1) + (dim >= 2 ? j + 1 : 0) + (dim >= 3 ? k + 1 : 0);
+                    if (s1 % 3 != colour) continue;
+                    size_t p = ((size_t)k * ny + j) * nx + i;
+                    double D = 1.0 + a * lap_diag_h2(dim, n, 4, i, j, k);
+                    double Le = e[p] - a * lap_h2(e, dim, n, 4, i, j, k);
+                    e[p] += omega * (f[p] - Le) / D;
+                }
+    }
 }
 
 /* one red-black Gauss-Seidel sweep: red points ((i+j+k) even in 1-based
@@ -261,10 +338,11 @@ static void smooth_rbgs(int dim, int n, double c, double omega, const double *f,
     }
 }
 
-static void smooth(const orc_mg *mg, int dim, int n, double c, const double *f, double *e, double *tmp)
+static void smooth(const orc_mg *mg, int dim, int n, int order, double c, const double *f, double *e, double *tmp)
 {
-    if (mg->smoother == 1) smooth_rbgs(dim, n, c, mg->omega, f, e);
-    else smooth_jacobi(dim, n, c, mg->omega, f, e, tmp);
+    if (mg->smoother == 1 && order == 4) smooth_gs3(dim, n, c, mg->omega, f, e);
+    else if (mg->smoother == 1) smooth_rbgs(dim, n, c, mg->omega, f, e);
+    else smooth_jacobi(dim, n, order, c, mg->omega, f, e, tmp);
 }
 
 /* per-axis full-weighting taps: fine 1-based index 2J-1, 2J, 2J+1 with 1/4, 1/2, 1/4 */
@@ -357,14 +435,14 @@ static int dense_solve(int N, double *A, double *b, double *x)
 
 /* exact solve of (I - c Lap_h) e = f on a small grid: the operator is assembled
  * column by column by applying it to unit vectors, then eliminated densely. */
-static void coarse_solve(int dim, int n, double c, const double *f, double *e)
+static void coarse_solve(int dim, int n, int order, double c, const double *f, double *e)
 {
     int N = (int)npts(dim, n);
     double *A = malloc(sizeof(double) * N * N), *unit = calloc(N, sizeof(double));
     double *col = malloc(sizeof(double) * N), *rhs = malloc(sizeof(double) * N);
     for (int q = 0; q < N; ++q) {
         unit[q] = 1.0;
-        apply_L(dim, n, c, unit, col);
+        apply_L(dim, n, order, c, unit, col);
         unit[q] = 0.0;
         for (int r = 0; r < N; ++r) A[r * N + q] = col[r];
     }
@@ -375,31 +453,33 @@ static void coarse_solve(int dim, int n, double c, const double *f, double *e)
 
 /* One V(nu1,nu2)-cycle for (I - c Lap_h) e = f on a grid with n = 2^p - 1
  * points per axis, with the operator rediscretised on every level ("standard
- * geometric multigrid", Sec. 4.1.1); the 3-point level is solved exactly. */
-static void vcycle(const orc_mg *mg, int dim, int n, double c, const double *f, double *e)
+ * geometric multigrid", Sec. 4.1.1); the 3-point level is solved exactly.  `order`
+ * is the Laplacian's order on this grid; every coarser grid is rediscretised with the
+ * second-order stencil (reading g24). */
+static void vcycle(const orc_mg *mg, int dim, int n, int order, double c, const double *f, double *e)
 {
-    if (n <= 3) { coarse_solve(dim, n, c, f, e); return; }
+    if (n <= 3) { coarse_solve(dim, n, order, c, f, e); return; }
     size_t N = npts(dim, n);
     int nc = (n - 1) / 2;
     size_t Nc = npts(dim, nc);
     double *tmp = malloc(sizeof(double) * N);
     double *fc = malloc(sizeof(double) * Nc), *ec = calloc(Nc, sizeof(double));
-    for (int s = 0; s < mg->nu1; ++s) smooth(mg, dim, n, c, f, e, tmp);
-    apply_L(dim, n, c, e, tmp);
+    for (int s = 0; s < mg->nu1; ++s) smooth(mg, dim, n, order, c, f, e, tmp);
+    apply_L(dim, n, order, c, e, tmp);
     for (size_t p = 0; p < N; ++p) tmp[p] = f[p] - tmp[p];       /* residual */
     restrict_fw(dim, n, tmp, fc);
-    vcycle(mg, dim, nc, c, fc, ec);
+    vcycle(mg, dim, nc, 2, c, fc, ec);
     prolong_add(dim, n, ec, e);
-    for (int s = 0; s < mg->nu2; ++s) smooth(mg, dim, n, c, f, e, tmp);
+    for (int s = 0; s < mg->nu2; ++s) smooth(mg, dim, n, order, c, f, e, tmp);
     free(tmp); free(fc); free(ec);
 }
 
 /* ||b - (I - c Lap_h) u||_inf */
-static double mg_resnorm(int dim, int n, double c, const double *b, const double *u)
+static double mg_resnorm(int dim, int n, int order, double c, const double *b, const double *u)
 {
     size_t N = npts(dim, n);
     double *t = malloc(sizeof(double) * N);
-    apply_L(dim, n, c, u, t);
+    apply_L(dim, n, order, c, u, t);
     for (size_t p = 0; p < N; ++p) t[p] = b[p] - t[p];
     double r = maxabs(t, N);
     free(t);
@@ -412,37 +492,51 @@ static double mg_resnorm(int dim, int n, double c, const double *b, const double
  * or until a cycle fails to bring the residual below stall * previous
  * (the 1e-12 / 75 % rule of Sec. 4.2.1), at most mg_maxcycles cycles.
  * Returns the number of V-cycles done. */
-int orc_mg_solve(const orc_mg *mg, int dim, int n, double c, const double *b, double *u)
+int orc_mg_solve_o(const orc_mg *mg, int dim, int n, int order, double c, const double *b, double *u)
 {
     if (mg->vcycles > 0) {
-        for (int v = 0; v < mg->vcycles; ++v) vcycle(mg, dim, n, c, b, u);
+        for (int v = 0; v < mg->vcycles; ++v) vcycle(mg, dim, n, order, c, b, u);
         return mg->vcycles;
     }
     double bn = maxabs(b, npts(dim, n));
     if (bn < 1.0) bn = 1.0;
-    double r = mg_resnorm(dim, n, c, b, u);
+    double r = mg_resnorm(dim, n, order, c, b, u);
     int cycles = 0;
     while (r > mg->mg_tol * bn && cycles < mg->mg_maxcycles) {
-        vcycle(mg, dim, n, c, b, u);
+        vcycle(mg, dim, n, order, c, b, u);
         ++cycles;
-        double rn = mg_resnorm(dim, n, c, b, u);
+        double rn = mg_resnorm(dim, n, order, c, b, u);
         if (rn >= mg->mg_stall * r) break;
         r = rn;
     }
     return cycles;
 }
 
+int orc_mg_solve(const orc_mg *mg, int dim, int n, double c, const double *b, double *u)
+{
+    return orc_mg_solve_o(mg, dim, n, 2, c, b, u);
+}
+
 /* One smoothing sweep, exported for the smoother pins. */
-void orc_smooth(const orc_mg *mg, int dim, int n, double c, const double *f, double *e)
+void orc_smooth_o(const orc_mg *mg, int dim, int n, int order, double c, const double *f, double *e)
 {
     double *tmp = malloc(sizeof(double) * npts(dim, n));
-    smooth(mg, dim, n, c, f, e, tmp);
+    smooth(mg, dim, n, order, c, f, e, tmp);
     free(tmp);
+}
+
+void orc_smooth(const orc_mg *mg, int dim, int n, double c, const double *f, double *e)
+{
+    orc_smooth_o(mg, dim, n, 2, c, f, e);
 }
 
 void orc_restrict_fw(int dim, int n, const double *r, double *fc) { restrict_fw(dim, n, r, fc); }
 void orc_prolong_add(int dim, int n, const double *ec, double *e) { prolong_add(dim, n, ec, e); }
-void orc_apply_L(int dim, int n, double c, const double *e, double *out) { apply_L(dim, n, c, e, out); }
+void orc_apply_L(int dim, int n, double c, const double *e, double *out) { apply_L(dim, n, 2, c, e, out); }
+void orc_apply_L_o(int dim, int n, int order, double c, const double *e, double *out)
+{
+    apply_L(dim, n, order, c, e, out);
+}
 
 /* ------------------------------------------------------------------------- */
 /* SDC on one time slice (Sec. 2.2)                                          */
@@ -453,7 +547,10 @@ typedef struct {
     int s;             /* number of nodes (M + 1)                */
     double nu, dt;     /* diffusion coefficient, slice length    */
     int family;        /* 0 Gauss-Lobatto, 1 uniform (see orc_nodes) */
+    int order;         /* Laplacian order: 2 (0 also means 2) or 4 */
 } orc_level;
+
+static int level_order(const orc_level *L) { return L->order == 4 ? 4 : 2; }
 
 static void level_nodes(const orc_level *L, double *tau, double *Q)
 {
@@ -486,8 +583,8 @@ int orc_sweep(const orc_level *L, const orc_mg *mg, double *U, double *F, const 
             b[p] = U[m * N + p] - dtm * Fk[(m + 1) * N + p] + I;
             if (fas) b[p] += fas[(m + 1) * N + p] - fas[m * N + p];
         }
-        cycles += orc_mg_solve(mg, L->dim, L->n, dtm * L->nu, b, U + (m + 1) * N);
-        orc_apply_A(L->dim, L->n, L->nu, U + (m + 1) * N, F + (m + 1) * N);
+        cycles += orc_mg_solve_o(mg, L->dim, L->n, level_order(L), dtm * L->nu, b, U + (m + 1) * N);
+        orc_apply_A_o(L->dim, L->n, level_order(L), L->nu, U + (m + 1) * N, F + (m + 1) * N);
     }
     free(Fk); free(b);
     return cycles;
@@ -601,7 +698,10 @@ typedef struct {
     double nu, dt;
     orc_mg mg;
     int fam_f, fam_c;  /* node families of the fine and coarse level */
+    int order_f;       /* Laplacian order of the fine level (2 or 4; 0 means 2); the coarse level is 2nd order */
 } orc_pfasst;
+
+static int fine_order(const orc_pfasst *P) { return P->order_f == 4 ? 4 : 2; }
 
 /* coarse node j coincides with fine node map[j] (coarse nodes are a subset) */
 static int node_map(const orc_pfasst *P, int *map)
@@ -673,18 +773,18 @@ static void interp_correction(const orc_pfasst *P, double *Uf, double *Ff, const
             if (w[j] != 0.0) orc_interp_add(dim, nf, P->interp_order, w[j], d, Uf + (size_t)m * Nf);
         }
     }
-    for (int m = 0; m < sf; ++m) orc_apply_A(dim, nf, P->nu, Uf + (size_t)m * Nf, Ff + (size_t)m * Nf);
+    for (int m = 0; m < sf; ++m) orc_apply_A_o(dim, nf, fine_order(P), P->nu, Uf + (size_t)m * Nf, Ff + (size_t)m * Nf);
     free(d);
 }
 
 static orc_level fine_level(const orc_pfasst *P)
 {
-    orc_level L = {P->dim, P->n_f, P->s_f, P->nu, P->dt, P->fam_f};
+    orc_level L = {P->dim, P->n_f, P->s_f, P->nu, P->dt, P->fam_f, fine_order(P)};
     return L;
 }
 static orc_level coarse_level(const orc_pfasst *P)
 {
-    orc_level L = {P->dim, (P->n_f - 1) / 2, P->s_c, P->nu, P->dt, P->fam_c};
+    orc_level L = {P->dim, (P->n_f - 1) / 2, P->s_c, P->nu, P->dt, P->fam_c, 2};
     return L;
 }
 
@@ -697,7 +797,7 @@ void orc_pfasst_spread(const orc_pfasst *P, const double *u0, double *Uf, double
         for (int m = 0; m < P->s_f; ++m) {
             double *u = Uf + ((size_t)p * P->s_f + m) * Nf;
             memcpy(u, u0, sizeof(double) * Nf);
-            orc_apply_A(P->dim, P->n_f, P->nu, u, Ff + ((size_t)p * P->s_f + m) * Nf);
+            orc_apply_A_o(P->dim, P->n_f, fine_order(P), P->nu, u, Ff + ((size_t)p * P->s_f + m) * Nf);
         }
 }
 
@@ -770,7 +870,7 @@ void orc_pfasst_iteration(const orc_pfasst *P, double *Uf, double *Ff,
     for (int p = Pn - 1; p >= 1; --p) {
         double *u0f = Uf + (size_t)p * sf * Nf;
         memcpy(u0f, Uf + ((size_t)(p - 1) * sf + sf - 1) * Nf, sizeof(double) * Nf);
-        orc_apply_A(P->dim, P->n_f, P->nu, u0f, Ff + (size_t)p * sf * Nf);
+        orc_apply_A_o(P->dim, P->n_f, fine_order(P), P->nu, u0f, Ff + (size_t)p * sf * Nf);
     }
     for (int p = 0; p < Pn; ++p)
         res[p] = orc_residual(&F, Uf + (size_t)p * sf * Nf, Ff + (size_t)p * sf * Nf, NULL);
@@ -786,7 +886,10 @@ typedef struct {
     int s[3], fam[3];          /* nodes and node family of every level        */
     double nu, dt;
     orc_mg mg;
+    int order0;                /* Laplacian order of level 0 (2 or 4; 0 means 2); coarser levels: 2 */
 } orc_ml;
+
+static int ml_order(const orc_ml *P, int l) { return l == 0 && P->order0 == 4 ? 4 : 2; }
 
 /* per level: U, F (slices x s_l x N_l), tau (FAS correction, unused on level 0) and
  * Ur (the restricted values the coarse correction is measured against) */
@@ -803,7 +906,7 @@ static int ml_n(const orc_ml *P, int l)
 
 static orc_level ml_level(const orc_ml *P, int l)
 {
-    orc_level L = {P->dim, ml_n(P, l), P->s[l], P->nu, P->dt, P->fam[l]};
+    orc_level L = {P->dim, ml_n(P, l), P->s[l], P->nu, P->dt, P->fam[l], ml_order(P, l)};
     return L;
 }
 
@@ -871,7 +974,7 @@ static void ml_interp(const orc_ml *P, const orc_mlstate *S, int l, int p)
             if (w[j] != 0.0) orc_interp_add(dim, nf, P->interp_order, w[j], d, Uf + (size_t)m * Nf);
         }
     }
-    for (int m = 0; m < sf; ++m) orc_apply_A(dim, nf, P->nu, Uf + (size_t)m * Nf, Ff + (size_t)m * Nf);
+    for (int m = 0; m < sf; ++m) orc_apply_A_o(dim, nf, ml_order(P, l), P->nu, Uf + (size_t)m * Nf, Ff + (size_t)m * Nf);
     free(d);
 }
 
@@ -888,7 +991,7 @@ static void ml_receive(const orc_ml *P, const orc_mlstate *S, int l, int p)
     size_t N = npts(P->dim, ml_n(P, l)), sl = ml_slab(P, l);
     double *u0 = S->U[l] + p * sl;
     memcpy(u0, S->U[l] + (p - 1) * sl + (size_t)(P->s[l] - 1) * N, sizeof(double) * N);
-    orc_apply_A(P->dim, ml_n(P, l), P->nu, u0, S->F[l] + p * sl);
+    orc_apply_A_o(P->dim, ml_n(P, l), ml_order(P, l), P->nu, u0, S->F[l] + p * sl);
 }
 
 void orc_ml_spread(const orc_ml *P, const double *u0, const orc_mlstate *S)
@@ -898,7 +1001,7 @@ void orc_ml_spread(const orc_ml *P, const double *u0, const orc_mlstate *S)
         for (int m = 0; m < P->s[0]; ++m) {
             double *u = S->U[0] + p * ml_slab(P, 0) + (size_t)m * N;
             memcpy(u, u0, sizeof(double) * N);
-            orc_apply_A(P->dim, P->n0, P->nu, u, S->F[0] + p * ml_slab(P, 0) + (size_t)m * N);
+            orc_apply_A_o(P->dim, P->n0, ml_order(P, 0), P->nu, u, S->F[0] + p * ml_slab(P, 0) + (size_t)m * N);
         }
 }
 
