@@ -50,8 +50,15 @@ extern "C" {
 
 /* Spatial grid: dim in {1,2,3}; n interior points per axis on the finest level,
  * n = 2^p - 1 with 3 <= n <= 1023 so that the multigrid hierarchy n -> (n-1)/2
- * reaches 3 points (Sec. 4.1.1 "standard geometric multigrid"). */
-typedef struct { int dim; int n; } pmg_grid;
+ * reaches 3 points (Sec. 4.1.1 "standard geometric multigrid").
+ * order: Laplacian stencil of the finest level (Sec. 4.2: second- or fourth-order
+ * finite differences).  0 or 2: u_{i-1} - 2u_i + u_{i+1} per axis; 4 (n >= 7):
+ * (-u_{i-2} + 16u_{i-1} - 30u_i + 16u_{i+1} - u_{i+2}) / 12 per axis, the point beyond
+ * a wall taking the odd reflection -u of its mirror image.  It applies to the fine
+ * PFASST level and to the finest grid of its multigrid solves (smoothed by weighted
+ * Jacobi, or by Gauss-Seidel in three colours (i+j+k) mod 3 instead of two); coarser
+ * PFASST levels and coarser multigrid grids use the second-order stencil. */
+typedef struct { int dim; int n; int order; } pmg_grid;
 
 /* Collocation nodes of one level: count = M + 1 nodes in [0,1] including both
  * endpoints.  family 0 = Gauss-Lobatto (Lobatto IIIA collocation); family 1 = the

@@ -46,7 +46,7 @@ NET_PARAMS = 7809  # W1[16][27], b1[16], W2[16][27][16], b2[16], W3[27][16], b3
 
 
 class pmg_grid(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int)]
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("order", ctypes.c_int)]
 
 
 class pmg_nodes_desc(ctypes.Structure):
@@ -603,13 +603,14 @@ class PFASSTSolver:
     """Owns a pfasst_mg handle and its torch workspace; methods call the C ABI."""
 
     def __init__(self, dim, n, fine_nodes, coarse_nodes, slices, nu, dt, nlevels=2, stream=None, family=0,
-                 coarsest_nodes=0, **opts):
+                 coarsest_nodes=0, order=2, **opts):
         """family: 0 Gauss-Lobatto nodes, 1 the uniform family (every level);
-        coarsest_nodes: node count of level 2 when nlevels == 3."""
+        coarsest_nodes: node count of level 2 when nlevels == 3; order: Laplacian stencil
+        of the fine level (2 or 4)."""
         self.dim, self.n, self.sf, self.sc, self.s2 = dim, n, fine_nodes, coarse_nodes, coarsest_nodes
         self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
         self.opt = pfasst_mg_default_options(**opts)
-        self.grid = pmg_grid(dim, n)
+        self.grid = pmg_grid(dim, n, order)
         self.fnodes = pmg_nodes_desc(fine_nodes, family)
         self.levels = pmg_levels(nlevels, pmg_nodes_desc(coarse_nodes if nlevels >= 2 else 0, family),
                                  pmg_nodes_desc(coarsest_nodes if nlevels == 3 else 0, family))

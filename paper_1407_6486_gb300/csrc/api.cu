@@ -208,6 +208,7 @@ struct NetDeploy {
 
 struct pmg_ctx {
   int dim = 0, nf = 0, nc = 0, sf = 0, sc = 0, P = 0, nlevels = 1;
+  int order = 2;           // Laplacian stencil of the fine level (coarser levels: 2)
   int famf = 0, famc = 0;  // node families (0 Gauss-Lobatto, 1 uniform)
   double nu = 0, dt = 0;
   pmg_options opt{};
@@ -306,6 +307,8 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
   if (!grid || !fn || !lv) { why = "null description"; return PMG_ERR_INVALID_ARG; }
   if (grid->dim < 1 || grid->dim > 3) { why = "dim must be 1, 2 or 3"; return PMG_ERR_INVALID_ARG; }
   if (!is_pow2_minus1(grid->n) || grid->n > 1023) { why = "n must be 2^p - 1 in [3, 1023]"; return PMG_ERR_INVALID_ARG; }
+  if (grid->order != 0 && grid->order != 2 && grid->order != 4) { why = "order must be 0, 2 or 4"; return PMG_ERR_INVALID_ARG; }
+  if (grid->order == 4 && grid->n < 7) { why = "the fourth-order stencil needs n >= 7"; return PMG_ERR_INVALID_ARG; }
   if (fn->family != 0 && fn->family != 1) { why = "node family must be 0 (Gauss-Lobatto) or 1 (uniform)"; return PMG_ERR_UNSUPPORTED; }
   if (fn->count < 2 || fn->count > kMaxNodes) { why = "fine node count must be in [2, 9]"; return PMG_ERR_INVALID_ARG; }
   if (lv->nlevels < 1 || lv->nlevels > 3) { why = "nlevels must be 1, 2 or 3"; return PMG_ERR_INVALID_ARG; }
@@ -349,19 +352,23 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
 // the z-marching tiled kernels pay off on large batched 3D grids; small or batch-1
 // grids (coarse levels, the serial coarse chain) keep the one-thread-per-point kernels
 bool tiled3d(const Grid &g, int B) {
-  return g.dim == 3 && g.n >= kTiled3dMinN && (long long)g.n * g.n * g.n * B >= (1LL << 24);
+  return g.dim == 3 && g.order != 4 && g.n >= kTiled3dMinN && (long long)g.n * g.n * g.n * B >= (1LL << 24);
 }
 
+int grid_order(const pmg_grid *grid) { return grid->order == 4 ? 4 : 2; }
+
 // multigrid hierarchy for `batch` grids of size n (levels n, (n-1)/2, ..., 3)
-// buffers of levels >= first (the levels a V-cycle from `first` touches)
-void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smoother, int first = 0) {
+// buffers of levels >= first (the levels a V-cycle from `first` touches); order0 is the
+// stencil of the finest grid (the coarser grids are rediscretised with 2nd order)
+void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smoother, int first = 0,
+               int order0 = 2) {
   H.L = mg_levels(n);
   H.pr = pr;
   H.tsize = pr == F64 ? 8 : 4;
   H.batch = batch;
   int nl = n;
   for (int l = 0; l < H.L; ++l) {
-    H.lev[l] = make_grid(dim, nl);
+    H.lev[l] = make_grid(dim, nl, l == 0 ? order0 : 2);
     for (int cls = 0; cls < 2; ++cls) {  // default choice; the autotuner may replace it
       Tune &t = H.tune[l][cls];
       t.fused = smoother == PMG_SMOOTHER_RBGS && tiled3d(H.lev[l], cls == 0 ? batch : 1);
@@ -379,7 +386,7 @@ void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smooth
   // the finest level from which the rest of the V-cycle fits one CTA's shared memory
   // (at least two levels, so that the tail replaces several launches)
   H.tail = -1;
-  for (int l = 0; l + 1 < H.L; ++l) {
+  for (int l = H.lev[0].order == 4 ? 1 : 0; l + 1 < H.L; ++l) {  // (the tail runs the 2nd-order stencil)
     VTailDesc d;
     if (vtail_plan(dim, H.lev[l].n, H.L - l, smoother == PMG_SMOOTHER_JACOBI ? 0 : 1, H.tsize, d) <= kVTailMaxSmem) {
       H.tail = l;
@@ -418,8 +425,8 @@ void plan_ctx(Plan &pl, pmg_ctx *h) {
     pl.add((void **)&h->q2, s2 * h->P * (h->s2 - 1));
   }
   const Prec pr = h->opt.precision == PMG_PREC_MIXED ? F32 : F64;
-  plan_hier(pl, h->H, h->dim, h->nf, h->P, pr, h->opt.smoother);
-  if (h->groups > 1) plan_hier(pl, h->Hc, h->dim, h->nf, 1, pr, h->opt.smoother, 1);  // coarse chain scratch
+  plan_hier(pl, h->H, h->dim, h->nf, h->P, pr, h->opt.smoother, 0, h->order);
+  if (h->groups > 1) plan_hier(pl, h->Hc, h->dim, h->nf, 1, pr, h->opt.smoother, 1, h->order);  // coarse chain scratch
   if (h->nlevels >= 2) pl.add(&h->dU, (size_t)h->gc.slab * h->P * h->sf * h->H.tsize);
   if (h->nlevels == 3) pl.add(&h->dU2, (size_t)h->g2.slab * h->P * h->sc * h->H.tsize);
   const int slots = minv_slots(h);
@@ -464,9 +471,10 @@ int smooth_with(MGCtx &M, const Tune &t, int l, int B, double c, void *&cur, boo
     PMG_CUDA(M.h, k_rbgs_sweep3d(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], u_upd, su, B, first,
                                  u_upd != nullptr, t.param, t.threads));
     cur = out;
-  } else {
-    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 0, first, t.param));
-    PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, 1, false, t.param));
+  } else {  // red, black (and a third colour for the fourth-order stencil)
+    for (int colour = 0; colour < (H.lev[l].order == 4 ? 3 : 2); ++colour)
+      PMG_CUDA(M.h, k_smooth_rbgs(M.L, H.lev[l], c, o.omega, H.pr, cur, H.f[l], B, colour, first && colour == 0,
+                                  t.param));
   }
   return PMG_OK;
 }
@@ -653,7 +661,7 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
       std::vector<Tune> cand;
       for (int th : {128, 256, 512}) cand.push_back(Tune{0, th, 256});
       const Grid &g = H.lev[l];
-      if (M.o->smoother == PMG_SMOOTHER_RBGS && g.dim == 3 && g.n >= 15)
+      if (M.o->smoother == PMG_SMOOTHER_RBGS && g.dim == 3 && g.n >= 15 && g.order != 4)
         for (int zc : {8, 16, 32})
           if (zc <= g.n) {
             cand.push_back(Tune{1, zc, 256});
@@ -1148,7 +1156,8 @@ pmg_ctx *make_ctx(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_leve
   h->P = slices;
   h->nu = nu;
   h->dt = dt;
-  h->gf = make_grid(h->dim, h->nf);
+  h->order = grid_order(grid);
+  h->gf = make_grid(h->dim, h->nf, h->order);
   if (h->nlevels >= 2) h->gc = make_grid(h->dim, h->nc);
   if (h->nlevels == 3) h->g2 = make_grid(h->dim, (h->nc - 1) / 2);
   h->n3 = h->dim == 1 ? 3 : (h->dim == 2 ? 9 : 27);
@@ -1422,6 +1431,7 @@ int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int par
   if (fused >= 1) {
     if (h->opt.smoother != PMG_SMOOTHER_RBGS || g.dim != 3 || g.n < 15 || param < 0 || param > g.n)
       return fail(h, PMG_ERR_UNSUPPORTED, "the fused sweep needs 3D red-black Gauss-Seidel, n >= 15, 0 <= z chunk <= n");
+    if (g.order == 4) return fail(h, PMG_ERR_UNSUPPORTED, "the fused sweeps run the second-order stencil only");
     if (fused == 1 && threads != 256 && !(threads == 512 && g.pitch >= 128))
       return fail(h, PMG_ERR_INVALID_ARG, "fused sweep threads: 256, or 512 for rows of >= 128");
     if (fused == 2 && !rbgs_tma_supported(g, h->H.pr))
@@ -1545,7 +1555,7 @@ int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const d
   pmg_options o;
   if (opt) o = *opt; else pfasst_mg_default_options(&o);
   cudaStream_t st = (cudaStream_t)stream;
-  Grid g = make_grid(grid->dim, grid->n);
+  Grid g = make_grid(grid->dim, grid->n, grid_order(grid));
   Hier H;
   Plan pl;
   double *bp = nullptr, *up = nullptr;
@@ -1554,7 +1564,8 @@ int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const d
   int *active = nullptr;
   pl.add((void **)&bp, (size_t)g.slab * batch * 8);
   pl.add((void **)&up, (size_t)g.slab * batch * 8);
-  plan_hier(pl, H, grid->dim, grid->n, batch, o.precision == PMG_PREC_MIXED ? F32 : F64, o.smoother);
+  plan_hier(pl, H, grid->dim, grid->n, batch, o.precision == PMG_PREC_MIXED ? F32 : F64, o.smoother, 0,
+            grid_order(grid));
   const int n3 = grid->dim == 1 ? 3 : (grid->dim == 2 ? 9 : 27);
   pl.add(&minv, (size_t)n3 * n3 * H.tsize);
   pl.add((void **)&red, sizeof(unsigned long long) * 2 * batch);
@@ -2184,9 +2195,9 @@ int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int
     return fail(h, PMG_ERR_UNSUPPORTED, "the learned correction needs dim 3, red-black Gauss-Seidel and nu1 >= 2");
   Hier &H = h->H;
   const int nmin = min_n > 7 ? min_n : 7;
-  int lfin = -1, lend = 0;  // eligible levels [lfin, lend): n >= nmin, not the coarsest
+  int lfin = -1, lend = 0;  // eligible levels [lfin, lend): n >= nmin, not the coarsest, 2nd order
   for (int l = 0; l < H.L - 1; ++l)
-    if (H.lev[l].n >= nmin) {
+    if (H.lev[l].n >= nmin && H.lev[l].order != 4) {
       if (lfin < 0) lfin = l;
       lend = l + 1;
     }
@@ -2320,14 +2331,15 @@ extern "C" int pfasst_mg_helmholtz_solve_noalloc(const pmg_grid *grid, double c,
   if (o.vcycles < 1)
     return fail(nullptr, PMG_ERR_UNSUPPORTED, "the allocation-free solve runs a fixed number of V-cycles (vcycles >= 1)");
   cudaStream_t st = (cudaStream_t)stream;
-  Grid g = make_grid(grid->dim, grid->n);
+  Grid g = make_grid(grid->dim, grid->n, grid_order(grid));
   Hier H;
   Plan pl;
   double *bp = nullptr, *up = nullptr;
   void *minv = nullptr;
   pl.add((void **)&bp, (size_t)g.slab * batch * 8);
   pl.add((void **)&up, (size_t)g.slab * batch * 8);
-  plan_hier(pl, H, grid->dim, grid->n, batch, o.precision == PMG_PREC_MIXED ? F32 : F64, o.smoother);
+  plan_hier(pl, H, grid->dim, grid->n, batch, o.precision == PMG_PREC_MIXED ? F32 : F64, o.smoother, 0,
+            grid_order(grid));
   const int n3 = grid->dim == 1 ? 3 : (grid->dim == 2 ? 9 : 27);
   pl.add(&minv, (size_t)n3 * n3 * H.tsize);
   if (pl.total > kNoAllocScratchBytes)

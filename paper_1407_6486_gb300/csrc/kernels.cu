@@ -52,6 +52,48 @@ __device__ __forceinline__ T nbsum(const T *__restrict__ u, const Grid &g, int i
   return s;
 }
 
+// one axis of h^2 times the fourth-order Laplacian at index c of an axis of length len
+// (stride st): (-u_{c-2} + 16 u_{c-1} - 30 u_c + 16 u_{c+1} - u_{c+2}) / 12.  The wall
+// value is zero; the one point beyond the wall that the stencil reaches is the odd
+// reflection -u of its mirror image, which for the first and last point of the axis is
+// the point itself (Sec. 4.2 stencil; the reflection keeps sine modes eigenvectors).
+template <typename T>
+__device__ __forceinline__ T axis4(const T *__restrict__ u, long long off, int c, int len, long long st, T uc) {
+  const T m1 = c >= 1 ? u[off - st] : T(0);
+  const T m2 = c >= 2 ? u[off - 2 * st] : (c == 0 ? -uc : T(0));
+  const T p1 = c + 1 < len ? u[off + st] : T(0);
+  const T p2 = c + 2 < len ? u[off + 2 * st] : (c == len - 1 ? -uc : T(0));
+  return (-m2 + T(16) * m1 - T(30) * uc + T(16) * p1 - p2) / T(12);
+}
+
+// h^2 times the fourth-order Laplacian at one point
+template <int DIM, typename T>
+__device__ __forceinline__ T lap4_h2(const T *__restrict__ u, const Grid &g, int i, int j, int k, long long off) {
+  const T uc = u[off];
+  T s = axis4(u, off, i, g.n, 1, uc);
+  if (DIM >= 2) s += axis4(u, off, j, g.ny, g.pitch, uc);
+  if (DIM >= 3) s += axis4(u, off, k, g.nz, (long long)g.ny * g.pitch, uc);
+  return s;
+}
+
+// h^2 Lap_h u at one point, for the grid's stencil order
+template <int DIM, typename T>
+__device__ __forceinline__ T lap_h2(const T *__restrict__ u, const Grid &g, int i, int j, int k, long long off) {
+  if (g.order == 4) return lap4_h2<DIM>(u, g, i, j, k, off);
+  return nbsum<DIM>(u, g, i, j, k, off) - T(2 * DIM) * u[off];
+}
+
+// -h^2 times the diagonal entry of Lap_h: 2 DIM, or for the fourth-order stencil 30/12
+// per axis (29/12 where the point is first or last on the axis: its reflected image)
+template <int DIM, typename T>
+__device__ __forceinline__ T diag_h2(const Grid &g, int i, int j, int k) {
+  if (g.order != 4) return T(2 * DIM);
+  T d = (i == 0 || i == g.n - 1) ? T(29) / T(12) : T(30) / T(12);
+  if (DIM >= 2) d += (j == 0 || j == g.ny - 1) ? T(29) / T(12) : T(30) / T(12);
+  if (DIM >= 3) d += (k == 0 || k == g.nz - 1) ? T(29) / T(12) : T(30) / T(12);
+  return d;
+}
+
 // max-reduce nonnegative doubles (NaN wins) across a warp, one atomic per warp
 __device__ __forceinline__ void warp_max_atomic(double v, unsigned long long *dst) {
   const unsigned full = 0xffffffffu;
@@ -79,7 +121,7 @@ __global__ void residual0_kernel(Grid g, double c, const double *__restrict__ um
         const long long off = ((long long)k * g.ny + j) * g.pitch + i;
         const double *U1 = u1 + b * s1;
         const double uc = U1[off];
-        const double Lu = uc - a * (nbsum<DIM>(U1, g, i, j, k, off) - 2.0 * DIM * uc);
+        const double Lu = uc - a * lap_h2<DIM>(U1, g, i, j, k, off);
         const double rhs = um[b * sum + off] + (qm ? qm[b * sq + off] : 0.0);
         const double r = rhs - Lu;
         f[b * g.slab + off] = (TO)r;
@@ -103,7 +145,16 @@ __global__ void jacobi_kernel(Grid g, T c, T omega, const T *__restrict__ ein, T
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
     const long long o = b * g.slab + off;
-    if (first) {
+    if (g.order == 4) {  // diagonal varies next to the walls
+      const T Dp = T(1) + a * diag_h2<DIM, T>(g, i, j, k);
+      if (first) {
+        eout[o] = omega * f[o] / Dp;
+      } else {
+        const T *E = ein + b * g.slab;
+        const T ec = E[off];
+        eout[o] = ec + omega * (f[o] - (ec - a * lap_h2<DIM>(E, g, i, j, k, off))) / Dp;
+      }
+    } else if (first) {
       eout[o] = wD * f[o];
     } else {
       const T *E = ein + b * g.slab;
@@ -114,7 +165,9 @@ __global__ void jacobi_kernel(Grid g, T c, T omega, const T *__restrict__ ein, T
   }
 }
 
-// red = (i+j+k) even in 1-based interior indices of the existing axes
+// red = (i+j+k) even in 1-based interior indices of the existing axes.  On a grid with
+// the fourth-order stencil the colour is (i+j+k) mod 3 instead (three half-sweeps):
+// points of one colour are at least 3 apart on every axis, outside each other's stencil.
 template <int DIM, typename T>
 __global__ void rbgs_kernel(Grid g, T c, T omega, T *e, const T *__restrict__ f, int batch, int colour,
                             int first) {
@@ -123,9 +176,20 @@ __global__ void rbgs_kernel(Grid g, T c, T omega, T *e, const T *__restrict__ f,
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
     const long long o = b * g.slab + off;
-    const int par = (i + j + k + DIM) & 1;
+    const int par = g.order == 4 ? (i + j + k + DIM) % 3 : (i + j + k + DIM) & 1;
     if (par != colour) {
       if (first && colour == 0) e[o] = T(0);
+      continue;
+    }
+    if (g.order == 4) {
+      const T Dp = T(1) + a * diag_h2<DIM, T>(g, i, j, k);
+      if (first && colour == 0) {
+        e[o] = omega * f[o] / Dp;
+        continue;
+      }
+      const T *E = e + b * g.slab;
+      const T ec = E[off];
+      e[o] = ec + omega * (f[o] - (ec - a * lap_h2<DIM>(E, g, i, j, k, off))) / Dp;
       continue;
     }
     if (first && colour == 0) {
@@ -157,7 +221,7 @@ __global__ void resrestrict_kernel(Grid gf, Grid gc, T c, const T *__restrict__ 
           const int fk = DIM >= 3 ? 2 * k + 1 + cz : 0;
           const long long fo = ((long long)fk * gf.ny + fj) * gf.pitch + fi;
           const T ec = E[fo];
-          const T r = Fp[fo] - (ec - a * (nbsum<DIM>(E, gf, fi, fj, fk, fo) - T(2 * DIM) * ec));
+          const T r = Fp[fo] - (ec - a * lap_h2<DIM>(E, gf, fi, fj, fk, fo));
           T w = w3[cx + 1];
           if (DIM >= 2) w *= w3[cy + 1];
           if (DIM >= 3) w *= w3[cz + 1];
@@ -255,7 +319,7 @@ __global__ void apply_A_kernel(Grid g, double nu, const double *__restrict__ u, 
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
     const double *U = u + b * su;
-    F[b * sF + off] = a * (nbsum<DIM>(U, g, i, j, k, off) - 2.0 * DIM * U[off]);
+    F[b * sF + off] = a * lap_h2<DIM>(U, g, i, j, k, off);
   }
 }
 
@@ -474,8 +538,9 @@ __global__ void colloc_residual_kernel(Grid g, ResCoef cf, const double *__restr
 //   q_m = P_{m+1} - P_m - U_{m+1}: u_m + q_m is the initial residual of sub-step m
 //   of the next sweep (Eq. SDCcompactLIII with initial guess u^k_{m+1}).
 // cf.dtQ holds (nu / h^2) dt Q here (scaled by the launcher).  S = number of nodes,
-// a compile-time constant so that no predicated-off FP64 work is issued.
-template <int DIM, int S>
+// a compile-time constant so that no predicated-off FP64 work is issued; O4 = the
+// fourth-order stencil.
+template <int DIM, int S, bool O4>
 __global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, const double *__restrict__ U, long long stride,
                                          double *__restrict__ q, long long sq, int batch, unsigned long long *res) {
   for (int zb = blockIdx.z; zb < g.nz * batch; zb += gridDim.z) {
@@ -491,7 +556,7 @@ __global__ void fine_rhs_residual_kernel(Grid g, ResCoef cf, const double *__res
         for (int jn = 0; jn < S; ++jn) {
           const double *Uj = Ub + jn * g.slab;
           Uv[jn] = Uj[off];
-          Gv[jn] = nbsum<DIM>(Uj, g, i, j, k, off) - 2.0 * DIM * Uv[jn];
+          Gv[jn] = O4 ? lap4_h2<DIM>(Uj, g, i, j, k, off) : nbsum<DIM>(Uj, g, i, j, k, off) - 2.0 * DIM * Uv[jn];
         }
         double Pprev = 0.0;
 #pragma unroll
@@ -606,7 +671,7 @@ __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double
     for (int in = 0; in < NF; ++in) {
       if (SF == 0 && in >= cf.sf) break;
       const double *U = Uf + b * sfine + in * gf.slab;
-      Ffv[in] = af * (nbsum<DIM>(U, gf, fi, fj, fk, fo) - 2.0 * DIM * U[fo]);
+      Ffv[in] = af * lap_h2<DIM>(U, gf, fi, fj, fk, fo);
     }
 #pragma unroll
     for (int jn = 0; jn < NC; ++jn) {
@@ -893,15 +958,19 @@ cudaError_t k_fine_rhs_residual(const Launch &L, const Grid &g, const ResCoef &c
   long long nblk = (total + 255) / 256;
   if (nblk > 152 * 8) nblk = 152 * 8;
   const size_t csmem = sizeof(unsigned long long) * batch;
-  chained = chained && batch > 1 && csmem <= 48 * 1024;
+  // (the chained variant serves the second-order stencil only)
+  chained = chained && batch > 1 && csmem <= 48 * 1024 && g.order != 4;
 #define PMG_FRR(S_)                                                                                            \
   case S_:                                                                                                     \
     if (chained)                                                                                               \
       PMG_DIM_SWITCH(g.dim, (fine_rhs_chain_kernel<D, S_><<<(unsigned)nblk, 256, csmem, L.stream>>>(           \
                                 g, scaled, U, stride, q, sq, batch, res)))                                     \
+    else if (g.order == 4)                                                                                     \
+      PMG_DIM_SWITCH(g.dim, (fine_rhs_residual_kernel<D, S_, true><<<gr, bl, 0, L.stream>>>(                   \
+                                g, scaled, U, stride, q, sq, batch, res)))                                     \
     else                                                                                                       \
-      PMG_DIM_SWITCH(g.dim, (fine_rhs_residual_kernel<D, S_><<<gr, bl, 0, L.stream>>>(g, scaled, U, stride, q, sq, \
-                                                                                       batch, res)));          \
+      PMG_DIM_SWITCH(g.dim, (fine_rhs_residual_kernel<D, S_, false><<<gr, bl, 0, L.stream>>>(                  \
+                                g, scaled, U, stride, q, sq, batch, res)));                                    \
     break;
   switch (cf.s) {
     PMG_FRR(2) PMG_FRR(3) PMG_FRR(4) PMG_FRR(5) PMG_FRR(6) PMG_FRR(7) PMG_FRR(8) PMG_FRR(9)

@@ -27,12 +27,14 @@ struct Grid {
   int ny, nz;       // n or 1 for missing axes
   long long slab;   // elements of one grid function (nz * ny * pitch)
   double ih2;       // 1 / h^2 = (n + 1)^2
+  int order;        // Laplacian stencil: 2 (3 points per axis) or 4 (5 points per axis)
 };
 
-inline Grid make_grid(int dim, int n) {
+inline Grid make_grid(int dim, int n, int order = 2) {
   Grid g;
   g.dim = dim;
   g.n = n;
+  g.order = order;
   g.pitch = n + 1;
   g.ny = dim >= 2 ? n : 1;
   g.nz = dim >= 3 ? n : 1;

@@ -306,7 +306,7 @@ cudaError_t launch_tma_pitch(const Launch &L, const Grid &g, float a, float iD, 
 int rbgs_tma_threads() { return TNT; }
 
 bool rbgs_tma_supported(const Grid &g, Prec pr) {
-  return pr == F32 && g.dim == 3 && (g.pitch == 128 || g.pitch == 256) && encoder() != nullptr;
+  return pr == F32 && g.dim == 3 && g.order != 4 && (g.pitch == 128 || g.pitch == 256) && encoder() != nullptr;
 }
 
 cudaError_t k_rbgs_sweep3d_tma(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout,

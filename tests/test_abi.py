@@ -237,3 +237,14 @@ def test_create_rejects_coarsest_nodes_that_do_not_nest(lib):
                               ctypes.byref(o), None, None, 0, ctypes.byref(h))
     assert rc == pmg.PMG_ERR_INVALID_ARG and not h.value
     assert "coarsest nodes are not a subset" in pmg.pfasst_mg_last_error()
+
+
+def test_stencil_order_is_validated(lib):
+    D = pmg.pmg_nodes_desc
+    lv = pmg.pmg_levels(2, D(3, 0))
+    for order, n, want in ((0, 31, pmg.PMG_OK), (2, 31, pmg.PMG_OK), (4, 31, pmg.PMG_OK), (4, 7, pmg.PMG_OK),
+                           (3, 31, pmg.PMG_ERR_INVALID_ARG), (4, 3, pmg.PMG_ERR_INVALID_ARG)):
+        rc, _ = _ws3(lib, pmg.pmg_grid(2, n, order), D(5, 0), lv if n >= 7 else pmg.pmg_levels(1, D(0, 0)))
+        assert rc == want, (order, n, rc)
+    # the fourth-order fine level needs no extra device memory
+    assert _ws3(lib, pmg.pmg_grid(3, 31, 4), D(5, 0), lv)[1] == _ws3(lib, pmg.pmg_grid(3, 31, 2), D(5, 0), lv)[1]
