@@ -480,8 +480,8 @@ def run_weak3(args):
     two V(2,2) Gauss-Seidel cycles, FP64; per N the iteration at which the PDE error of
     the last step first comes within 1.6x of its level after 20 iterations, and the time
     per iteration.  Part 2: the 3D workload (255^3, 32 slices, 5/3 Gauss-Lobatto nodes,
-    mixed precision) with two levels against three (5/3/2, level 2 on 63^3): time and
-    iterations to the collocation residual that two levels reach in 10 iterations."""
+    mixed precision) with two levels against three (5/3/3 and 5/3/2, level 2 on 63^3): time
+    and iterations to the collocation residual that two levels reach in 10 iterations."""
     import math
     import torch
     import paper_1407_6486_gb300 as pmg
@@ -519,8 +519,8 @@ def run_weak3(args):
     wl = inputs.heat3d_c3()
     u0 = torch.tensor(wl.u0(), device="cuda")
     three, target = [], None
-    for nl in (2, 3):
-        s = pmg.PFASSTSolver(3, wl.n, 5, 3, wl.slices, wl.nu, wl.dt, nlevels=nl, coarsest_nodes=2 if nl == 3 else 0,
+    for nl, s2 in ((2, 0), (3, 3), (3, 2)):
+        s = pmg.PFASSTSolver(3, wl.n, 5, 3, wl.slices, wl.nu, wl.dt, nlevels=nl, coarsest_nodes=s2,
                              smoother=1, omega=1.0, vcycles=2, precision=1)
         s.set_initial(u0)
         _, _, r10 = s.iterate(10, 0.0)  # warm-up; two levels fix the target
@@ -532,7 +532,7 @@ def run_weak3(args):
         rc, it, res = s.iterate(60, target)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
-        three.append({"levels": nl, "nodes": "5/3" if nl == 2 else "5/3/2", "seconds": sec, "iterations": it,
+        three.append({"levels": nl, "nodes": "5/3" if nl == 2 else f"5/3/{s2}", "seconds": sec, "iterations": it,
                       "final_residual": res, "target": target, "reached": rc == pmg.PMG_OK})
         s.close()
         torch.cuda.empty_cache()
@@ -544,6 +544,79 @@ def run_weak3(args):
             "config": {"workload": "heat3d_n255_P32_two_vs_three_levels", "best_levels": best["levels"],
                        "three_vs_two": three, "weak_scaling_1d_three_levels": weak,
                        "l2": "not flushed (state of GBs per solve)"},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_order4(args):
+    """The three discretisations of the paper's 3D study (Sec. 4.2.1): u_t = nu Lap u on the
+    unit cube, nu = 1/3, u0 = sin(pi x) sin(pi y) sin(pi z), T = 1, uniform nodes:
+      2/2: 127^3, 2nd-order stencil, 128 steps, midpoint + right node (M = 2), coarse
+           backward Euler on 63^3;
+      2/4: 127^3, 2nd-order stencil, 24 steps, M = 4 (fourth order), coarse backward Euler;
+      4/4: 31^3, 4th-order stencil, 24 steps, M = 4, coarse 15^3 with the 2nd-order
+           stencil and backward Euler.
+    Each runs as PFASST with up to 32 steps batched on the GPU per block (the paper's
+    largest number of time ranks; 128 steps = 4 blocks one after another) and as serial
+    ISDC (one step after another), with two V(2,2) red-black Gauss-Seidel cycles per
+    sub-step in mixed precision, until the collocation residual of every step is <= 1e-9
+    (the paper's tolerance).  Reported: time, iterations, and the max error of the final
+    value against the analytical solution exp(-pi^2) sin sin sin."""
+    import math
+    import torch
+    import paper_1407_6486_gb300 as pmg
+    from paper_1407_6486_gb300 import _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    pmg.load()
+    nu, T, tol, maxit = 1.0 / 3.0, 1.0, 1e-9, 200
+    configs = [("2/2", 127, 2, 128, 3), ("2/4", 127, 2, 24, 5), ("4/4", 31, 4, 24, 5)]
+    rows = []
+    for name, n, order, steps, nodes in configs:
+        x = np.arange(1, n + 1) / (n + 1)
+        s1 = np.sin(np.pi * x)
+        u0 = np.einsum("k,j,i->kji", s1, s1, s1).reshape(-1)
+        exact = math.exp(-3 * math.pi ** 2 * nu * T) * u0
+        u0d = torch.tensor(u0, device="cuda")
+        out = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+        dt = T / steps
+        for method in ("pfasst", "isdc"):
+            P, nl = (min(steps, 32), 2) if method == "pfasst" else (1, 1)
+            s = pmg.PFASSTSolver(3, n, nodes, 2 if nl == 2 else 0, P, nu, dt, nlevels=nl, family=1, order=order,
+                                 smoother=1, omega=1.0, nu1=2, nu2=2, vcycles=2, precision=1)
+
+            def solve():
+                # blocks of P steps; each block starts from the previous block's end value
+                u, its, ok, res = u0d, 0, True, 0.0
+                for _ in range(steps // P):
+                    s.set_initial(u)
+                    rc, it, r = s.iterate(maxit, tol)
+                    its, ok, res = its + it, ok and rc == pmg.PMG_OK, max(res, r)
+                    pmg.pfasst_mg_get_solution(s.h, P - 1, nodes - 1, out)
+                    u = out.clone()
+                return its, res, ok
+
+            solve()  # warm-up: graph capture, autotuned kernels
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its, res, ok = solve()
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            err = float(np.abs(out.cpu().numpy() - exact).max())
+            rows.append({"config": name, "method": method, "grid": f"{n}^3", "stencil_order": order, "steps": steps,
+                         "steps_per_block": P, "nodes": nodes, "seconds": sec, "iterations": its, "final_residual": res,
+                         "reached_1e-9": ok, "max_error_vs_exact": err})
+            s.close()
+            torch.cuda.empty_cache()
+    best = min((r for r in rows if r["reached_1e-9"]), key=lambda r: r["seconds"], default=rows[0])
+    line = {"metric": "seconds to collocation residual 1e-9", "value": best["seconds"], "unit": "s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": best["seconds"] * 1000, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "heat3d_sinsinsin_T1_three_discretisations", "best": best["config"] + " " +
+                       best["method"], "runs": rows, "l2": "not flushed between runs"},
             "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -765,7 +838,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d",
                     choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "compare",
-                             "weak3"])
+                             "weak3", "order4"])
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
                          "no CPU baseline")
@@ -789,6 +862,8 @@ def main():
         run_compare(args)
     elif args.workload == "weak3":
         run_weak3(args)
+    elif args.workload == "order4":
+        run_order4(args)
     else:
         run_ours(args)
 
