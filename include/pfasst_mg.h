@@ -218,6 +218,13 @@ int pfasst_mg_profile_read(pmg_handle h, pmg_kernel_stat *out, int capacity, int
 /* Name of a kernel identifier ("smooth_rbgs", ...); "unknown" if out of range. */
 const char *pfasst_mg_kernel_name(int kernel);
 
+/* Self-check of the library's integer-pipe FP64 -> FP32 rounding (used where mixed
+ * precision narrows a value per grid point) against the hardware conversion, on
+ * `samples` generated inputs (uniform bit patterns, the float range with subnormal and
+ * overflow edges, exact ties).  *mismatches (host) receives the number of differing
+ * results (0 expected).  Synchronises the default stream.  Errors: INVALID_ARG, CUDA. */
+int pfasst_mg_check_narrowing(long long samples, unsigned long long seed, long long *mismatches);
+
 /* Release the handle and any device memory it allocated.  NULL is accepted. */
 int pfasst_mg_destroy(pmg_handle h);
 

@@ -40,6 +40,7 @@ EXPORTS = [
     "pfasst_mg_net_get_params", "pfasst_mg_net_forward", "pfasst_mg_net_gradients", "pfasst_mg_net_sample",
     "pfasst_mg_net_train", "pfasst_mg_net_launch_count", "pfasst_mg_net_destroy", "pfasst_mg_net_last_error",
     "pfasst_mg_set_smoother_net", "pfasst_mg_net_step", "pfasst_mg_net_profile", "pfasst_mg_net_profile_read",
+    "pfasst_mg_check_narrowing",
 ]
 
 NET_PARAMS = 7809  # W1[16][27], b1[16], W2[16][27][16], b2[16], W3[27][16], b3
@@ -154,6 +155,7 @@ def load() -> ctypes.CDLL:
     L.pfasst_mg_net_last_error.restype = ctypes.c_char_p
     L.pfasst_mg_set_smoother_net.argtypes = [_P, _P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D),
                                              ctypes.POINTER(_I)]
+    L.pfasst_mg_check_narrowing.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]
     for name in EXPORTS:
         if name not in ("pfasst_mg_default_options", "pfasst_mg_launch_count", "pfasst_mg_last_error",
                         "pfasst_mg_kernel_name", "pfasst_mg_net_launch_count", "pfasst_mg_net_last_error"):
@@ -321,6 +323,14 @@ def pfasst_mg_profile_read(h):
     _check(load().pfasst_mg_profile_read(h, arr, cap, ctypes.byref(cnt)), h)
     return [dict(kernel=pfasst_mg_kernel_name(a.kernel), n=a.n, precision=a.precision, launches=a.launches,
                  points=a.points, ms=a.ms) for a in arr[:min(cnt.value, cap)]]
+
+
+def pfasst_mg_check_narrowing(samples, seed=1):
+    """Mismatches of the library's FP64 -> FP32 integer rounding against the hardware
+    conversion on `samples` generated inputs (0 expected)."""
+    bad = ctypes.c_longlong(-1)
+    _check(load().pfasst_mg_check_narrowing(samples, seed, ctypes.byref(bad)))
+    return bad.value
 
 
 def pfasst_mg_kernel_name(k) -> str:

@@ -1100,7 +1100,10 @@ void fill_coefficients(pmg_ctx *h) {
     ic.sf = s;
     ic.sc = sc;
     ic.order = h->opt.interp_order;
-    for (int m = 0; m < s; ++m) lagrange_row(sc, tc, t[m], ic.T[m]);
+    for (int m = 0; m < s; ++m) {
+      lagrange_row(sc, tc, t[m], ic.T[m]);
+      for (int j = 0; j < sc; ++j) ic.T32[m][j] = (float)ic.T[m][j];
+    }
   };
   if (h->nlevels >= 2) {
     node_positions(h->sc, h->famc, h->tauc);
@@ -1543,6 +1546,22 @@ int pfasst_mg_destroy(pmg_handle h) {
 }
 
 const char *pfasst_mg_last_error(pmg_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int pfasst_mg_check_narrowing(long long samples, unsigned long long seed, long long *mismatches) {
+  if (samples < 0 || !mismatches) return fail(nullptr, PMG_ERR_INVALID_ARG, "bad argument");
+  unsigned long long *bad = nullptr, hbad = 0;
+  if (cudaMalloc(&bad, sizeof bad[0]) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, PMG_ERR_CUDA, "cudaMalloc failed");
+  }
+  cudaError_t e = cudaMemset(bad, 0, sizeof bad[0]);
+  if (e == cudaSuccess) e = k_narrow_check(nullptr, samples, seed, bad);
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (e != cudaSuccess) return fail(nullptr, PMG_ERR_CUDA, std::string("narrowing check: ") + cudaGetErrorString(e));
+  *mismatches = (long long)hbad;
+  return PMG_OK;
+}
 
 int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const double *b, double *u,
                               const pmg_options *opt, void *stream, int *cycles_done) {

@@ -288,7 +288,7 @@ __global__ void resid_pt_kernel(Grid g, const double *__restrict__ um, long long
                                 long long sq, T *__restrict__ f, int batch) {
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
-    f[b * g.slab + off] = (T)(um[b * sum + off] + qm[b * sq + off]);
+    f[b * g.slab + off] = to_storage<T>(um[b * sum + off] + qm[b * sq + off]);
   }
 }
 
@@ -388,26 +388,29 @@ __global__ void fas_restrict_kernel(Grid gf, Grid gc, FASCoef cf, const double *
 }
 
 // time interpolation of the coarse correction on the coarse grid:
-// dU_m = sum_j T[m][j] (U_c,j - U_c0,j) for every fine node m (stored as T)
+// dU_m = sum_j T[m][j] (U_c,j - U_c0,j) for every fine node m (stored and combined as T)
 template <typename T>
 __global__ void interp_time_kernel(Grid gc, InterpCoef cf, const double *__restrict__ Uc,
                                    const double *__restrict__ Uc0, long long scoarse, T *__restrict__ dU, int batch,
                                    int m0) {
   PMG_FOR_POINTS(gc, batch) {
     PMG_POINT(gc);
-    double d[kMaxNodes];
+    // the differences in FP64 (they cancel), the Lagrange combination in the storage
+    // precision T: with FP32 storage that keeps all but 2 of the 5 FP64 operations per
+    // coarse node off GB300's narrow FP64 pipe
+    T d[kMaxNodes];
 #pragma unroll
     for (int jn = 0; jn < kMaxNodes; ++jn) {
       if (jn >= cf.sc) break;
       const long long co = b * scoarse + jn * gc.slab + off;
-      d[jn] = Uc[co] - Uc0[co];
+      d[jn] = to_storage<T>(Uc[co] - Uc0[co]);
     }
     for (int m = m0; m < cf.sf; ++m) {
-      double acc = 0.0;
+      T acc = T(0);
 #pragma unroll
       for (int jn = 0; jn < kMaxNodes; ++jn)
-        if (jn < cf.sc) acc += cf.T[m][jn] * d[jn];
-      dU[((long long)b * cf.sf + m) * gc.slab + off] = (T)acc;
+        if (jn < cf.sc) acc += (sizeof(T) == 4 ? (T)cf.T32[m][jn] : (T)cf.T[m][jn]) * d[jn];
+      dU[((long long)b * cf.sf + m) * gc.slab + off] = acc;
     }
   }
 }
@@ -506,6 +509,113 @@ __global__ void __launch_bounds__(256) interp_space_kernel(Grid gf, Grid gc, int
     }
     __syncthreads();
   }
+}
+
+// The 3D interpolation with the thread mapping fixed: 256 threads = 32 (x) x 8 (y), and
+// every tile origin even, so that the parity of a fine index -- injection or a 4-tap
+// (2-tap) stencil -- is known from the thread's own x, y and the unrolled z loop; the
+// coarse box is read without reflection arithmetic unless it touches a wall.  The same
+// passes as interp_space_kernel (x, then y, then z with the FP64 update), with far fewer
+// index instructions per fine point.
+template <typename T, int ORD>
+__global__ void __launch_bounds__(256) interp_space3d_kernel(Grid gf, Grid gc, int sf, const T *__restrict__ dU,
+                                                             double *__restrict__ Uf, long long sfine, int ntz,
+                                                             int m0) {
+  constexpr int CX = ITX / 2 + 4, CY = ITY / 2 + 4, CZ = ITZ / 2 + 4;
+  __shared__ T C[CZ * CY * CX];
+  __shared__ T X[CZ * CY * ITX];
+  __shared__ T Y[CZ * ITY * ITX];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * ITX, y0 = blockIdx.y * ITY;
+  const int zt = blockIdx.z % ntz, b = blockIdx.z / ntz, z0 = zt * ITZ;
+  const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = z0 / 2 - 1;  // 1-based coarse index of box entry 0
+  const int nc = gc.n;
+  const bool inside = cx0 >= 1 && cx0 + CX - 1 <= nc && cy0 >= 1 && cy0 + CY - 1 <= nc && cz0 >= 1 &&
+                      cz0 + CZ - 1 <= nc;
+  // taps of one axis for a local fine index t (tile origins are even): t odd -> the
+  // fine point sits on coarse box entry (t+1)/2 + 1 (injection); t even -> between box
+  // entries t/2 + 1 and t/2 + 2 (ORD 2), or taps t/2 .. t/2 + 3 (ORD 4)
+  auto taps = [](int t, const T *src, int stride) -> T {
+    if (t & 1) return src[((t + 1) / 2 + 1) * stride];
+    const int c = t / 2;
+    if (ORD == 2) return T(0.5) * (src[(c + 1) * stride] + src[(c + 2) * stride]);
+    return T(-1.0 / 16) * (src[c * stride] + src[(c + 3) * stride]) +
+           T(9.0 / 16) * (src[(c + 1) * stride] + src[(c + 2) * stride]);
+  };
+  const int i = x0 + tx, j = y0 + ty;
+  const bool mine = i < gf.n && j < gf.n;
+  const long long plane = (long long)gf.ny * gf.pitch;
+  for (int m = m0; m < sf; ++m) {
+    const T *src = dU + ((long long)b * sf + m) * gc.slab;
+    double *dst = Uf + (long long)b * sfine + (long long)m * gf.slab + (long long)j * gf.pitch + i;
+    // this thread's fine column, loaded before the staging so that its HBM latency
+    // overlaps the shared-memory passes
+    double uold[ITZ];
+#pragma unroll
+    for (int z = 0; z < ITZ; ++z) uold[z] = mine && z0 + z < gf.n ? dst[(z0 + z) * plane] : 0.0;
+    if (inside) {
+      for (int q = threadIdx.x; q < CZ * CY * CX; q += 256) {
+        const int a = q % CX, bb = (q / CX) % CY, cc = q / (CX * CY);
+        C[q] = src[((long long)(cz0 + cc - 1) * gc.ny + (cy0 + bb - 1)) * gc.pitch + (cx0 + a - 1)];
+      }
+    } else {
+      for (int q = threadIdx.x; q < CZ * CY * CX; q += 256) {
+        const int a = q % CX, bb = (q / CX) % CY, cc = q / (CX * CY);
+        float sx, sy, sz;
+        const int ix = reflect_index(cx0 + a, nc, &sx);
+        const int iy = reflect_index(cy0 + bb, nc, &sy);
+        const int iz = reflect_index(cz0 + cc, nc, &sz);
+        const float sg = sx * sy * sz;
+        C[q] = sg == 0.f ? T(0) : T(sg) * src[((long long)iz * gc.ny + iy) * gc.pitch + ix];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = ty; r < CZ * CY; r += 8) X[r * ITX + tx] = taps(tx, C + r * CX, 1);  // x pass
+    __syncthreads();
+#pragma unroll
+    for (int zc = 0; zc < CZ; ++zc) Y[(zc * ITY + ty) * ITX + tx] = taps(ty, X + zc * CY * ITX + tx, ITX);  // y
+    __syncthreads();
+    if (mine) {
+#pragma unroll
+      for (int z = 0; z < ITZ; ++z) {  // z pass and the FP64 update
+        const int k = z0 + z;
+        if (k < gf.n) dst[k * plane] = uold[z] + (double)taps(z, Y + ty * ITX + tx, ITY * ITX);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// self-check of narrow_rn against the hardware conversion on generated bit patterns:
+// a quarter uniform over all doubles, the rest steered into the float range around
+// subnormals and overflow, onto exact ties and onto exactly representable values
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return x;
+}
+
+__global__ void narrow_check_kernel(long long count, unsigned long long seed, unsigned long long *bad) {
+  unsigned long long nbad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long bits = mix64(seed + (unsigned long long)i);
+    const unsigned sel = (unsigned)(i & 3);
+    if (sel != 0) {
+      const unsigned long long ex = 1023 - 160 + mix64(seed ^ (unsigned long long)(3 * i + 1)) % 300;
+      bits = (bits & 0x800fffffffffffffULL) | (ex << 52);
+      if (sel == 2) bits = (bits & ~0xfffffffULL) | 0x10000000ULL;  // a tie at the float rounding position
+      if (sel == 3 && (i & 4)) bits &= ~0x1fffffffULL;              // representable when normal
+    }
+    const double v = __longlong_as_double((long long)bits);
+    const float hw = __double2float_rn(v), sw = narrow_rn(v);
+    if (v != v ? !(sw != sw) : __float_as_uint(hw) != __float_as_uint(sw)) ++nbad;
+  }
+  if (nbad) atomicAdd(bad, nbad);
 }
 
 __global__ void colloc_residual_kernel(Grid g, ResCoef cf, const double *__restrict__ U, const double *__restrict__ F,
@@ -703,6 +813,55 @@ __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double
   }
 }
 
+// Pointwise kernels over whole padded slabs: blockIdx.y selects the grid of the batch and
+// the x blocks stride over its slab two elements at a time.  The pitch n + 1 is a power
+// of two, so every slab and stride is even and a pair never straddles rows; the pair
+// that ends a row holds the last interior point and the pad, and the pad is written as
+// zero.  Few long-lived blocks instead of one block per row.
+template <typename T>
+__global__ void resid_pt_flat_kernel(long long slab, int pitch, const double *__restrict__ um, long long sum,
+                                     const double *__restrict__ qm, long long sq, T *__restrict__ f) {
+  const int b = blockIdx.y;
+  const double2 *U = (const double2 *)(um + b * sum), *Q = (const double2 *)(qm + b * sq);
+  const long long n2 = slab / 2;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2; p += (long long)gridDim.x * blockDim.x) {
+    const double2 u = U[p], q = Q[p];
+    const bool padpair = (((unsigned)(2 * p)) & (unsigned)(pitch - 1)) == (unsigned)(pitch - 2);
+    if constexpr (sizeof(T) == 4) {
+      ((float2 *)(f + b * slab))[p] = make_float2(narrow_rn(u.x + q.x), padpair ? 0.f : narrow_rn(u.y + q.y));
+    } else {
+      ((double2 *)(f + b * slab))[p] = make_double2(u.x + q.x, padpair ? 0.0 : u.y + q.y);
+    }
+  }
+}
+
+__global__ void copy_flat_kernel(long long slab, int pitch, const double *__restrict__ src, long long ss,
+                                 double *__restrict__ dst, long long sd) {
+  const int b = blockIdx.y;
+  const double2 *S = (const double2 *)(src + b * ss);
+  double2 *D = (double2 *)(dst + b * sd);
+  const long long n2 = slab / 2;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2; p += (long long)gridDim.x * blockDim.x) {
+    double2 v = S[p];
+    if ((((unsigned)(2 * p)) & (unsigned)(pitch - 1)) == (unsigned)(pitch - 2)) v.y = 0.0;
+    D[p] = v;
+  }
+}
+
+// the flat kernels need a power-of-two pitch, even strides and slab positions that fit
+// 32 bits (the pad test), and at most 65535 grids
+bool flat_ok(const Grid &g, int batch, long long strides) {
+  return batch <= 65535 && (g.pitch & (g.pitch - 1)) == 0 && ((strides | g.slab) & 1) == 0 && g.slab < (1LL << 31);
+}
+
+// x blocks per grid for the flat kernels: about 8 blocks of 256 per SM in total
+dim3 flat_grid(long long slab, int batch) {
+  long long gx = (152LL * 8 + batch - 1) / batch, need = (slab / 2 + 255) / 256;
+  if (gx > need) gx = need;
+  if (gx < 1) gx = 1;
+  return dim3((unsigned)gx, (unsigned)batch, 1);
+}
+
 __global__ void copy_kernel(Grid g, const double *__restrict__ src, long long ss, double *__restrict__ dst,
                             long long sd, int batch) {
   PMG_FOR_POINTS(g, batch) {
@@ -860,9 +1019,17 @@ cudaError_t k_apply_A(const Launch &L, const Grid &g, double nu, const double *u
 
 cudaError_t k_resid_pt(const Launch &L, const Grid &g, Prec pr, const double *um, long long sum, const double *qm,
                        long long sq, void *f, int batch) {
+  Scope sc(L, K_RESID_PT, g, batch, pr);
+  if (flat_ok(g, batch, sum | sq)) {
+    const dim3 gr = flat_grid(g.slab, batch);
+    if (pr == F64)
+      resid_pt_flat_kernel<double><<<gr, 256, 0, L.stream>>>(g.slab, g.pitch, um, sum, qm, sq, (double *)f);
+    else
+      resid_pt_flat_kernel<float><<<gr, 256, 0, L.stream>>>(g.slab, g.pitch, um, sum, qm, sq, (float *)f);
+    return sc.done();
+  }
   dim3 gr, bl;
   config(g, batch, gr, bl);
-  Scope sc(L, K_RESID_PT, g, batch, pr);
   if (pr == F64)
     resid_pt_kernel<double><<<gr, bl, 0, L.stream>>>(g, um, sum, qm, sq, (double *)f, batch);
   else
@@ -926,9 +1093,26 @@ cudaError_t launch_interp_space(const Launch &L, const Grid &gf, const Grid &gc,
   return cudaSuccess;
 }
 
+template <typename T>
+cudaError_t launch_interp_space3d(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, const void *dU,
+                                  double *Uf, long long sfine, int batch, int m0) {
+  const int ntx = (gf.n + ITX - 1) / ITX, nty = (gf.n + ITY - 1) / ITY, ntz = (gf.n + ITZ - 1) / ITZ;
+  dim3 gr(ntx, nty, ntz * batch);
+  if (order == 2)
+    interp_space3d_kernel<T, 2><<<gr, 256, 0, L.stream>>>(gf, gc, sf, (const T *)dU, Uf, sfine, ntz, m0);
+  else
+    interp_space3d_kernel<T, 4><<<gr, 256, 0, L.stream>>>(gf, gc, sf, (const T *)dU, Uf, sfine, ntz, m0);
+  return cudaSuccess;
+}
+
 cudaError_t k_interp_space_add(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, Prec pr,
                                const void *dU, double *Uf, long long sfine, int batch, int m0) {
   Scope sc(L, K_INTERP, gf, batch * (sf - m0), pr);
+  if (gf.dim == 3 && (long long)((gf.n + ITZ - 1) / ITZ) * batch <= 65535) {
+    if (pr == F64) launch_interp_space3d<double>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0);
+    else launch_interp_space3d<float>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0);
+    return sc.done();
+  }
   if (pr == F64)
     PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, double>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0)))
   else
@@ -1000,11 +1184,20 @@ cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, co
   return sc.done();
 }
 
+cudaError_t k_narrow_check(cudaStream_t st, long long count, unsigned long long seed, unsigned long long *bad) {
+  narrow_check_kernel<<<152 * 8, 256, 0, st>>>(count, seed, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t k_copy(const Launch &L, const Grid &g, const double *src, long long ss, double *dst, long long sd,
                    int batch) {
   dim3 gr, bl;
   config(g, batch, gr, bl);
   Scope sc(L, K_COPY, g, batch, 0);
+  if (flat_ok(g, batch, ss | sd)) {
+    copy_flat_kernel<<<flat_grid(g.slab, batch), 256, 0, L.stream>>>(g.slab, g.pitch, src, ss, dst, sd);
+    return sc.done();
+  }
   copy_kernel<<<gr, bl, 0, L.stream>>>(g, src, ss, dst, sd, batch);
   return sc.done();
 }

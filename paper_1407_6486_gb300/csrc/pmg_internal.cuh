@@ -43,6 +43,43 @@ inline Grid make_grid(int dim, int n, int order = 2) {
   return g;
 }
 
+#ifdef __CUDACC__
+// binary64 -> binary32 with round-to-nearest-even, done with integer operations on the
+// IEEE-754 encodings (sign, biased exponent, significand): GB300 runs the hardware
+// conversion on its narrow FP64 pipe, where it bounds the bandwidth of kernels that
+// narrow every point.  Bitwise equal to the hardware conversion for every input class
+// (normal, subnormal result, overflow to Inf, zero, Inf, NaN stays NaN).
+__device__ __forceinline__ float narrow_rn(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long m = b & 0xfffffffffffffULL;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? (0x400000u | (unsigned)(m >> 29)) : 0u));
+  const int E = e - 1023;
+  if (E >= -126) {  // normal result: keep 23 significand bits, round on the 29 dropped ones
+    if (E > 127) return __uint_as_float(sign | 0x7f800000u);
+    unsigned r = ((unsigned)(E + 127) << 23) | (unsigned)(m >> 29);
+    const unsigned rest = (unsigned)(m & 0x1fffffffULL);
+    if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ++r;  // a carry may reach Inf: correct
+    return __uint_as_float(sign | r);
+  }
+  if (E < -151) return __uint_as_float(sign);  // below half the smallest subnormal
+  // subnormal result: (2^52 + m) 2^(E-52) in units of 2^-149
+  const unsigned long long full = m | 0x10000000000000ULL;
+  const int sh = -97 - E;
+  const unsigned long long rem = full & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+  unsigned r = (unsigned)(full >> sh);
+  if (rem > half || (rem == half && (r & 1u))) ++r;
+  return __uint_as_float(sign | r);
+}
+
+template <typename T>
+__device__ __forceinline__ T to_storage(double v) {
+  if constexpr (sizeof(T) == 4) return narrow_rn(v);
+  else return v;
+}
+#endif
+
 // kernel identifiers for launch accounting and the event profiler
 enum KernelId {
   K_RESIDUAL0 = 0, K_JACOBI, K_RBGS, K_RESRESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_ZERO,
@@ -173,6 +210,7 @@ struct FASCoef {
 struct InterpCoef {
   int sf, sc, order;
   double T[kMaxNodes][kMaxNodes];
+  float T32[kMaxNodes][kMaxNodes];  // the same weights rounded to FP32
 };
 
 // ---- multigrid kernels (precision of e, f chosen by Prec) ----
@@ -245,6 +283,9 @@ cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, co
                              int batch);
 cudaError_t k_colloc_residual(const Launch &L, const Grid &g, const ResCoef &cf, const double *U, const double *F,
                               long long stride, int batch, unsigned long long *out);
+// compares narrow_rn with the hardware FP64 -> FP32 conversion on `count` generated
+// inputs; adds the number of differing results to *bad (device memory)
+cudaError_t k_narrow_check(cudaStream_t st, long long count, unsigned long long seed, unsigned long long *bad);
 cudaError_t k_copy(const Launch &L, const Grid &g, const double *src, long long ss, double *dst, long long sd,
                    int batch);
 cudaError_t k_pack(const Launch &L, const Grid &g, const double *dense, long long sdense, double *pad, long long spad,

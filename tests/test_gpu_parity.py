@@ -519,3 +519,11 @@ def test_three_level_weak_scaling_shape_of_the_paper():
         s.close()
         reach.append(next(k + 1 for k, e in enumerate(errs) if e <= 1.6 * errs[-1]))
     assert max(reach) <= 6 and reach[2] <= reach[0], reach
+
+
+def test_integer_narrowing_matches_the_hardware_conversion():
+    """The FP64 -> FP32 rounding done with integer operations (mixed-precision residuals,
+    time interpolation) equals the hardware round-to-nearest-even conversion bit for bit
+    on 2^28 inputs: uniform bit patterns, the float range down to subnormals and up to
+    overflow, exact ties."""
+    assert pmg.pfasst_mg_check_narrowing(1 << 28, seed=12345) == 0
