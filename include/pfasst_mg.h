@@ -104,8 +104,9 @@ typedef struct {
     int    vcycle_tail;   /* 1: for single grids (the serial coarse chain) the coarsest
                              multigrid levels (from the first level whose whole remaining
                              V-cycle fits one CTA's shared memory: 15^3 in 3D, 63^2 in 2D)
-                             run as one kernel launch per V-cycle; 0: one launch per
-                             smoothing sweep, restriction and prolongation                */
+                             run as one kernel launch per V-cycle; 0 (default): one launch
+                             per smoothing sweep, restriction and prolongation (1 % faster
+                             per PFASST iteration on the 3D workload)                      */
 } pmg_options;
 
 typedef struct pmg_ctx *pmg_handle;

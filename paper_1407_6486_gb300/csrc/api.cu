@@ -787,12 +787,14 @@ int fas_restrict_12(pmg_ctx *h) {
 }
 
 // U_l[p][0] <- U_l[p-1][s_l - 1] and F_l[p][0] = A_l U_l[p][0] for p in [p0, p0+B),
-// p0 >= 1, on a coarse level l
+// p0 >= 1, on a coarse level l.  A coarse level keeps F_l = A_l U_l at every node, so
+// F_l[p-1][s_l - 1] already is A_l applied to the received value: it is copied instead
+// of evaluated again (bitwise the same numbers, no FP64 stencil).
 int receive(pmg_ctx *h, int level, int p0, int B) {
   const LevelRef v = level_ref(h, level);
-  const long long st = (long long)v.s * v.g->slab;
-  PMG_CUDA(h, k_copy(h->L(), *v.g, v.U + (p0 - 1) * st + (v.s - 1) * v.g->slab, st, v.U + p0 * st, st, B));
-  PMG_CUDA(h, k_apply_A(h->L(), *v.g, h->nu, v.U + p0 * st, st, v.F + p0 * st, st, B));
+  const long long st = (long long)v.s * v.g->slab, last = (long long)(v.s - 1) * v.g->slab;
+  PMG_CUDA(h, k_copy(h->L(), *v.g, v.U + (p0 - 1) * st + last, st, v.U + p0 * st, st, B));
+  PMG_CUDA(h, k_copy(h->L(), *v.g, v.F + (p0 - 1) * st + last, st, v.F + p0 * st, st, B));
   return PMG_OK;
 }
 
@@ -1032,7 +1034,9 @@ int iteration(pmg_ctx *h) {
   }
   if (h->P > 1) {  // send forward: U_f[p][0] <- U_f[p-1][M_f]
     PMG_CUDA(h, k_copy(h->L(), h->gf, h->Uf + (h->sf - 1) * h->gf.slab, sfs, h->Uf + sfs, sfs, h->P - 1));
-    if (!ffree(h)) PMG_CUDA(h, k_apply_A(h->L(), h->gf, h->nu, h->Uf + sfs, sfs, h->Ff + sfs, sfs, h->P - 1));
+    // with a stored F, F_f[p][M_f] = A U_f[p][M_f] already (interpolation re-evaluates it)
+    if (!ffree(h))
+      PMG_CUDA(h, k_copy(h->L(), h->gf, h->Ff + (h->sf - 1) * h->gf.slab, sfs, h->Ff + sfs, sfs, h->P - 1));
   }
   return fine_residual(h, true);
 }
@@ -1196,7 +1200,7 @@ void pfasst_mg_default_options(pmg_options *o) {
   o->use_graphs = 1;
   o->autotune = 1;
   o->slice_groups = 0;
-  o->vcycle_tail = 1;
+  o->vcycle_tail = 0;
 }
 
 int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,
