@@ -526,7 +526,9 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, vo
       else PMG_RET(smooth(M, l, B, c, cur[l], zero && s == 0));
     }
     if (tiled3d(H.lev[l], B))
-      PMG_CUDA(M.h, k_resrestrict3d(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
+      PMG_CUDA(M.h, resrestrict_tma_supported(H.lev[l], H.pr)
+                        ? k_resrestrict3d_tma(M.L, H.lev[l], H.lev[l + 1], c, cur[l], H.f[l], H.f[l + 1], B)
+                        : k_resrestrict3d(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
     else
       PMG_CUDA(M.h, k_residual_restrict(M.L, H.lev[l], H.lev[l + 1], c, H.pr, cur[l], H.f[l], H.f[l + 1], B));
   }

@@ -249,6 +249,10 @@ cudaError_t k_rbgs_sweep3d_tma(const Launch &L, const Grid &g, double c, double 
 int sweep_timeouts();
 cudaError_t k_resrestrict3d(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
                             const void *f, void *fc, int batch);
+// the same residual + full weighting with TMA-staged planes (sweep_tma.cu): FP32, pitch >= 128
+bool resrestrict_tma_supported(const Grid &gf, Prec pr);
+cudaError_t k_resrestrict3d_tma(const Launch &L, const Grid &gf, const Grid &gc, double c, const void *e, const void *f,
+                                void *fc, int batch);
 cudaError_t k_prolong3d(const Launch &L, const Grid &gf, const Grid &gc, Prec pr, const void *ec, void *e, int batch);
 
 // ---- SDC / PFASST kernels (FP64) ----

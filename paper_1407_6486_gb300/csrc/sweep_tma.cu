@@ -242,6 +242,113 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------- residual + restriction
+//
+// fc = full weighting of r = f - (I - c Lap_h) e on batched 3D grids (FP32), with the
+// e and f planes of a coarse tile streamed by TMA into a shared-memory ring, RD planes
+// ahead.  Coarse tile RX x RY points, RZC coarse planes per CTA; the fine residual of
+// one plane is formed in shared memory (double-buffered, so one barrier per fine plane
+// suffices) and weighted in x and y; the z weights (1/4, 1/2, 1/4) accumulate in a
+// register across the three fine planes of each coarse plane.  Boxes start at fine
+// x = 2 I0 - 4 (a multiple of 4 floats: 16-byte aligned) and rows or planes outside
+// the grid arrive as zeros.
+constexpr int RX = 32, RY = 8, RZC = 16;
+constexpr int RBX = 2 * RX + 8;    // staged columns: fine x 2I0-4 .. 2I0+67
+constexpr int REY = 2 * RY + 3;    // e rows: fine y 2J0-1 .. 2J0+17
+constexpr int RFY = 2 * RY + 1;    // f and residual rows: fine y 2J0 .. 2J0+16
+constexpr int RRX = 2 * RX + 1;    // residual columns: fine x 2I0 .. 2I0+64
+constexpr int RRS = RRX + 1;       // residual row stride
+constexpr int RD = 2;              // planes in flight ahead of the computation
+constexpr int RNE = 3 + RD, RNF = 1 + RD;
+constexpr int RNT = RX * RY;       // 256 threads: one coarse point each
+constexpr uint32_t REB = REY * RBX * 4, RFB = RFY * RBX * 4;
+constexpr uint32_t RES = (REB + 127) / 128 * 128, RFS = (RFB + 127) / 128 * 128;  // 128-byte aligned slots
+constexpr size_t RSMEM = RNE * RES + RNF * RFS + 2 * RFY * RRS * 4 + (RNE + RNF) * 8;
+
+__global__ void __launch_bounds__(RNT, 4) resrestrict_tma_kernel(const __grid_constant__ CUtensorMap tme,
+                                                                 const __grid_constant__ CUtensorMap tmf, Grid gf,
+                                                                 Grid gc, float a, float *__restrict__ fc, int nzc) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  float *Eb = (float *)sm;                                   // RNE slots of [REY][RBX]
+  float *Fb = (float *)(sm + RNE * RES);                     // RNF slots of [RFY][RBX]
+  float *Rb = (float *)(sm + RNE * RES + RNF * RFS);         // 2 x [RFY][RRS]
+  uint64_t *bar = (uint64_t *)(sm + RNE * RES + RNF * RFS + 2 * RFY * RRS * 4);
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nc = gc.n;
+  const int I0 = blockIdx.x * RX, J0 = blockIdx.y * RY;
+  const int zc = blockIdx.z % nzc, b = blockIdx.z / nzc;
+  const int K0 = zc * RZC, K1 = min(K0 + RZC, nc);
+  const int zb = 2 * K0, ze = 2 * K1;  // fine planes 2K .. 2K+2 feed coarse plane K
+  // e plane p (zb-1 .. ze+1) in slot (p - zb + 1) % RNE, f plane p (zb .. ze) in slot
+  // (p - zb) % RNF; the j-th use of a slot completes phase j of its barrier
+  auto eslot = [&](int p) { return (p - zb + 1) % RNE; };
+  auto fslot = [&](int p) { return (p - zb) % RNF; };
+  auto issue_e = [&](int p) {
+    const int sl = eslot(p);
+    mbar_expect_tx(&bar[sl], REB);
+    tma_load_4d((char *)Eb + sl * RES, &tme, 2 * I0 - 4, 2 * J0 - 1, p, b, &bar[sl]);
+  };
+  auto issue_f = [&](int p) {
+    const int sl = fslot(p);
+    mbar_expect_tx(&bar[RNE + sl], RFB);
+    tma_load_4d((char *)Fb + sl * RFS, &tmf, 2 * I0 - 4, 2 * J0, p, b, &bar[RNE + sl]);
+  };
+  if (tid == 0) {
+    for (int i = 0; i < RNE + RNF; ++i) mbar_init(&bar[i]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_bad = 0;
+    for (int p = zb - 1; p <= min(zb + RD, ze + 1); ++p) issue_e(p);
+    for (int p = zb; p <= min(zb + RD - 1, ze); ++p) issue_f(p);
+  }
+  __syncthreads();
+  const int cx = tid % RX, cy = tid / RX;
+  const int I = I0 + cx, J = J0 + cy;
+  const long long cplane = (long long)gc.ny * gc.pitch;
+  float acc = 0.f;
+  bool ok = mbar_wait(&bar[eslot(zb - 1)], 0) && mbar_wait(&bar[eslot(zb)], 0);
+  for (int z = zb; z <= ze; ++z) {
+    if (tid == 0) {  // refill the slots of planes z-2 (e) and z-1 (f), read before the last barrier
+      if (z + 1 + RD <= ze + 1) issue_e(z + 1 + RD);
+      if (z + RD <= ze) issue_f(z + RD);
+    }
+    if (ok) ok = mbar_wait(&bar[eslot(z + 1)], ((z + 1 - zb + 1) / RNE) & 1);
+    if (ok) ok = mbar_wait(&bar[RNE + fslot(z)], ((z - zb) / RNF) & 1);
+    if (!ok) s_bad = 1;
+    const float *E0 = Eb + eslot(z) * (RES / 4), *El = Eb + eslot(z - 1) * (RES / 4),
+                *Eh = Eb + eslot(z + 1) * (RES / 4), *F0 = Fb + fslot(z) * (RFS / 4);
+    float *R = Rb + (z & 1) * RFY * RRS;
+    for (int q = tid; q < RFY * RRX; q += RNT) {  // residual of fine plane z
+      const int ry = q / RRX, rx = q % RRX;
+      const int eo = (ry + 1) * RBX + rx + 4;
+      const float ec = E0[eo];
+      const float nb = E0[eo - 1] + E0[eo + 1] + E0[eo - RBX] + E0[eo + RBX] + El[eo] + Eh[eo];
+      R[ry * RRS + rx] = F0[ry * RBX + rx + 4] - (ec - a * (nb - 6.f * ec));
+    }
+    __syncthreads();
+    if (s_bad) break;  // uniform: read after the barrier
+    // x-y full weighting at the thread's coarse point: fine x = 2I+1 is residual column
+    // 2cx+1, fine y = 2J+1 is residual row 2cy+1
+    const int c0 = 2 * cx + 1, r0 = 2 * cy + 1;
+    const float *Rm = R + (r0 - 1) * RRS + c0, *Rc = R + r0 * RRS + c0, *Rp = R + (r0 + 1) * RRS + c0;
+    const float rxy = 0.25f * (0.25f * Rm[-1] + 0.5f * Rm[0] + 0.25f * Rm[1]) +
+                      0.5f * (0.25f * Rc[-1] + 0.5f * Rc[0] + 0.25f * Rc[1]) +
+                      0.25f * (0.25f * Rp[-1] + 0.5f * Rp[0] + 0.25f * Rp[1]);
+    if ((z & 1) == 0) {
+      if (z > zb && I < nc && J < nc) fc[b * gc.slab + (z / 2 - 1) * cplane + (long long)J * gc.pitch + I] = acc + 0.25f * rxy;
+      acc = 0.25f * rxy;
+    } else {
+      acc += 0.5f * rxy;
+    }
+  }
+  if (s_bad && tid == 0) {
+    atomicExch(&g_sweep_timeout, 1);
+    // let loads still in flight land before the CTA's shared memory is released
+    const long long t0 = clock64();
+    while (clock64() - t0 < 2000000) __nanosleep(64);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -265,6 +372,19 @@ bool make_map(CUtensorMap *m, const void *base, const Grid &g, int batch, int ro
   const cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)batch};
   const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.ny * g.pitch * 4, (cuuint64_t)g.slab * 4};
   const cuuint32_t box[4] = {(cuuint32_t)g.pitch, (cuuint32_t)rows, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// tensor map with a box of box_x columns and `rows` rows of one plane
+bool make_map_box(CUtensorMap *m, const void *base, const Grid &g, int batch, int box_x, int rows) {
+  auto enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.ny * g.pitch * 4, (cuuint64_t)g.slab * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)rows, 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -321,6 +441,31 @@ cudaError_t k_rbgs_sweep3d_tma(const Launch &L, const Grid &g, double c, double 
   else e = launch_tma_pitch<false, false>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
   cudaError_t e2 = sc.done();
   return e != cudaSuccess ? e : e2;
+}
+
+bool resrestrict_tma_supported(const Grid &gf, Prec pr) {
+  return pr == F32 && gf.dim == 3 && gf.order != 4 && gf.pitch >= 128 && encoder() != nullptr;
+}
+
+cudaError_t k_resrestrict3d_tma(const Launch &L, const Grid &gf, const Grid &gc, double c, const void *e, const void *f,
+                                void *fc, int batch) {
+  Scope sc(L, K_RESRESTRICT3D, gc, batch, F32);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t er = cudaFuncSetAttribute(resrestrict_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)RSMEM);
+    if (er != cudaSuccess) return er;
+    attr = true;
+  }
+  CUtensorMap me, mf;
+  if (!make_map_box(&me, e, gf, batch, RBX, REY) || !make_map_box(&mf, f, gf, batch, RBX, RFY))
+    return cudaErrorInvalidValue;
+  const int ntx = (gc.n + RX - 1) / RX, nty = (gc.n + RY - 1) / RY, nzc = (gc.n + RZC - 1) / RZC;
+  dim3 gr(ntx, nty, nzc * batch);
+  resrestrict_tma_kernel<<<gr, RNT, RSMEM, L.stream>>>(me, mf, gf, gc, (float)(c * gf.ih2), (float *)fc, nzc);
+  cudaError_t er = cudaGetLastError();
+  cudaError_t e2 = sc.done();
+  return er != cudaSuccess ? er : e2;
 }
 
 int sweep_timeouts() {
