@@ -133,10 +133,18 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
   __syncthreads();
   bool ok = true;
   if (!ZERO) ok = wait_e(z0 - 2) && wait_e(z0 - 1);
+  double2 upre[PB];  // UPD: this thread's u pairs of plane k-1, loaded before the red phase
   for (int k = z0 - 1; k <= z1; ++k) {
     if (tid == 0) {  // refill the slots the previous plane released
       if (!ZERO && k + 1 + DEPTH <= z1 + 1) issue_e(k + 1 + DEPTH);
       if (k + DEPTH <= z1) issue_f(k + DEPTH);
+    }
+    if (UPD && k - 1 >= z0 && k - 1 < z1) {
+#pragma unroll
+      for (int h = 0; h < PB; ++h) {
+        const int r = ry + RS * h, y = y0 + r;
+        if (r < TTY && y < n) upre[h] = *(const double2 *)(u + b * su + (k - 1) * plane + (long long)y * g.pitch + 2 * px);
+      }
     }
     if (ok && !ZERO) ok = wait_e(k + 1);
     if (ok) ok = wait_f(k);
@@ -219,11 +227,10 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
         }
         const long long o = kb * plane + (long long)y * g.pitch + 2 * px;
         if (UPD) {
-          double2 *up2 = (double2 *)(u + b * su + o);
-          double2 w = *up2;
+          double2 w = upre[h];
           w.x += (double)out.x;
           w.y += (double)out.y;
-          *up2 = w;
+          *(double2 *)(u + b * su + o) = w;
         } else {
           *(float2 *)(eout + b * g.slab + o) = out;
         }
