@@ -770,19 +770,20 @@ def run_ours(args):
     def roof_of(d):
         flops = algo_fp64_flops_per_point(d["kernel"], wl.fine_nodes, wl.coarse_nodes)
         sec = d["ms"] / 1000.0
+        tpp = traffic_for(d["kernel"], d["n"])
+        traffic = (tpp * d["points"] / d["launches"]) if tpp is not None else None
         if flops > 0:
             achieved = flops * d["points"] / sec / 1e9
             return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                    "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                    "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
                     "kernel": d["kernel"], "grid": d["n"], "launches": d["launches"],
                     "avg_launch_ms": d["ms"] / d["launches"], "algo_fp64_flops_per_point": flops,
                     "peak_source": "FP64 nominal: 152 SMs x 2.07 GHz x 4 flop/clk"}
         ts = 4 if d["precision"] == 1 else 8
         bpp = algo_bytes_per_point(d["kernel"], ts, wl.fine_nodes, wl.coarse_nodes)
         achieved = bpp * d["points"] / sec / 1e9
-        tpp = traffic_for(d["kernel"], d["n"])
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tpp * d["points"] / d["launches"]) if tpp is not None else None,
+                "traffic": traffic,
                 "kernel": d["kernel"], "grid": d["n"], "launches": d["launches"],
                 "avg_launch_ms": d["ms"] / d["launches"], "algo_bytes_per_point": bpp,
                 "peak_source": f"{peak_kind} hbm_gbs"}
