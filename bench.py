@@ -78,6 +78,18 @@ def dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def job_time_and_value(ms_local, units_per_rank, world, device="cuda"):
+    """Replicas (one independent problem per GPU): the job's step time is the slowest
+    rank's (MAX over ranks), and the whole-job throughput counts every rank's units.
+    Returns (ms, units per second)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1000.0)
+
+
 def sample_clocks_start():
     try:
         f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
@@ -737,13 +749,8 @@ def run_ours(args):
             print(f"{d['kernel']:>18} n={d['n']:>4} prec={d['precision']} launches/step={d['launches'] / args.steps:8.0f} "
                   f"ms/step={d['ms'] / args.steps:9.2f} share={d['ms'] / tot:6.1%}", file=sys.stderr)
     stats = [d for d in stats if d["n"] == wl.n]
-    ms = ms_total / args.steps
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(t.item())
     dof_sweeps = wl.dofs * (wl.fine_nodes - 1) * wl.slices * k_ref
-    value = world * dof_sweeps / (ms / 1000.0)
+    ms, value = job_time_and_value(ms_total / args.steps, dof_sweeps, world)
 
     # end to end through the C ABI with host buffers (h2d of u0, d2h of the end value)
     e2e_steps = 0 if args.quick else args.steps
@@ -757,11 +764,7 @@ def run_ours(args):
         s.iterate(maxit, target)
         pmg.pfasst_mg_get_solution(s.h, wl.slices - 1, wl.fine_nodes - 1, out_np)
     torch.cuda.synchronize()
-    e2e_ms = 1000 * (time.perf_counter() - t0) / max(e2e_steps, 1)
-    t = torch.tensor([e2e_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms, e2e_value = job_time_and_value(1000 * (time.perf_counter() - t0) / max(e2e_steps, 1), dof_sweeps, world)
 
     # roofline of the dominant kernel (by summed launch time on the fine grid): HBM for
     # the stencils / node mixes, the FP64 ALU for kernels bound by the FP64 pipe
@@ -814,7 +817,7 @@ def run_ours(args):
                             "launches_per_step": d["launches"] / args.steps} for d in stats),
                           key=lambda d: -d["ms_per_step"])[:8],
         "e2e": None if e2e_steps == 0 else {
-            "value": world * dof_sweeps / (e2e_ms / 1000.0), "unit": "DOF-sweeps/s",
+            "value": e2e_value, "unit": "DOF-sweeps/s",
             "h2d_bytes_per_step": wl.dofs * 8, "d2h_bytes_per_step": wl.dofs * 8, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks,
