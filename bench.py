@@ -180,6 +180,26 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 class OracleSample:
     """The FP64 oracle on `slices` of the workload's slices: predictor once, then each
     sample() times one PFASST iteration (fine sweeps, FAS restriction, coarse chain,
@@ -223,7 +243,8 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name},
-            "cpu_baseline": {"value": value, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -826,7 +847,8 @@ def run_ours(args):
         v, tsec, cores = OracleSample(wl, args.ref_slices).sample()
         line["cpu_baseline"] = {"value": v, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one FP64 oracle PFASST iteration on {args.ref_slices} of the "
-                                          f"{wl.slices} slices ({tsec:.1f} s)"}
+                                          f"{wl.slices} slices ({tsec:.1f} s)",
+                                "nproc": os.cpu_count(), "cpu_model": cpu_model()}
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
