@@ -506,6 +506,67 @@ def run_compare(args):
         print(json.dumps(line), flush=True)
 
 
+def run_heat1d(args):
+    """The 1D configuration: heat u_t = u_xx on 127 points, u0 = sin(pi x) + 0.5 sin(3 pi x),
+    single-level SDC with 3 Gauss-Lobatto nodes, dt = 0.01 to T = 0.1 (10 steps), each step
+    swept until its collocation residual is <= 1e-9 (at most 50 sweeps), sub-steps solved by
+    2 V(2,1) cycles of weighted Jacobi (2/3) down to 3 points, FP64.  A latency-bound case:
+    time and sweeps/s only, no roofline.  The error of the end value against the discrete
+    solution of the semi-discrete problem (Pade(2,2) per sine mode) is reported too."""
+    import math
+    import torch
+    import paper_1407_6486_gb300 as pmg
+    from paper_1407_6486_gb300 import _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    pmg.load()
+    wl = inputs.heat1d_c1()
+    s = pmg.PFASSTSolver(1, wl.n, wl.fine_nodes, 0, 1, wl.nu, wl.dt, nlevels=1, smoother=wl.smoother,
+                         omega=wl.omega, vcycles=wl.vcycles, precision=wl.precision)
+    u0 = torch.tensor(wl.u0(), device="cuda")
+    out = torch.empty(wl.n, dtype=torch.float64, device="cuda")
+
+    def solve():
+        u, sweeps = u0, 0
+        for _ in range(wl.steps):
+            s.set_initial(u)
+            rc, it, res = s.iterate(wl.iterations, 1e-9)
+            sweeps += it
+            pmg.pfasst_mg_get_solution(s.h, 0, wl.fine_nodes - 1, out)
+            u = out.clone()
+        return sweeps, u
+
+    for _ in range(max(args.warmup, 1)):
+        solve()
+    torch.cuda.synchronize()
+    times, sweeps = [], 0
+    for _ in range(max(args.steps, 1)):
+        t0 = time.perf_counter()
+        sweeps, u = solve()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    sec = min(times)
+    h = 1.0 / (wl.n + 1)
+    x = np.arange(1, wl.n + 1) * h
+    want = np.zeros(wl.n)
+    for k, a in zip(wl.modes, wl.amps):
+        z = wl.dt * wl.nu * (2 * math.cos(k[0] * math.pi * h) - 2) / h ** 2
+        want += a * _pade(z, wl.fine_nodes) ** wl.steps * np.sin(k[0] * math.pi * x)
+    err = float(np.abs(u.cpu().numpy() - want).max())
+    dof_sweeps = wl.n * (wl.fine_nodes - 1) * sweeps
+    line = {"metric": "DOF-sweeps/s", "value": dof_sweeps / sec, "unit": "DOF-sweeps/s", "n_gpus": world,
+            "steps": len(times), "warmup": max(args.warmup, 1), "ms_per_step": 1000 * sec, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sweeps_to_1e-9_over_10_steps": sweeps, "sweeps_per_s": sweeps / sec,
+                       "max_error_vs_collocation": err, "timing": "wall clock of the 10-step solve, best of the runs"},
+            "gpu_launches": None}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_weak3(args):
     """Three-level PFASST (Sec. 2.4 with a middle level).  Part 1, the weak-scaling runs
     of Sec. 4.2.2 on the GPU: 1D heat, k = nu = T = 1, N_x = N_t = N parallel steps
@@ -864,7 +925,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d",
                     choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "compare",
-                             "weak3", "order4"])
+                             "weak3", "order4", "heat1d"])
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
                          "no CPU baseline")
@@ -890,6 +951,8 @@ def main():
         run_weak3(args)
     elif args.workload == "order4":
         run_order4(args)
+    elif args.workload == "heat1d":
+        run_heat1d(args)
     else:
         run_ours(args)
 
