@@ -192,7 +192,8 @@ int pfasst_mg_tuning(pmg_handle h, int level, int narrow, int *fused, int *param
 
 /* Pin the smoother variant of a level (same encoding as pfasst_mg_tuning; the exact
  * coarsest level has none).  Later iterations use it (captured graphs are rebuilt).
- * Errors: INVALID_ARG, UNSUPPORTED (a variant the level or precision cannot run). */
+ * Errors: INVALID_ARG, UNSUPPORTED (a variant the level or precision cannot run; the
+ * fused and TMA-staged sweeps run the second-order stencil only). */
 int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int param, int threads);
 
 /* ---- launch profiling ------------------------------------------------------ */
