@@ -145,16 +145,19 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def kernel_src_hash():
+def kernel_src_hash(files=None):
+    """sha256 prefix of the given files of paper_1407_6486_gb300/csrc (all of them by default)."""
+    csrc = os.path.join(ROOT, "paper_1407_6486_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1407_6486_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_1407_6486_gb300", "csrc", f), "rb") as fh:
+    for f in sorted(files if files else os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(kernel: str, n: int):
-    """DRAM bytes per grid point from a committed ncu summary, if taken on the current sources."""
+    """DRAM bytes per grid point from a committed ncu summary, if taken on the current
+    sources of that kernel (the entry lists the source files its hash covers)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -162,7 +165,7 @@ def traffic_for(kernel: str, n: int):
     except Exception:
         return None
     e = d.get(f"{kernel}@{n}")
-    if not e or e.get("src_hash") != kernel_src_hash():
+    if not e or e.get("src_hash") != kernel_src_hash(e.get("src_files")):
         return None
     return float(e["bytes_per_point"])
 
