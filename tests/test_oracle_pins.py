@@ -6,6 +6,7 @@ brute-force dense solve assembled independently in the test.  They are chosen so
 that a dropped term, a wrong sign or index, or a transposed operand fails one.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -685,3 +686,9 @@ def test_three_level_weak_scaling_shape_of_the_paper():
         floor = errs[-1]
         reach.append(next(k + 1 for k, e in enumerate(errs) if e <= 1.6 * floor))
     assert max(reach) <= 6 and reach[2] <= reach[0], reach
+    # against the counts the paper states (golden, Sec. 4.2.2), one iteration of reading slack
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "paper_e3_iterations.txt"))
+            if l.strip() and not l.startswith("#")]
+    paper = {int(a): int(b) for a, b in rows}
+    for N, r in zip((32, 64, 128), reach):
+        assert abs(r - paper[N]) <= 1, (N, r, paper[N])
