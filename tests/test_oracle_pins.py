@@ -692,3 +692,14 @@ def test_three_level_weak_scaling_shape_of_the_paper():
     paper = {int(a): int(b) for a, b in rows}
     for N, r in zip((32, 64, 128), reach):
         assert abs(r - paper[N]) <= 1, (N, r, paper[N])
+
+
+@pytest.mark.parametrize("dim,order", [(1, 4), (2, 4), (3, 2), (3, 4)])
+def test_injection_after_interpolation_returns_the_coarse_values(dim, order):
+    """Interpolation puts the coarse value itself on every fine point that coincides with
+    a coarse point (Sec. 4.2.1 transfers), so injecting the interpolant gives it back."""
+    n = 15
+    nc = (n - 1) // 2
+    uc = np.random.default_rng(dim + order).standard_normal(nc ** dim)
+    uf = O.interp_add(dim, n, order, 1.0, uc, np.zeros(n ** dim))
+    np.testing.assert_array_equal(O.inject(dim, n, uf), uc)
