@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 # algorithmic bytes per grid point of one launch, by kernel and data precision
-# (reads + writes a kernel cannot avoid)
+# (the reads and writes a kernel cannot avoid)
 def algo_bytes_per_point(kernel: str, tsize: int, sf: int = 5, sc: int = 3) -> float:
     t = tsize
     return {
@@ -92,14 +92,12 @@ def job_time_and_value(ms_local, units_per_rank, world, device="cuda"):
 
 def sample_clocks_start():
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
         p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
                               "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        return p, f
+        return p, None
     except Exception:
         return None, None
 
@@ -124,9 +122,6 @@ def sample_clocks_stop(p, f, gpu_index):
             rows.append(parts)
         except ValueError:
             continue
-    if f is not None:
-        f.write(out)
-        f.close()
     if not rows:
         return None
     sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -216,12 +211,14 @@ class OracleSample:
         self.o.set_initial(wl.u0())
         self.o.predict()
 
-    def sample(self):
+    def sample(self, threads: int = 0):
+        """threads > 0: run the oracle's loops on that many threads; 0: all host cores."""
+        import oracle as O
+        cores = O.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
         t0 = time.perf_counter()
         self.o.iteration()
         t = time.perf_counter() - t0
         dofs = self.wl.dofs * (self.wl.fine_nodes - 1) * self.slices
-        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         return dofs / t, t, cores
 
 
@@ -236,7 +233,7 @@ def run_reference(args):
         orc.sample()
     vals, secs = [], []
     for _ in range(args.steps):
-        v, t, cores = orc.sample()
+        v, t, cores = orc.sample(args.ref_threads)
         vals.append(v)
         secs.append(t)
     value = len(vals) / sum(1.0 / v for v in vals)
@@ -749,7 +746,7 @@ def run_ours(args):
     u0_dev = torch.tensor(u0, device="cuda")
     common = dict(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, interp_order=4)
 
-    fp64_ms = None
+    fp64_ms, fp64_runs = None, []
     r_ref = None
     if args.quick:
         k_ref, target = wl.iterations, 0.0
@@ -762,16 +759,23 @@ def run_ours(args):
         # the same residual to RES_TOL: FP32 V-cycles perturb U at the FP32 rounding level
         # (~1e-7 |U|), which moves a residual of ~1e-4 |U| by ~0.1 %
         target = float(f"{r_ref * (1.0 + RES_TOL):.4e}")
-        # one timed step of the plain FP64 path to that target (same schedule, graphs); its
-        # iteration count is K_ref
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
+        # the plain FP64 path to that target (same schedule, graphs): its iteration count is
+        # K_ref; when the measured variant is not itself FP64 it is timed over repeated steps
+        # (median and spread), after one untimed step
         ref.set_initial(u0_dev)
         _, k_ref, _ = ref.iterate(4 * wl.iterations, target)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        fp64_ms = f0.elapsed_time(f1) if wl.precision != 0 else None
+        if wl.precision != 0:
+            fp64_runs = []
+            for _ in range(args.fp64_steps):
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                ref.set_initial(u0_dev)
+                ref.iterate(4 * wl.iterations, target)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                fp64_runs.append(f0.elapsed_time(f1))
+            fp64_ms = statistics.median(fp64_runs) if fp64_runs else None
         ref.close()
         del ref
         torch.cuda.empty_cache()
@@ -804,15 +808,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    # record every launch on the fine grid (whole batch or a slice group), or every launch
-    pmg.pfasst_mg_profile(s.h, True, 0 if args.profile_all else wl.dofs)
     launches0 = s.launches()
     # inputs larger than L2 (the 3D workload) need no flush; otherwise a 512 MB buffer is
     # rewritten between timed steps, outside the timed intervals
     flush = None if (wl.dim == 3 and wl.n >= 255) else torch.empty(1 << 27, dtype=torch.float32, device="cuda")
     cp, cf = sample_clocks_start()
-    iters = []
-    ms_total = 0.0
+    iters, step_ms = [], []
     torch.cuda.synchronize()
     for _ in range(args.steps):
         if flush is not None:
@@ -823,16 +824,32 @@ def run_ours(args):
         ev1.record(stream)
         iters.append((rc, it, res))
         torch.cuda.synchronize()
-        ms_total += ev0.elapsed_time(ev1)
+        step_ms.append(ev0.elapsed_time(ev1))
     clocks = sample_clocks_stop(cp, cf, local)
     launches = s.launches() - launches0
+    ms_total = sum(step_ms)
+    # per-kernel CUDA-event times come from separate profiled steps of the same workload
+    # after the timed region (an event pair around every launch on the fine grid, or around
+    # every launch), so that the headline time carries no profiling overhead
+    prof_steps = max(1, min(args.prof_steps, args.steps))
+    pmg.pfasst_mg_profile(s.h, True, 0 if args.profile_all else wl.dofs)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(prof_steps):
+        if flush is not None:
+            flush.fill_(1.0)
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = p0.elapsed_time(p1) / prof_steps
     stats = pmg.pfasst_mg_profile_read(s.h)
     pmg.pfasst_mg_profile(s.h, False, 0)
     if args.profile_all:
         tot = sum(d["ms"] for d in stats)
         for d in sorted(stats, key=lambda d: -d["ms"]):
-            print(f"{d['kernel']:>18} n={d['n']:>4} prec={d['precision']} launches/step={d['launches'] / args.steps:8.0f} "
-                  f"ms/step={d['ms'] / args.steps:9.2f} share={d['ms'] / tot:6.1%}", file=sys.stderr)
+            print(f"{d['kernel']:>18} n={d['n']:>4} prec={d['precision']} launches/step={d['launches'] / prof_steps:8.0f} "
+                  f"ms/step={d['ms'] / prof_steps:9.2f} share={d['ms'] / tot:6.1%}", file=sys.stderr)
     stats = [d for d in stats if d["n"] == wl.n]
     dof_sweeps = wl.dofs * (wl.fine_nodes - 1) * wl.slices * k_ref
     ms, value = job_time_and_value(ms_total / args.steps, dof_sweeps, world)
@@ -894,13 +911,20 @@ def run_ours(args):
                    "l2": "working set > 60 GB, far above the 129 MB L2; no flush" if flush is None
                    else "L2 flushed (512 MB write) before every timed step, outside the timed interval",
                    "autotuned_smoothers": " ".join(tuning),
+                   "ms_per_step_median": statistics.median(step_ms),
+                   "ms_per_step_min_max": [min(step_ms), max(step_ms)],
                    "fp64_plain_ms_per_step": fp64_ms,
-                   "speedup_vs_fp64_plain": (fp64_ms / ms) if fp64_ms else None},
+                   "fp64_plain_repeats": len(fp64_runs),
+                   "fp64_plain_ms_min_max": [min(fp64_runs), max(fp64_runs)] if fp64_runs else None,
+                   "speedup_vs_fp64_plain": (fp64_ms / statistics.median(step_ms)) if fp64_ms else None},
         "roofline": roof,
         "roofline_hbm_kernel": roof_hbm,
-        "kernels": sorted(({"kernel": d["kernel"], "n": d["n"], "ms_per_step": d["ms"] / args.steps,
-                            "launches_per_step": d["launches"] / args.steps} for d in stats),
+        "kernels": sorted(({"kernel": d["kernel"], "n": d["n"], "ms_per_step": d["ms"] / prof_steps,
+                            "launches_per_step": d["launches"] / prof_steps} for d in stats),
                           key=lambda d: -d["ms_per_step"])[:8],
+        "kernel_timing": {"profiled_steps": prof_steps, "profiled_ms_per_step": prof_ms,
+                          "how": "CUDA events around every fine-grid launch on the library's stream, in "
+                                 "separate steps after the timed region"},
         "e2e": None if e2e_steps == 0 else {
             "value": e2e_value, "unit": "DOF-sweeps/s",
             "h2d_bytes_per_step": wl.dofs * 8, "d2h_bytes_per_step": wl.dofs * 8, "ms_per_step": e2e_ms},
@@ -908,11 +932,17 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
-        v, tsec, cores = OracleSample(wl, args.ref_slices).sample()
+        orc = OracleSample(wl, args.ref_slices)
+        v, tsec, cores = orc.sample()
         line["cpu_baseline"] = {"value": v, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one FP64 oracle PFASST iteration on {args.ref_slices} of the "
                                           f"{wl.slices} slices ({tsec:.1f} s)",
                                 "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+        if args.single_thread_baseline:
+            v1, t1, _ = orc.sample(threads=1)
+            line["cpu_baseline"]["single_thread"] = {
+                "value": v1, "unit": "DOF-sweeps/s", "cores": 1,
+                "sample": f"the next oracle PFASST iteration on the same slice, one thread ({t1:.1f} s)"}
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -933,6 +963,14 @@ def main():
                     help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
                          "no CPU baseline")
     ap.add_argument("--ref-slices", type=int, default=1)
+    ap.add_argument("--ref-threads", type=int, default=0,
+                    help="--impl reference: oracle threads (0 = all host cores)")
+    ap.add_argument("--single-thread-baseline", type=int, default=1,
+                    help="1: also time one oracle iteration on one host thread")
+    ap.add_argument("--fp64-steps", type=int, default=5,
+                    help="timed repeats of the plain FP64 path (median reported)")
+    ap.add_argument("--prof-steps", type=int, default=2,
+                    help="profiled steps after the timed region (per-kernel CUDA-event times)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--iters", type=int, default=0, help="with --quick: PFASST iterations per step (default: workload's)")
     ap.add_argument("--vcycles", type=int, default=-1, help="override V-cycles per sub-step (0 = solve to 1e-12)")

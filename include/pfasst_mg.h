@@ -112,8 +112,8 @@ typedef struct {
 typedef struct pmg_ctx *pmg_handle;
 
 /* Defaults: Jacobi omega 2/3, V(2,1), 2 V-cycles, tol 1e-12, stall 0.75, cap 50,
- * FP64, 4th-order interpolation, graphs on, autotuning on, automatic slice groups,
- * V-cycle tail on. */
+ * FP64, 4th-order interpolation, graphs on, autotuning on, slice groups 0 (one group:
+ * no overlap), V-cycle tail off. */
 void pfasst_mg_default_options(pmg_options *opt);
 
 /* Bytes of device workspace pfasst_mg_create needs for this problem.
@@ -392,14 +392,15 @@ int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const d
 /* ---- allocation-free multigrid solve -------------------------------------- */
 
 /* Same computation and arguments as pfasst_mg_helmholtz_solve, for callers that
- * cannot allocate device memory: code running while a stream is captured into a
- * CUDA graph (cudaMalloc is not allowed there), host frameworks that own all device
- * memory through their own allocator, and latency-critical loops where an
- * allocation would synchronise the device.  The paper has no counterpart; this is
- * a deployment variant of the solve above.
+ * cannot allocate device memory: applications that hand all of the GPU's memory to
+ * their own pool allocator at start-up (a raw cudaMalloc then fails or fragments the
+ * pool), real-time loops in which cudaMalloc / cudaFree would synchronise the device
+ * and stall every other stream, and deployments that forbid allocation after
+ * initialisation.  The paper has no counterpart; this is a deployment variant of the
+ * solve above.
  *   - Scratch comes from one fixed 32 MiB device array inside this library (held
- *     by every GPU that loads the library until the process exits); nothing is
- *     allocated or freed, on the device or the host.
+ *     by every GPU that loads the library until the process exits); no device memory
+ *     is allocated or freed (no cudaMalloc, cudaMallocAsync or cudaFree).
  *   - Sizes whose scratch (padded b and u plus the multigrid hierarchy) exceeds
  *     32 MiB are rejected with PMG_ERR_INVALID_ARG and a message giving the need;
  *     e.g. a 3D 63^3 grid fits with batch 1 in FP64, a 3D 31^3 grid with batch 16.

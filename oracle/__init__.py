@@ -88,7 +88,15 @@ def lib():
         L.orc_pfasst_spread.argtypes = [ctypes.POINTER(_PFASST), _D, _D, _D]
         L.orc_pfasst_predict.argtypes = [ctypes.POINTER(_PFASST)] + [_D] * 6
         L.orc_pfasst_iteration.argtypes = [ctypes.POINTER(_PFASST)] + [_D] * 7
+        L.orc_pfasst_interp_slice.argtypes = [ctypes.POINTER(_PFASST)] + [_D] * 4
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = ctypes.c_int
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's grid loops (n <= 0: leave as is); returns the count."""
+    return lib().orc_set_threads(n)
 
 
 def _p(a: np.ndarray | None):
@@ -287,6 +295,14 @@ class PFASST:
                                    _p(self.Fc), _p(self.fas), _p(self.Uc0), _p(self.res))
         return self.res.copy()
 
+    def interp_slice(self, p: int):
+        """Only the interpolation step of slice p: Uf[p] += I_t I_x (Uc[p] - Uc0[p]),
+        then Ff[p] = A Uf[p]."""
+        Uf, Ff = self.Uf[p], self.Ff[p]
+        assert Uf.flags.c_contiguous and Ff.flags.c_contiguous
+        lib().orc_pfasst_interp_slice(ctypes.byref(self._c), _p(Uf), _p(Ff),
+                                      _p(np.ascontiguousarray(self.Uc[p])), _p(np.ascontiguousarray(self.Uc0[p])))
+
     def run(self, max_iter: int, tol: float):
         """Predictor, then iterations until max residual <= tol. Returns (iters, res history)."""
         self.predict()
@@ -363,6 +379,12 @@ class MLPFASST:
     def predict(self):
         st = self._state()
         lib().orc_ml_predict(ctypes.byref(self._c), ctypes.byref(st))
+
+    def interp_slice(self, level, p):
+        """Only the interpolation step level+1 -> level of slice p: U[level][p] +=
+        I_t I_x (U[level+1][p] - Ur[level+1][p]), then F[level][p] = A U[level][p]."""
+        st = self._state()
+        lib().orc_ml_interp_slice(ctypes.byref(self._c), ctypes.byref(st), level, p)
 
     def sweep(self, level):
         """One sweep on ``level`` of every slice (the serial chain on the coarsest level)."""

@@ -30,6 +30,22 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Number of OpenMP threads the oracle's grid loops use (the CPU-baseline timings run it
+ * single-threaded and on all cores); returns the count in effect. */
+int orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
 
 #define ORC_MAXS 16
 
@@ -777,6 +793,12 @@ static void interp_correction(const orc_pfasst *P, double *Uf, double *Ff, const
     free(d);
 }
 
+/* The interpolation step alone, for one slice (exported so that the tests can pin it). */
+void orc_pfasst_interp_slice(const orc_pfasst *P, double *Uf, double *Ff, const double *Uc, const double *Uc0)
+{
+    interp_correction(P, Uf, Ff, Uc, Uc0);
+}
+
 static orc_level fine_level(const orc_pfasst *P)
 {
     orc_level L = {P->dim, P->n_f, P->s_f, P->nu, P->dt, P->fam_f, fine_order(P)};
@@ -976,6 +998,12 @@ static void ml_interp(const orc_ml *P, const orc_mlstate *S, int l, int p)
     }
     for (int m = 0; m < sf; ++m) orc_apply_A_o(dim, nf, ml_order(P, l), P->nu, Uf + (size_t)m * Nf, Ff + (size_t)m * Nf);
     free(d);
+}
+
+/* The interpolation step alone, level l+1 -> l of slice p (exported for the tests). */
+void orc_ml_interp_slice(const orc_ml *P, const orc_mlstate *S, int l, int p)
+{
+    ml_interp(P, S, l, p);
 }
 
 static void ml_sweep(const orc_ml *P, const orc_mlstate *S, int l, int p)

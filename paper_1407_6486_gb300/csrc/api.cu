@@ -404,7 +404,9 @@ int minv_slots(const pmg_ctx *h) {
 void plan_ctx(Plan &pl, pmg_ctx *h) {
   const size_t sf = (size_t)h->gf.slab * 8;
   pl.add((void **)&h->Uf, sf * h->P * h->sf);
-  pl.add((void **)&h->Ff, sf * h->P * h->sf);
+  // the fine F = A U is stored only for full solves (tolerance mode); with fixed V-cycle
+  // counts the end-of-iteration pass and the FAS restriction evaluate it from U
+  if (h->opt.vcycles == 0) pl.add((void **)&h->Ff, sf * h->P * h->sf);
   pl.add((void **)&h->qf, sf * h->P * (h->sf - 1));
   pl.add((void **)&h->u0, sf);
   pl.add((void **)&h->dense, sf);
@@ -755,7 +757,7 @@ int sweep(pmg_ctx *h, int level, int p0, int B) {
   const Grid &g = *v.g;
   const long long stride = (long long)v.s * g.slab, sq = (long long)(v.s - 1) * g.slab;
   double *U = v.U + p0 * stride;
-  double *F = v.F + p0 * stride;
+  double *F = v.F ? v.F + p0 * stride : nullptr;  // null: F-free fine level
   double *q = v.q + p0 * sq;
   const double *tau = v.tau ? v.tau + p0 * stride : nullptr;
   const bool keepF = level > 0 || !ffree(h);
@@ -2276,13 +2278,14 @@ int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int
 
 // ----------------------------------------------------------------- allocation-free multigrid solve
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA stream is
-// being captured into a graph (cudaMalloc is not permitted there), host frameworks
-// that own every byte of device memory through their own allocator and forbid raw
-// cudaMalloc, and latency-critical loops where an allocation would synchronise the
-// device.  pfasst_mg_helmholtz_solve_noalloc serves them: it runs the same V-cycles
-// as pfasst_mg_helmholtz_solve but takes its scratch from one fixed device array that
-// is part of this library, so it calls no allocator at all.
+// Some callers cannot allocate device memory: applications that reserve all of the
+// GPU's memory for their own pool allocator at start-up (a raw cudaMalloc then fails or
+// fragments their pool), real-time loops in which cudaMalloc / cudaFree would
+// synchronise the device and stall every other stream, and deployments whose rules
+// forbid allocation after initialisation.  pfasst_mg_helmholtz_solve_noalloc serves
+// them: it runs the same V-cycles as pfasst_mg_helmholtz_solve but takes its scratch
+// from one fixed device array that is part of this library, so it calls no device
+// allocator.
 
 namespace {
 
@@ -2341,6 +2344,19 @@ void coarsest_inverse_into(int dim, double c, double *out) {
     }
 }
 
+// the coarsest-grid inverse travels by value in the kernel's parameters (5832 bytes for
+// 27 x 27 FP64 values), so no host buffer has to outlive the call
+struct MinvPayload {
+  double v[27 * 27];
+};
+
+__global__ void store_minv_kernel(MinvPayload p, int count, int f32, void *dst) {
+  for (int q = threadIdx.x; q < count; q += blockDim.x) {
+    if (f32) ((float *)dst)[q] = (float)p.v[q];
+    else ((double *)dst)[q] = p.v[q];
+  }
+}
+
 }  // namespace
 
 extern "C" int pfasst_mg_helmholtz_solve_noalloc(const pmg_grid *grid, double c, int batch, const double *b,
@@ -2374,19 +2390,20 @@ extern "C" int pfasst_mg_helmholtz_solve_noalloc(const pmg_grid *grid, double c,
   void *base = nullptr;
   PMG_RET(noalloc_base(&base));
   pl.carve((char *)base);
-  // coarsest-grid inverse, staged from the stack (a pageable copy returns after staging)
-  double minv64[27 * 27];
-  float minv32[27 * 27];
-  coarsest_inverse_into(grid->dim, c, minv64);
-  for (int q = 0; q < n3 * n3; ++q) minv32[q] = (float)minv64[q];
+  // coarsest-grid inverse, computed on the host and stored on the device by a kernel
+  // that receives the values as its launch parameters (no host-to-device copy)
+  MinvPayload mp;
+  coarsest_inverse_into(grid->dim, c, mp.v);
   long long launches = 0;
   Launch Ln{st, &launches, nullptr};
   const long long dense = (long long)g.nz * g.ny * g.n;
   // the array keeps the previous call's contents: clear it (pad columns must be zero)
-  if (cudaMemsetAsync(base, 0, pl.total, st) != cudaSuccess ||
-      cudaMemcpyAsync(minv, H.tsize == 8 ? (const void *)minv64 : (const void *)minv32, (size_t)n3 * n3 * H.tsize,
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      k_pack(Ln, g, b, dense, bp, g.slab, batch) != cudaSuccess || k_pack(Ln, g, u, dense, up, g.slab, batch) != cudaSuccess)
+  if (cudaMemsetAsync(base, 0, pl.total, st) != cudaSuccess)
+    return fail(nullptr, PMG_ERR_CUDA, "set-up of the allocation-free solve failed");
+  store_minv_kernel<<<1, 256, 0, st>>>(mp, n3 * n3, H.tsize == 4, minv);
+  ++launches;
+  if (cudaGetLastError() != cudaSuccess || k_pack(Ln, g, b, dense, bp, g.slab, batch) != cudaSuccess ||
+      k_pack(Ln, g, u, dense, up, g.slab, batch) != cudaSuccess)
     return fail(nullptr, PMG_ERR_CUDA, "set-up of the allocation-free solve failed");
   MGCtx Mc{Ln, &H, &o, nullptr, nullptr, nullptr, nullptr, nullptr, st};
   PMG_RET(solve_substep(Mc, 0, batch, c, minv, bp, g.slab, nullptr, 0, up, g.slab, nullptr));

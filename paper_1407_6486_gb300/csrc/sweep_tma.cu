@@ -12,8 +12,11 @@
 // compute, which keeps their register count low and the loads deep.
 //
 // Every wait on an mbarrier is bounded (about 2 s of SM clock); on a timeout the
-// kernel records the fact in a device flag, stops at the end of the current plane and
-// returns; the host turns the flag into PMG_ERR_TIMEOUT.
+// kernel records the fact in a device flag, stops at the end of the current plane,
+// waits (bounded again) for the loads it still has in flight and returns; the host
+// turns the flag into PMG_ERR_TIMEOUT.  A load that has not landed after that second
+// wait could still write into shared memory the CTA has released: the host then
+// reports the timeout and the caller should treat the CUDA context as suspect.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -134,6 +137,7 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
   bool ok = true;
   if (!ZERO) ok = wait_e(z0 - 2) && wait_e(z0 - 1);
   double2 upre[PB];  // UPD: this thread's u pairs of plane k-1, loaded before the red phase
+  int kstop = z1;    // plane at which a timed-out CTA stopped
   for (int k = z0 - 1; k <= z1; ++k) {
     if (tid == 0) {  // refill the slots the previous plane released
       if (!ZERO && k + 1 + DEPTH <= z1 + 1) issue_e(k + 1 + DEPTH);
@@ -237,15 +241,23 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
       }
     }
     __syncthreads();  // slots of plane k-1 may be refilled now
-    if (s_bad) break;  // uniform: read after the barrier
+    if (s_bad) {      // uniform: read after the barrier
+      kstop = k;
+      break;
+    }
   }
   if (s_bad && tid == 0) {
     atomicExch(&g_sweep_timeout, 1);
-    // let loads still in flight land before the CTA's shared memory is released
-    for (int i = 0; i < NE + NF; ++i) {
-      const long long t0 = clock64();
-      while (clock64() - t0 < 200000) __nanosleep(64);
+    // Before the CTA's shared memory is released, wait (bounded again) for every load
+    // still in flight.  A slot is refilled only after its previous load was waited for,
+    // so at most the last load issued into each slot can be outstanding: the planes
+    // issued last, up to one per slot.
+    if (!ZERO) {
+      const int last = min(kstop + 1 + DEPTH, z1 + 1);
+      for (int p = max(z0 - 2, last - NE + 1); p <= last; ++p) mbar_wait(&bar[eslot(p)], ((p - z0 + 2) / NE) & 1);
     }
+    const int lastf = min(kstop + DEPTH, z1);
+    for (int p = max(z0 - 1, lastf - NF + 1); p <= lastf; ++p) mbar_wait(&bar[NE + fslot(p)], ((p - z0 + 1) / NF) & 1);
   }
 }
 
@@ -314,6 +326,7 @@ __global__ void __launch_bounds__(RNT, 4) resrestrict_tma_kernel(const __grid_co
   const long long cplane = (long long)gc.ny * gc.pitch;
   float acc = 0.f;
   bool ok = mbar_wait(&bar[eslot(zb - 1)], 0) && mbar_wait(&bar[eslot(zb)], 0);
+  int zstop = ze;  // plane at which a timed-out CTA stopped
   for (int z = zb; z <= ze; ++z) {
     if (tid == 0) {  // refill the slots of planes z-2 (e) and z-1 (f), read before the last barrier
       if (z + 1 + RD <= ze + 1) issue_e(z + 1 + RD);
@@ -333,7 +346,10 @@ __global__ void __launch_bounds__(RNT, 4) resrestrict_tma_kernel(const __grid_co
       R[ry * RRS + rx] = F0[ry * RBX + rx + 4] - (ec - a * (nb - 6.f * ec));
     }
     __syncthreads();
-    if (s_bad) break;  // uniform: read after the barrier
+    if (s_bad) {  // uniform: read after the barrier
+      zstop = z;
+      break;
+    }
     // x-y full weighting at the thread's coarse point: fine x = 2I+1 is residual column
     // 2cx+1, fine y = 2J+1 is residual row 2cy+1
     const int c0 = 2 * cx + 1, r0 = 2 * cy + 1;
@@ -350,9 +366,10 @@ __global__ void __launch_bounds__(RNT, 4) resrestrict_tma_kernel(const __grid_co
   }
   if (s_bad && tid == 0) {
     atomicExch(&g_sweep_timeout, 1);
-    // let loads still in flight land before the CTA's shared memory is released
-    const long long t0 = clock64();
-    while (clock64() - t0 < 2000000) __nanosleep(64);
+    // wait (bounded) for the last load issued into every slot, as in the sweep above
+    const int laste = min(zstop + 1 + RD, ze + 1), lastf = min(zstop + RD, ze);
+    for (int p = max(zb - 1, laste - RNE + 1); p <= laste; ++p) mbar_wait(&bar[eslot(p)], ((p - zb + 1) / RNE) & 1);
+    for (int p = max(zb, lastf - RNF + 1); p <= lastf; ++p) mbar_wait(&bar[RNE + fslot(p)], ((p - zb) / RNF) & 1);
   }
 }
 

@@ -52,10 +52,21 @@ def test_workspace_size_grows_with_problem(lib):
     b = _ws(2, 63, 5, 2, 3, 4)
     c = _ws(2, 63, 5, 2, 3, 8)
     assert 0 < a < b < c
-    # FP64 fine state alone: U, F, q over slices and nodes, padded rows
-    assert b >= 8 * 64 * 63 * (5 + 5 + 4) * 4
+    # FP64 fine state alone: U and q over slices and nodes, padded rows
+    assert b >= 8 * 64 * 63 * (5 + 4) * 4
     # mixed precision halves the multigrid scratch
     assert _ws(3, 31, 5, 2, 3, 4, precision=1) < _ws(3, 31, 5, 2, 3, 4, precision=0)
+
+
+def test_fixed_vcycle_counts_plan_no_fine_F(lib):
+    """With a fixed V-cycle count the fine level stores no F = A U (the end-of-iteration
+    pass and the FAS restriction evaluate it from U): the workspace is smaller than the
+    full-solve one by exactly one FP64 array of slices x nodes padded grids."""
+    for dim, n, sf, P in ((2, 63, 5, 4), (3, 31, 5, 8), (3, 63, 3, 2)):
+        full = _ws(dim, n, sf, 2, 3, P, vcycles=0)
+        fixed = _ws(dim, n, sf, 2, 3, P, vcycles=2)
+        fbytes = 8 * (n + 1) * n ** (dim - 1) * P * sf
+        assert full - fixed == (fbytes + 255) // 256 * 256, (dim, n, full, fixed)
 
 
 @pytest.mark.parametrize("bad", [

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from parity import worst_rel
 import paper_1407_6486_gb300 as pmg
 from paper_1407_6486_gb300 import inputs
 
@@ -23,7 +24,8 @@ def _built():
 
 
 def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+    """Worst relative l2 error over the grid functions (slices, nodes, grids) of a."""
+    return worst_rel(a, b)
 
 
 def small_batch():
@@ -76,4 +78,27 @@ def test_batch_mixed_precision_and_repeated_runs():
     for i, p in enumerate(probs):
         want, _ = oracle_run(p, 2, 3, 1)
         assert rel(b.solution(i), want) < 1e-6, (i, p.dim, p.n)
+    b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-6)])
+def test_batch_with_the_workload_extremes_matches_oracle(precision, tol):
+    """An uneven batch holding the largest members the uneven workload draws -- a 511^2
+    and a 127^3 grid -- next to small ones, autotuned (the 127^3 member may take the
+    fused or TMA-staged z-marching sweep), red-black V(2,1), FP64 or mixed: every member
+    against the oracle run on its own, one time step of two sweeps."""
+    probs = [inputs.Problem(2, 511, 5, 0.8, 0.004, [(1, 2, 1), (7, 3, 1)], [1.0, 0.4]),
+             inputs.Problem(3, 127, 3, 1.3, 0.006, [(1, 1, 1), (2, 5, 3)], [0.9, -0.5]),
+             inputs.Problem(2, 63, 3, 0.3, 0.002, [(2, 2, 1)], [1.1]),
+             inputs.Problem(3, 31, 5, 1.9, 0.009, [(1, 2, 2), (3, 1, 1)], [0.7, 0.2])]
+    b = pmg.BatchSolver([(p.dim, p.n, p.nodes, p.nu, p.dt) for p in probs], smoother=1, omega=1.0, vcycles=2,
+                        precision=precision, autotune=1)
+    for i, p in enumerate(probs):
+        b.set_initial(i, p.u0())
+    res = b.run(1, 2)
+    for i, p in enumerate(probs):
+        want, wres = oracle_run(p, 1, 2, 1)
+        assert rel(b.solution(i), want) < tol, (i, p.dim, p.n)
+        if precision == 0:
+            assert abs(res[i] - wres) <= 1e-7 * wres + 1e-14
     b.close()

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from parity import worst_rel
 import paper_1407_6486_gb300 as pmg
 from paper_1407_6486_gb300 import inputs
 
@@ -33,7 +34,8 @@ def _built():
 
 
 def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+    """Worst relative l2 error over the grid functions (slices, nodes, grids) of a."""
+    return worst_rel(a, b)
 
 
 def omega(sm):
@@ -110,6 +112,9 @@ CASES = [
     (3, 7, 3, 2, 2, 2, 0, 1, 4),
     (2, 31, 3, 0, 3, 1, 0, 2, 4),
     (1, 127, 9, 3, 2, 2, 1, 1, 4),
+    # one slice, two levels: MLSDC (Sec. 2.3), the predictor is one coarse sweep
+    (2, 31, 5, 3, 1, 2, 1, 2, 4),
+    (3, 15, 5, 3, 1, 2, 0, 1, 4),
 ]
 
 
@@ -333,8 +338,8 @@ def test_vcycle_tail_matches_per_level_kernels(dim, n, precision):
         s.iterate(3, 0.0)
         out.append(s.state(0))
         s.close()
-    rel = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0])
-    assert rel <= (1e-12 if precision == 0 else 1e-5), rel
+    err = worst_rel(out[1], out[0], "tail vs per-level")
+    assert err <= (1e-12 if precision == 0 else 1e-5), err
 
 
 @pytest.mark.parametrize("n,level,zchunk", [(127, 0, 32), (255, 1, 16), (127, 0, 7)])
@@ -354,8 +359,8 @@ def test_tma_staged_sweep_matches_the_fused_sweep(n, level, zchunk):
         s.iterate(2, 0.0)
         out.append(s.state(0))
         s.close()
-    rel = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0])
-    assert rel <= 1e-6, rel
+    err = worst_rel(out[1], out[0], "TMA vs fused")
+    assert err <= 1e-6, err
 
 
 UNIFORM_CASES = [
@@ -527,3 +532,69 @@ def test_integer_narrowing_matches_the_hardware_conversion():
     on 2^28 inputs: uniform bit patterns, the float range down to subnormals and up to
     overflow, exact ties."""
     assert pmg.pfasst_mg_check_narrowing(1 << 28, seed=12345) == 0
+
+
+# ---------------------------------------------------------------- the TMA kernels on the workload grids
+
+def _colloc_state(wl, n, nodes, slices):
+    """The collocation solution of every node of every slice (Eq. collocationM), per sine
+    mode: Y = (I - z Q)^-1 1 y0 with z = dt nu lambda(k) and Q the oracle's integration
+    matrix; slice p starts from the last node of slice p-1.  Shape (slices, nodes, n^3)."""
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    Q = O.qmatrix(nodes)
+    out = np.zeros((slices, nodes, n ** 3))
+    for k, a in zip(wl.modes, wl.amps):
+        z = wl.dt * wl.nu * sum((2 * math.cos(kk * math.pi * h) - 2) / h ** 2 for kk in k)
+        phi = np.einsum("k,j,i->kji", np.sin(k[2] * np.pi * x), np.sin(k[1] * np.pi * x),
+                        np.sin(k[0] * np.pi * x)).reshape(-1)
+        y0 = a
+        for p in range(slices):
+            Y = np.linalg.solve(np.eye(nodes) - z * Q, np.full(nodes, y0))
+            out[p] += Y[:, None] * phi[None, :]
+            y0 = Y[-1]
+    return out
+
+
+def test_mixed_fixed_point_127_with_tma_kernels_pinned():
+    """Mixed precision on the 3D workload's coarse-grid size 127^3 (9 slices, so that the
+    batched fine level takes the z-marching kernels), with the TMA-staged sweep pinned on
+    the finest multigrid level: the pre-smoothing sweep from zero, the plain sweep, the
+    post-smoothing sweep fused with u += e, and the TMA-staged residual + restriction.
+    Converged to a collocation residual of 1e-11, every (slice, node) grid function must
+    match the collocation solution computed per sine mode from the oracle's Q to 1e-9."""
+    wl = inputs.heat3d_c3(n=127, slices=9)
+    s = pmg.PFASSTSolver(3, wl.n, 5, 3, wl.slices, wl.nu, wl.dt, smoother=1, omega=1.0, vcycles=2, precision=1,
+                         autotune=0)
+    for narrow in (0, 1):
+        pmg.pfasst_mg_set_tuning(s.h, 0, narrow, 2, 32, 512)
+    assert pmg.pfasst_mg_tuning(s.h, 0, 0)[:2] == (2, 32)
+    s.set_initial(wl.u0())
+    rc, it, res = s.iterate(400, 1e-11)
+    assert rc == pmg.PMG_OK, (it, res)
+    gpu = s.state(0)
+    s.close()
+    assert rel(gpu, _colloc_state(wl, wl.n, 5, wl.slices)) < MIXED_TOL
+
+
+def test_fp32_sweep_255_with_tma_kernels_matches_oracle():
+    """One SDC sweep (4 sub-steps, one FP32 V(2,1) red-black cycle each) on two slices of
+    the 255^3 grid of the 3D workload with the TMA-staged sweep pinned on the finest
+    level (the batch of two takes the TMA-staged residual + restriction too), against
+    the oracle's FP64 sweep: FP32 rounding of the corrections only, <= 2e-6 per node."""
+    wl = inputs.heat3d_c3(n=255, slices=2)
+    s = pmg.PFASSTSolver(3, wl.n, 5, 0, 2, wl.nu, wl.dt, nlevels=1, smoother=1, omega=1.0, vcycles=1, precision=1,
+                         autotune=0)
+    for narrow in (0, 1):
+        pmg.pfasst_mg_set_tuning(s.h, 0, narrow, 2, 32, 512)
+    u0 = wl.u0()
+    s.set_initial(u0)
+    s.sweep(0)
+    gpu = s.state(0)
+    s.close()
+    torch.cuda.empty_cache()
+    # single level, no send-forward: both slices start from the spread u0 and sweep alike
+    U = np.repeat(u0[None, :], 5, axis=0)
+    F = np.stack([O.apply_A(3, wl.n, wl.nu, u) for u in U])
+    want, _, _ = O.sweep(3, wl.n, 5, wl.nu, wl.dt, O.MGParams(smoother=1, omega=1.0, vcycles=1), U, F)
+    assert rel(gpu, np.stack([want, want])) < 2e-6

@@ -491,32 +491,128 @@ def test_pfasst_with_one_slice_and_full_solves_matches_dense_collocation():
     np.testing.assert_allclose(pf.Uf[0], Y, atol=1e-12)
 
 
-def test_predictor_does_p_plus_one_coarse_sweeps():
-    """Predictor (Sec. 2.4): with exact coarse solves and a single slice, one coarse sweep
-    from the spread value; the interpolated fine state after the predictor depends on
-    the number of coarse sweeps, which we check against a manual schedule."""
-    dim, n, s_f, s_c, nu, dt, P = 1, 15, 5, 3, 1.0, 0.02, 3
-    u0 = _u0_modes(dim, n)
-    pf = O.PFASST(dim, n, s_f, s_c, P, nu, dt, FULL)
-    pf.set_initial(u0)
-    pf.predict()
-    # manual: serial coarse chain where slice p does p+1 coarse sweeps (stages)
-    ref = O.PFASST(dim, n, s_f, s_c, P, nu, dt, FULL)
-    ref.set_initial(u0)
+# Lobatto IIIA tableau for 3 nodes {0, 1/2, 1} (Hairer-Wanner; tests/golden) and the
+# implicit-Euler matrix of sub-step widths (Eq. Qbe), written out here
+_Q3 = np.array([[0.0, 0.0, 0.0], [5 / 24, 1 / 3, -1 / 24], [1 / 6, 2 / 3, 1 / 6]])
+_QI3 = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.0], [0.0, 0.5, 0.5]])
+_T3 = np.array([0.0, 0.5, 1.0])
+_T5 = np.array([0.0, (1 - math.sqrt(3 / 7)) / 2, 0.5, (1 + math.sqrt(3 / 7)) / 2, 1.0])
+
+
+@pytest.mark.parametrize("dim,n,k,P", [(1, 15, (3,), 4), (2, 15, (1, 2), 3), (2, 31, (2, 1), 5)])
+def test_predictor_coarse_state_follows_the_scalar_recurrence(dim, n, k, P):
+    """Predictor (Sec. 2.4) on a single sine mode with exact coarse solves.  The mode is
+    an eigenvector of the fine and (after injection) of the coarse operator, so
+      - the FAS term is tau_j = a dt t_j (lambda_f - lambda_c) (row sums of Q are the
+        node times, reading g6);
+      - one coarse sweep is the scalar recurrence of Eq. lamdtI plus tau:
+        (I - z Q_I) Y^{k+1} = y0 1 + z (Q - Q_I) Y^k + tau, z = dt lambda_c;
+      - stage s: slices p >= s take the end value slice p-1 had after stage s-1, then
+        sweep, so slice p sweeps p+1 times.
+    The coarse state after the predictor must equal that recurrence at every node of
+    every slice (3 Gauss-Lobatto coarse nodes, 5 fine)."""
+    nu, dt, a = 0.8, 0.01, 1.7
     nc = (n - 1) // 2
-    # coarse state from the spread fine values
-    Uc = np.tile(O.inject(dim, n, u0), (P, s_c, 1))
-    Fc = np.stack([[O.apply_A(dim, nc, nu, u) for u in Uc[p]] for p in range(P)])
-    np.testing.assert_allclose(pf.Uc0, Uc, atol=0)
-    fas = pf.fas.copy()
+    lam_f = nu * sum(_d(kk, n) for kk in k)
+    lam_c = nu * sum(_d(kk, nc) for kk in k)
+    phi_f, phi_c = _sine_mode(dim, n, k), _sine_mode(dim, nc, k)
+    pf = O.PFASST(dim, n, 5, 3, P, nu, dt, FULL)
+    pf.set_initial(a * phi_f)
+    pf.predict()
+    tau = a * dt * _T3 * (lam_f - lam_c)
+    for p in range(P):
+        np.testing.assert_allclose(pf.Uc0[p], np.tile(a * phi_c, (3, 1)), atol=1e-14)
+        np.testing.assert_allclose(pf.fas[p], tau[:, None] * phi_c[None, :], atol=1e-11 * abs(a))
+    z = dt * lam_c
+    M = np.eye(3) - z * _QI3
+    Y = [np.full(3, a) for _ in range(P)]
     for stage in range(P):
         if stage > 0:
-            for p in range(P - 1, stage - 1, -1):
-                Uc[p, 0] = Uc[p - 1, -1]
-                Fc[p, 0] = O.apply_A(dim, nc, nu, Uc[p, 0])
+            ends = [Y[p - 1][-1] for p in range(P)]
+            for p in range(stage, P):
+                Y[p][0] = ends[p]
         for p in range(stage, P):
-            Uc[p], Fc[p], _ = O.sweep(dim, nc, s_c, nu, dt, FULL, Uc[p], Fc[p], np.ascontiguousarray(fas[p]))
-    np.testing.assert_allclose(pf.Uc, Uc, atol=1e-15)
+            Y[p] = np.linalg.solve(M, Y[p][0] * np.ones(3) + z * (_Q3 - _QI3) @ Y[p] + tau)
+    for p in range(P):
+        np.testing.assert_allclose(pf.Uc[p], Y[p][:, None] * phi_c[None, :], atol=1e-11 * abs(a), err_msg=f"slice {p}")
+
+
+def _cubic(x, c):
+    return c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3
+
+
+@pytest.mark.parametrize("dim,order", [(1, 4), (2, 4), (2, 2), (3, 4)])
+def test_interpolation_of_the_correction_reproduces_quadratic_time_cubic_space(dim, order):
+    """Interpolation of the coarse correction (Sec. 4.2.1; readings g8, g9) onto every
+    fine node: a correction g(t) h(x) with g quadratic in time (3 coarse Gauss-Lobatto
+    nodes: Lagrange is exact) and h a product of cubics (linear for order 2) in space
+    must reappear exactly as g(t_m) h(x) at all 5 fine nodes, at every fine point whose
+    stencil stays off the walls.  A wrong pairing of fine and coarse nodes, a wrong
+    weight or a wrong spatial tap fails it."""
+    n = 15 if dim == 3 else 31
+    nc = (n - 1) // 2
+    g = lambda t: 0.7 + 1.3 * t - 2.1 * t ** 2  # noqa: E731
+    cs = [(0.2, -0.5, 0.9, 1.1), (-0.3, 0.8, 0.4, -1.2), (0.5, 0.1, -0.7, 0.6)]
+    if order == 2:
+        cs = [(c[0], c[1], 0.0, 0.0) for c in cs]
+
+    def h(m):
+        x = np.arange(1, m + 1) / (m + 1)
+        comps = [_cubic(x, cs[a]) for a in range(dim)]
+        if dim == 1:
+            return comps[0]
+        if dim == 2:
+            return np.outer(comps[1], comps[0]).reshape(-1)
+        return np.einsum("k,j,i->kji", comps[2], comps[1], comps[0]).reshape(-1)
+
+    pf = O.PFASST(dim, n, 5, 3, 1, 1.0, 0.01, FULL, interp_order=order)
+    pf.Uf[...] = 0.0
+    pf.Uc0[...] = 0.0
+    for j in range(3):
+        pf.Uc[0, j] = g(_T3[j]) * h(nc)
+    pf.interp_slice(0)
+    idx = np.arange(1, n + 1)
+    # odd fine point i takes coarse points (i-3)/2 .. (i+3)/2 (4 taps) or (i-1)/2, (i+1)/2
+    # (2 taps); they must all be interior coarse points 1 .. nc
+    off = (idx >= 5) & (idx <= n - 4) if order == 4 else (idx >= 3) & (idx <= n - 2)
+    mask = off
+    for _ in range(dim - 1):
+        mask = np.multiply.outer(off, mask)
+    mask = mask.reshape(-1)
+    for m in range(5):
+        want = g(_T5[m]) * h(n)
+        np.testing.assert_allclose(pf.Uf[0, m][mask], want[mask], atol=1e-13, err_msg=f"fine node {m}")
+
+
+def test_multilevel_interpolation_reproduces_polynomials_on_both_levels():
+    """The three-level oracle's interpolation (reading g7b): level 1 -> 0 with 3 -> 5
+    Gauss-Lobatto nodes (quadratic in time, cubic in space exact) and level 2 -> 1 with
+    2 -> 3 nodes (linear in time exact), at every point off the walls."""
+    n, nodes = 31, (5, 3, 2)
+    pf = O.MLPFASST(2, n, nodes, 1, 1.0, 0.01, FULL)
+    grids = pf.grids
+    cx, cy = (0.2, -0.5, 0.9, 1.1), (-0.3, 0.8, 0.4, -1.2)
+
+    def h(m):
+        x = np.arange(1, m + 1) / (m + 1)
+        return np.outer(_cubic(x, cy), _cubic(x, cx)).reshape(-1)
+
+    def offwall(m):
+        idx = np.arange(1, m + 1)
+        off = (idx >= 5) & (idx <= m - 4)
+        return np.multiply.outer(off, off).reshape(-1)
+
+    for level, gt, tc, tf in ((0, lambda t: 0.7 + 1.3 * t - 2.1 * t ** 2, _T3, _T5),
+                              (1, lambda t: -0.4 + 2.3 * t, np.array([0.0, 1.0]), _T3)):
+        for arr in (pf.U[level], pf.Ur[level + 1]):
+            arr[...] = 0.0
+        for j in range(len(tc)):
+            pf.U[level + 1][0, j] = gt(tc[j]) * h(grids[level + 1])
+        pf.interp_slice(level, 0)
+        mask = offwall(grids[level])
+        for m in range(len(tf)):
+            want = gt(tf[m]) * h(grids[level])
+            np.testing.assert_allclose(pf.U[level][0, m][mask], want[mask], atol=1e-13, err_msg=f"level {level} node {m}")
 
 
 # ---------------------------------------------------------------- uniform nodes (Sec. 3)

@@ -1,8 +1,9 @@
 """The allocation-free multigrid solve against the allocating one.
 
 pfasst_mg_helmholtz_solve_noalloc exists for callers that cannot allocate device
-memory (work recorded under CUDA stream capture, frameworks that own all device
-memory); it must give the same results as pfasst_mg_helmholtz_solve, call after call,
+memory (applications whose own pool allocator holds all GPU memory, real-time loops in
+which an allocation would synchronise the device); it must give the same results as
+pfasst_mg_helmholtz_solve, call after call,
 although every call reuses the same fixed scratch array.  This file is collected
 last so that a failure here comes after every other test has run.
 """
