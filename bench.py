@@ -70,8 +70,9 @@ def algo_fp64_flops_per_point(kernel: str, sf: int = 5, sc: int = 3) -> float:
     }.get(kernel, 0.0)
 
 
-# FP64 peak from unit counts and clock: 152 SMs x 2.07 GHz x 2 DFMA/clk x 2 flops
-FP64_PEAK_GFLOPS = 152 * 2.07 * 2 * 2
+# nominal FP64 peak from unit counts and clock: 152 SMs x 2.07 GHz x 2 DFMA/clk x 2 flops
+# (context only: the roofline uses the library's measured FP64 FMA probe)
+FP64_NOMINAL_GFLOPS = 152 * 2.07 * 2 * 2
 
 
 def dist_env():
@@ -277,13 +278,14 @@ def run_uneven(args):
         job(b)
     torch.cuda.synchronize()
     l0 = b.launches()
-    t0 = time.perf_counter()
+    cp, cf = sample_clocks_start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for _ in range(args.steps):
         res = job(b)
     ev1.record()
     torch.cuda.synchronize()
+    clocks = sample_clocks_stop(cp, cf, local)
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = b.launches() - l0
     dof_sweeps = sum(p.dofs * (p.nodes - 1) for p in probs) * sweeps * steps
@@ -321,7 +323,7 @@ def run_uneven(args):
                        "l2": "problems are small; the graph is replayed on warm caches (no flush)"},
             "e2e": {"value": dof_sweeps / (e2e_ms / 1000.0), "unit": "DOF-sweeps/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms},
-            "gpu_launches": launches}
+            "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -523,8 +525,9 @@ def run_heat1d(args):
     _build.build()
     pmg.load()
     wl = inputs.heat1d_c1()
+    tail = dict(vcycle_tail=args.vcycle_tail) if args.vcycle_tail >= 0 else {}
     s = pmg.PFASSTSolver(1, wl.n, wl.fine_nodes, 0, 1, wl.nu, wl.dt, nlevels=1, smoother=wl.smoother,
-                         omega=wl.omega, vcycles=wl.vcycles, precision=wl.precision)
+                         omega=wl.omega, vcycles=wl.vcycles, precision=wl.precision, **tail)
     u0 = torch.tensor(wl.u0(), device="cuda")
     out = torch.empty(wl.n, dtype=torch.float64, device="cuda")
 
@@ -542,11 +545,15 @@ def run_heat1d(args):
         solve()
     torch.cuda.synchronize()
     times, sweeps = [], 0
+    l0 = s.launches()
+    cp, cf = sample_clocks_start()
     for _ in range(max(args.steps, 1)):
         t0 = time.perf_counter()
         sweeps, u = solve()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+    clocks = sample_clocks_stop(cp, cf, local)
+    launches = (s.launches() - l0) // max(args.steps, 1)
     sec = min(times)
     h = 1.0 / (wl.n + 1)
     x = np.arange(1, wl.n + 1) * h
@@ -560,9 +567,31 @@ def run_heat1d(args):
             "steps": len(times), "warmup": max(args.warmup, 1), "ms_per_step": 1000 * sec, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "sweeps_to_1e-9_over_10_steps": sweeps, "sweeps_per_s": sweeps / sec,
-                       "max_error_vs_collocation": err, "timing": "wall clock of the 10-step solve, best of the runs"},
-            "gpu_launches": None}
+                       "max_error_vs_collocation": err, "timing": "wall clock of the 10-step solve, best of the runs",
+                       "l2": "127 points: the whole state stays in L2 and L1 (latency-bound; no flush)"},
+            "gpu_launches": launches, "clocks": clocks}
     s.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the FP64 oracle runs the same 10-step solve (single-level SDC, sweeps to 1e-9)
+        import oracle as O
+        cores = O.set_threads(1)
+        o = O.PFASST(1, wl.n, wl.fine_nodes, 2, 1, wl.nu, wl.dt,
+                     O.MGParams(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles), nlevels=1)
+        ctimes = []
+        for _ in range(3):
+            u, osweeps = wl.u0(), 0
+            t0 = time.perf_counter()
+            for _ in range(wl.steps):
+                o.set_initial(u)
+                it, _ = o.run(wl.iterations, 1e-9)
+                osweeps += it
+                u = o.end_value()
+            ctimes.append(time.perf_counter() - t0)
+        csec = min(ctimes)
+        line["cpu_baseline"] = {"value": wl.n * (wl.fine_nodes - 1) * osweeps / csec, "unit": "DOF-sweeps/s",
+                                "cores": cores, "kind": "oracle",
+                                "sample": f"the whole 10-step solve ({osweeps} sweeps), best of 3, {1000 * csec:.1f} ms",
+                                "nproc": os.cpu_count(), "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -869,8 +898,10 @@ def run_ours(args):
     e2e_ms, e2e_value = job_time_and_value(1000 * (time.perf_counter() - t0) / max(e2e_steps, 1), dof_sweeps, world)
 
     # roofline of the dominant kernel (by summed launch time on the fine grid): HBM for
-    # the stencils / node mixes, the FP64 ALU for kernels bound by the FP64 pipe
+    # the stencils / node mixes, the FP64 ALU for kernels bound by the FP64 pipe, against
+    # the FP64 FMA rate the library's probe kernel measures on this GPU (best of 5)
     peak, peak_kind = measured_peak_gbs()
+    fp64_peak = pmg.pfasst_mg_fp64_peak(5)
 
     def roof_of(d):
         flops = algo_fp64_flops_per_point(d["kernel"], wl.fine_nodes, wl.coarse_nodes)
@@ -879,11 +910,13 @@ def run_ours(args):
         traffic = (tpp * d["points"] / d["launches"]) if tpp is not None else None
         if flops > 0:
             achieved = flops * d["points"] / sec / 1e9
-            return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                    "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+            return {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                    "unit": "GFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                     "kernel": d["kernel"], "grid": d["n"], "launches": d["launches"],
                     "avg_launch_ms": d["ms"] / d["launches"], "algo_fp64_flops_per_point": flops,
-                    "peak_source": "FP64 nominal: 152 SMs x 2.07 GHz x 4 flop/clk"}
+                    "peak_source": "measured: FP64 FMA probe kernel (pfasst_mg_fp64_peak, best of 5 launches "
+                                   "of ~60 ms, every SM)",
+                    "fp64_nominal_gflops": FP64_NOMINAL_GFLOPS}
         ts = 4 if d["precision"] == 1 else 8
         bpp = algo_bytes_per_point(d["kernel"], ts, wl.fine_nodes, wl.coarse_nodes)
         achieved = bpp * d["points"] / sec / 1e9
@@ -975,6 +1008,8 @@ def main():
     ap.add_argument("--iters", type=int, default=0, help="with --quick: PFASST iterations per step (default: workload's)")
     ap.add_argument("--vcycles", type=int, default=-1, help="override V-cycles per sub-step (0 = solve to 1e-12)")
     ap.add_argument("--precision", type=int, default=-1, help="override precision: 0 FP64, 1 mixed")
+    ap.add_argument("--vcycle-tail", type=int, default=-1,
+                    help="heat1d: 1 = run each V-cycle's levels that fit one CTA in one launch, 0 = per level")
     ap.add_argument("--tma", action="store_true",
                     help="pin the TMA-staged sweep on every level that can run it (profiling runs)")
     ap.add_argument("--profile-all", action="store_true",

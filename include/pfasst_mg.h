@@ -107,13 +107,20 @@ typedef struct {
                              run as one kernel launch per V-cycle; 0 (default): one launch
                              per smoothing sweep, restriction and prolongation (1 % faster
                              per PFASST iteration on the 3D workload)                      */
+    int    coarse_vcycles;/* sub-step solves on the coarse PFASST levels (levels >= 1):
+                             -1 (default) = vcycles; 0 = solve to mg_tol with the stall
+                             rule; > 0 = that many V-cycles.  The paper leaves the coarse
+                             level's solver open (Sec. 4.2.1); inexact coarse solves can
+                             limit PFASST's convergence with backward Euler on the coarse
+                             level.  Any 0 (here or in vcycles) runs the iteration without
+                             CUDA graphs (the full solve decides its cycle count on the host) */
 } pmg_options;
 
 typedef struct pmg_ctx *pmg_handle;
 
 /* Defaults: Jacobi omega 2/3, V(2,1), 2 V-cycles, tol 1e-12, stall 0.75, cap 50,
  * FP64, 4th-order interpolation, graphs on, autotuning on, slice groups 0 (one group:
- * no overlap), V-cycle tail off. */
+ * no overlap), V-cycle tail off, coarse levels as the fine level (coarse_vcycles -1). */
 void pfasst_mg_default_options(pmg_options *opt);
 
 /* Bytes of device workspace pfasst_mg_create needs for this problem.
@@ -226,6 +233,14 @@ const char *pfasst_mg_kernel_name(int kernel);
  * overflow edges, exact ties).  *mismatches (host) receives the number of differing
  * results (0 expected).  Synchronises the default stream.  Errors: INVALID_ARG, CUDA. */
 int pfasst_mg_check_narrowing(long long samples, unsigned long long seed, long long *mismatches);
+
+/* Measured FP64 FMA throughput of the current device in GFLOP/s (*gflops, host): a
+ * probe kernel of independent FMA chains on every SM (8 CTAs of 256 threads per SM, 8
+ * chains per thread), warmed up once and then launched `launches` times (1..100) on
+ * `stream`, each timed with CUDA events; the best launch counts (FMA = 2 flops).  The
+ * roofline denominator of the library's FP64-bound kernels; the paper has no
+ * counterpart.  Synchronises the stream.  Errors: INVALID_ARG, CUDA. */
+int pfasst_mg_fp64_peak(void *stream, int launches, double *gflops);
 
 /* Release the handle and any device memory it allocated.  NULL is accepted. */
 int pfasst_mg_destroy(pmg_handle h);

@@ -51,7 +51,7 @@ class _PFASST(ctypes.Structure):
                 ("s_c", ctypes.c_int), ("slices", ctypes.c_int), ("nlevels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("nu", ctypes.c_double),
                 ("dt", ctypes.c_double), ("mg", _MG), ("fam_f", ctypes.c_int), ("fam_c", ctypes.c_int),
-                ("order_f", ctypes.c_int)]
+                ("order_f", ctypes.c_int), ("mg_c", _MG)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -253,8 +253,9 @@ class PFASST:
     """
 
     def __init__(self, dim, n, s_f, s_c, slices, nu, dt, mg: MGParams, nlevels=2, interp_order=4, family=0,
-                 coarse_family=None, order=2):
-        """order: Laplacian order of the fine level (2 or 4); the coarse level is 2nd order."""
+                 coarse_family=None, order=2, mg_coarse: MGParams | None = None):
+        """order: Laplacian order of the fine level (2 or 4); the coarse level is 2nd order.
+        mg_coarse: multigrid settings of the coarse level's sub-step solves (default: mg)."""
         self.dim, self.n, self.s_f, self.s_c = dim, n, s_f, s_c
         self.slices, self.nu, self.dt, self.nlevels = slices, nu, dt, nlevels
         self.mg = mg
@@ -269,7 +270,7 @@ class PFASST:
         if order == 4 and n < 7:
             raise ValueError("the fourth-order stencil needs n >= 7")
         self._c = _PFASST(dim, n, s_f, s_c if nlevels > 1 else 2, slices, nlevels,
-                          interp_order, nu, dt, mg.c(), family, fam_c, order)
+                          interp_order, nu, dt, mg.c(), family, fam_c, order, (mg_coarse or mg).c())
         Nf = n ** dim
         nc = (n - 1) // 2
         Nc = max(nc, 1) ** dim
@@ -321,7 +322,8 @@ class PFASST:
 class _ML(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n0", ctypes.c_int), ("slices", ctypes.c_int), ("nlevels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("s", ctypes.c_int * 3), ("fam", ctypes.c_int * 3),
-                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("mg", _MG), ("order0", ctypes.c_int)]
+                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("mg", _MG), ("order0", ctypes.c_int),
+                ("mg_c", _MG)]
 
 
 class _MLState(ctypes.Structure):
@@ -336,7 +338,8 @@ class MLPFASST:
     With two levels the schedule is the one of :class:`PFASST`.
     """
 
-    def __init__(self, dim, n, nodes, slices, nu, dt, mg: MGParams, families=None, interp_order=4, order=2):
+    def __init__(self, dim, n, nodes, slices, nu, dt, mg: MGParams, families=None, interp_order=4, order=2,
+                 mg_coarse: MGParams | None = None):
         L = len(nodes)
         assert 1 <= L <= 3
         families = list(families) if families is not None else [0] * L
@@ -354,7 +357,7 @@ class MLPFASST:
         self.grids = grids
         s = (ctypes.c_int * 3)(*(list(nodes) + [2] * (3 - L)))
         f = (ctypes.c_int * 3)(*(families + [0] * (3 - L)))
-        self._c = _ML(dim, n, slices, L, interp_order, s, f, nu, dt, mg.c(), order)
+        self._c = _ML(dim, n, slices, L, interp_order, s, f, nu, dt, mg.c(), order, (mg_coarse or mg).c())
         self.U = [np.zeros((slices, nodes[l], grids[l] ** dim)) for l in range(L)]
         self.F = [np.zeros_like(u) for u in self.U]
         self.tau = [np.zeros_like(u) for u in self.U]

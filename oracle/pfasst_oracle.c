@@ -715,6 +715,8 @@ typedef struct {
     orc_mg mg;
     int fam_f, fam_c;  /* node families of the fine and coarse level */
     int order_f;       /* Laplacian order of the fine level (2 or 4; 0 means 2); the coarse level is 2nd order */
+    orc_mg mg_c;       /* multigrid settings of the coarse level's sub-step solves (reading g16:
+                          the same as mg unless chosen otherwise) */
 } orc_pfasst;
 
 static int fine_order(const orc_pfasst *P) { return P->order_f == 4 ? 4 : 2; }
@@ -847,7 +849,7 @@ void orc_pfasst_predict(const orc_pfasst *P, double *Uf, double *Ff,
                 orc_apply_A(P->dim, C.n, P->nu, u0c, Fc + (size_t)p * sc * Nc);
             }
         for (int p = s; p < Pn; ++p)
-            orc_sweep(&C, &P->mg, Uc + (size_t)p * sc * Nc, Fc + (size_t)p * sc * Nc, fas + (size_t)p * sc * Nc);
+            orc_sweep(&C, &P->mg_c, Uc + (size_t)p * sc * Nc, Fc + (size_t)p * sc * Nc, fas + (size_t)p * sc * Nc);
     }
     for (int p = 0; p < Pn; ++p)
         interp_correction(P, Uf + (size_t)p * sf * Nf, Ff + (size_t)p * sf * Nf,
@@ -883,7 +885,7 @@ void orc_pfasst_iteration(const orc_pfasst *P, double *Uf, double *Ff,
                 memcpy(u0c, Uc + ((size_t)(p - 1) * sc + sc - 1) * Nc, sizeof(double) * Nc);
                 orc_apply_A(P->dim, C.n, P->nu, u0c, Fc + (size_t)p * sc * Nc);
             }
-            orc_sweep(&C, &P->mg, Uc + (size_t)p * sc * Nc, Fc + (size_t)p * sc * Nc, fas + (size_t)p * sc * Nc);
+            orc_sweep(&C, &P->mg_c, Uc + (size_t)p * sc * Nc, Fc + (size_t)p * sc * Nc, fas + (size_t)p * sc * Nc);
         }
         for (int p = 0; p < Pn; ++p)
             interp_correction(P, Uf + (size_t)p * sf * Nf, Ff + (size_t)p * sf * Nf,
@@ -909,6 +911,7 @@ typedef struct {
     double nu, dt;
     orc_mg mg;
     int order0;                /* Laplacian order of level 0 (2 or 4; 0 means 2); coarser levels: 2 */
+    orc_mg mg_c;               /* multigrid settings of the sub-step solves on levels >= 1 */
 } orc_ml;
 
 static int ml_order(const orc_ml *P, int l) { return l == 0 && P->order0 == 4 ? 4 : 2; }
@@ -1009,7 +1012,7 @@ void orc_ml_interp_slice(const orc_ml *P, const orc_mlstate *S, int l, int p)
 static void ml_sweep(const orc_ml *P, const orc_mlstate *S, int l, int p)
 {
     orc_level L = ml_level(P, l);
-    orc_sweep(&L, &P->mg, S->U[l] + p * ml_slab(P, l), S->F[l] + p * ml_slab(P, l),
+    orc_sweep(&L, l > 0 ? &P->mg_c : &P->mg, S->U[l] + p * ml_slab(P, l), S->F[l] + p * ml_slab(P, l),
               l > 0 ? S->tau[l] + p * ml_slab(P, l) : NULL);
 }
 

@@ -40,7 +40,7 @@ EXPORTS = [
     "pfasst_mg_net_get_params", "pfasst_mg_net_forward", "pfasst_mg_net_gradients", "pfasst_mg_net_sample",
     "pfasst_mg_net_train", "pfasst_mg_net_launch_count", "pfasst_mg_net_destroy", "pfasst_mg_net_last_error",
     "pfasst_mg_set_smoother_net", "pfasst_mg_net_step", "pfasst_mg_net_profile", "pfasst_mg_net_profile_read",
-    "pfasst_mg_check_narrowing",
+    "pfasst_mg_check_narrowing", "pfasst_mg_fp64_peak",
 ]
 
 NET_PARAMS = 7809  # W1[16][27], b1[16], W2[16][27][16], b2[16], W3[27][16], b3
@@ -64,7 +64,7 @@ class pmg_options(ctypes.Structure):
                 ("mg_stall", ctypes.c_double), ("mg_maxcycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("interp_order", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("slice_groups", ctypes.c_int),
-                ("vcycle_tail", ctypes.c_int)]
+                ("vcycle_tail", ctypes.c_int), ("coarse_vcycles", ctypes.c_int)]
 
 
 class pmg_problem_desc(ctypes.Structure):
@@ -331,6 +331,15 @@ def pfasst_mg_check_narrowing(samples, seed=1):
     bad = ctypes.c_longlong(-1)
     _check(load().pfasst_mg_check_narrowing(samples, seed, ctypes.byref(bad)))
     return bad.value
+
+
+def pfasst_mg_fp64_peak(launches=5, stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device in GFLOP/s (best of `launches`)."""
+    g = ctypes.c_double(0.0)
+    L = load()
+    L.pfasst_mg_fp64_peak.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    _check(L.pfasst_mg_fp64_peak(_stream_ptr(stream), launches, ctypes.byref(g)))
+    return g.value
 
 
 def pfasst_mg_kernel_name(k) -> str:

@@ -212,6 +212,7 @@ struct pmg_ctx {
   int famf = 0, famc = 0;  // node families (0 Gauss-Lobatto, 1 uniform)
   double nu = 0, dt = 0;
   pmg_options opt{};
+  pmg_options opt_c{};     // options of the coarse PFASST levels' sub-step solves (coarse_vcycles)
   cudaStream_t stream = nullptr;
   Grid gf{}, gc{}, gd{};
   long double tauf[kMaxNodes] = {}, tauc[kMaxNodes] = {};
@@ -245,6 +246,7 @@ struct pmg_ctx {
   void *ws = nullptr;
   bool ws_owned = false;
   bool predicted = false;
+  bool spread_state = false;  // every slice holds the spread initial value (nothing has run since)
   bool q_valid = false;  // F-free mode: qf holds the right-hand sides of the current U_f
   long long launches = 0;
   Profiler prof;
@@ -255,7 +257,7 @@ struct pmg_ctx {
     bool with_prof = false;
     long long prof_min = 0;
     std::vector<ProfRec> recs;
-  } g_pred, g_iter;
+  } g_pred, g_pred_spread, g_iter;
   cudaStream_t cap_stream = nullptr;
   // uneven batch: one single-level solver per problem, run as branches of one graph
   std::vector<pmg_ctx *> kids;
@@ -336,7 +338,11 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
     if (o->smoother != PMG_SMOOTHER_JACOBI && o->smoother != PMG_SMOOTHER_RBGS) { why = "bad smoother"; return PMG_ERR_INVALID_ARG; }
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 == 0 || o->nu1 > 16 || o->nu2 > 16) { why = "bad nu1/nu2"; return PMG_ERR_INVALID_ARG; }
     if (o->vcycles < 0 || o->vcycles > 1000) { why = "bad vcycles"; return PMG_ERR_INVALID_ARG; }
-    if (o->vcycles == 0 && (o->mg_maxcycles < 1 || !(o->mg_tol > 0))) { why = "bad full-solve settings"; return PMG_ERR_INVALID_ARG; }
+    if (o->coarse_vcycles < -1 || o->coarse_vcycles > 1000) { why = "bad coarse_vcycles"; return PMG_ERR_INVALID_ARG; }
+    if ((o->vcycles == 0 || o->coarse_vcycles == 0) && (o->mg_maxcycles < 1 || !(o->mg_tol > 0))) {
+      why = "bad full-solve settings";
+      return PMG_ERR_INVALID_ARG;
+    }
     if (o->precision != PMG_PREC_FP64 && o->precision != PMG_PREC_MIXED) { why = "bad precision"; return PMG_ERR_INVALID_ARG; }
     if (o->interp_order != 2 && o->interp_order != 4) { why = "interp_order must be 2 or 4"; return PMG_ERR_INVALID_ARG; }
     if (o->vcycle_tail != 0 && o->vcycle_tail != 1) { why = "vcycle_tail must be 0 or 1"; return PMG_ERR_INVALID_ARG; }
@@ -753,6 +759,7 @@ LevelRef level_ref(pmg_ctx *h, int level) {
 // fine_residual.
 int sweep(pmg_ctx *h, int level, int p0, int B) {
   MGCtx M = mgctx(h);
+  if (level > 0) M.o = &h->opt_c;  // the coarse levels' sub-step solver (coarse_vcycles)
   const LevelRef v = level_ref(h, level);
   const Grid &g = *v.g;
   const long long stride = (long long)v.s * g.slab, sq = (long long)(v.s - 1) * g.slab;
@@ -887,7 +894,7 @@ int run_graph(pmg_ctx *h, pmg_ctx::Captured &G, int (*body)(pmg_ctx *)) {
   return PMG_OK;
 }
 
-bool use_graphs(const pmg_ctx *h) { return h->opt.use_graphs && h->opt.vcycles > 0; }
+bool use_graphs(const pmg_ctx *h) { return h->opt.use_graphs && h->opt.vcycles > 0 && h->opt_c.vcycles > 0; }
 
 // predictor (Sec. 2.4): restrict down to the coarsest level, P stages there (stage s
 // sweeps slices s..P-1 after they received the end values of s-1..P-2), interpolate up
@@ -906,16 +913,50 @@ int predict_body(pmg_ctx *h) {
   return ffree(h) ? fine_residual(h) : PMG_OK;  // right-hand sides of the first fine sweep
 }
 
+// The predictor right after a spread.  Every slice then starts from the same values,
+// and FAS restricts identical fine states to identical coarse states and FAS terms, so
+// before stage s all slices p >= s hold one and the same state A_s: stage s computes
+// one sweep of A_s (with node 0 replaced by its own end value) P - s times over.  Slice
+// p keeps A_{p+1}.  The same numbers come from a serial chain: slice s takes the state
+// of slice s-1 (its final A_s), receives slice s-1's end value at node 0 and sweeps
+// once -- P single-slice sweeps instead of P (P + 1) / 2 slice-sweeps in P stages.
+int predict_body_spread(pmg_ctx *h) {
+  if (h->nlevels >= 2) {
+    const int lc = h->nlevels - 1;
+    PMG_RET(fas_restrict_all(h));
+    if (h->nlevels == 3) PMG_RET(fas_restrict_12(h));
+    const LevelRef v = level_ref(h, lc);
+    const long long st = (long long)v.s * v.g->slab;
+    for (int s = 0; s < h->P; ++s) {
+      if (s > 0) {  // nodes 1..M of slice s-1, then node 0 received from its end
+        PMG_CUDA(h, k_copy(h->L(), *v.g, v.U + (s - 1) * st + v.g->slab, v.g->slab, v.U + s * st + v.g->slab,
+                           v.g->slab, v.s - 1));
+        PMG_CUDA(h, k_copy(h->L(), *v.g, v.F + (s - 1) * st + v.g->slab, v.g->slab, v.F + s * st + v.g->slab,
+                           v.g->slab, v.s - 1));
+        PMG_RET(receive(h, lc, s, 1));
+      }
+      PMG_RET(sweep(h, lc, s, 1));
+    }
+    if (h->nlevels == 3) PMG_RET(interp_21(h));
+    PMG_RET(interp_all(h));
+  }
+  return ffree(h) ? fine_residual(h) : PMG_OK;
+}
+
 int predict(pmg_ctx *h) {
+  const bool fast = h->spread_state;
+  pmg_ctx::Captured &G = fast ? h->g_pred_spread : h->g_pred;
+  int (*body)(pmg_ctx *) = fast ? predict_body_spread : predict_body;
   if (use_graphs(h)) {
-    PMG_RET(run_graph(h, h->g_pred, predict_body));
-    if (!h->g_pred.recs.empty()) {
+    PMG_RET(run_graph(h, G, body));
+    if (!G.recs.empty()) {
       PMG_CUDA(h, cudaStreamSynchronize(h->stream));
-      PMG_RET(harvest(h, h->g_pred));
+      PMG_RET(harvest(h, G));
     }
   } else {
-    PMG_RET(predict_body(h));
+    PMG_RET(body(h));
   }
+  h->spread_state = false;
   h->predicted = true;
   h->q_valid = ffree(h);
   return PMG_OK;
@@ -1060,6 +1101,7 @@ int spread(pmg_ctx *h) {
   PMG_CUDA(h, k_copy(h->L(), h->gf, h->u0, 0, h->Uf, h->gf.slab, h->P * h->sf));
   h->predicted = false;
   h->q_valid = false;
+  h->spread_state = true;
   return PMG_OK;
 }
 
@@ -1067,10 +1109,11 @@ void fill_coefficients(pmg_ctx *h) {
   long double Qf[kMaxNodes][kMaxNodes], Qc[kMaxNodes][kMaxNodes];
   node_positions(h->sf, h->famf, h->tauf);
   integration_matrix(h->sf, h->tauf, Qf, h->famf);
-  auto fill_sf = [&](SFCoef &cf, int s, const long double *t, long double Q[kMaxNodes][kMaxNodes], double *csub) {
+  auto fill_sf = [&](SFCoef &cf, int s, const long double *t, long double Q[kMaxNodes][kMaxNodes], double *csub,
+                     int vcycles) {
     std::memset(&cf, 0, sizeof cf);
     cf.s = s;
-    cf.sub_next = h->opt.vcycles > 0;  // fixed V-cycle counts start from the pointwise residual
+    cf.sub_next = vcycles > 0;  // fixed V-cycle counts start from the pointwise residual
     for (int m = 0; m < s - 1; ++m) {
       const long double dtm = (long double)h->dt * (t[m + 1] - t[m]);
       csub[m] = (double)(dtm * h->nu);
@@ -1081,7 +1124,7 @@ void fill_coefficients(pmg_ctx *h) {
       }
     }
   };
-  fill_sf(h->sff, h->sf, h->tauf, Qf, h->cf_sub);
+  fill_sf(h->sff, h->sf, h->tauf, Qf, h->cf_sub, h->opt.vcycles);
   std::memset(&h->resf, 0, sizeof h->resf);
   h->resf.s = h->sf;
   for (int m = 0; m < h->sf; ++m)
@@ -1116,7 +1159,7 @@ void fill_coefficients(pmg_ctx *h) {
   if (h->nlevels >= 2) {
     node_positions(h->sc, h->famc, h->tauc);
     integration_matrix(h->sc, h->tauc, Qc, h->famc);
-    fill_sf(h->sfc, h->sc, h->tauc, Qc, h->cc_sub);
+    fill_sf(h->sfc, h->sc, h->tauc, Qc, h->cc_sub, h->opt_c.vcycles);
     fill_fas(h->fas, h->sf, h->tauf, Qf, h->sc, h->tauc, Qc);
     fill_interp(h->interp, h->sf, h->tauf, h->sc, h->tauc);
   }
@@ -1124,7 +1167,7 @@ void fill_coefficients(pmg_ctx *h) {
     long double Q2[kMaxNodes][kMaxNodes];
     node_positions(h->s2, h->fam2, h->tau2n);
     integration_matrix(h->s2, h->tau2n, Q2, h->fam2);
-    fill_sf(h->sf2c, h->s2, h->tau2n, Q2, h->c2_sub);
+    fill_sf(h->sf2c, h->s2, h->tau2n, Q2, h->c2_sub, h->opt_c.vcycles);
     fill_fas(h->fas2, h->sc, h->tauc, Qc, h->s2, h->tau2n, Q2);
     fill_interp(h->interp2, h->sc, h->tauc, h->s2, h->tau2n);
   }
@@ -1154,6 +1197,8 @@ pmg_ctx *make_ctx(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_leve
   pmg_ctx *h = new (std::nothrow) pmg_ctx();
   if (!h) return nullptr;
   if (opt) h->opt = *opt; else pfasst_mg_default_options(&h->opt);
+  h->opt_c = h->opt;
+  if (h->opt.coarse_vcycles >= 0) h->opt_c.vcycles = h->opt.coarse_vcycles;
   h->dim = grid->dim;
   h->nf = grid->n;
   h->nc = (grid->n - 1) / 2;
@@ -1179,7 +1224,7 @@ pmg_ctx *make_ctx(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_leve
   // already fills the GPU), and overlapping kernels blur per-kernel timings.
   if (G == 0) G = 1;
   if (G > slices) G = slices;
-  h->groups = (h->nlevels == 2 && h->opt.vcycles > 0 && G > 1) ? G : 1;
+  h->groups = (h->nlevels == 2 && h->opt.vcycles > 0 && h->opt_c.vcycles > 0 && G > 1) ? G : 1;
   return h;
 }
 
@@ -1205,6 +1250,7 @@ void pfasst_mg_default_options(pmg_options *o) {
   o->autotune = 1;
   o->slice_groups = 0;
   o->vcycle_tail = 0;
+  o->coarse_vcycles = -1;
 }
 
 int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,
@@ -1332,6 +1378,7 @@ int pfasst_mg_predict(pmg_handle h) {
 int pfasst_mg_sweep(pmg_handle h, int level) {
   if (h && !h->kids.empty()) return fail(h, PMG_ERR_INVALID_ARG, "batch handle: use the pfasst_mg_batch_* calls");
   if (!h) return fail(h, PMG_ERR_INVALID_ARG, "null handle");
+  h->spread_state = false;
   if (level == 0) {
     if (ffree(h) && !h->q_valid) PMG_RET(fine_residual(h));
     h->q_valid = false;
@@ -1451,6 +1498,7 @@ int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int par
   }
   PMG_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graph(h->g_pred);
+  drop_graph(h->g_pred_spread);
   drop_graph(h->g_iter);
   h->H.tune[level][narrow ? 1 : 0] = t;
   if (h->groups > 1 && narrow) h->Hc.tune[level][0] = h->Hc.tune[level][1] = t;
@@ -1522,6 +1570,7 @@ int pfasst_mg_destroy(pmg_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
   for (pmg_ctx *k : h->kids) {
     drop_graph(k->g_pred);
+    drop_graph(k->g_pred_spread);
     drop_graph(k->g_iter);
     if (k->hred) cudaFreeHost(k->hred);
     if (k->hactive) cudaFreeHost(k->hactive);
@@ -1532,6 +1581,7 @@ int pfasst_mg_destroy(pmg_handle h) {
   if (h->fork) cudaEventDestroy(h->fork);
   if (h->bexec) cudaGraphExecDestroy(h->bexec);
   drop_graph(h->g_pred);
+  drop_graph(h->g_pred_spread);
   drop_graph(h->g_iter);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->s_chain) cudaStreamDestroy(h->s_chain);
@@ -2210,6 +2260,7 @@ int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int
   if (is_batch(h)) return fail(h, PMG_ERR_UNSUPPORTED, "the learned correction is not available on batch handles");
   PMG_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graph(h->g_pred);
+  drop_graph(h->g_pred_spread);
   drop_graph(h->g_iter);
   if (h->net) {
     if (h->net->mem) cudaFree(h->net->mem);

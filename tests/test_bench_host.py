@@ -26,7 +26,7 @@ def test_traffic_lookup_ignores_unknown_kernels():
 
 
 def test_fp64_peak_is_the_unit_count_times_the_clock():
-    assert abs(bench.FP64_PEAK_GFLOPS - 152 * 2.07 * 4) < 1e-9
+    assert abs(bench.FP64_NOMINAL_GFLOPS - 152 * 2.07 * 4) < 1e-9
 
 
 def test_algorithmic_bytes_of_the_fine_kernels():

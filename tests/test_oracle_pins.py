@@ -465,17 +465,20 @@ def test_fas_coarse_sweep_keeps_converged_fine_solution(dim, n):
     assert res[0] < 1e-12
 
 
-@pytest.mark.parametrize("vcycles", [0, 2])
-def test_pfasst_limit_is_serial_collocation(vcycles):
+@pytest.mark.parametrize("vcycles,coarse", [(0, None), (2, None), (2, 0), (1, 5), (0, 1)])
+def test_pfasst_limit_is_serial_collocation(vcycles, coarse):
     """Many PFASST iterations converge to the serial fine collocation solution over all
-    slices: on an eigenmode the end of slice p is R(z)^(p+1) times the mode."""
+    slices: on an eigenmode the end of slice p is R(z)^(p+1) times the mode -- whatever
+    multigrid settings the coarse level's sub-step solves use (coarse: its own V-cycle
+    count, 0 = solved to the tolerance; None = the fine level's settings)."""
     dim, n, P, s_f, nu, dt = 1, 31, 4, 5, 1.0, 0.01
     mode = _sine_mode(dim, n, (2,))
     z = nu * _d(2, n) * dt
     mg = FULL if vcycles == 0 else O.MGParams(vcycles=vcycles, smoother=1, omega=1.0)
-    pf = O.PFASST(dim, n, s_f, 3, P, nu, dt, mg)
+    mgc = None if coarse is None else (FULL if coarse == 0 else O.MGParams(vcycles=coarse, smoother=1, omega=1.0))
+    pf = O.PFASST(dim, n, s_f, 3, P, nu, dt, mg, mg_coarse=mgc)
     pf.set_initial(mode)
-    it, hist = pf.run(60, 1e-14)
+    it, hist = pf.run(200, 1e-14)
     assert hist[-1].max() < 1e-13
     for p in range(P):
         np.testing.assert_allclose(pf.Uf[p, -1], _pade(z, s_f) ** (p + 1) * mode, atol=1e-12)
