@@ -206,6 +206,15 @@ struct NetDeploy {
   bool on[kMaxLevels] = {};
 };
 
+// the device-side PFASST iteration loop: the host writes max_iter and tol, the check
+// kernel at the end of every iteration counts k and keeps the residual (max over slices)
+struct LoopCtl {
+  int max_iter;
+  int k;
+  double tol;
+  unsigned long long res_bits;
+};
+
 struct pmg_ctx {
   int dim = 0, nf = 0, nc = 0, sf = 0, sc = 0, P = 0, nlevels = 1;
   int order = 2;           // Laplacian stencil of the fine level (coarser levels: 2)
@@ -242,6 +251,9 @@ struct pmg_ctx {
   unsigned long long *red = nullptr;  // [3P]: rnorm, bnorm, colloc residual
   int *active = nullptr;
   unsigned long long *hred = nullptr;  // pinned
+  LoopCtl *ctl = nullptr;               // device-side iteration loop: limits and results
+  LoopCtl *hctl = nullptr;              // pinned
+  bool in_loop = false;                 // capturing the body of the device-side loop
   int *hactive = nullptr;              // pinned
   void *ws = nullptr;
   bool ws_owned = false;
@@ -257,7 +269,7 @@ struct pmg_ctx {
     bool with_prof = false;
     long long prof_min = 0;
     std::vector<ProfRec> recs;
-  } g_pred, g_pred_spread, g_iter;
+  } g_pred, g_pred_spread, g_iter, g_loop;
   cudaStream_t cap_stream = nullptr;
   // uneven batch: one single-level solver per problem, run as branches of one graph
   std::vector<pmg_ctx *> kids;
@@ -441,6 +453,7 @@ void plan_ctx(Plan &pl, pmg_ctx *h) {
   pl.add(&h->minv, (size_t)slots * h->n3 * h->n3 * h->H.tsize);
   pl.add((void **)&h->red, sizeof(unsigned long long) * 3 * h->P);
   pl.add((void **)&h->active, sizeof(int) * h->P);
+  pl.add((void **)&h->ctl, sizeof(LoopCtl));
 }
 
 // ----------------------------------------------------------------- multigrid schedule
@@ -732,8 +745,9 @@ int fine_residual(pmg_ctx *h, bool chained = false) {
                                     h->P, h->red + 2 * h->P, chained));
   else
     PMG_CUDA(h, k_colloc_residual(h->L(), h->gf, h->resf, h->Uf, h->Ff, sfs, h->P, h->red + 2 * h->P));
-  PMG_CUDA(h, cudaMemcpyAsync(h->hred + 2 * h->P, h->red + 2 * h->P, sizeof(unsigned long long) * h->P,
-                              cudaMemcpyDeviceToHost, h->stream));
+  if (!h->in_loop)  // the device-side loop keeps the residual on the device (loop_check_kernel)
+    PMG_CUDA(h, cudaMemcpyAsync(h->hred + 2 * h->P, h->red + 2 * h->P, sizeof(unsigned long long) * h->P,
+                                cudaMemcpyDeviceToHost, h->stream));
   return PMG_OK;
 }
 
@@ -1086,6 +1100,103 @@ int iteration(pmg_ctx *h) {
   return fine_residual(h, true);
 }
 
+// End of one iteration of the device-side loop (one warp): the collocation residual of
+// the iteration (max over slices of the per-slice maxima, as bit patterns of
+// non-negative doubles, so Inf and NaN compare largest), the iteration count, and
+// whether the loop goes on: fewer than max_iter iterations, residual above tol and
+// finite.
+__global__ void loop_check_kernel(const unsigned long long *__restrict__ res, int P, LoopCtl *ctl,
+                                  cudaGraphConditionalHandle cond) {
+  unsigned long long mx = 0ULL;
+  for (int p = threadIdx.x; p < P; p += 32) mx = res[p] > mx ? res[p] : mx;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = w > mx ? w : mx;
+  }
+  if (threadIdx.x == 0) {
+    const int k = ctl->k + 1;
+    ctl->k = k;
+    ctl->res_bits = mx;
+    const bool finite = mx < 0x7ff0000000000000ULL;
+    const bool go = k < ctl->max_iter && finite && !(__longlong_as_double((long long)mx) <= ctl->tol);
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+  }
+}
+
+// The PFASST iteration loop as one CUDA graph: a conditional while-node whose body is
+// one iteration (captured once) followed by loop_check_kernel, which decides on the
+// device whether the body runs again.  One graph launch runs the whole loop with no
+// host round trip between iterations.  Conditional bodies hold no event nodes, so this
+// serves the single-stream schedule without the launch profiler.
+bool device_loop_ok(const pmg_ctx *h) { return use_graphs(h) && h->groups == 1 && !h->prof.on; }
+
+int build_loop_graph(pmg_ctx *h) {
+  if (!h->cap_stream) PMG_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  PMG_CUDA(h, cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};  // remaining members zero
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(h, PMG_ERR_CUDA, std::string("conditional graph node: ") + cudaGetErrorString(e));
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t user = h->stream;
+  const long long before = h->launches;
+  h->stream = h->cap_stream;
+  h->in_loop = true;
+  e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? iteration(h) : PMG_ERR_CUDA;
+  if (rc == PMG_OK) {
+    loop_check_kernel<<<1, 32, 0, h->cap_stream>>>(h->red + 2 * h->P, h->P, h->ctl, cond);
+    if (cudaGetLastError() != cudaSuccess) rc = fail(h, PMG_ERR_CUDA, "loop check launch failed");
+    ++h->launches;
+  }
+  cudaGraph_t body_out = nullptr;
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &body_out) : e;
+  h->stream = user;
+  h->in_loop = false;
+  h->g_loop.kernels = h->launches - before;
+  h->launches = before;
+  if (rc == PMG_OK && e2 != cudaSuccess)
+    rc = fail(h, PMG_ERR_CUDA, std::string("loop body capture: ") + cudaGetErrorString(e2));
+  if (rc == PMG_OK) {
+    e = cudaGraphInstantiate(&h->g_loop.exec, graph, 0);
+    if (e != cudaSuccess) {
+      h->g_loop.exec = nullptr;
+      rc = fail(h, PMG_ERR_CUDA, std::string("cudaGraphInstantiate (loop): ") + cudaGetErrorString(e));
+    }
+  }
+  cudaGraphDestroy(graph);
+  return rc;
+}
+
+// run up to max_iter iterations (>= 1) on the device; *k and *res receive the
+// iterations done and the last residual
+int run_device_loop(pmg_ctx *h, int max_iter, double tol, int *k, double *res) {
+  if (!h->g_loop.exec) PMG_RET(build_loop_graph(h));
+  h->hctl->max_iter = max_iter;
+  h->hctl->k = 0;
+  h->hctl->tol = tol;
+  h->hctl->res_bits = 0ULL;
+  PMG_CUDA(h, cudaMemcpyAsync(h->ctl, h->hctl, sizeof(LoopCtl), cudaMemcpyHostToDevice, h->stream));
+  PMG_CUDA(h, cudaGraphLaunch(h->g_loop.exec, h->stream));
+  PMG_CUDA(h, cudaMemcpyAsync(h->hctl, h->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, h->stream));
+  PMG_CUDA(h, cudaStreamSynchronize(h->stream));
+  *k = h->hctl->k;
+  std::memcpy(res, &h->hctl->res_bits, 8);
+  h->launches += h->g_loop.kernels * (long long)*k;
+  return PMG_OK;
+}
+
 double bits_to_double(unsigned long long v) {
   double d;
   std::memcpy(&d, &v, 8);
@@ -1315,11 +1426,13 @@ int pfasst_mg_create(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_l
     if (h->ws_owned) cudaFree(h->ws);
     if (h->hred) cudaFreeHost(h->hred);
     if (h->hactive) cudaFreeHost(h->hactive);
+    if (h->hctl) cudaFreeHost(h->hctl);
     delete h;
     return fail(nullptr, code, m);
   };
   if (cudaMallocHost(&h->hred, sizeof(unsigned long long) * 3 * h->P) != cudaSuccess ||
-      cudaMallocHost(&h->hactive, sizeof(int) * h->P) != cudaSuccess)
+      cudaMallocHost(&h->hactive, sizeof(int) * h->P) != cudaSuccess ||
+      cudaMallocHost(&h->hctl, sizeof(LoopCtl)) != cudaSuccess)
     return bail(PMG_ERR_OOM, "pinned host allocation failed");
   // zero everything: the pad columns of every grid function must stay zero
   cudaError_t e = cudaMemsetAsync(h->ws, 0, pl.total, h->stream);
@@ -1399,6 +1512,17 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
   if (iters_done) *iters_done = 0;
   if (!h->predicted) PMG_RET(predict(h));
   double res = INFINITY;
+  if (max_iter > 0 && device_loop_ok(h)) {
+    if (ffree(h) && !h->q_valid) PMG_RET(fine_residual(h));  // after a standalone sweep
+    int k = 0;
+    PMG_RET(run_device_loop(h, max_iter, tol, &k, &res));
+    h->q_valid = ffree(h);
+    if (sweep_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a TMA-staged sweep timed out waiting for its loads");
+    if (iters_done) *iters_done = k;
+    if (final_res) *final_res = res;
+    if (std::isnan(res) || std::isinf(res)) return fail(h, PMG_ERR_DIVERGED, "collocation residual is NaN/Inf");
+    return res <= tol ? PMG_OK : PMG_NOT_CONVERGED;
+  }
   for (int k = 0; k < max_iter; ++k) {
     if (ffree(h) && !h->q_valid) PMG_RET(fine_residual(h));  // after a standalone sweep
     if (use_graphs(h)) PMG_RET(run_graph(h, h->g_iter, iteration));
@@ -1500,6 +1624,7 @@ int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int par
   drop_graph(h->g_pred);
   drop_graph(h->g_pred_spread);
   drop_graph(h->g_iter);
+  drop_graph(h->g_loop);
   h->H.tune[level][narrow ? 1 : 0] = t;
   if (h->groups > 1 && narrow) h->Hc.tune[level][0] = h->Hc.tune[level][1] = t;
   return PMG_OK;
@@ -1572,6 +1697,7 @@ int pfasst_mg_destroy(pmg_handle h) {
     drop_graph(k->g_pred);
     drop_graph(k->g_pred_spread);
     drop_graph(k->g_iter);
+    drop_graph(k->g_loop);
     if (k->hred) cudaFreeHost(k->hred);
     if (k->hactive) cudaFreeHost(k->hactive);
     delete k;
@@ -1583,6 +1709,7 @@ int pfasst_mg_destroy(pmg_handle h) {
   drop_graph(h->g_pred);
   drop_graph(h->g_pred_spread);
   drop_graph(h->g_iter);
+  drop_graph(h->g_loop);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->s_chain) cudaStreamDestroy(h->s_chain);
   if (h->s_post) cudaStreamDestroy(h->s_post);
@@ -1599,6 +1726,7 @@ int pfasst_mg_destroy(pmg_handle h) {
   if (h->ws_owned && h->ws) cudaFree(h->ws);
   if (h->hred) cudaFreeHost(h->hred);
   if (h->hactive) cudaFreeHost(h->hactive);
+  if (h->hctl) cudaFreeHost(h->hctl);
   delete h;
   return PMG_OK;
 }
@@ -2262,6 +2390,7 @@ int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int
   drop_graph(h->g_pred);
   drop_graph(h->g_pred_spread);
   drop_graph(h->g_iter);
+  drop_graph(h->g_loop);
   if (h->net) {
     if (h->net->mem) cudaFree(h->net->mem);
     delete h->net;

@@ -694,3 +694,29 @@ def test_coarse_level_vcycle_count_matches_oracle(nl, cvc, sm, fam):
             assert worst_rel_floor(s.state(l), o.U[l], op.U[l], FP64_TOL, f"iteration {k} level {l}") < 1
         np.testing.assert_allclose(s.residual(), ores, rtol=1e-7, atol=1e-13)
     s.close()
+
+
+@pytest.mark.parametrize("dim,n,P,nl,precision", [(2, 31, 4, 2, 0), (3, 15, 3, 3, 1), (1, 127, 1, 1, 0)])
+def test_device_side_iteration_loop_matches_host_loop(dim, n, P, nl, precision):
+    """With graphs on, pfasst_mg_iterate runs the whole loop as one graph launch (a
+    conditional while-node; the check of residual and iteration count is a kernel).
+    Against the host-driven loop (graphs off): the same iteration count, residual and
+    bitwise state, when stopping on the tolerance and when the iteration cap is reached."""
+    u0 = _u0(dim, n)
+    out = []
+    for graphs in (1, 0):
+        s = pmg.PFASSTSolver(dim, n, 5, 3 if nl >= 2 else 0, P, 1.0, 0.01, nlevels=nl,
+                             coarsest_nodes=2 if nl == 3 else 0, smoother=1, omega=1.0, vcycles=2,
+                             precision=precision, use_graphs=graphs)
+        s.set_initial(u0)
+        rc1, it1, res1 = s.iterate(200, 1e-8)
+        st1 = s.state(0)
+        s.set_initial(u0)
+        rc2, it2, res2 = s.iterate(3, 0.0)
+        out.append((rc1, it1, res1, st1, rc2, it2, res2, s.state(0)))
+        s.close()
+    g, h = out
+    assert g[0] == h[0] == pmg.PMG_OK and g[1] == h[1] and g[2] == h[2] and g[2] <= 1e-8
+    assert np.array_equal(g[3], h[3])
+    assert g[4] == h[4] == pmg.PMG_NOT_CONVERGED and g[5] == h[5] == 3 and g[6] == h[6]
+    assert np.array_equal(g[7], h[7])
