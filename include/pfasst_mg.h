@@ -234,6 +234,13 @@ const char *pfasst_mg_kernel_name(int kernel);
  * results (0 expected).  Synchronises the default stream.  Errors: INVALID_ARG, CUDA. */
 int pfasst_mg_check_narrowing(long long samples, unsigned long long seed, long long *mismatches);
 
+/* Self-check of the library's integer-pipe FP32 -> FP64 widening (used where an FP32
+ * multigrid correction is added to an FP64 iterate) against the hardware conversion on
+ * every one of the 2^32 float bit patterns (NaN inputs: both results must be NaN).
+ * *mismatches (host) receives the number of differing results (0 expected).
+ * Synchronises the default stream.  Errors: INVALID_ARG, CUDA. */
+int pfasst_mg_check_widening(long long *mismatches);
+
 /* Measured FP64 FMA throughput of the current device in GFLOP/s (*gflops, host): a
  * probe kernel of independent FMA chains on every SM (8 CTAs of 256 threads per SM, 8
  * chains per thread), warmed up once and then launched `launches` times (1..100) on

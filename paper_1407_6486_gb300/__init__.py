@@ -40,7 +40,7 @@ EXPORTS = [
     "pfasst_mg_net_get_params", "pfasst_mg_net_forward", "pfasst_mg_net_gradients", "pfasst_mg_net_sample",
     "pfasst_mg_net_train", "pfasst_mg_net_launch_count", "pfasst_mg_net_destroy", "pfasst_mg_net_last_error",
     "pfasst_mg_set_smoother_net", "pfasst_mg_net_step", "pfasst_mg_net_profile", "pfasst_mg_net_profile_read",
-    "pfasst_mg_check_narrowing", "pfasst_mg_fp64_peak",
+    "pfasst_mg_check_narrowing", "pfasst_mg_fp64_peak", "pfasst_mg_check_widening",
 ]
 
 NET_PARAMS = 7809  # W1[16][27], b1[16], W2[16][27][16], b2[16], W3[27][16], b3
@@ -330,6 +330,14 @@ def pfasst_mg_check_narrowing(samples, seed=1):
     conversion on `samples` generated inputs (0 expected)."""
     bad = ctypes.c_longlong(-1)
     _check(load().pfasst_mg_check_narrowing(samples, seed, ctypes.byref(bad)))
+    return bad.value
+
+
+def pfasst_mg_check_widening():
+    """Mismatches of the library's FP32 -> FP64 integer widening against the hardware
+    conversion over all 2^32 float bit patterns (0 expected)."""
+    bad = ctypes.c_longlong(-1)
+    _check(load().pfasst_mg_check_widening(ctypes.byref(bad)))
     return bad.value
 
 

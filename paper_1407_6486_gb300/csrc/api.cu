@@ -1749,6 +1749,22 @@ int pfasst_mg_check_narrowing(long long samples, unsigned long long seed, long l
   return PMG_OK;
 }
 
+int pfasst_mg_check_widening(long long *mismatches) {
+  if (!mismatches) return fail(nullptr, PMG_ERR_INVALID_ARG, "bad argument");
+  unsigned long long *bad = nullptr, hbad = 0;
+  if (cudaMalloc(&bad, sizeof bad[0]) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, PMG_ERR_CUDA, "cudaMalloc failed");
+  }
+  cudaError_t e = cudaMemset(bad, 0, sizeof bad[0]);
+  if (e == cudaSuccess) e = k_widen_check(nullptr, bad);
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (e != cudaSuccess) return fail(nullptr, PMG_ERR_CUDA, std::string("widening check: ") + cudaGetErrorString(e));
+  *mismatches = (long long)hbad;
+  return PMG_OK;
+}
+
 int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const double *b, double *u,
                               const pmg_options *opt, void *stream, int *cycles_done) {
   pmg_nodes_desc fn{3, 0};

@@ -298,7 +298,8 @@ __global__ void update_u_kernel(Grid g, double *__restrict__ u, long long su, co
   PMG_FOR_POINTS(g, batch) {
     PMG_POINT(g);
     if (active && !active[b]) continue;
-    u[b * su + off] += (double)e[b * g.slab + off];
+    if constexpr (sizeof(T) == 4) u[b * su + off] += widen_exact(e[b * g.slab + off]);
+    else u[b * su + off] += e[b * g.slab + off];
   }
 }
 
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(256) interp_space_kernel(Grid gf, Grid gc, int
       } else {
         v = Src[y * ITX + x];
       }
-      dst[((long long)(DIM >= 3 ? k : 0) * gf.ny + (DIM >= 2 ? j : 0)) * gf.pitch + i] += (double)v;
+      dst[((long long)(DIM >= 3 ? k : 0) * gf.ny + (DIM >= 2 ? j : 0)) * gf.pitch + i] += to_f64(v);
     }
     __syncthreads();
   }
@@ -580,7 +581,11 @@ __global__ void __launch_bounds__(256) interp_space3d_kernel(Grid gf, Grid gc, i
 #pragma unroll
       for (int z = 0; z < ITZ; ++z) {  // z pass and the FP64 update
         const int k = z0 + z;
-        if (k < gf.n) dst[k * plane] = uold[z] + (double)taps(z, Y + ty * ITX + tx, ITY * ITX);
+        if (k < gf.n) {
+          const T dv = taps(z, Y + ty * ITX + tx, ITY * ITX);
+          if constexpr (sizeof(T) == 4) dst[k * plane] = uold[z] + widen_exact(dv);
+          else dst[k * plane] = uold[z] + dv;
+        }
       }
     }
     __syncthreads();
@@ -614,6 +619,18 @@ __global__ void narrow_check_kernel(long long count, unsigned long long seed, un
     const double v = __longlong_as_double((long long)bits);
     const float hw = __double2float_rn(v), sw = narrow_rn(v);
     if (v != v ? !(sw != sw) : __float_as_uint(hw) != __float_as_uint(sw)) ++nbad;
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+// every float bit pattern once: widen_exact against the hardware conversion
+__global__ void widen_check_kernel(unsigned long long *bad) {
+  unsigned long long nbad = 0;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < (1ULL << 32);
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const float f = __uint_as_float((unsigned)i);
+    const double hw = (double)f, sw = widen_exact(f);
+    if (f != f ? !(sw != sw) : __double_as_longlong(hw) != __double_as_longlong(sw)) ++nbad;
   }
   if (nbad) atomicAdd(bad, nbad);
 }
@@ -1182,6 +1199,11 @@ cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, co
   PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D, 0, 0><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Fc, tau,
                                                                                     Uc0, scoarse, batch)))
   return sc.done();
+}
+
+cudaError_t k_widen_check(cudaStream_t st, unsigned long long *bad) {
+  widen_check_kernel<<<152 * 16, 256, 0, st>>>(bad);
+  return cudaGetLastError();
 }
 
 cudaError_t k_narrow_check(cudaStream_t st, long long count, unsigned long long seed, unsigned long long *bad) {

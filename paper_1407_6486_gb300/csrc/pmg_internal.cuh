@@ -73,6 +73,36 @@ __device__ __forceinline__ float narrow_rn(double v) {
   return __uint_as_float(sign | r);
 }
 
+// binary32 -> binary64 on the integer pipe: the widening is exact, so its result is
+// fixed by the encodings alone (sign kept; exponent rebiased by 1023 - 127 = 896;
+// significand shifted left by 52 - 23 = 29; a subnormal input is normalised by its
+// leading one; Inf stays Inf, NaN stays NaN with the quiet bit set).  GB300 runs the
+// hardware conversion on its narrow FP64 pipe, next to the FP64 add it feeds.
+__device__ __forceinline__ double widen_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  unsigned long long r;
+  if (e - 1u < 254u) {  // normal
+    r = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (e == 0xffu) {
+    r = sign | 0x7ff0000000000000ULL | (m ? (0x0008000000000000ULL | ((unsigned long long)m << 29)) : 0ULL);
+  } else if (m == 0u) {
+    r = sign;
+  } else {  // subnormal m 2^-149 = 2^(p-149) (1 + fraction), p = position of the leading one
+    const int p = 31 - __clz((int)m);
+    r = sign | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffULL);
+  }
+  return __longlong_as_double((long long)r);
+}
+
+// a multigrid value of storage type T as FP64 (FP32 through widen_exact)
+template <typename T>
+__device__ __forceinline__ double to_f64(T v) {
+  if constexpr (sizeof(T) == 4) return widen_exact(v);
+  else return v;
+}
+
 template <typename T>
 __device__ __forceinline__ T to_storage(double v) {
   if constexpr (sizeof(T) == 4) return narrow_rn(v);
@@ -290,6 +320,9 @@ cudaError_t k_colloc_residual(const Launch &L, const Grid &g, const ResCoef &cf,
 // compares narrow_rn with the hardware FP64 -> FP32 conversion on `count` generated
 // inputs; adds the number of differing results to *bad (device memory)
 cudaError_t k_narrow_check(cudaStream_t st, long long count, unsigned long long seed, unsigned long long *bad);
+// compares widen_exact with the hardware FP32 -> FP64 conversion on every one of the 2^32
+// float bit patterns (NaN inputs: both results must be NaN); adds the mismatches to *bad
+cudaError_t k_widen_check(cudaStream_t st, unsigned long long *bad);
 cudaError_t k_copy(const Launch &L, const Grid &g, const double *src, long long ss, double *dst, long long sd,
                    int batch);
 cudaError_t k_pack(const Launch &L, const Grid &g, const double *dense, long long sdense, double *pad, long long spad,

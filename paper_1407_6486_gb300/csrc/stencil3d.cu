@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(256, 4) rbgs_sweep3d_kernel(Grid g, T a, T D, 
         if (UPD) {
           double2 *up = (double2 *)(u + b * su + o);
           double2 w = *up;
-          w.x += (double)v[0];
-          w.y += (double)v[1];
+          w.x += to_f64(v[0]);
+          w.y += to_f64(v[1]);
           *up = w;
         } else {
           T2 w;
@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(NT, 512 / NT * 2 > 4 ? 4 : 512 / NT * 2) rbgs_
         if (UPD) {
           double2 *up2 = (double2 *)(u + b * su + o);
           double2 w = *up2;
-          w.x += (double)out.x;
-          w.y += (double)out.y;
+          w.x += to_f64(out.x);
+          w.y += to_f64(out.y);
           *up2 = w;
         } else {
           *(T2 *)(eout + b * g.slab + o) = out;

@@ -10,6 +10,11 @@
 // mbarrier per slot.  The tensor-map box covers whole rows (x = 0, 16-byte aligned); rows and
 // planes outside the grid arrive as zeros (the Dirichlet wall).  The threads only
 // compute, which keeps their register count low and the loads deep.
+// The red half-sweep writes its results into the e slot of its plane, in place: a red
+// point reads only black neighbours (and its own value), so the red updates of one plane
+// do not interfere, and the black half-sweep then finds the red values of planes k-2,
+// k-1, k and the old black values in the same slots.  Without a separate red buffer the
+// ring holds two planes in flight at two CTAs per SM.
 //
 // Every wait on an mbarrier is bounded (about 2 s of SM clock); on a timeout the
 // kernel records the fact in a device flag, stops at the end of the current plane,
@@ -30,11 +35,10 @@ namespace {
 constexpr int TTY = 8;             // output rows per tile
 constexpr int TEY = TTY + 4;       // e_in rows staged per plane (y0-2 .. y0+TTY+1)
 constexpr int TMY = TTY + 2;       // red / f rows (y0-1 .. y0+TTY)
-constexpr int DEPTH = 1;           // planes in flight ahead of the computation
-constexpr int NE = 3 + DEPTH;      // e_in slots: planes k-1, k, k+1 in use, DEPTH more in flight
+constexpr int DEPTH = 2;           // planes in flight ahead of the computation
+constexpr int NE = 4 + DEPTH;      // e_in slots: planes k-2 .. k+1 in use, DEPTH more in flight
 constexpr int NF = 2 + DEPTH;      // f slots: planes k-1, k in use, DEPTH more in flight
-constexpr int TNT = 512;           // threads per CTA (two CTAs per SM: ~108 KB of ring each;
-                                   // measured faster than 16-row tiles with 1024 threads)
+constexpr int TNT = 512;           // threads per CTA (two CTAs per SM: ~112 KB of ring each)
 constexpr int TZC = 32;            // default z planes per CTA
 
 __device__ int g_sweep_timeout;    // set by a timed-out mbarrier wait
@@ -92,8 +96,7 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
   extern __shared__ __align__(1024) unsigned char sm[];
   float2(*E)[TEY][NP] = (float2(*)[TEY][NP])sm;                                   // [NE]
   float2(*Fs)[TMY][NP] = (float2(*)[TMY][NP])(sm + NE * EB);                       // [NF]
-  float2(*M)[TMY][NP] = (float2(*)[TMY][NP])(sm + NE * EB + NF * FB);              // [3]
-  uint64_t *bar = (uint64_t *)(sm + NE * EB + NF * FB + 3 * FB);                   // [NE + NF]
+  uint64_t *bar = (uint64_t *)(sm + NE * EB + NF * FB);                            // [NE + NF]
   __shared__ int s_bad;
   const int n = g.n, tid = threadIdx.x, px = tid % NP, ry = tid / NP, lane = tid & 31;
   const int y0 = blockIdx.y * TTY;
@@ -103,8 +106,8 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
   const unsigned full = 0xffffffffu;
   // ring positions: e plane p in slot (p - z0 + 2) % NE, f plane p in slot (p - z0 + 1) % NF;
   // the j-th use of a slot completes phase j of its barrier
-  auto eslot = [&](int p) { return (p - z0 + 2) % NE; };
-  auto fslot = [&](int p) { return (p - z0 + 1) % NF; };
+  auto eslot = [&](int p) { return (p - z0 + 2) % NE; };  // p >= z0 - 2
+  auto fslot = [&](int p) { return (p - z0 + 1) % NF; };  // p >= z0 - 1
   auto issue_e = [&](int p) {
     const int s = eslot(p);
     mbar_expect_tx(&bar[s], EB);
@@ -153,63 +156,63 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
     if (ok && !ZERO) ok = wait_e(k + 1);
     if (ok) ok = wait_f(k);
     if (!ok) s_bad = 1;
-    {  // red half-sweep on plane k, rows y0-1 .. y0+TTY
-      const int se = eslot(k), sl = eslot(k - 1), sh = eslot(k + 1), sf = fslot(k), s3 = (k + 3) % 3;
+    {  // red half-sweep on plane k, rows y0-1 .. y0+TTY, into the e slot of plane k
+      const int se = eslot(k), sl = eslot(k - 1), sh = eslot(k + 1), sf = fslot(k);
       const bool kin = k >= 0 && k < n;
 #pragma unroll
       for (int h = 0; h < PF; ++h) {
         const int r = ry + RS * h;
         if (r >= TMY) break;  // uniform per warp (a warp lies in one row)
         const int y = y0 - 1 + r;
-        float2 out = make_float2(0.f, 0.f);
         const bool yin = kin && y >= 0 && y < n;
         const float2 fv = Fs[sf][r][px];
         const int ro = ((y + k) & 1) ? 0 : 1;  // red: x + y + k odd
         const int xr = 2 * px + ro;
         if (ZERO) {
+          // from e = 0 the slot was never loaded: write the whole pair (black lane zero)
+          float2 out = make_float2(0.f, 0.f);
           const float v = (yin && xr < n) ? omega * ((ro ? fv.y : fv.x) * iD) : 0.f;
           if (ro) out.y = v; else out.x = v;
+          E[se][r + 1][px] = out;
         } else {
+          // reads of black values only (neighbours and, through the pair, the other lane);
+          // the store touches only this pair's red lane
           const float2 c = E[se][r + 1][px];
           float left, right;
           xnb(c, E[se][r + 1], left, right);
-          if (yin) {
+          if (yin && xr < n) {
             const float2 up = E[se][r][px], dn = E[se][r + 2][px], zl = E[sl][r + 1][px], zh = E[sh][r + 1][px];
-            out = c;
-            if (xr < n) {
-              float nb, fr, old;
-              if (ro == 0) {
-                nb = left + c.y + up.x + dn.x + zl.x + zh.x;
-                fr = fv.x;
-                old = c.x;
-              } else {
-                nb = c.x + right + up.y + dn.y + zl.y + zh.y;
-                fr = fv.y;
-                old = c.y;
-              }
-              const float gs = (fr + a * nb) * iD;
-              const float v = omega == 1.f ? gs : old + omega * (gs - old);
-              if (ro) out.y = v; else out.x = v;
+            float nb, fr, old;
+            if (ro == 0) {
+              nb = left + c.y + up.x + dn.x + zl.x + zh.x;
+              fr = fv.x;
+              old = c.x;
+            } else {
+              nb = c.x + right + up.y + dn.y + zl.y + zh.y;
+              fr = fv.y;
+              old = c.y;
             }
+            const float gs = (fr + a * nb) * iD;
+            const float v = omega == 1.f ? gs : old + omega * (gs - old);
+            if (ro) E[se][r + 1][px].y = v; else E[se][r + 1][px].x = v;
           }
         }
-        M[s3][r][px] = out;
       }
     }
     __syncthreads();
     const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+TTY-1
     if (kb >= z0 && kb < z1) {
-      const int s0 = (kb + 3) % 3, sl = (kb + 2) % 3, sh = (kb + 4) % 3, se = eslot(kb), sf = fslot(kb);
+      const int s0 = eslot(kb), sl = eslot(kb - 1), sh = eslot(kb + 1), sf = fslot(kb);
 #pragma unroll
       for (int h = 0; h < PB; ++h) {
         const int r = ry + RS * h;
         if (r >= TTY) break;
         const int y = y0 + r;
-        const float2 c = M[s0][r + 1][px];
+        const float2 c = E[s0][r + 2][px];  // red lane updated, black lane old
         float left, right;
-        xnb(c, M[s0][r + 1], left, right);
+        xnb(c, E[s0][r + 2], left, right);
         if (y >= n) continue;
-        const float2 up = M[s0][r][px], dn = M[s0][r + 2][px], zl = M[sl][r + 1][px], zh = M[sh][r + 1][px];
+        const float2 up = E[s0][r + 1][px], dn = E[s0][r + 3][px], zl = E[sl][r + 2][px], zh = E[sh][r + 2][px];
         const float2 fv = Fs[sf][r + 1][px];
         const int bo = ((y + kb) & 1) ? 1 : 0;  // black: x + y + kb even
         float2 out = c;
@@ -219,11 +222,11 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
           if (bo == 0) {
             nb = left + c.y + up.x + dn.x + zl.x + zh.x;
             fr = fv.x;
-            old = ZERO ? 0.f : E[se][r + 2][px].x;
+            old = ZERO ? 0.f : c.x;
           } else {
             nb = c.x + right + up.y + dn.y + zl.y + zh.y;
             fr = fv.y;
-            old = ZERO ? 0.f : E[se][r + 2][px].y;
+            old = ZERO ? 0.f : c.y;
           }
           const float gs = (fr + a * nb) * iD;
           const float v = omega == 1.f ? gs : old + omega * (gs - old);
@@ -232,8 +235,8 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
         const long long o = kb * plane + (long long)y * g.pitch + 2 * px;
         if (UPD) {
           double2 w = upre[h];
-          w.x += (double)out.x;
-          w.y += (double)out.y;
+          w.x += widen_exact(out.x);
+          w.y += widen_exact(out.y);
           *(double2 *)(u + b * su + o) = w;
         } else {
           *(float2 *)(eout + b * g.slab + o) = out;
@@ -419,11 +422,15 @@ template <int NX, bool ZERO, bool UPD>
 cudaError_t launch_tma(const Launch &L, const Grid &g, float a, float iD, float omega, const void *ein, void *eout,
                        const void *f, double *u, long long su, int batch, int zchunk) {
   constexpr uint32_t EB = TEY * NX * 4, FB = TMY * NX * 4;
-  const size_t smem = NE * EB + NF * FB + 3 * FB + (NE + NF) * 8;
+  const size_t smem = NE * EB + NF * FB + (NE + NF) * 8;
   static bool attr = false;
   if (!attr) {
+    // two CTAs of ~112 KB per SM: ask for the largest shared-memory carveout
     cudaError_t e = cudaFuncSetAttribute(rbgs_tma_kernel<NX, ZERO, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(rbgs_tma_kernel<NX, ZERO, UPD>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr = true;
   }

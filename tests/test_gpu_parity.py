@@ -655,6 +655,13 @@ def test_fp32_sweep_255_with_tma_kernels_matches_oracle():
     assert rel(gpu, np.stack([want, want])) < 2e-6
 
 
+def test_integer_widening_matches_the_hardware_conversion_on_every_float():
+    """The FP32 -> FP64 widening done with integer operations (FP32 corrections added to
+    FP64 iterates: interpolation, update sweeps) equals the hardware conversion bit for
+    bit on all 2^32 float bit patterns (normal, subnormal, zero, Inf; NaN stays NaN)."""
+    assert pmg.pfasst_mg_check_widening() == 0
+
+
 def test_fp64_probe_reports_a_plausible_rate():
     """The FP64 FMA probe (the roofline denominator of the FP64-bound kernels) measures a
     positive rate no higher than the unit-count bound 152 SMs x 2 FMA/clk x 2 flops at
