@@ -118,8 +118,11 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
     mbar_expect_tx(&bar[NE + s], FB);
     tma_load_4d(&Fs[s][0][0], &tmf, 0, y0 - 1, p, b, &bar[NE + s]);
   };
-  auto wait_e = [&](int p) { return mbar_wait(&bar[eslot(p)], ((p - z0 + 2) / NE) & 1); };
-  auto wait_f = [&](int p) { return mbar_wait(&bar[NE + fslot(p)], ((p - z0 + 1) / NF) & 1); };
+  // ring slots above a given one, wrapped (d < N)
+  auto eup = [](int sl, int d) { return sl + d >= NE ? sl + d - NE : sl + d; };
+  auto edn = [](int sl, int d) { return sl - d < 0 ? sl - d + NE : sl - d; };
+  auto fup = [](int sl, int d) { return sl + d >= NF ? sl + d - NF : sl + d; };
+  auto fdn = [](int sl, int d) { return sl - d < 0 ? sl - d + NF : sl - d; };
   // x neighbours of the pair c in smem row `row` (lanes, or smem at a warp edge, or 0)
   auto xnb = [&](float2 c, const float2 *row, float &left, float &right) {
     const float l = __shfl_up_sync(full, c.y, 1), r = __shfl_down_sync(full, c.x, 1);
@@ -138,13 +141,25 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
   }
   __syncthreads();
   bool ok = true;
-  if (!ZERO) ok = wait_e(z0 - 2) && wait_e(z0 - 1);
+  if (!ZERO) ok = mbar_wait(&bar[0], 0) && mbar_wait(&bar[1], 0);  // planes z0-2, z0-1: slots 0, 1, phase 0
   double2 upre[PB];  // UPD: this thread's u pairs of plane k-1, loaded before the red phase
   int kstop = z1;    // plane at which a timed-out CTA stopped
+  // ring positions kept incrementally (the same for every thread): the e slot of plane k+1
+  // and the phase of its barrier, the f slot of plane k and its phase
+  int s1 = 2, sfk = 0;
+  uint32_t ph1 = 0, phf = 0;
   for (int k = z0 - 1; k <= z1; ++k) {
     if (tid == 0) {  // refill the slots the previous plane released
-      if (!ZERO && k + 1 + DEPTH <= z1 + 1) issue_e(k + 1 + DEPTH);
-      if (k + DEPTH <= z1) issue_f(k + DEPTH);
+      if (!ZERO && k + 1 + DEPTH <= z1 + 1) {
+        const int sl = eup(s1, DEPTH);
+        mbar_expect_tx(&bar[sl], EB);
+        tma_load_4d(&E[sl][0][0], &tme, 0, y0 - 2, k + 1 + DEPTH, b, &bar[sl]);
+      }
+      if (k + DEPTH <= z1) {
+        const int sl = fup(sfk, DEPTH);
+        mbar_expect_tx(&bar[NE + sl], FB);
+        tma_load_4d(&Fs[sl][0][0], &tmf, 0, y0 - 1, k + DEPTH, b, &bar[NE + sl]);
+      }
     }
     if (UPD && k - 1 >= z0 && k - 1 < z1) {
 #pragma unroll
@@ -153,11 +168,11 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
         if (r < TTY && y < n) upre[h] = *(const double2 *)(u + b * su + (k - 1) * plane + (long long)y * g.pitch + 2 * px);
       }
     }
-    if (ok && !ZERO) ok = wait_e(k + 1);
-    if (ok) ok = wait_f(k);
+    if (ok && !ZERO) ok = mbar_wait(&bar[s1], ph1);
+    if (ok) ok = mbar_wait(&bar[NE + sfk], phf);
     if (!ok) s_bad = 1;
     {  // red half-sweep on plane k, rows y0-1 .. y0+TTY, into the e slot of plane k
-      const int se = eslot(k), sl = eslot(k - 1), sh = eslot(k + 1), sf = fslot(k);
+      const int se = edn(s1, 1), sl = edn(s1, 2), sh = s1, sf = sfk;
       const bool kin = k >= 0 && k < n;
 #pragma unroll
       for (int h = 0; h < PF; ++h) {
@@ -202,7 +217,7 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
     __syncthreads();
     const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+TTY-1
     if (kb >= z0 && kb < z1) {
-      const int s0 = eslot(kb), sl = eslot(kb - 1), sh = eslot(kb + 1), sf = fslot(kb);
+      const int s0 = edn(s1, 2), sl = edn(s1, 3), sh = edn(s1, 1), sf = fdn(sfk, 1);
 #pragma unroll
       for (int h = 0; h < PB; ++h) {
         const int r = ry + RS * h;
@@ -248,6 +263,8 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
       kstop = k;
       break;
     }
+    if (++s1 == NE) { s1 = 0; ph1 ^= 1u; }
+    if (++sfk == NF) { sfk = 0; phf ^= 1u; }
   }
   if (s_bad && tid == 0) {
     atomicExch(&g_sweep_timeout, 1);
@@ -328,26 +345,51 @@ __global__ void __launch_bounds__(RNT, 4) resrestrict_tma_kernel(const __grid_co
   const int I = I0 + cx, J = J0 + cy;
   const long long cplane = (long long)gc.ny * gc.pitch;
   float acc = 0.f;
-  bool ok = mbar_wait(&bar[eslot(zb - 1)], 0) && mbar_wait(&bar[eslot(zb)], 0);
+  // the residual points of a fine plane this thread forms: the same for every plane, so
+  // their staged-tile offsets are computed once (eo: e and f tiles, ro: residual tile)
+  constexpr int NQ = (RFY * RRX + RNT - 1) / RNT;
+  int eo_q[NQ], ro_q[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int q = tid + i * RNT, ry = q / RRX, rx = q % RRX;
+    eo_q[i] = q < RFY * RRX ? (ry + 1) * RBX + rx + 4 : -1;
+    ro_q[i] = ry * RRS + rx;
+  }
+  bool ok = mbar_wait(&bar[0], 0) && mbar_wait(&bar[1], 0);  // e planes zb-1, zb: slots 0, 1, phase 0
   int zstop = ze;  // plane at which a timed-out CTA stopped
+  // ring positions kept incrementally: e slot of plane z+1 and its phase, f slot of plane z
+  int s1 = 2, sfz = 0;
+  uint32_t ph1 = 0, phf = 0;
   for (int z = zb; z <= ze; ++z) {
+    const int s0 = s1 == 0 ? RNE - 1 : s1 - 1, sm1 = s0 == 0 ? RNE - 1 : s0 - 1;
     if (tid == 0) {  // refill the slots of planes z-2 (e) and z-1 (f), read before the last barrier
-      if (z + 1 + RD <= ze + 1) issue_e(z + 1 + RD);
-      if (z + RD <= ze) issue_f(z + RD);
+      if (z + 1 + RD <= ze + 1) {
+        const int sl = s1 + RD >= RNE ? s1 + RD - RNE : s1 + RD;
+        mbar_expect_tx(&bar[sl], REB);
+        tma_load_4d((char *)Eb + sl * RES, &tme, 2 * I0 - 4, 2 * J0 - 1, z + 1 + RD, b, &bar[sl]);
+      }
+      if (z + RD <= ze) {
+        const int sl = sfz + RD >= RNF ? sfz + RD - RNF : sfz + RD;
+        mbar_expect_tx(&bar[RNE + sl], RFB);
+        tma_load_4d((char *)Fb + sl * RFS, &tmf, 2 * I0 - 4, 2 * J0, z + RD, b, &bar[RNE + sl]);
+      }
     }
-    if (ok) ok = mbar_wait(&bar[eslot(z + 1)], ((z + 1 - zb + 1) / RNE) & 1);
-    if (ok) ok = mbar_wait(&bar[RNE + fslot(z)], ((z - zb) / RNF) & 1);
+    if (ok) ok = mbar_wait(&bar[s1], ph1);
+    if (ok) ok = mbar_wait(&bar[RNE + sfz], phf);
     if (!ok) s_bad = 1;
-    const float *E0 = Eb + eslot(z) * (RES / 4), *El = Eb + eslot(z - 1) * (RES / 4),
-                *Eh = Eb + eslot(z + 1) * (RES / 4), *F0 = Fb + fslot(z) * (RFS / 4);
+    const float *E0 = Eb + s0 * (RES / 4), *El = Eb + sm1 * (RES / 4), *Eh = Eb + s1 * (RES / 4),
+                *F0 = Fb + sfz * (RFS / 4);
     float *R = Rb + (z & 1) * RFY * RRS;
-    for (int q = tid; q < RFY * RRX; q += RNT) {  // residual of fine plane z
-      const int ry = q / RRX, rx = q % RRX;
-      const int eo = (ry + 1) * RBX + rx + 4;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {  // residual of fine plane z
+      const int eo = eo_q[i];
+      if (eo < 0) break;
       const float ec = E0[eo];
       const float nb = E0[eo - 1] + E0[eo + 1] + E0[eo - RBX] + E0[eo + RBX] + El[eo] + Eh[eo];
-      R[ry * RRS + rx] = F0[ry * RBX + rx + 4] - (ec - a * (nb - 6.f * ec));
+      R[ro_q[i]] = F0[eo - RBX] - (ec - a * (nb - 6.f * ec));
     }
+    if (++s1 == RNE) { s1 = 0; ph1 ^= 1u; }
+    if (++sfz == RNF) { sfz = 0; phf ^= 1u; }
     __syncthreads();
     if (s_bad) {  // uniform: read after the barrier
       zstop = z;

@@ -99,6 +99,22 @@ def heat3d_c3(n: int = 255, slices: int = 32, precision: int = 1, iterations: in
                     iterations, modes=modes, amps=list(amps))
 
 
+def gaussian_random_field(n: int, ell: float, seed: int) -> np.ndarray:
+    """Seeded Gaussian random field on the n^3 interior points with zero walls, by
+    spectral synthesis: u = sum_k a_k sin(k_x pi x) sin(k_y pi y) sin(k_z pi z) with
+    independent N(0, 1) draws scaled by exp(-(pi |k| ell)^2 / 4), the square root of the
+    spectral density of the Gaussian covariance exp(-r^2 / (2 ell^2)) at the wave number
+    pi |k|; summed as a type-I sine transform (its basis is exactly sin(k pi i / (n+1)) on
+    the interior points).  Scaled to max |u| = 1; dense layout [z][y][x]."""
+    from scipy.fft import idstn
+    rng = np.random.default_rng(seed)
+    k = np.arange(1, n + 1, dtype=np.float64)
+    kk = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+    coef = rng.standard_normal((n, n, n)) * np.exp(-(np.pi ** 2) * kk * ell ** 2 / 4.0)
+    u = idstn(coef, type=1, norm="forward")  # sum_k coef_k prod sin(k pi i / (n + 1))
+    return (u / np.abs(u).max()).reshape(-1)
+
+
 @dataclass
 class Problem:
     """One member of an uneven batch (single-level SDC, one time step per run step)."""
