@@ -418,6 +418,144 @@ def run_learned(args):
         print(json.dumps(line), flush=True)
 
 
+def run_learned_deploy(args):
+    """The learned-correction workload: train the 3-layer 3x3x3 BF16 convolutional
+    correction network (16 channels, ReLU) on error/residual pairs of the sub-step
+    problems of 3D heat on 127^3 with Gaussian-random-field initial values (length
+    scale 0.1, seeds 5, 6, ...), then deploy it in two-level PFASST on 255^3 / 127^3,
+    16 slices, 5/3 Gauss-Lobatto nodes, one V(2,1) red-black cycle per sub-step, mixed
+    precision, with the plain V-cycle kept on every level where the measured contraction
+    does not drop.  Pairs: the library's FP64 multigrid solves each sub-step
+    (I - c Lap_h) u = u0 to 1e-12; its initial error u* - u0 after one red-black sweep is
+    the target, the scaled residual the input (pfasst_mg_net_substep_pairs); cut into
+    32^3 crops.  value = DOF-sweeps/s of the deployed solver to the residual the plain
+    solver reaches in 10 iterations (the same metric as the 3D workload); the plain
+    solver's value and the error of both against the per-mode collocation solution of the
+    sine-mode initial value of the 3D workload are in `config`."""
+    import math
+    import torch
+    import paper_1407_6486_gb300 as pmg
+    from paper_1407_6486_gb300 import _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    pmg.load()
+    # ---- training pairs: 127^3 GRF fields, kappa over the deployment's operators
+    ng, gb, crop = 127, 8, 32
+    fields = args.learned_fields
+    rng = np.random.default_rng(5)
+    t0 = time.perf_counter()
+    gen = pmg.NetTrainer(gb, ng)
+    offs = [0, 32, 64, ng - crop]
+    xs, ts, ks = [], [], []
+    u0d = torch.empty((gb, ng ** 3), dtype=torch.float64, device="cuda")
+    xg = torch.empty((gb, ng ** 3), dtype=torch.float32, device="cuda")
+    tg = torch.empty_like(xg)
+    for f0 in range(0, fields, gb):
+        kap = rng.uniform(0.03, 1.0 / 6.0 - 1e-3, gb).astype(np.float32)
+        for b in range(gb):
+            u0d[b] = torch.from_numpy(inputs.gaussian_random_field(ng, 0.1, 5 + f0 + b))
+        gen.substep_pairs(u0d, kap, xg, tg)
+        xv, tv = xg.view(gb, ng, ng, ng), tg.view(gb, ng, ng, ng)
+        for b in range(gb):
+            for oz in offs:
+                for oy in offs:
+                    for ox in offs:
+                        xs.append(xv[b, oz:oz + crop, oy:oy + crop, ox:ox + crop].reshape(-1))
+                        ts.append(tv[b, oz:oz + crop, oy:oy + crop, ox:ox + crop].reshape(-1))
+                        ks.append(kap[b])
+    gen.close()
+    X, T, K = torch.stack(xs), torch.stack(ts), np.array(ks, dtype=np.float32)
+    del xs, ts
+    torch.cuda.synchronize()
+    pair_s = time.perf_counter() - t0
+    # ---- training on the GPU: Adam on batches of 16 crops, power-1 loss (scaled residual)
+    npairs, tb = X.shape[0], 16
+    hold = torch.arange(npairs - 64, npairs, device="cuda")
+    tr = pmg.NetTrainer(tb, crop)
+    t1 = time.perf_counter()
+    hist = []
+    for ep in range(args.learned_epochs):
+        perm = torch.randperm(npairs - 64, device="cuda", generator=torch.Generator(device="cuda").manual_seed(ep))
+        for i in range(0, npairs - 64 - tb + 1, tb):
+            idx = perm[i:i + tb]
+            hist.append(tr.step(X[idx].contiguous(), T[idx].contiguous(), K[idx.cpu().numpy()], power=1,
+                                lr=2e-3 if ep == 0 else 1e-3))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    prm = tr.params()
+    held = [tr.gradients(X[hold[j:j + tb]].contiguous().cpu().numpy(), T[hold[j:j + tb]].contiguous().cpu().numpy(),
+                         K[hold[j:j + tb].cpu().numpy()], power=1)[0] for j in range(0, 64, tb)]
+    held_zero = float(0.5 * (X[hold].double() ** 2).mean())  # the same loss with no correction (y = 0)
+    tr.close()
+    del X, T
+    torch.cuda.empty_cache()
+    # ---- deployment: 255^3 / 127^3, 16 slices, one V-cycle per sub-step, mixed
+    wl = inputs.heat3d_c3(n=255, slices=16)
+    wl.vcycles = 1
+    u0 = torch.tensor(wl.u0(), device="cuda")
+    n, h = wl.n, 1.0 / (wl.n + 1)
+    xg1 = np.arange(1, n + 1) * h
+    want = np.zeros((n, n, n))
+    for k, a in zip(wl.modes, wl.amps):
+        z = wl.dt * wl.nu * sum((2 * math.cos(kk * math.pi * h) - 2) / h ** 2 for kk in k)
+        want += a * _pade(z, wl.fine_nodes) ** wl.slices * np.einsum(
+            "k,j,i->kji", np.sin(k[2] * np.pi * xg1), np.sin(k[1] * np.pi * xg1), np.sin(k[0] * np.pi * xg1))
+    out = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+    opts = dict(smoother=1, omega=1.0, vcycles=1, precision=1)
+    rows, target, k_ref = {}, None, None
+    for name in ("plain", "net"):
+        s = pmg.PFASSTSolver(3, n, 5, 3, wl.slices, wl.nu, wl.dt, **opts)
+        rho = None
+        if name == "net":
+            rho = s.set_smoother_net(prm, min_n=15, calibrate=1)
+        if target is None:
+            s.set_initial(u0)
+            _, k_ref, r10 = s.iterate(10, 0.0)
+            target = float(f"{r10 * 1.01:.4e}")
+        for _ in range(max(args.warmup, 1)):
+            s.set_initial(u0)
+            s.iterate(60, target)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, its = [], []
+        for _ in range(args.steps):
+            ev0.record()
+            s.set_initial(u0)
+            rc, it, res = s.iterate(60, target)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            its.append(it)
+        pmg.pfasst_mg_get_solution(s.h, wl.slices - 1, 4, out)
+        err = float(np.abs(out.cpu().numpy().reshape(n, n, n) - want).max() / np.abs(want).max())
+        dof = n ** 3 * 4 * wl.slices * k_ref
+        rows[name] = {"ms_per_step": statistics.median(ms), "iterations": its[-1], "final_residual": res,
+                      "reached": rc == pmg.PMG_OK, "dof_sweeps_per_s": dof / (statistics.median(ms) / 1000.0),
+                      "rel_error_vs_collocation": err}
+        if rho is not None:
+            rows[name].update({"rho_plain": rho[0], "rho_net": rho[1], "levels_kept_mask": rho[2]})
+        s.close()
+        torch.cuda.empty_cache()
+    net, plain = rows["net"], rows["plain"]
+    line = {"metric": "DOF-sweeps/s", "value": net["dof_sweeps_per_s"], "unit": "DOF-sweeps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": net["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
+            "config": {"workload": "learned_heat3d_n255_pfasst5x3_P16_1vc",
+                       "training": {"pairs": int(npairs), "fields": fields, "field": "127^3 GRF, length scale 0.1",
+                                    "crop": "32^3", "epochs": args.learned_epochs, "steps": len(hist),
+                                    "final_loss": float(np.mean(hist[-20:])), "held_out_loss": float(np.mean(held)),
+                                    "held_out_loss_without_correction": held_zero,
+                                    "pair_seconds": pair_s, "train_seconds": train_s},
+                       "K_ref": k_ref, "residual_target": target, "with_network": net, "plain_vcycle": plain,
+                       "gain_vs_plain": net["dof_sweeps_per_s"] / plain["dof_sweeps_per_s"],
+                       "l2": "working set ~27 GB per solver, far above L2; no flush"},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def _pade(z, s):
     """Diagonal (s-1, s-1) Pade approximant of exp(z): the Gauss-Lobatto collocation step."""
     import math
@@ -783,6 +921,8 @@ def run_ours(args):
     u0 = wl.u0()
     u0_dev = torch.tensor(u0, device="cuda")
     common = dict(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, interp_order=4)
+    # the measured variant's coarse-level V-cycles (the FP64 reference keeps the workload's)
+    variant = dict(coarse_vcycles=args.coarse_vcycles) if args.coarse_vcycles >= 0 else {}
 
     fp64_ms, fp64_runs = None, []
     r_ref = None
@@ -819,7 +959,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
 
     s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
-                         nlevels=wl.nlevels, precision=wl.precision, **common)
+                         nlevels=wl.nlevels, precision=wl.precision, **common, **variant)
     maxit = wl.iterations if args.quick else 4 * wl.iterations
     if args.tma:
         for lev in range(8):
@@ -946,7 +1086,8 @@ def run_ours(args):
         "config": {"workload": wl.name, "grid": f"{wl.n}^{wl.dim}/{(wl.n - 1) // 2}^{wl.dim}",
                    "slices": wl.slices, "nodes": f"{wl.fine_nodes}/{wl.coarse_nodes} Gauss-Lobatto",
                    "smoother": "V(2,1) " + ("red-black Gauss-Seidel" if wl.smoother == 1 else "Jacobi 2/3"),
-                   "vcycles": wl.vcycles, "precision": "FP32 V-cycles, FP64 SDC/FAS" if wl.precision else "FP64",
+                   "vcycles": wl.vcycles, "coarse_vcycles": args.coarse_vcycles if args.coarse_vcycles >= 0 else wl.vcycles,
+                   "precision": "FP32 V-cycles, FP64 SDC/FAS" if wl.precision else "FP64",
                    "K_ref": k_ref, "residual_target": target, "residual_tolerance": RES_TOL,
                    "fp64_residual_at_K_ref": r_ref, "iterations": [it for _, it, _ in iters],
                    "final_residual": iters[-1][2], "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
@@ -999,8 +1140,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d",
-                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "compare",
-                             "weak3", "order4", "heat1d"])
+                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "learned",
+                             "compare", "weak3", "order4", "heat1d"])
+    ap.add_argument("--learned-fields", type=int, default=160,
+                    help="learned: 127^3 GRF fields for the training pairs (64 crops each)")
+    ap.add_argument("--learned-epochs", type=int, default=2)
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no FP64 calibration (run the workload's iteration count), no e2e, "
                          "no CPU baseline")
@@ -1018,6 +1162,8 @@ def main():
     ap.add_argument("--vcycles", type=int, default=-1, help="override V-cycles per sub-step (0 = solve to 1e-12)")
     ap.add_argument("--precision", type=int, default=-1, help="override precision: 0 FP64, 1 mixed")
     ap.add_argument("--order4-only", default="", help="order4: comma-separated subset of 2/2,2/4,4/4")
+    ap.add_argument("--coarse-vcycles", type=int, default=-1,
+                    help="measured variant: V-cycles per coarse-level sub-step (-1: the workload's)")
     ap.add_argument("--vcycle-tail", type=int, default=-1,
                     help="heat1d: 1 = run each V-cycle's levels that fit one CTA in one launch, 0 = per level")
     ap.add_argument("--tma", action="store_true",
@@ -1031,6 +1177,8 @@ def main():
         run_uneven(args)
     elif args.workload == "learned-train":
         run_learned(args)
+    elif args.workload == "learned":
+        run_learned_deploy(args)
     elif args.workload == "compare":
         run_compare(args)
     elif args.workload == "weak3":

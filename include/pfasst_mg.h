@@ -351,6 +351,18 @@ int pfasst_mg_net_gradients(pmg_net_handle h, const float *x, const float *t, co
 int pfasst_mg_net_sample(pmg_net_handle h, unsigned long long seed, double kappa_lo, double kappa_hi,
                          int vcycles_max, float *x, float *t, float *kappa, int on_device);
 
+/* Training pairs from the sub-step problems of an SDC sweep: for every grid b of the
+ * batch, u0 (dense FP64 [batch][n^3], device memory if on_device) is the initial value
+ * and kappa[b] (host, in [0, 1/6)) fixes c_b / h^2 = kappa_b / (1 - 6 kappa_b).  The
+ * library's FP64 multigrid (red-black V(2,1), solved to 1e-12) solves the sub-step
+ * (I - c_b Lap_h) u = u0 from the initial guess u0; its initial error e0 = u* - u0 --
+ * what the first V-cycle of a sweep's sub-step starts from -- scaled to max |e0| = 1,
+ * after one red-black Gauss-Seidel sweep of Ahat t = 0 gives the target t, and x =
+ * Ahat t the input (layout and Ahat as for pfasst_mg_net_sample).  Needs n = 2^p - 1.
+ * Outputs x, t as [batch][n^3] floats.  Errors: INVALID_ARG, CUDA.  Synchronises. */
+int pfasst_mg_net_substep_pairs(pmg_net_handle h, const double *u0, const float *kappa, float *x, float *t,
+                                int on_device);
+
 /* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the loss of
  * power p, each on a fresh batch from pfasst_mg_net_sample(seed + k * golden,
  * kappa_lo, kappa_hi, vcycles_max).  train_bias = 0 keeps the

@@ -40,7 +40,7 @@ EXPORTS = [
     "pfasst_mg_net_get_params", "pfasst_mg_net_forward", "pfasst_mg_net_gradients", "pfasst_mg_net_sample",
     "pfasst_mg_net_train", "pfasst_mg_net_launch_count", "pfasst_mg_net_destroy", "pfasst_mg_net_last_error",
     "pfasst_mg_set_smoother_net", "pfasst_mg_net_step", "pfasst_mg_net_profile", "pfasst_mg_net_profile_read",
-    "pfasst_mg_check_narrowing", "pfasst_mg_fp64_peak", "pfasst_mg_check_widening",
+    "pfasst_mg_check_narrowing", "pfasst_mg_fp64_peak", "pfasst_mg_check_widening", "pfasst_mg_net_substep_pairs",
 ]
 
 NET_PARAMS = 7809  # W1[16][27], b1[16], W2[16][27][16], b2[16], W3[27][16], b3
@@ -537,6 +537,44 @@ def pfasst_mg_net_step(h, x, t, kappa, npts, power=1, lr=1e-3, train_bias=0):
     return loss.value
 
 
+def _is_dev(a):
+    try:
+        import torch
+        return isinstance(a, torch.Tensor) and a.is_cuda
+    except ImportError:
+        return False
+
+
+def pfasst_mg_net_step_dev(h, x, t, kappa, power=1, lr=1e-3, train_bias=0):
+    """One Adam step on device tensors x, t (float32, contiguous, [batch][n^3]) and host
+    kappa; returns the loss."""
+    import numpy as np
+    assert _is_dev(x) and _is_dev(t) and x.is_contiguous() and t.is_contiguous()
+    ka = np.ascontiguousarray(kappa, dtype=np.float32)
+    loss = ctypes.c_double(0.0)
+    _ncheck(load().pfasst_mg_net_step(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                      ka.ctypes.data_as(ctypes.c_void_p), power, lr, train_bias, 1,
+                                      ctypes.byref(loss)), h)
+    return loss.value
+
+
+def pfasst_mg_net_substep_pairs(h, u0, kappa, x, t):
+    """Sub-step training pairs (see include/pfasst_mg.h): u0 float64 [batch][n^3], x and t
+    float32 outputs of the same shape -- all device tensors, or all host numpy arrays;
+    kappa host floats, one per grid."""
+    import numpy as np
+    ka = np.ascontiguousarray(kappa, dtype=np.float32)
+    dev = _is_dev(u0)
+    if dev:
+        assert _is_dev(x) and _is_dev(t) and u0.is_contiguous() and x.is_contiguous() and t.is_contiguous()
+        ptr = lambda a: ctypes.c_void_p(a.data_ptr())  # noqa: E731
+    else:
+        assert u0.dtype == np.float64 and x.dtype == np.float32 and t.dtype == np.float32
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _ncheck(load().pfasst_mg_net_substep_pairs(h, ptr(u0), ka.ctypes.data_as(ctypes.c_void_p), ptr(x), ptr(t),
+                                               1 if dev else 0), h)
+
+
 def pfasst_mg_net_profile(h, enable, min_points=0):
     _ncheck(load().pfasst_mg_net_profile(h, enable, min_points), h)
 
@@ -609,7 +647,12 @@ class NetTrainer:
         return pfasst_mg_net_profile_read(self.h)
 
     def step(self, x, t, kappa, power=1, lr=1e-3, train_bias=0):
+        if _is_dev(x):
+            return pfasst_mg_net_step_dev(self.h, x, t, kappa, power, lr, train_bias)
         return pfasst_mg_net_step(self.h, x, t, kappa, self.npts, power, lr, train_bias)
+
+    def substep_pairs(self, u0, kappa, x, t):
+        pfasst_mg_net_substep_pairs(self.h, u0, kappa, x, t)
 
     def launches(self):
         return pfasst_mg_net_launch_count(self.h)

@@ -2308,6 +2308,46 @@ int pfasst_mg_net_gradients(pmg_net_handle h, const float *x, const float *t, co
   return PMG_OK;
 }
 
+int pfasst_mg_net_substep_pairs(pmg_net_handle h, const double *u0, const float *kappa, float *x, float *t,
+                                int on_device) {
+  if (!h || !u0 || !kappa || !x || !t) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or array");
+  if (h->n < 7 || ((h->n + 1) & h->n) != 0) return nfail(h, PMG_ERR_INVALID_ARG, "sub-step pairs need n = 2^p - 1 >= 7");
+  for (int b = 0; b < h->batch; ++b)
+    if (!(kappa[b] >= 0.0f && kappa[b] < 1.0f / 6.0f)) return nfail(h, PMG_ERR_INVALID_ARG, "need 0 <= kappa < 1/6");
+  const NetGrid g = h->grid();
+  const size_t n3 = (size_t)h->n * h->n * h->n;
+  // u64 <- u0 (the initial guess), zero64 <- u0 (the right-hand side, restored to zero below)
+  PMG_NCUDA(h, cudaMemcpyAsync(h->u64, u0, h->pts() * sizeof(double), kind_in(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(h->zero64, u0, h->pts() * sizeof(double), kind_in(on_device), h->stream));
+  PMG_NCUDA(h, cudaMemcpyAsync(h->s.kappa, kappa, sizeof(float) * h->batch, cudaMemcpyHostToDevice, h->stream));
+  pmg_options o;
+  pfasst_mg_default_options(&o);
+  o.smoother = PMG_SMOOTHER_RBGS;
+  o.omega = 1.0;
+  o.vcycles = 0;  // solved to the tolerance (1e-12)
+  o.use_graphs = 0;
+  o.autotune = 0;
+  const pmg_grid grid{3, h->n, 2};
+  const double ih2 = (double)(h->n + 1) * (h->n + 1);
+  int rc = PMG_OK;
+  for (int b = 0; b < h->batch && rc == PMG_OK; ++b) {
+    const double k = kappa[b];
+    const double c = k / ((1.0 - 6.0 * k) * ih2);  // kappa = (c/h^2) / (1 + 6 c/h^2)
+    rc = pfasst_mg_helmholtz_solve(&grid, c, 1, h->zero64 + b * n3, h->u64 + b * n3, &o, h->stream, nullptr);
+    if (rc != PMG_OK) rc = nfail(h, rc, std::string("sub-step solve: ") + pfasst_mg_last_error(nullptr));
+  }
+  if (rc == PMG_OK) {
+    PMG_NCUDA(h, k_net_sub64(h->L(), g, h->u64, h->zero64));  // e0 = u* - u0
+    PMG_NCUDA(h, k_net_sample_finish(h->L(), g, h->u64, h->mx, h->xs, h->ts, h->s.kappa));
+    const size_t bytes = h->pts() * sizeof(float);
+    PMG_NCUDA(h, cudaMemcpyAsync(x, h->xs, bytes, kind_out(on_device), h->stream));
+    PMG_NCUDA(h, cudaMemcpyAsync(t, h->ts, bytes, kind_out(on_device), h->stream));
+  }
+  PMG_NCUDA(h, cudaMemsetAsync(h->zero64, 0, h->pts() * sizeof(double), h->stream));
+  PMG_NCUDA(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
 int pfasst_mg_net_sample(pmg_net_handle h, unsigned long long seed, double kappa_lo, double kappa_hi,
                          int vcycles_max, float *x, float *t, float *kappa, int on_device) {
   if (!h || !x || !t || !kappa) return nfail(h, PMG_ERR_INVALID_ARG, "null handle or array");

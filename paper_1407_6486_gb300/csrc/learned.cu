@@ -758,6 +758,19 @@ cudaError_t k_net_sample_noise64(const Launch &L, const NetGrid &g, unsigned lon
   return cudaGetLastError();
 }
 
+// a -= b over n FP64 values (the initial error u* - u0 of a sub-step solve)
+__global__ void sub64_kernel(long long n, double *__restrict__ a, const double *__restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] -= b[i];
+}
+
+cudaError_t k_net_sub64(const Launch &L, const NetGrid &g, double *a, const double *b) {
+  const long long npts = (long long)g.batch * g.slab;
+  Scope sc(L, K_NET_SAMPLE, cube(g.n), g.batch, 0);
+  sub64_kernel<<<grid_blocks(npts, 256), 256, 0, L.stream>>>(npts, a, b);
+  return sc.done();
+}
+
 cudaError_t k_net_sample_finish(const Launch &L, const NetGrid &g, const double *u, unsigned long long *mx,
                                 float *x, float *t, const float *kappa) {
   const long long npts = (long long)g.batch * g.slab;

@@ -400,6 +400,8 @@ int net_sample_vcycles(unsigned long long seed, int vmax, int b);
 cudaError_t k_net_sample_noise64(const Launch &L, const NetGrid &g, unsigned long long seed, double *u);
 cudaError_t k_net_sample_finish(const Launch &L, const NetGrid &g, const double *u, unsigned long long *mx,
                                 float *x, float *t, const float *kappa);
+// a -= b on the dense FP64 grids of a net batch
+cudaError_t k_net_sub64(const Launch &L, const NetGrid &g, double *a, const double *b);
 // correction step on a multigrid level: x = D^-1 (f - (I - c Lap) e), e += net(x)
 cudaError_t k_net_correct(const Launch &L, const Grid &g, double c, Prec pr, void *e, const void *f, int batch,
                           const float *prm, const NetScratch &s);
