@@ -1239,7 +1239,10 @@ void fill_coefficients(pmg_ctx *h) {
   std::memset(&h->resf, 0, sizeof h->resf);
   h->resf.s = h->sf;
   for (int m = 0; m < h->sf; ++m)
-    for (int i = 0; i < h->sf; ++i) h->resf.dtQ[m][i] = (double)((long double)h->dt * Qf[m][i]);
+    for (int i = 0; i < h->sf; ++i) {
+      h->resf.dtQ[m][i] = (double)((long double)h->dt * Qf[m][i]);
+      if (m + 1 < h->sf) h->resf.dS[m][i] = (double)((long double)h->dt * (Qf[m + 1][i] - Qf[m][i]));
+    }
   // restriction from a level with s nodes t (integration matrix Q) to one with sc nodes
   // tc (Qc): map[j] = the finer node at the time of coarse node j (-1: none)
   auto fill_fas = [&](FASCoef &cf, int s, const long double *t, long double Q[kMaxNodes][kMaxNodes], int sc,

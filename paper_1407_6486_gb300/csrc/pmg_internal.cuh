@@ -225,6 +225,7 @@ struct SFCoef {
 struct ResCoef {
   int s;
   double dtQ[kMaxNodes][kMaxNodes];
+  double dS[kMaxNodes - 1][kMaxNodes];  // dt (Q[m+1][j] - Q[m][j]): node-to-node quadrature S
 };
 
 // FAS restriction coefficients (coarse node j <-> fine node map[j])
