@@ -401,9 +401,13 @@ const char *pfasst_mg_net_last_error(pmg_net_handle h);
  * over V-cycles 2..4, worst over the fine sub-step operators) without the network
  * (*rho_plain) and then add levels finest first, keeping a level only when rho drops
  * (*rho_net = the final rho); levels that do not help keep the plain sweep, and with
- * no level kept the handle runs exactly as before.  calibrate = 0: use every
- * eligible level (*rho_plain and *rho_net are still measured).  *level_mask gets bit l set for level l (0 =
- * finest).  params = NULL removes a deployed network.  The correction allocates up to
+ * no level kept the handle runs exactly as before.  calibrate = 2: the same search,
+ * judged by the handle's own PFASST iteration instead: the max collocation residual after
+ * three iterations from the spread initial value (set it first with
+ * pfasst_mg_set_initial), without the network (*rho_plain) and with each level added
+ * (*rho_net = the final residual); afterwards the state is the spread initial value
+ * again.  calibrate = 0: use every eligible level (*rho_plain and *rho_net are still
+ * measured as for calibrate = 1).  *level_mask gets bit l set for level l (0 = finest).  params = NULL removes a deployed network.  The correction allocates up to
  * about 1 GiB of scratch (cudaMalloc; grids of a batch are processed in chunks).
  * Errors: UNSUPPORTED unless dim = 3, red-black Gauss-Seidel and nu1 >= 2, and on
  * batch handles; INVALID_ARG if no level qualifies; OOM.  Synchronises. */

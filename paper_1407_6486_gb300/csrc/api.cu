@@ -2486,8 +2486,41 @@ int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int
   PMG_CUDA(h, cudaMemcpyAsync(d->prm, params, kNetParams * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   PMG_CUDA(h, k_net_pack(h->L(), d->prm, d->s));
   double rp = 0.0, rb = 0.0;
-  PMG_RET(net_measure(h, &rp));
-  if (calibrate) {
+  if (calibrate == 2) {
+    // judge by the handle's own PFASST iteration: the fine collocation residual after
+    // three iterations from the spread initial value, plain and with each level added
+    auto run3 = [&](double *res) -> int {
+      drop_graph(h->g_pred);
+      drop_graph(h->g_pred_spread);
+      drop_graph(h->g_iter);
+      drop_graph(h->g_loop);
+      PMG_RET(spread(h));
+      int it = 0;
+      const int rc = pfasst_mg_iterate(h, 3, 0.0, &it, res);
+      if (rc != PMG_OK && rc != PMG_NOT_CONVERGED) return rc;
+      if (!std::isfinite(*res)) *res = INFINITY;
+      return PMG_OK;
+    };
+    PMG_RET(run3(&rp));
+    rb = rp;
+    for (int l = lfin; l < lend; ++l) {
+      d->on[l] = true;
+      double r = 0.0;
+      PMG_RET(run3(&r));
+      if (r < rb) rb = r;
+      else d->on[l] = false;
+    }
+    drop_graph(h->g_pred);
+    drop_graph(h->g_pred_spread);
+    drop_graph(h->g_iter);
+    drop_graph(h->g_loop);
+    PMG_RET(spread(h));  // the caller's next iterate starts from the initial value again
+  } else {
+    PMG_RET(net_measure(h, &rp));
+  }
+  if (calibrate == 2) {
+    // levels chosen above
+  } else if (calibrate) {
     rb = rp;
     for (int l = lfin; l < lend; ++l) {  // finest first; keep a level only if it helps
       d->on[l] = true;
@@ -2509,6 +2542,12 @@ int pfasst_mg_set_smoother_net(pmg_handle h, const float *params, int min_n, int
     cudaFree(d->mem);
     delete d;
     h->net = nullptr;
+  }
+  if (calibrate == 2) {  // graphs captured during the calibration hold earlier level choices
+    drop_graph(h->g_pred);
+    drop_graph(h->g_pred_spread);
+    drop_graph(h->g_iter);
+    drop_graph(h->g_loop);
   }
   return PMG_OK;
 }

@@ -222,6 +222,27 @@ def test_trained_network_gains_over_a_smoothing_sweep(trained):
         assert res["net"] == res["plain"]
 
 
+def test_calibration_on_the_pfasst_residual(trained):
+    """calibrate = 2 judges each level by the handle's own PFASST iteration (residual after
+    three iterations from the spread initial value).  Checked against separate runs: the
+    residuals it reports are those of a plain handle and of the deployed handle iterated
+    again from the initial value, and the deployed handle never ends above the plain one."""
+    p, _ = trained
+    wl = inputs.heat3d_c3(n=63, slices=4)
+    wl.vcycles = 1
+    plain = _solver(wl, pmg.PMG_PREC_FP64)
+    plain.set_initial(wl.u0())
+    r_plain = plain.iterate(3, 0.0)[2]
+    plain.close()
+    s = _solver(wl, pmg.PMG_PREC_FP64)
+    s.set_initial(wl.u0())
+    rp, rn, mask = s.set_smoother_net(p, min_n=7, calibrate=2)
+    r_dep = s.iterate(3, 0.0)[2]
+    print(f"PFASST residual after 3 iterations: plain {rp:.4e}, calibrated network {rn:.4e} (levels {mask:#x})")
+    assert rp == r_plain and rn == r_dep and rn <= rp
+    s.close()
+
+
 def _pade(z, s):
     M = s - 1
     c = [math.factorial(2 * M - j) * math.factorial(M) / (math.factorial(2 * M) * math.factorial(j)
