@@ -64,7 +64,7 @@ class pmg_options(ctypes.Structure):
                 ("mg_stall", ctypes.c_double), ("mg_maxcycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("interp_order", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("slice_groups", ctypes.c_int),
-                ("vcycle_tail", ctypes.c_int), ("coarse_vcycles", ctypes.c_int)]
+                ("vcycle_tail", ctypes.c_int), ("coarse_vcycles", ctypes.c_int), ("single_grid_vcycle", ctypes.c_int)]
 
 
 class pmg_problem_desc(ctypes.Structure):

@@ -169,6 +169,7 @@ struct Hier {
   Tune tune[kMaxLevels][2];       // [level][0: wide batches, 1: narrow (a single grid)]
   int tail = -1;                  // first level of the one-launch V-cycle bottom (-1: none)
   VTailDesc td;                   // its shared-memory plan
+  unsigned *count = nullptr;      // grid-barrier word of the persistent single-grid V-cycle
   // wide tuning for batches of a few grids or more (slice groups), narrow for single grids
   const Tune &tune_for(int l, int B) const { return tune[l][(2 * B >= batch || B >= 4) ? 0 : 1]; }
 };
@@ -351,6 +352,10 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 == 0 || o->nu1 > 16 || o->nu2 > 16) { why = "bad nu1/nu2"; return PMG_ERR_INVALID_ARG; }
     if (o->vcycles < 0 || o->vcycles > 1000) { why = "bad vcycles"; return PMG_ERR_INVALID_ARG; }
     if (o->coarse_vcycles < -1 || o->coarse_vcycles > 1000) { why = "bad coarse_vcycles"; return PMG_ERR_INVALID_ARG; }
+    if (o->single_grid_vcycle != 0 && o->single_grid_vcycle != 1) {
+      why = "single_grid_vcycle must be 0 or 1";
+      return PMG_ERR_INVALID_ARG;
+    }
     if ((o->vcycles == 0 || o->coarse_vcycles == 0) && (o->mg_maxcycles < 1 || !(o->mg_tol > 0))) {
       why = "bad full-solve settings";
       return PMG_ERR_INVALID_ARG;
@@ -401,6 +406,7 @@ void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smooth
     }
     nl = (nl - 1) / 2;
   }
+  pl.add((void **)&H.count, 256);
   // the finest level from which the rest of the V-cycle fits one CTA's shared memory
   // (at least two levels, so that the tail replaces several launches)
   H.tail = -1;
@@ -602,6 +608,22 @@ int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const dou
       PMG_CUDA(M.h, k_resid_pt(M.L, g, H.pr, um, sum, qm, sq, H.f[l0], B));
     else
       PMG_CUDA(M.h, k_residual0(M.L, g, c, H.pr, um, sum, qm, sq, u1, s1, H.f[l0], B, nullptr, nullptr));
+    // a single grid (the serial coarse chain): every V-cycle and the update in one
+    // persistent launch, unless a learned correction acts on one of the levels
+    bool net_here = false;
+    for (int l = l0; M.net && l < H.L; ++l) net_here = net_here || M.net->on[l];
+    if (B == 1 && o.single_grid_vcycle && !net_here &&
+        vcycle_coop_supported(g, H.L - l0, o.smoother == PMG_SMOOTHER_RBGS, o.nu1)) {
+      void *ev[kMaxLevels], *fv[kMaxLevels];
+      for (int l = l0; l < H.L; ++l) {
+        ev[l - l0] = H.e[l];
+        fv[l - l0] = H.f[l];
+      }
+      PMG_CUDA(M.h, k_vcycle_coop(M.L, &H.lev[l0], H.L - l0, H.pr, c, o.omega, o.nu1, o.nu2, o.vcycles, ev, fv, minv,
+                                  u1, H.count));
+      if (cycles) *cycles = o.vcycles;
+      return PMG_OK;
+    }
     for (int v = 0; v < o.vcycles; ++v) {
       const bool last = v == o.vcycles - 1;
       PMG_RET(vcycle(M, l0, B, c, minv, e, &e, last ? u1 : nullptr, s1, last ? &fused : nullptr));
@@ -1365,6 +1387,7 @@ void pfasst_mg_default_options(pmg_options *o) {
   o->slice_groups = 0;
   o->vcycle_tail = 0;
   o->coarse_vcycles = -1;
+  o->single_grid_vcycle = 1;
 }
 
 int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,
@@ -1521,6 +1544,7 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
     PMG_RET(run_device_loop(h, max_iter, tol, &k, &res));
     h->q_valid = ffree(h);
     if (sweep_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a TMA-staged sweep timed out waiting for its loads");
+    if (coop_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a grid barrier of the persistent V-cycle timed out");
     if (iters_done) *iters_done = k;
     if (final_res) *final_res = res;
     if (std::isnan(res) || std::isinf(res)) return fail(h, PMG_ERR_DIVERGED, "collocation residual is NaN/Inf");
@@ -1533,6 +1557,7 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
     h->q_valid = ffree(h);
     PMG_CUDA(h, cudaStreamSynchronize(h->stream));
     if (sweep_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a TMA-staged sweep timed out waiting for its loads");
+    if (coop_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a grid barrier of the persistent V-cycle timed out");
     if (!h->g_iter.recs.empty() && use_graphs(h)) PMG_RET(harvest(h, h->g_iter));
     res = 0.0;
     for (int p = 0; p < h->P; ++p) {
@@ -1689,7 +1714,7 @@ const char *pfasst_mg_kernel_name(int kernel) {
                                        "resid_pt", "fine_rhs_residual", "rbgs_sweep3d_zero",
                                        "rbgs_sweep3d_upd", "net_resid", "net_layer1", "net_layer2_mma",
                                        "net_layer3", "net_loss", "net_layer3_bwd", "net_layer2_mma_bwd",
-                                       "net_wgrad", "net_adam", "net_sample", "vcycle_tail"};
+                                       "net_wgrad", "net_adam", "net_sample", "vcycle_tail", "vcycle_coop"};
   return kernel >= 0 && kernel < K_COUNT ? names[kernel] : "unknown";
 }
 
@@ -1840,6 +1865,8 @@ int pfasst_mg_helmholtz_solve(const pmg_grid *grid, double c, int batch, const d
   if (hred) cudaFreeHost(hred);
   if (hactive) cudaFreeHost(hactive);
   if (result == PMG_OK && e != cudaSuccess) result = fail(nullptr, PMG_ERR_CUDA, cudaGetErrorString(e));
+  if (result == PMG_OK && coop_timeouts())
+    result = fail(nullptr, PMG_ERR_TIMEOUT, "a grid barrier of the persistent V-cycle timed out");
   return result;
 }
 
@@ -1871,7 +1898,11 @@ int validate_problem(const pmg_problem_desc &d, const pmg_options *o, std::strin
 pmg_ctx *make_kid(const pmg_problem_desc &d, const pmg_options &o) {
   pmg_nodes_desc fn{d.nodes, 0};
   pmg_levels lv{1, {0, 0}};
-  return make_ctx(&d.grid, &fn, &lv, d.nu, d.dt, 1, &o);
+  // the problems of a batch run side by side on graph branches: a persistent V-cycle
+  // that holds every SM would serialise them, so they keep the per-level launches
+  pmg_options ko = o;
+  ko.single_grid_vcycle = 0;
+  return make_ctx(&d.grid, &fn, &lv, d.nu, d.dt, 1, &ko);
 }
 
 // one time step of one problem (captured into the batch graph)

@@ -116,7 +116,7 @@ enum KernelId {
   K_APPLY_A, K_SF_RHS, K_FAS, K_INTERP, K_COLLOC, K_COPY, K_PACK, K_UNPACK, K_INTERP_T,
   K_RBGS3D, K_RESRESTRICT3D, K_PROLONG3D, K_RESID_PT, K_FINE_RHS, K_RBGS3D_ZERO, K_RBGS3D_UPD,
   K_NET_RESID, K_NET_L1, K_NET_L2, K_NET_L3, K_NET_LOSS, K_NET_L3BWD, K_NET_L2BWD, K_NET_WGRAD, K_NET_ADAM,
-  K_NET_SAMPLE, K_VTAIL, K_COUNT
+  K_NET_SAMPLE, K_VTAIL, K_VCOOP, K_COUNT
 };
 
 // CUDA-event timing of individual launches on the launching stream (only launches
@@ -331,6 +331,18 @@ cudaError_t k_pack(const Launch &L, const Grid &g, const double *dense, long lon
 cudaError_t k_unpack(const Launch &L, const Grid &g, const double *pad, long long spad, double *dense,
                      long long sdense, int batch);
 
+
+// ---- all V-cycles of a single-grid sub-step solve in one persistent launch (vcycle_coop.cu) ----
+// red-black Gauss-Seidel (nu1 >= 1), 2D or 3D, second order
+bool vcycle_coop_supported(const Grid &g0, int levels, int smoother_rbgs, int nu1);
+// nv V(nu1, nu2)-cycles for (I - c Lap) e = f[0] on levels lev[0..nlev-1] (one grid each,
+// e[l], f[l] in the precision pr; e[0] from zero), then u += e[0] if u is not null;
+// count: a device word for the grid barrier (zeroed here, on the stream)
+cudaError_t k_vcycle_coop(const Launch &L, const Grid *lev, int nlev, Prec pr, double c, double omega, int nu1,
+                          int nu2, int nv, void *const *e, void *const *f, const void *minv, double *u,
+                          unsigned *count);
+// nonzero if a grid barrier of the persistent V-cycle timed out since the last call (clears it)
+int coop_timeouts();
 
 // ---- bottom of a V-cycle in one launch (tail.cu) ----
 // levels top .. 3^d of one grid per CTA in shared memory: offsets (elements) of the

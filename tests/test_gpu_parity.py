@@ -727,3 +727,41 @@ def test_device_side_iteration_loop_matches_host_loop(dim, n, P, nl, precision):
     assert np.array_equal(g[3], h[3])
     assert g[4] == h[4] == pmg.PMG_NOT_CONVERGED and g[5] == h[5] == 3 and g[6] == h[6]
     assert np.array_equal(g[7], h[7])
+
+
+@pytest.mark.parametrize("dim,n,P,precision,nl", [(3, 63, 4, 1, 2), (3, 31, 3, 0, 2), (2, 127, 4, 0, 2),
+                                                  (3, 31, 2, 1, 3), (3, 63, 1, 0, 1)])
+def test_persistent_single_grid_vcycles_match_per_level_launches(dim, n, P, precision, nl):
+    """The V-cycles of single-grid sub-step solves (the serial coarse chain; every solve of
+    a one-slice handle) as one persistent cooperative launch with grid-wide barriers give
+    the same iterates, bit for bit, as one launch per sweep, restriction and prolongation
+    (point smoothers: autotuning off), FP64 and mixed, two and three levels."""
+    rng = np.random.default_rng(dim * 10 + n)
+    u0 = rng.standard_normal(n ** dim)
+    out = []
+    for coop in (1, 0):
+        s = pmg.PFASSTSolver(dim, n, 5, 3 if nl >= 2 else 0, P, 0.5, 0.002, nlevels=nl,
+                             coarsest_nodes=2 if nl == 3 else 0, smoother=1, omega=1.0, vcycles=2,
+                             precision=precision, autotune=0, single_grid_vcycle=coop)
+        s.set_initial(u0)
+        s.iterate(3, 0.0)
+        out.append([s.state(l) for l in range(nl)] + [s.residual()])
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_persistent_single_grid_vcycles_in_the_standalone_solve():
+    """pfasst_mg_helmholtz_solve on one grid (batch 1) takes the persistent V-cycles: against
+    the oracle's V-cycles to 1e-12."""
+    dim, n, vc = 3, 31, 2
+    c = 0.37 / (n + 1) ** 2 * 4
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((1, n ** dim))
+    u = rng.standard_normal((1, n ** dim))
+    opt = pmg.pfasst_mg_default_options(smoother=1, omega=1.0, vcycles=vc)
+    assert opt.single_grid_vcycle == 1
+    ut = torch.tensor(u, device="cuda")
+    pmg.pfasst_mg_helmholtz_solve(pmg.pmg_grid(dim, n), c, 1, torch.tensor(b, device="cuda"), ut, opt)
+    want = O.mg_solve(O.MGParams(smoother=1, omega=1.0, vcycles=vc), dim, n, c, b[0], u[0])[0]
+    assert rel(ut.cpu().numpy(), want[None]) < FP64_TOL
