@@ -783,12 +783,14 @@ __global__ void __launch_bounds__(256, 4) fine_rhs_chain_kernel(Grid g, ResCoef 
       if (smax[b] != 0ULL) atomicMax(res + b, smax[b]);
 }
 
-// FAS restriction with the fine F evaluated from U_f at the coarse points only
+// FAS restriction with the fine F evaluated from U_f at the coarse points only.  cf.dtQf
+// holds (nu / h_f^2) dt Q_fine here (scaled by the launcher), so the fine Laplacians enter
+// unscaled; a coarse node whose quadrature rows are zero (t = 0) gets tau = 0 directly.
 template <int DIM, int SF, int SC>
 __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double *__restrict__ Uf, long long sfine,
                                       double *__restrict__ Uc, double *__restrict__ Fc, double *__restrict__ tau,
                                       double *__restrict__ Uc0, long long scoarse, int batch) {
-  const double ac = cf.nu * gc.ih2, af = cf.nu * gf.ih2;
+  const double ac = cf.nu * gc.ih2;
   const long long plf = (long long)gf.ny * gf.pitch;
   PMG_FOR_POINTS(gc, batch) {
     PMG_POINT(gc);
@@ -800,7 +802,7 @@ __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double
     for (int in = 0; in < NF; ++in) {
       if (SF == 0 && in >= cf.sf) break;
       const double *U = Uf + b * sfine + in * gf.slab;
-      Ffv[in] = af * lap_h2<DIM>(U, gf, fi, fj, fk, fo);
+      Ffv[in] = lap_h2<DIM>(U, gf, fi, fj, fk, fo);  // h_f^2 Lap_h U (nu / h_f^2 is in dtQf)
     }
 #pragma unroll
     for (int jn = 0; jn < NC; ++jn) {
@@ -819,6 +821,10 @@ __global__ void fas_restrict_u_kernel(Grid gf, Grid gc, FASCoef cf, const double
 #pragma unroll
     for (int jn = 0; jn < NC; ++jn) {
       if (SC == 0 && jn >= cf.sc) break;
+      if (cf.zero_rows & (1 << jn)) {  // uniform over the launch
+        tau[b * scoarse + jn * gc.slab + off] = 0.0;
+        continue;
+      }
       double If = 0.0;
 #pragma unroll
       for (int in = 0; in < NF; ++in)
@@ -1192,16 +1198,27 @@ cudaError_t k_fas_restrict_u(const Launch &L, const Grid &gf, const Grid &gc, co
   dim3 gr, bl;
   config(gc, batch, gr, bl);
   Scope sc(L, K_FAS, gc, batch, 0);
+  FASCoef cs = cf;  // fine weights times nu / h_f^2; rows with no quadrature weight flagged
+  cs.zero_rows = 0;
+  for (int j = 0; j < cf.sc; ++j) {
+    bool zero = true;
+    for (int i = 0; i < cf.sf; ++i) {
+      zero = zero && cf.dtQf[j][i] == 0.0;
+      cs.dtQf[j][i] = cf.nu * gf.ih2 * cf.dtQf[j][i];
+    }
+    for (int i = 0; i < cf.sc; ++i) zero = zero && cf.dtQc[j][i] == 0.0;
+    if (zero) cs.zero_rows |= 1 << j;
+  }
   // node counts as compile-time constants: coarse nodes are a subset of the fine ones
 #define PMG_FAS(SF_, SC_)                                                                                        \
   if (cf.sf == SF_ && cf.sc == SC_) {                                                                            \
-    PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D, SF_, SC_><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Fc, \
+    PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D, SF_, SC_><<<gr, bl, 0, L.stream>>>(gf, gc, cs, Uf, sfine, Uc, Fc, \
                                                                                          tau, Uc0, scoarse, batch))); \
     return sc.done();                                                                                          \
   }
   PMG_FAS(5, 3) PMG_FAS(3, 2) PMG_FAS(5, 2) PMG_FAS(9, 3)
 #undef PMG_FAS
-  PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D, 0, 0><<<gr, bl, 0, L.stream>>>(gf, gc, cf, Uf, sfine, Uc, Fc, tau,
+  PMG_DIM_SWITCH(gf.dim, (fas_restrict_u_kernel<D, 0, 0><<<gr, bl, 0, L.stream>>>(gf, gc, cs, Uf, sfine, Uc, Fc, tau,
                                                                                     Uc0, scoarse, batch)))
   return sc.done();
 }

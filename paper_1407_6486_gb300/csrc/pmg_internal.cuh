@@ -235,6 +235,7 @@ struct FASCoef {
   double dtQf[kMaxNodes][kMaxNodes];     // rows map[j] of dt * Q_fine
   double dtQc[kMaxNodes][kMaxNodes];     // dt * Q_coarse
   double nu;
+  int zero_rows;                         // bit j: rows j of dtQf and dtQc are zero, so tau_j = 0
 };
 
 // coarse-correction interpolation: U_f,m += sum_j T[m][j] I_x (U_c,j - U_c0,j)

@@ -4,7 +4,7 @@
 // A single 127^3 grid does not fill the GPU, and one V-cycle with red-black smoothing
 // is about 30 launches of which most work on grids of 31^3 and smaller, so the coarse
 // chain is bound by launch latency.  Here every CTA stays resident for the whole solve
-// (cooperative launch: all CTAs co-resident, one of 512 threads per SM) and the phases of the V-cycles
+// (cooperative launch: all CTAs co-resident, one per SM) and the phases of the V-cycles
 // -- each colour of each smoothing sweep, the residual with full weighting, the exact
 // 3^d solve, the prolongation -- are separated by a grid-wide barrier instead of kernel
 // boundaries.  The per-point arithmetic is that of the per-level kernels in kernels.cu
@@ -30,13 +30,15 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   return v;
 }
 
-// grid-wide barrier number `b` (0, 1, 2, ... in program order); false on a timeout
+// grid-wide barrier number `b` (0, 1, 2, ... in program order); false on a timeout.
+// bar.sync orders the CTA's writes before thread 0's release-add; thread 0's acquire
+// loads and the closing bar.sync order every later read of the CTA after the other CTAs'
+// writes
 __device__ __forceinline__ bool grid_sync(unsigned *count, unsigned b) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     const unsigned target = (b + 1u) * gridDim.x;
     if (ld_acquire_u32(count) < target) {
       const long long t0 = clock64();
@@ -45,10 +47,8 @@ __device__ __forceinline__ bool grid_sync(unsigned *count, unsigned b) {
           ok = 0;
           break;
         }
-        __nanosleep(40);
       }
     }
-    __threadfence();
   }
   return __syncthreads_and(ok) != 0;
 }
@@ -111,14 +111,24 @@ __device__ __forceinline__ int lin_taps_c(int i, int nc, int *idx, float *w) {
   return t;
 }
 
+// threads per CTA: 768 in FP32 (as many as the registers allow without spills: more warps
+// to cover the L2 latency of the stencil loads), 512 in FP64
+template <typename T>
+constexpr int coop_threads() { return sizeof(T) == 4 ? 768 : 512; }
+
+// grids of at most this many points per axis run in CTA 0 alone, with block barriers
+constexpr int kCoopLocalN = 15;
+
 template <int DIM, typename T>
-__global__ void __launch_bounds__(512, 1) vcycle_coop_kernel(CoopArgs A) {
+__global__ void __launch_bounds__(coop_threads<T>(), 1) vcycle_coop_kernel(CoopArgs A) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned nb = 0;  // barriers passed
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, gnwarps = (gridDim.x * blockDim.x) >> 5;
+  const int lwarp = threadIdx.x >> 5, lnwarps = blockDim.x >> 5;
+  unsigned nb = 0;  // grid barriers passed
   const T omega = (T)A.omega;
-  // one red-black colour on level l (first: the first sweep from e = 0)
-  auto colour_pass = [&](int l, int colour, bool first) {
+  // one red-black colour on level l over the points of that colour (first: the first
+  // sweep from e = 0, which also clears the other colour); two points per lane in flight
+  auto colour_pass = [&](int l, int colour, bool first, int warp, int nwarps) {
     const CoopLevel &v = A.lev[l];
     T *e = (T *)v.e;
     const T *f = (const T *)v.f;
@@ -128,24 +138,30 @@ __global__ void __launch_bounds__(512, 1) vcycle_coop_kernel(CoopArgs A) {
       int j, k;
       row_of<DIM>(r, v.n, j, k);
       const long long ro = ((long long)k * v.n + j) * v.pitch;
-      for (int i = lane; i < v.n; i += 32) {
-        const long long o = ro + i;
-        const int par = (i + j + k + DIM) & 1;
-        if (par != colour) {
-          if (first && colour == 0) e[o] = T(0);
-          continue;
+      if (first && colour == 0) {
+        for (int i = lane; i < v.n; i += 32) {
+          const long long o = ro + i;
+          e[o] = ((i + j + k + DIM) & 1) == 0 ? omega * (f[o] / D) : T(0);
         }
-        if (first && colour == 0) {
-          e[o] = omega * (f[o] / D);
-          continue;
+        continue;
+      }
+      const int i0 = (colour + j + k + DIM) & 1;  // first x of this colour in the row
+      for (int i = i0 + 2 * lane; i < v.n; i += 128) {
+        const int i2 = i + 64;
+        const long long o = ro + i, o2 = ro + i2;
+        const T g1 = (f[o] + a * nbsum_c<DIM>(e, v.n, v.pitch, i, j, k, o)) / D;
+        T g2 = T(0), e2 = T(0);
+        if (i2 < v.n) {
+          g2 = (f[o2] + a * nbsum_c<DIM>(e, v.n, v.pitch, i2, j, k, o2)) / D;
+          e2 = e[o2];
         }
-        const T gs = (f[o] + a * nbsum_c<DIM>(e, v.n, v.pitch, i, j, k, o)) / D;
-        e[o] = (T(1) - omega) * e[o] + omega * gs;
+        e[o] = (T(1) - omega) * e[o] + omega * g1;
+        if (i2 < v.n) e[o2] = (T(1) - omega) * e2 + omega * g2;
       }
     }
   };
   // fc = full weighting of f - (I - c Lap) e from level l onto level l + 1
-  auto restrict_pass = [&](int l) {
+  auto restrict_pass = [&](int l, int warp, int nwarps) {
     const CoopLevel &vf = A.lev[l], &vc = A.lev[l + 1];
     const T a = (T)A.c * (T)vf.ih2;
     const T w3[3] = {T(0.25), T(0.5), T(0.25)};
@@ -174,7 +190,7 @@ __global__ void __launch_bounds__(512, 1) vcycle_coop_kernel(CoopArgs A) {
     }
   };
   // e_l += P e_{l+1} (d-linear)
-  auto prolong_pass = [&](int l) {
+  auto prolong_pass = [&](int l, int warp, int nwarps) {
     const CoopLevel &vf = A.lev[l], &vc = A.lev[l + 1];
     T *e = (T *)vf.e;
     const T *ec = (const T *)vc.e;
@@ -199,15 +215,15 @@ __global__ void __launch_bounds__(512, 1) vcycle_coop_kernel(CoopArgs A) {
       }
     }
   };
-  // exact solve on the coarsest level: e = Minv f
-  auto coarse_pass = [&]() {
+  // exact solve on the coarsest level: e = Minv f (threads of the given warps)
+  auto coarse_pass = [&](int warp, int nwarps) {
     constexpr int N3 = DIM == 2 ? 9 : 27;
     const CoopLevel &v = A.lev[A.L - 1];
     const T *minv = (const T *)A.minv, *f = (const T *)v.f;
     T *e = (T *)v.e;
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gt < N3) {
-      const int p = gt, pi = p % 3, pj = (p / 3) % 3, pk = p / 9;
+    const int t = warp * 32 + lane;
+    if (t < N3) {
+      const int p = t, pi = p % 3, pj = (p / 3) % 3, pk = p / 9;
       T acc = T(0);
       for (int q = 0; q < N3; ++q) {
         const int qi = q % 3, qj = (q / 3) % 3, qk = q / 9;
@@ -216,30 +232,57 @@ __global__ void __launch_bounds__(512, 1) vcycle_coop_kernel(CoopArgs A) {
       e[((long long)pk * v.n + pj) * v.pitch + pi] = acc;
     }
   };
+  // the first level that CTA 0 handles alone (its grid and every coarser one are small)
+  int lb = A.L - 1;
+  while (lb > 0 && A.lev[lb - 1].n <= kCoopLocalN) --lb;
+  const bool cta0 = blockIdx.x == 0;
   bool ok = true;
   for (int cyc = 0; cyc < A.nv && ok; ++cyc) {
-    for (int l = 0; l + 1 < A.L && ok; ++l) {
+    // down, grid-wide, on the levels above lb
+    for (int l = 0; l < lb && ok; ++l) {
       const bool zero = l > 0 || cyc == 0;
       for (int s = 0; s < A.nu1 && ok; ++s)
         for (int colour = 0; colour < 2 && ok; ++colour) {
-          colour_pass(l, colour, zero && s == 0);
+          colour_pass(l, colour, zero && s == 0, gwarp, gnwarps);
           ok = grid_sync(A.count, nb++);
         }
       if (ok) {
-        restrict_pass(l);
+        restrict_pass(l, gwarp, gnwarps);
         ok = grid_sync(A.count, nb++);
       }
     }
-    if (ok) {
-      coarse_pass();
-      ok = grid_sync(A.count, nb++);
+    // the bottom of the cycle from level lb, in CTA 0 with block barriers
+    if (ok && cta0) {
+      for (int l = lb; l + 1 < A.L; ++l) {
+        const bool zero = l > 0 || cyc == 0;
+        for (int s = 0; s < A.nu1; ++s)
+          for (int colour = 0; colour < 2; ++colour) {
+            colour_pass(l, colour, zero && s == 0, lwarp, lnwarps);
+            __syncthreads();
+          }
+        restrict_pass(l, lwarp, lnwarps);
+        __syncthreads();
+      }
+      coarse_pass(lwarp, lnwarps);
+      __syncthreads();
+      for (int l = A.L - 2; l >= lb; --l) {
+        prolong_pass(l, lwarp, lnwarps);
+        __syncthreads();
+        for (int s = 0; s < A.nu2; ++s)
+          for (int colour = 0; colour < 2; ++colour) {
+            colour_pass(l, colour, false, lwarp, lnwarps);
+            __syncthreads();
+          }
+      }
     }
-    for (int l = A.L - 2; l >= 0 && ok; --l) {
-      prolong_pass(l);
+    if (ok) ok = grid_sync(A.count, nb++);
+    // up, grid-wide, on the levels above lb
+    for (int l = lb - 1; l >= 0 && ok; --l) {
+      prolong_pass(l, gwarp, gnwarps);
       ok = grid_sync(A.count, nb++);
       for (int s = 0; s < A.nu2 && ok; ++s)
         for (int colour = 0; colour < 2 && ok; ++colour) {
-          colour_pass(l, colour, false);
+          colour_pass(l, colour, false, gwarp, gnwarps);
           ok = grid_sync(A.count, nb++);
         }
     }
@@ -252,7 +295,7 @@ __global__ void __launch_bounds__(512, 1) vcycle_coop_kernel(CoopArgs A) {
     const CoopLevel &v = A.lev[0];
     const T *e = (const T *)v.e;
     const int rows = DIM == 3 ? v.n * v.n : v.n;
-    for (int r = warp; r < rows; r += nwarps) {
+    for (int r = gwarp; r < rows; r += gnwarps) {
       int j, k;
       row_of<DIM>(r, v.n, j, k);
       const long long ro = ((long long)k * v.n + j) * v.pitch;
@@ -268,11 +311,11 @@ int coop_blocks() {
     int dev = 0, sms = 0, per = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, vcycle_coop_kernel<DIM, T>, 512, 0) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, vcycle_coop_kernel<DIM, T>, coop_threads<T>(), 0) != cudaSuccess) {
       cudaGetLastError();
       blocks = 0;
     } else {
-      blocks = (coop && per >= 1) ? sms : 0;  // one CTA of 512 threads per SM
+      blocks = (coop && per >= 1) ? sms : 0;  // one CTA per SM
     }
   }
   return blocks;
@@ -314,7 +357,7 @@ cudaError_t k_vcycle_coop(const Launch &L, const Grid *lev, int nlev, Prec pr, d
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeCooperative;
   attr.val.cooperative = 1;
-  cfg.blockDim = dim3(512);
+  cfg.blockDim = dim3(pr == F32 ? coop_threads<float>() : coop_threads<double>());
   cfg.dynamicSmemBytes = 0;
   cfg.stream = L.stream;
   cfg.attrs = &attr;
