@@ -401,8 +401,9 @@ void plan_hier(Plan &pl, Hier &H, int dim, int n, int batch, Prec pr, int smooth
     if (l >= first) {
       pl.add(&H.e[l], bytes);
       pl.add(&H.f[l], bytes);
-      // second correction buffer: Jacobi ping-pong, or the out-of-place fused 3D sweep
-      if (smoother == PMG_SMOOTHER_JACOBI || dim == 3) pl.add(&H.e2[l], bytes);
+      // second correction buffer: Jacobi ping-pong, the out-of-place fused 3D sweep, or
+      // the residual scratch of the persistent single-grid V-cycle (2D)
+      if (smoother == PMG_SMOOTHER_JACOBI || dim >= 2) pl.add(&H.e2[l], bytes);
     }
     nl = (nl - 1) / 2;
   }
@@ -614,13 +615,14 @@ int solve_substep(MGCtx &M, int l0, int B, double c, const void *minv, const dou
     for (int l = l0; M.net && l < H.L; ++l) net_here = net_here || M.net->on[l];
     if (B == 1 && o.single_grid_vcycle && !net_here &&
         vcycle_coop_supported(g, H.L - l0, o.smoother == PMG_SMOOTHER_RBGS, o.nu1)) {
-      void *ev[kMaxLevels], *fv[kMaxLevels];
+      void *ev[kMaxLevels], *fv[kMaxLevels], *rv[kMaxLevels];
       for (int l = l0; l < H.L; ++l) {
         ev[l - l0] = H.e[l];
         fv[l - l0] = H.f[l];
+        rv[l - l0] = H.e2[l];  // free during a red-black V-cycle: the residual scratch
       }
-      PMG_CUDA(M.h, k_vcycle_coop(M.L, &H.lev[l0], H.L - l0, H.pr, c, o.omega, o.nu1, o.nu2, o.vcycles, ev, fv, minv,
-                                  u1, H.count));
+      PMG_CUDA(M.h, k_vcycle_coop(M.L, &H.lev[l0], H.L - l0, H.pr, c, o.omega, o.nu1, o.nu2, o.vcycles, ev, fv, rv,
+                                  minv, u1, H.count));
       if (cycles) *cycles = o.vcycles;
       return PMG_OK;
     }

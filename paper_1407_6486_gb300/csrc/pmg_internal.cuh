@@ -337,11 +337,12 @@ cudaError_t k_unpack(const Launch &L, const Grid &g, const double *pad, long lon
 // red-black Gauss-Seidel (nu1 >= 1), 2D or 3D, second order
 bool vcycle_coop_supported(const Grid &g0, int levels, int smoother_rbgs, int nu1);
 // nv V(nu1, nu2)-cycles for (I - c Lap) e = f[0] on levels lev[0..nlev-1] (one grid each,
-// e[l], f[l] in the precision pr; e[0] from zero), then u += e[0] if u is not null;
+// e[l], f[l] and the residual scratch r[l] in the precision pr; e[0] from zero), then
+// u += e[0] if u is not null;
 // count: a device word for the grid barrier (zeroed here, on the stream)
 cudaError_t k_vcycle_coop(const Launch &L, const Grid *lev, int nlev, Prec pr, double c, double omega, int nu1,
-                          int nu2, int nv, void *const *e, void *const *f, const void *minv, double *u,
-                          unsigned *count);
+                          int nu2, int nv, void *const *e, void *const *f, void *const *r, const void *minv,
+                          double *u, unsigned *count);
 // nonzero if a grid barrier of the persistent V-cycle timed out since the last call (clears it)
 int coop_timeouts();
 

@@ -5,10 +5,13 @@
 // is about 30 launches of which most work on grids of 31^3 and smaller, so the coarse
 // chain is bound by launch latency.  Here every CTA stays resident for the whole solve
 // (cooperative launch: all CTAs co-resident, one per SM) and the phases of the V-cycles
-// -- each colour of each smoothing sweep, the residual with full weighting, the exact
+// -- each colour of each smoothing sweep, the residual, its full weighting, the exact
 // 3^d solve, the prolongation -- are separated by a grid-wide barrier instead of kernel
 // boundaries.  The per-point arithmetic is that of the per-level kernels in kernels.cu
-// (same formulas, same order of the sums), so the results are bitwise the same.
+// (same formulas, same order of the sums), so the results are bitwise the same.  The
+// residual of a level is formed once per fine point into a scratch array and weighted in
+// a second phase: evaluated inside the weighting, as the per-level kernel does, each
+// coarse point would chain 27 stencils of L2 loads on far too few warps to hide them.
 //
 // Grid barrier: one 32-bit counter in device memory, zeroed before the launch; barrier
 // number b is passed once the counter reaches (b + 1) * gridDim.x.  Every wait is
@@ -58,7 +61,7 @@ struct CoopLevel {
   int n, pitch;       // interior points per axis, row pitch (n + 1)
   long long slab;     // elements of one grid function
   double ih2;         // 1 / h^2 of the level
-  void *e, *f;
+  void *e, *f, *r;    // correction, right-hand side, residual scratch
 };
 
 struct CoopArgs {
@@ -160,12 +163,30 @@ __global__ void __launch_bounds__(coop_threads<T>(), 1) vcycle_coop_kernel(CoopA
       }
     }
   };
-  // fc = full weighting of f - (I - c Lap) e from level l onto level l + 1
-  auto restrict_pass = [&](int l, int warp, int nwarps) {
-    const CoopLevel &vf = A.lev[l], &vc = A.lev[l + 1];
+  // residual r = f - (I - c Lap) e on level l, into its scratch array (the same
+  // expression as the per-level restriction kernel evaluates at every fine point)
+  auto residual_pass = [&](int l, int warp, int nwarps) {
+    const CoopLevel &vf = A.lev[l];
     const T a = (T)A.c * (T)vf.ih2;
-    const T w3[3] = {T(0.25), T(0.5), T(0.25)};
     const T *e = (const T *)vf.e, *fp = (const T *)vf.f;
+    T *rs = (T *)vf.r;
+    const int rows = DIM == 3 ? vf.n * vf.n : vf.n;
+    for (int r = warp; r < rows; r += nwarps) {
+      int j, k;
+      row_of<DIM>(r, vf.n, j, k);
+      const long long ro = ((long long)k * vf.n + j) * vf.pitch;
+      for (int i = lane; i < vf.n; i += 32) {
+        const long long fo = ro + i;
+        const T ec = e[fo];
+        rs[fo] = fp[fo] - (ec - a * (nbsum_c<DIM>(e, vf.n, vf.pitch, i, j, k, fo) - T(2 * DIM) * ec));
+      }
+    }
+  };
+  // fc = full weighting of the residual of level l onto level l + 1
+  auto weight_pass = [&](int l, int warp, int nwarps) {
+    const CoopLevel &vf = A.lev[l], &vc = A.lev[l + 1];
+    const T w3[3] = {T(0.25), T(0.5), T(0.25)};
+    const T *rs = (const T *)vf.r;
     T *fc = (T *)vc.f;
     const int rows = DIM == 3 ? vc.n * vc.n : vc.n;
     for (int r = warp; r < rows; r += nwarps) {
@@ -173,17 +194,17 @@ __global__ void __launch_bounds__(coop_threads<T>(), 1) vcycle_coop_kernel(CoopA
       row_of<DIM>(r, vc.n, j, k);
       for (int i = lane; i < vc.n; i += 32) {
         T acc = T(0);
+#pragma unroll
         for (int cz = (DIM >= 3 ? -1 : 0); cz <= (DIM >= 3 ? 1 : 0); ++cz)
+#pragma unroll
           for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
               const int fi = 2 * i + 1 + cx, fj = 2 * j + 1 + cy, fk = DIM >= 3 ? 2 * k + 1 + cz : 0;
-              const long long fo = ((long long)fk * vf.n + fj) * vf.pitch + fi;
-              const T ec = e[fo];
-              const T rr = fp[fo] - (ec - a * (nbsum_c<DIM>(e, vf.n, vf.pitch, fi, fj, fk, fo) - T(2 * DIM) * ec));
               T w = w3[cx + 1];
               w *= w3[cy + 1];
               if (DIM >= 3) w *= w3[cz + 1];
-              acc += w * rr;
+              acc += w * rs[((long long)fk * vf.n + fj) * vf.pitch + fi];
             }
         fc[((long long)k * vc.n + j) * vc.pitch + i] = acc;
       }
@@ -247,7 +268,11 @@ __global__ void __launch_bounds__(coop_threads<T>(), 1) vcycle_coop_kernel(CoopA
           ok = grid_sync(A.count, nb++);
         }
       if (ok) {
-        restrict_pass(l, gwarp, gnwarps);
+        residual_pass(l, gwarp, gnwarps);
+        ok = grid_sync(A.count, nb++);
+      }
+      if (ok) {
+        weight_pass(l, gwarp, gnwarps);
         ok = grid_sync(A.count, nb++);
       }
     }
@@ -260,7 +285,9 @@ __global__ void __launch_bounds__(coop_threads<T>(), 1) vcycle_coop_kernel(CoopA
             colour_pass(l, colour, zero && s == 0, lwarp, lnwarps);
             __syncthreads();
           }
-        restrict_pass(l, lwarp, lnwarps);
+        residual_pass(l, lwarp, lnwarps);
+        __syncthreads();
+        weight_pass(l, lwarp, lnwarps);
         __syncthreads();
       }
       coarse_pass(lwarp, lnwarps);
@@ -329,8 +356,8 @@ bool vcycle_coop_supported(const Grid &g0, int levels, int smoother_rbgs, int nu
 }
 
 cudaError_t k_vcycle_coop(const Launch &L, const Grid *lev, int nlev, Prec pr, double c, double omega, int nu1,
-                          int nu2, int nv, void *const *e, void *const *f, const void *minv, double *u,
-                          unsigned *count) {
+                          int nu2, int nv, void *const *e, void *const *f, void *const *r, const void *minv,
+                          double *u, unsigned *count) {
   CoopArgs A;
   A.L = nlev;
   A.c = c;
@@ -348,6 +375,7 @@ cudaError_t k_vcycle_coop(const Launch &L, const Grid *lev, int nlev, Prec pr, d
     A.lev[l].ih2 = lev[l].ih2;
     A.lev[l].e = e[l];
     A.lev[l].f = f[l];
+    A.lev[l].r = r[l];
   }
   Scope sc(L, K_VCOOP, lev[0], 1, pr);
   cudaError_t err = cudaMemsetAsync(count, 0, sizeof(unsigned), L.stream);
