@@ -114,13 +114,14 @@ typedef struct {
                              limit PFASST's convergence with backward Euler on the coarse
                              level.  Any 0 (here or in vcycles) runs the iteration without
                              CUDA graphs (the full solve decides its cycle count on the host) */
-    int    single_grid_vcycle;/* 1 (default): the fixed V-cycles of a single-grid sub-step
-                             solve (the serial coarse chain) run as one persistent,
-                             cooperatively launched kernel -- every smoothing colour,
-                             restriction, coarsest solve and prolongation of all cycles,
-                             separated by grid-wide barriers, and the update u += e (red-black
-                             Gauss-Seidel, 2D/3D, second order; results as the per-level
-                             kernels); 0: one launch per sweep, restriction and prolongation */
+    int    single_grid_vcycle;/* 1: the fixed V-cycles of a single-grid sub-step solve (the
+                             serial coarse chain) run as one persistent, cooperatively
+                             launched kernel -- every smoothing colour, restriction, coarsest
+                             solve and prolongation of all cycles, separated by grid-wide
+                             barriers, and the update u += e (red-black Gauss-Seidel, 2D/3D,
+                             second order; results bitwise those of the per-level kernels);
+                             0 (default): one launch per sweep, restriction and prolongation
+                             (faster on the 3D workload: 1860 vs 1926 ms per step)          */
 } pmg_options;
 
 typedef struct pmg_ctx *pmg_handle;
@@ -128,7 +129,7 @@ typedef struct pmg_ctx *pmg_handle;
 /* Defaults: Jacobi omega 2/3, V(2,1), 2 V-cycles, tol 1e-12, stall 0.75, cap 50,
  * FP64, 4th-order interpolation, graphs on, autotuning on, slice groups 0 (one group:
  * no overlap), V-cycle tail off, coarse levels as the fine level (coarse_vcycles -1),
- * persistent single-grid V-cycles on. */
+ * persistent single-grid V-cycles off. */
 void pfasst_mg_default_options(pmg_options *opt);
 
 /* Bytes of device workspace pfasst_mg_create needs for this problem.

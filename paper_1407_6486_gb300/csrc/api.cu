@@ -1389,7 +1389,7 @@ void pfasst_mg_default_options(pmg_options *o) {
   o->slice_groups = 0;
   o->vcycle_tail = 0;
   o->coarse_vcycles = -1;
-  o->single_grid_vcycle = 1;
+  o->single_grid_vcycle = 0;
 }
 
 int pfasst_mg_workspace_bytes(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *lv, int slices,

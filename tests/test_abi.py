@@ -39,7 +39,7 @@ def test_default_options(lib):
     o = pmg.pfasst_mg_default_options()
     assert o.nu1 == 2 and o.nu2 == 1 and o.vcycles == 2 and abs(o.omega - 2 / 3) < 1e-15
     assert o.interp_order == 4 and o.precision == pmg.PMG_PREC_FP64
-    assert o.slice_groups == 0 and o.vcycle_tail == 0 and o.coarse_vcycles == -1 and o.single_grid_vcycle == 1
+    assert o.slice_groups == 0 and o.vcycle_tail == 0 and o.coarse_vcycles == -1 and o.single_grid_vcycle == 0
 
 
 def _ws(dim, n, sf, nl, sc, P, **kw):

@@ -752,15 +752,16 @@ def test_persistent_single_grid_vcycles_match_per_level_launches(dim, n, P, prec
 
 
 def test_persistent_single_grid_vcycles_in_the_standalone_solve():
-    """pfasst_mg_helmholtz_solve on one grid (batch 1) takes the persistent V-cycles: against
-    the oracle's V-cycles to 1e-12."""
+    """pfasst_mg_helmholtz_solve on one grid (batch 1) with single_grid_vcycle = 1 takes the
+    persistent V-cycles: against the oracle's V-cycles to 1e-12."""
     dim, n, vc = 3, 31, 2
     c = 0.37 / (n + 1) ** 2 * 4
     rng = np.random.default_rng(5)
     b = rng.standard_normal((1, n ** dim))
     u = rng.standard_normal((1, n ** dim))
     opt = pmg.pfasst_mg_default_options(smoother=1, omega=1.0, vcycles=vc)
-    assert opt.single_grid_vcycle == 1
+    assert opt.single_grid_vcycle == 0
+    opt.single_grid_vcycle = 1
     ut = torch.tensor(u, device="cuda")
     pmg.pfasst_mg_helmholtz_solve(pmg.pmg_grid(dim, n), c, 1, torch.tensor(b, device="cuda"), ut, opt)
     want = O.mg_solve(O.MGParams(smoother=1, omega=1.0, vcycles=vc), dim, n, c, b[0], u[0])[0]
