@@ -174,6 +174,8 @@ def make_workload(name):
         return inputs.heat3d_c3(n=63, slices=8)
     if name == "heat3d-mid":  # small enough for ncu replays, large enough for the tiled kernels
         return inputs.heat3d_c3(n=127, slices=12)
+    if name == "heat3d-255x4":  # the fine grid of the 3D workload on 4 slices: ncu case of the 256-wide rows
+        return inputs.heat3d_c3(n=255, slices=4)
     if name == "heat2d":
         return inputs.heat2d_c2(vcycles=2, precision=1)
     raise SystemExit(f"unknown workload {name}")
@@ -969,14 +971,14 @@ def run_ours(args):
         for lev in range(8):
             for narrow in (0, 1):
                 try:
-                    pmg.pfasst_mg_set_tuning(s.h, lev, narrow, 2, 32, 512)
+                    pmg.pfasst_mg_set_tuning(s.h, lev, narrow, args.tma, 32, 512)
                 except pmg.PMGError:
                     pass
     tuning = []
     for lev in range(8):
         try:
             fz, prm, thr = pmg.pfasst_mg_tuning(s.h, lev, 0)
-            kind = {0: f"point x{prm}", 1: f"fused z{prm or 32} x{thr}", 2: f"tma z{prm}"}.get(fz, "?")
+            kind = {0: f"point x{prm}", 1: f"fused z{prm or 32} x{thr}", 2: f"tma z{prm}", 3: f"tma4 z{prm}"}.get(fz, "?")
             tuning.append(f"L{lev}:{kind}")
         except pmg.PMGError:
             break
@@ -1144,7 +1146,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d",
-                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat2d", "uneven", "learned-train", "learned",
+                    choices=["heat3d", "heat3d-small", "heat3d-mid", "heat3d-255x4", "heat2d", "uneven", "learned-train", "learned",
                              "compare", "weak3", "order4", "heat1d"])
     ap.add_argument("--learned-fields", type=int, default=160,
                     help="learned: 127^3 GRF fields for the training pairs (64 crops each)")
@@ -1170,8 +1172,9 @@ def main():
                     help="measured variant: V-cycles per coarse-level sub-step (-1: the workload's)")
     ap.add_argument("--vcycle-tail", type=int, default=-1,
                     help="heat1d: 1 = run each V-cycle's levels that fit one CTA in one launch, 0 = per level")
-    ap.add_argument("--tma", action="store_true",
-                    help="pin the TMA-staged sweep on every level that can run it (profiling runs)")
+    ap.add_argument("--tma", type=int, nargs="?", const=3, default=0, choices=(0, 2, 3),
+                    help="pin the TMA-staged sweep on every level that can run it (profiling runs): "
+                         "2 = two x points per thread, 3 (bare flag) = four")
     ap.add_argument("--profile-all", action="store_true",
                     help="time every launch (not only fine-grid ones) and print the breakdown to stderr")
     args = ap.parse_args()

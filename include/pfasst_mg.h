@@ -202,8 +202,9 @@ long long pfasst_mg_launch_count(pmg_handle h);
 /* Smoother chosen for multigrid level `level` (0 = finest) of the handle's hierarchy,
  * for wide batches (narrow = 0) or a single grid (narrow = 1): *fused = 1 for the fused
  * 3D red-black sweep (then *param = z chunk, 0 = default, and *threads per CTA), 2 for
- * its variant with TMA-staged planes (FP32), 0 for the one-point-per-thread kernels
- * (*param = threads per block). */
+ * its variant with TMA-staged planes (FP32; two x points per thread), 3 for the same with
+ * four x points per thread, 0 for the one-point-per-thread kernels (*param = threads per
+ * block). */
 int pfasst_mg_tuning(pmg_handle h, int level, int narrow, int *fused, int *param, int *threads);
 
 /* Pin the smoother variant of a level (same encoding as pfasst_mg_tuning; the exact

@@ -489,10 +489,10 @@ int smooth_with(MGCtx &M, const Tune &t, int l, int B, double c, void *&cur, boo
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
     PMG_CUDA(M.h, k_smooth_jacobi(M.L, H.lev[l], c, o.omega, H.pr, cur, out, H.f[l], B, first, t.param));
     cur = out;
-  } else if (t.fused == 2) {
+  } else if (t.fused >= 2) {
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
     PMG_CUDA(M.h, k_rbgs_sweep3d_tma(M.L, H.lev[l], c, o.omega, cur, out, H.f[l], u_upd, su, B, first,
-                                     u_upd != nullptr, t.param));
+                                     u_upd != nullptr, t.param, t.fused == 3));
     cur = out;
   } else if (t.fused) {
     void *out = cur == H.e[l] ? H.e2[l] : H.e[l];
@@ -716,7 +716,8 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
           }
       if (M.o->smoother == PMG_SMOOTHER_RBGS && rbgs_tma_supported(g, H.pr))
         for (int zc : {16, 32, 64})
-          if (zc <= g.n) cand.push_back(Tune{2, zc, rbgs_tma_threads()});
+          if (zc <= g.n)
+            for (int kind : {2, 3}) cand.push_back(Tune{kind, zc, rbgs_tma_threads(g, kind == 3)});
       float best = 1e30f;
       Tune pick = H.tune[l][cls];
       for (const Tune &t : cand) {
@@ -1546,6 +1547,8 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
     PMG_RET(run_device_loop(h, max_iter, tol, &k, &res));
     h->q_valid = ffree(h);
     if (sweep_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a TMA-staged sweep timed out waiting for its loads");
+    if (interp_timeouts())
+      return fail(h, PMG_ERR_TIMEOUT, "the TMA-staged interpolation timed out waiting for its loads");
     if (coop_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a grid barrier of the persistent V-cycle timed out");
     if (iters_done) *iters_done = k;
     if (final_res) *final_res = res;
@@ -1559,6 +1562,8 @@ int pfasst_mg_iterate(pmg_handle h, int max_iter, double tol, int *iters_done, d
     h->q_valid = ffree(h);
     PMG_CUDA(h, cudaStreamSynchronize(h->stream));
     if (sweep_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a TMA-staged sweep timed out waiting for its loads");
+    if (interp_timeouts())
+      return fail(h, PMG_ERR_TIMEOUT, "the TMA-staged interpolation timed out waiting for its loads");
     if (coop_timeouts()) return fail(h, PMG_ERR_TIMEOUT, "a grid barrier of the persistent V-cycle timed out");
     if (!h->g_iter.recs.empty() && use_graphs(h)) PMG_RET(harvest(h, h->g_iter));
     res = 0.0;
@@ -1635,7 +1640,7 @@ int pfasst_mg_tuning(pmg_handle h, int level, int narrow, int *fused, int *param
 }
 
 int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int param, int threads) {
-  if (!h || !h->kids.empty() || level < 0 || level >= h->H.L - 1 || fused < 0 || fused > 2)
+  if (!h || !h->kids.empty() || level < 0 || level >= h->H.L - 1 || fused < 0 || fused > 3)
     return fail(h, PMG_ERR_INVALID_ARG, "bad argument");
   const Grid &g = h->H.lev[level];
   Tune t{fused, param, threads};
@@ -1646,9 +1651,9 @@ int pfasst_mg_set_tuning(pmg_handle h, int level, int narrow, int fused, int par
     if (g.order == 4) return fail(h, PMG_ERR_UNSUPPORTED, "the fused sweeps run the second-order stencil only");
     if (fused == 1 && threads != 256 && !(threads == 512 && g.pitch >= 128))
       return fail(h, PMG_ERR_INVALID_ARG, "fused sweep threads: 256, or 512 for rows of >= 128");
-    if (fused == 2 && !rbgs_tma_supported(g, h->H.pr))
+    if (fused >= 2 && !rbgs_tma_supported(g, h->H.pr))
       return fail(h, PMG_ERR_UNSUPPORTED, "the TMA-staged sweep needs FP32 (mixed precision) and n = 127 or 255");
-    if (fused == 2) t.threads = rbgs_tma_threads();
+    if (fused >= 2) t.threads = rbgs_tma_threads(g, fused == 3);
   }
   PMG_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graph(h->g_pred);

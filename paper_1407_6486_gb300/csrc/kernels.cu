@@ -13,9 +13,12 @@
 // covered.  All accesses stay inside the interior of each grid; the pad column is
 // never written.
 #include "pmg_internal.cuh"
+#include "tma.cuh"
 
 namespace pmg {
 namespace {
+
+__device__ int g_interp_timeout;  // set by a timed-out wait of interp_space3d_tma_kernel
 
 #define PMG_FOR_POINTS(g, batch)                                                                   \
   for (int zb = blockIdx.z; zb < (g).nz * (batch); zb += gridDim.z)                                \
@@ -518,31 +521,65 @@ __global__ void __launch_bounds__(256) interp_space_kernel(Grid gf, Grid gc, int
 // coarse box is read without reflection arithmetic unless it touches a wall.  The same
 // passes as interp_space_kernel (x, then y, then z with the FP64 update), with far fewer
 // index instructions per fine point.
+constexpr int I3CX = ITX / 2 + 4, I3CY = ITY / 2 + 4, I3CZ = ITZ / 2 + 4;
+
+// taps of one axis for a local fine index t (tile origins are even): t odd -> the fine
+// point sits on coarse box entry (t+1)/2 + 1 (injection); t even -> between box entries
+// t/2 + 1 and t/2 + 2 (ORD 2), or taps t/2 .. t/2 + 3 (ORD 4)
+template <typename T, int ORD>
+__device__ __forceinline__ T interp3d_tap(int t, const T *src, int stride) {
+  if (t & 1) return src[((t + 1) / 2 + 1) * stride];
+  const int c = t / 2;
+  if (ORD == 2) return T(0.5) * (src[(c + 1) * stride] + src[(c + 2) * stride]);
+  return T(-1.0 / 16) * (src[c * stride] + src[(c + 3) * stride]) +
+         T(9.0 / 16) * (src[(c + 1) * stride] + src[(c + 2) * stride]);
+}
+
+// the coarse box of a fine tile staged in C (odd reflection at the walls), then the x
+// pass into X and the y pass into Y; Y is complete after the caller's next barrier
+template <typename T, int ORD>
+__device__ __forceinline__ void interp3d_xy(const T *__restrict__ src, const Grid &gc, int x0, int y0, int z0, T *C,
+                                            T *X, T *Y) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = z0 / 2 - 1;  // 1-based coarse index of box entry 0
+  const int nc = gc.n;
+  const bool inside = cx0 >= 1 && cx0 + I3CX - 1 <= nc && cy0 >= 1 && cy0 + I3CY - 1 <= nc && cz0 >= 1 &&
+                      cz0 + I3CZ - 1 <= nc;
+  if (inside) {
+    for (int q = threadIdx.x; q < I3CZ * I3CY * I3CX; q += 256) {
+      const int a = q % I3CX, bb = (q / I3CX) % I3CY, cc = q / (I3CX * I3CY);
+      C[q] = src[((long long)(cz0 + cc - 1) * gc.ny + (cy0 + bb - 1)) * gc.pitch + (cx0 + a - 1)];
+    }
+  } else {
+    for (int q = threadIdx.x; q < I3CZ * I3CY * I3CX; q += 256) {
+      const int a = q % I3CX, bb = (q / I3CX) % I3CY, cc = q / (I3CX * I3CY);
+      float sx, sy, sz;
+      const int ix = reflect_index(cx0 + a, nc, &sx);
+      const int iy = reflect_index(cy0 + bb, nc, &sy);
+      const int iz = reflect_index(cz0 + cc, nc, &sz);
+      const float sg = sx * sy * sz;
+      C[q] = sg == 0.f ? T(0) : T(sg) * src[((long long)iz * gc.ny + iy) * gc.pitch + ix];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = ty; r < I3CZ * I3CY; r += 8) X[r * ITX + tx] = interp3d_tap<T, ORD>(tx, C + r * I3CX, 1);  // x pass
+  __syncthreads();
+#pragma unroll
+  for (int zc = 0; zc < I3CZ; ++zc)  // y pass
+    Y[(zc * ITY + ty) * ITX + tx] = interp3d_tap<T, ORD>(ty, X + zc * I3CY * ITX + tx, ITX);
+}
+
 template <typename T, int ORD>
 __global__ void __launch_bounds__(256) interp_space3d_kernel(Grid gf, Grid gc, int sf, const T *__restrict__ dU,
                                                              double *__restrict__ Uf, long long sfine, int ntz,
                                                              int m0) {
-  constexpr int CX = ITX / 2 + 4, CY = ITY / 2 + 4, CZ = ITZ / 2 + 4;
-  __shared__ T C[CZ * CY * CX];
-  __shared__ T X[CZ * CY * ITX];
-  __shared__ T Y[CZ * ITY * ITX];
+  __shared__ T C[I3CZ * I3CY * I3CX];
+  __shared__ T X[I3CZ * I3CY * ITX];
+  __shared__ T Y[I3CZ * ITY * ITX];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x0 = blockIdx.x * ITX, y0 = blockIdx.y * ITY;
   const int zt = blockIdx.z % ntz, b = blockIdx.z / ntz, z0 = zt * ITZ;
-  const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = z0 / 2 - 1;  // 1-based coarse index of box entry 0
-  const int nc = gc.n;
-  const bool inside = cx0 >= 1 && cx0 + CX - 1 <= nc && cy0 >= 1 && cy0 + CY - 1 <= nc && cz0 >= 1 &&
-                      cz0 + CZ - 1 <= nc;
-  // taps of one axis for a local fine index t (tile origins are even): t odd -> the
-  // fine point sits on coarse box entry (t+1)/2 + 1 (injection); t even -> between box
-  // entries t/2 + 1 and t/2 + 2 (ORD 2), or taps t/2 .. t/2 + 3 (ORD 4)
-  auto taps = [](int t, const T *src, int stride) -> T {
-    if (t & 1) return src[((t + 1) / 2 + 1) * stride];
-    const int c = t / 2;
-    if (ORD == 2) return T(0.5) * (src[(c + 1) * stride] + src[(c + 2) * stride]);
-    return T(-1.0 / 16) * (src[c * stride] + src[(c + 3) * stride]) +
-           T(9.0 / 16) * (src[(c + 1) * stride] + src[(c + 2) * stride]);
-  };
   const int i = x0 + tx, j = y0 + ty;
   const bool mine = i < gf.n && j < gf.n;
   const long long plane = (long long)gf.ny * gf.pitch;
@@ -554,41 +591,99 @@ __global__ void __launch_bounds__(256) interp_space3d_kernel(Grid gf, Grid gc, i
     double uold[ITZ];
 #pragma unroll
     for (int z = 0; z < ITZ; ++z) uold[z] = mine && z0 + z < gf.n ? dst[(z0 + z) * plane] : 0.0;
-    if (inside) {
-      for (int q = threadIdx.x; q < CZ * CY * CX; q += 256) {
-        const int a = q % CX, bb = (q / CX) % CY, cc = q / (CX * CY);
-        C[q] = src[((long long)(cz0 + cc - 1) * gc.ny + (cy0 + bb - 1)) * gc.pitch + (cx0 + a - 1)];
-      }
-    } else {
-      for (int q = threadIdx.x; q < CZ * CY * CX; q += 256) {
-        const int a = q % CX, bb = (q / CX) % CY, cc = q / (CX * CY);
-        float sx, sy, sz;
-        const int ix = reflect_index(cx0 + a, nc, &sx);
-        const int iy = reflect_index(cy0 + bb, nc, &sy);
-        const int iz = reflect_index(cz0 + cc, nc, &sz);
-        const float sg = sx * sy * sz;
-        C[q] = sg == 0.f ? T(0) : T(sg) * src[((long long)iz * gc.ny + iy) * gc.pitch + ix];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = ty; r < CZ * CY; r += 8) X[r * ITX + tx] = taps(tx, C + r * CX, 1);  // x pass
-    __syncthreads();
-#pragma unroll
-    for (int zc = 0; zc < CZ; ++zc) Y[(zc * ITY + ty) * ITX + tx] = taps(ty, X + zc * CY * ITX + tx, ITX);  // y
+    interp3d_xy<T, ORD>(src, gc, x0, y0, z0, C, X, Y);
     __syncthreads();
     if (mine) {
 #pragma unroll
       for (int z = 0; z < ITZ; ++z) {  // z pass and the FP64 update
         const int k = z0 + z;
         if (k < gf.n) {
-          const T dv = taps(z, Y + ty * ITX + tx, ITY * ITX);
+          const T dv = interp3d_tap<T, ORD>(z, Y + ty * ITX + tx, ITY * ITX);
           if constexpr (sizeof(T) == 4) dst[k * plane] = uold[z] + widen_exact(dv);
           else dst[k * plane] = uold[z] + dv;
         }
       }
     }
     __syncthreads();
+  }
+}
+
+// The same interpolation with the FP64 fine tiles streamed through shared memory by TMA:
+// the 32 x 8 x 8 tile of node m+1 is loaded (cp.async.bulk.tensor, one elected thread)
+// while node m's coarse passes run, the z pass adds the interpolated correction to the
+// staged tile in place, and the tile goes back by a TMA bulk store.  No thread touches
+// the fine grid in global memory.  Rows and planes past the grid arrive as zeros and
+// are clipped from the store; the pad column is written back as it was read.  Two tile
+// buffers: a buffer is refilled only after the bulk store of its previous node has read
+// it out.  Same arithmetic as interp_space3d_kernel, so the results are bitwise equal.
+template <typename T, int ORD>
+__global__ void __launch_bounds__(256) interp_space3d_tma_kernel(const __grid_constant__ CUtensorMap tmu, Grid gf,
+                                                                 Grid gc, int sf, const T *__restrict__ dU, int ntz,
+                                                                 int m0) {
+  using namespace tma;
+  constexpr uint32_t UB = ITX * ITY * ITZ * 8;  // bytes of one FP64 tile
+  extern __shared__ __align__(1024) unsigned char sm[];
+  double(*Ut)[ITZ][ITY][ITX] = (double(*)[ITZ][ITY][ITX])sm;  // [2]
+  T *C = (T *)(sm + 2 * UB);
+  T *X = C + I3CZ * I3CY * I3CX;
+  T *Y = X + I3CZ * I3CY * ITX;
+  uint64_t *bar = (uint64_t *)(Y + I3CZ * ITY * ITX);  // [2]
+  __shared__ int s_bad;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * ITX, y0 = blockIdx.y * ITY;
+  const int zt = blockIdx.z % ntz, b = blockIdx.z / ntz, z0 = zt * ITZ;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool mine = i < gf.n && j < gf.n;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_proxy_async_smem();
+    s_bad = 0;
+    mbar_expect_tx(&bar[0], UB);
+    tma_load_4d(&Ut[0][0][0][0], &tmu, x0, y0, z0, b * sf + m0, &bar[0]);
+  }
+  __syncthreads();
+  int issued = m0;  // last node whose tile load was issued
+  for (int m = m0; m < sf; ++m) {
+    const int t = m - m0, buf = t & 1;
+    if (threadIdx.x == 0 && m + 1 < sf) {
+      bulk_wait_read_all();  // the store of node m-1 has read buffer buf^1 out
+      mbar_expect_tx(&bar[buf ^ 1], UB);
+      tma_load_4d(&Ut[buf ^ 1][0][0][0], &tmu, x0, y0, z0, b * sf + m + 1, &bar[buf ^ 1]);
+      issued = m + 1;
+    }
+    interp3d_xy<T, ORD>(dU + ((long long)b * sf + m) * gc.slab, gc, x0, y0, z0, C, X, Y);
+    const bool ok = mbar_wait(&bar[buf], (uint32_t)(t >> 1) & 1u);  // the j-th load into a buffer: phase j
+    if (!ok) s_bad = 1;
+    __syncthreads();
+    if (s_bad) break;  // uniform: read after the barrier
+    if (mine) {
+#pragma unroll
+      for (int z = 0; z < ITZ; ++z) {  // z pass and the FP64 update, in the staged tile
+        if (z0 + z < gf.n) {
+          const T dv = interp3d_tap<T, ORD>(z, Y + ty * ITX + tx, ITY * ITX);
+          if constexpr (sizeof(T) == 4) Ut[buf][z][ty][tx] = Ut[buf][z][ty][tx] + widen_exact(dv);
+          else Ut[buf][z][ty][tx] = Ut[buf][z][ty][tx] + dv;
+        }
+      }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma_store_4d(&tmu, &Ut[buf][0][0][0], x0, y0, z0, b * sf + m);
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (s_bad) {
+      atomicExch(&g_interp_timeout, 1);
+      // the last two loads issued (one per buffer, phases as numbered above) may still be
+      // in flight: wait for them (bounded) before the CTA's shared memory is released
+      for (int t = issued - m0 - 1; t <= issued - m0; ++t)
+        if (t >= 0) mbar_wait(&bar[t & 1], (uint32_t)(t >> 1) & 1u);
+    }
+    bulk_wait_all();  // every bulk store complete before the CTA exits
   }
 }
 
@@ -1118,9 +1213,43 @@ cudaError_t launch_interp_space(const Launch &L, const Grid &gf, const Grid &gc,
   return cudaSuccess;
 }
 
+template <typename T, int ORD>
+cudaError_t launch_interp_space3d_tma(const Launch &L, const Grid &gf, const Grid &gc, int sf, const void *dU,
+                                      double *Uf, int batch, int m0) {
+  const size_t smem = 2 * (size_t)ITX * ITY * ITZ * 8 +
+                      sizeof(T) * (I3CZ * I3CY * I3CX + I3CZ * I3CY * ITX + I3CZ * ITY * ITX) + 2 * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(interp_space3d_tma_kernel<T, ORD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  // the fine grid functions of all slices and nodes as one 4D tensor (x, y, z, slice * sf + node)
+  CUtensorMap mu;
+  const cuuint64_t dims[4] = {(cuuint64_t)gf.pitch, (cuuint64_t)gf.ny, (cuuint64_t)gf.nz, (cuuint64_t)batch * sf};
+  const cuuint64_t strides[3] = {(cuuint64_t)gf.pitch * 8, (cuuint64_t)gf.ny * gf.pitch * 8, (cuuint64_t)gf.slab * 8};
+  const cuuint32_t box[4] = {ITX, ITY, ITZ, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  if (tma::encoder()(&mu, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, Uf, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const int ntx = gf.pitch / ITX, nty = (gf.n + ITY - 1) / ITY, ntz = (gf.n + ITZ - 1) / ITZ;
+  dim3 gr(ntx, nty, ntz * batch);
+  interp_space3d_tma_kernel<T, ORD><<<gr, 256, smem, L.stream>>>(mu, gf, gc, sf, (const T *)dU, ntz, m0);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_interp_space3d(const Launch &L, const Grid &gf, const Grid &gc, int order, int sf, const void *dU,
                                   double *Uf, long long sfine, int batch, int m0) {
+  // TMA-staged fine tiles: whole 32-column tiles per row, tiles no larger than the grid,
+  // slices stored back to back (sfine = sf slabs), 16-byte aligned base
+  if (gf.pitch % ITX == 0 && gf.n >= 31 && sfine == (long long)sf * gf.slab && ((uintptr_t)Uf & 15) == 0 &&
+      tma::encoder() != nullptr)
+    return order == 2 ? launch_interp_space3d_tma<T, 2>(L, gf, gc, sf, dU, Uf, batch, m0)
+                      : launch_interp_space3d_tma<T, 4>(L, gf, gc, sf, dU, Uf, batch, m0);
   const int ntx = (gf.n + ITX - 1) / ITX, nty = (gf.n + ITY - 1) / ITY, ntz = (gf.n + ITZ - 1) / ITZ;
   dim3 gr(ntx, nty, ntz * batch);
   if (order == 2)
@@ -1134,9 +1263,10 @@ cudaError_t k_interp_space_add(const Launch &L, const Grid &gf, const Grid &gc, 
                                const void *dU, double *Uf, long long sfine, int batch, int m0) {
   Scope sc(L, K_INTERP, gf, batch * (sf - m0), pr);
   if (gf.dim == 3 && (long long)((gf.n + ITZ - 1) / ITZ) * batch <= 65535) {
-    if (pr == F64) launch_interp_space3d<double>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0);
-    else launch_interp_space3d<float>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0);
-    return sc.done();
+    const cudaError_t e = pr == F64 ? launch_interp_space3d<double>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0)
+                                    : launch_interp_space3d<float>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0);
+    const cudaError_t e2 = sc.done();
+    return e != cudaSuccess ? e : e2;
   }
   if (pr == F64)
     PMG_DIM_SWITCH(gf.dim, (launch_interp_space<D, double>(L, gf, gc, order, sf, dU, Uf, sfine, batch, m0)))
@@ -1262,6 +1392,19 @@ cudaError_t k_unpack(const Launch &L, const Grid &g, const double *pad, long lon
   Scope sc(L, K_UNPACK, g, batch, 0);
   unpack_kernel<<<gr, bl, 0, L.stream>>>(g, pad, spad, dense, sdense, batch);
   return sc.done();
+}
+
+int interp_timeouts() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_interp_timeout, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_interp_timeout, &zero, sizeof(int));
+  }
+  return v;
 }
 
 }  // namespace pmg

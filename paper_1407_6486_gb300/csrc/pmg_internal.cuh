@@ -273,12 +273,15 @@ cudaError_t k_rbgs_sweep3d(const Launch &L, const Grid &g, double c, double omeg
 bool rbgs_rows_supported(const Grid &g);
 // the same fused sweep with TMA-staged planes (sweep_tma.cu): FP32, pitch 128 or 256
 bool rbgs_tma_supported(const Grid &g, Prec pr);
-int rbgs_tma_threads();
+// threads per CTA: two x points per thread, or four (quad)
+int rbgs_tma_threads(const Grid &g, bool quad);
 cudaError_t k_rbgs_sweep3d_tma(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout,
                                const void *f, double *u, long long su, int batch, bool zero, bool update_u,
-                               int zchunk);
+                               int zchunk, bool quad);
 // nonzero if a bounded device-side wait of a sweep timed out since the last call (clears it)
 int sweep_timeouts();
+// the same for the TMA-staged interpolation of the coarse correction
+int interp_timeouts();
 cudaError_t k_resrestrict3d(const Launch &L, const Grid &gf, const Grid &gc, double c, Prec pr, const void *e,
                             const void *f, void *fc, int batch);
 // the same residual + full weighting with TMA-staged planes (sweep_tma.cu): FP32, pitch >= 128

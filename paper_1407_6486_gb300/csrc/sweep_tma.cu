@@ -22,15 +22,13 @@
 // turns the flag into PMG_ERR_TIMEOUT.  A load that has not landed after that second
 // wait could still write into shared memory the CTA has released: the host then
 // reports the timeout and the caller should treat the CUDA context as suspect.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include <mutex>
-
 #include "pmg_internal.cuh"
+#include "tma.cuh"
 
 namespace pmg {
 namespace {
+
+using namespace tma;
 
 constexpr int TTY = 8;             // output rows per tile
 constexpr int TEY = TTY + 4;       // e_in rows staged per plane (y0-2 .. y0+TTY+1)
@@ -42,47 +40,6 @@ constexpr int TNT = 512;           // threads per CTA (two CTAs per SM: ~112 KB 
 constexpr int TZC = 32;            // default z planes per CTA
 
 __device__ int g_sweep_timeout;    // set by a timed-out mbarrier wait
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// bounded wait for the completion of phase `parity` of a barrier
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  if (mbar_test(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > 4000000000LL) return false;  // ~2 s at 2 GHz
-    __nanosleep(32);
-  }
-  return true;
-}
-
-// 4D tiled TMA load (x, y, z, batch) of one box into shared memory, completing on bar
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
-      : "memory");
-}
 
 template <int NX, bool ZERO, bool UPD>
 __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant__ CUtensorMap tme,
@@ -281,6 +238,222 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
   }
 }
 
+// The same sweep with four consecutive x points per thread (a float4 of a staged row):
+// 2 * NX threads, eight rows per round.  The colour of a row is uniform over its warp
+// (a warp lies in one row), so each half-sweep takes one of two branches for the whole
+// warp: the two points of the colour in the quad (positions 0, 2 or 1, 3), one x
+// neighbour from the adjacent lane's quad by a shuffle (or from shared memory at a warp
+// edge), the other three from the quad itself; 128-bit shared loads and stores.  The red
+// half-sweep stores the whole quad (its other colour unchanged) in place.  Per-point
+// arithmetic, summation order and ring schedule are those of rbgs_tma_kernel, so the
+// results are bitwise the same.
+template <int NX, bool ZERO, bool UPD>
+__global__ void __launch_bounds__(2 * NX, 2) rbgs_tma4_kernel(const __grid_constant__ CUtensorMap tme,
+                                                              const __grid_constant__ CUtensorMap tmf, Grid g,
+                                                              float a, float iD, float omega,
+                                                              float *__restrict__ eout, double *__restrict__ u,
+                                                              long long su, int nzc, int zchunk) {
+  constexpr int NQ = NX / 4;          // quads per row
+  constexpr int RS = 8;               // rows per round of the CTA
+  constexpr int PF = (TMY + RS - 1) / RS, PB = (TTY + RS - 1) / RS;
+  constexpr uint32_t EB = TEY * NX * 4, FB = TMY * NX * 4;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float4(*E)[TEY][NQ] = (float4(*)[TEY][NQ])sm;                                   // [NE]
+  float4(*Fs)[TMY][NQ] = (float4(*)[TMY][NQ])(sm + NE * EB);                       // [NF]
+  uint64_t *bar = (uint64_t *)(sm + NE * EB + NF * FB);                            // [NE + NF]
+  __shared__ int s_bad;
+  const int n = g.n, tid = threadIdx.x, qx = tid % NQ, ry = tid / NQ, lane = tid & 31;
+  const int x0 = 4 * qx;
+  const int y0 = blockIdx.y * TTY;
+  const int zc = blockIdx.z % nzc, b = blockIdx.z / nzc;
+  const int z0 = zc * zchunk, z1 = min(z0 + zchunk, n);
+  const long long plane = (long long)g.ny * g.pitch;
+  const unsigned full = 0xffffffffu;
+  auto eslot = [&](int p) { return (p - z0 + 2) % NE; };  // p >= z0 - 2
+  auto fslot = [&](int p) { return (p - z0 + 1) % NF; };  // p >= z0 - 1
+  auto issue_e = [&](int p) {
+    const int s = eslot(p);
+    mbar_expect_tx(&bar[s], EB);
+    tma_load_4d(&E[s][0][0], &tme, 0, y0 - 2, p, b, &bar[s]);
+  };
+  auto issue_f = [&](int p) {
+    const int s = fslot(p);
+    mbar_expect_tx(&bar[NE + s], FB);
+    tma_load_4d(&Fs[s][0][0], &tmf, 0, y0 - 1, p, b, &bar[NE + s]);
+  };
+  auto eup = [](int sl, int d) { return sl + d >= NE ? sl + d - NE : sl + d; };
+  auto edn = [](int sl, int d) { return sl - d < 0 ? sl - d + NE : sl - d; };
+  auto fup = [](int sl, int d) { return sl + d >= NF ? sl + d - NF : sl + d; };
+  auto fdn = [](int sl, int d) { return sl - d < 0 ? sl - d + NF : sl - d; };
+  // x neighbours outside the quad: the previous quad's last value, the next quad's first
+  auto leftq = [&](const float4 &c, const float4 *row) {
+    const float l = __shfl_up_sync(full, c.w, 1);
+    return lane != 0 ? l : (qx > 0 ? row[qx - 1].w : 0.f);
+  };
+  auto rightq = [&](const float4 &c, const float4 *row) {
+    const float r = __shfl_down_sync(full, c.x, 1);
+    return lane != 31 ? r : (qx < NQ - 1 ? row[qx + 1].x : 0.f);
+  };
+  // relaxed Gauss-Seidel value of one point from its neighbour sum, f and old value
+  auto relax = [&](float nb, float fr, float old) {
+    const float gs = (fr + a * nb) * iD;
+    return omega == 1.f ? gs : old + omega * (gs - old);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < NE + NF; ++i) mbar_init(&bar[i]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_bad = 0;
+    if (!ZERO)
+      for (int p = z0 - 2; p <= min(z0 - 1 + DEPTH, z1 + 1); ++p) issue_e(p);
+    for (int p = z0 - 1; p <= min(z0 - 2 + DEPTH, z1); ++p) issue_f(p);
+  }
+  __syncthreads();
+  bool ok = true;
+  if (!ZERO) ok = mbar_wait(&bar[0], 0) && mbar_wait(&bar[1], 0);
+  double2 upre[PB][2];
+  int kstop = z1;
+  int s1 = 2, sfk = 0;
+  uint32_t ph1 = 0, phf = 0;
+  for (int k = z0 - 1; k <= z1; ++k) {
+    if (tid == 0) {
+      if (!ZERO && k + 1 + DEPTH <= z1 + 1) {
+        const int sl = eup(s1, DEPTH);
+        mbar_expect_tx(&bar[sl], EB);
+        tma_load_4d(&E[sl][0][0], &tme, 0, y0 - 2, k + 1 + DEPTH, b, &bar[sl]);
+      }
+      if (k + DEPTH <= z1) {
+        const int sl = fup(sfk, DEPTH);
+        mbar_expect_tx(&bar[NE + sl], FB);
+        tma_load_4d(&Fs[sl][0][0], &tmf, 0, y0 - 1, k + DEPTH, b, &bar[NE + sl]);
+      }
+    }
+    if (UPD && k - 1 >= z0 && k - 1 < z1) {
+#pragma unroll
+      for (int h = 0; h < PB; ++h) {
+        const int r = ry + RS * h, y = y0 + r;
+        if (r < TTY && y < n) {
+          const double2 *up = (const double2 *)(u + b * su + (k - 1) * plane + (long long)y * g.pitch + x0);
+          upre[h][0] = up[0];
+          upre[h][1] = up[1];
+        }
+      }
+    }
+    if (ok && !ZERO) ok = mbar_wait(&bar[s1], ph1);
+    if (ok) ok = mbar_wait(&bar[NE + sfk], phf);
+    if (!ok) s_bad = 1;
+    {  // red half-sweep on plane k, rows y0-1 .. y0+TTY, into the e slot of plane k
+      const int se = edn(s1, 1), sl = edn(s1, 2), sh = s1, sf = sfk;
+      const bool kin = k >= 0 && k < n;
+#pragma unroll
+      for (int h = 0; h < PF; ++h) {
+        const int r = ry + RS * h;
+        if (r >= TMY) break;  // uniform per warp
+        const int y = y0 - 1 + r;
+        const bool yin = kin && y >= 0 && y < n;
+        const float4 fv = Fs[sf][r][qx];
+        const bool ro = ((y + k) & 1) == 0;  // red at x + y + k odd: odd positions when y + k is even
+        if (ZERO) {
+          // from e = 0 the slot was never loaded: write the whole quad (black lanes zero)
+          float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (yin) {
+            if (ro) {
+              out.y = omega * (fv.y * iD);
+              if (x0 + 3 < n) out.w = omega * (fv.w * iD);
+            } else {
+              out.x = omega * (fv.x * iD);
+              out.z = omega * (fv.z * iD);
+            }
+          }
+          E[se][r + 1][qx] = out;
+        } else {
+          float4 c = E[se][r + 1][qx];
+          if (ro) {
+            const float right = rightq(c, E[se][r + 1]);
+            if (yin) {
+              const float4 up = E[se][r][qx], dn = E[se][r + 2][qx], zl = E[sl][r + 1][qx], zh = E[sh][r + 1][qx];
+              const float v1 = relax(c.x + c.z + up.y + dn.y + zl.y + zh.y, fv.y, c.y);
+              if (x0 + 3 < n) c.w = relax(c.z + right + up.w + dn.w + zl.w + zh.w, fv.w, c.w);
+              c.y = v1;
+              E[se][r + 1][qx] = c;
+            }
+          } else {
+            const float left = leftq(c, E[se][r + 1]);
+            if (yin) {
+              const float4 up = E[se][r][qx], dn = E[se][r + 2][qx], zl = E[sl][r + 1][qx], zh = E[sh][r + 1][qx];
+              const float v0 = relax(left + c.y + up.x + dn.x + zl.x + zh.x, fv.x, c.x);
+              c.z = relax(c.y + c.w + up.z + dn.z + zl.z + zh.z, fv.z, c.z);
+              c.x = v0;
+              E[se][r + 1][qx] = c;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+TTY-1
+    if (kb >= z0 && kb < z1) {
+      const int s0 = edn(s1, 2), sl = edn(s1, 3), sh = edn(s1, 1), sf = fdn(sfk, 1);
+#pragma unroll
+      for (int h = 0; h < PB; ++h) {
+        const int r = ry + RS * h;
+        if (r >= TTY) break;
+        const int y = y0 + r;
+        float4 c = E[s0][r + 2][qx];  // red lanes updated, black lanes old
+        const bool bo = ((y + kb) & 1) != 0;  // black at x + y + kb even: odd positions when y + kb is odd
+        if (bo) {
+          const float right = rightq(c, E[s0][r + 2]);
+          if (y >= n) continue;
+          const float4 up = E[s0][r + 1][qx], dn = E[s0][r + 3][qx], zl = E[sl][r + 2][qx], zh = E[sh][r + 2][qx];
+          const float4 fv = Fs[sf][r + 1][qx];
+          const float v1 = relax(c.x + c.z + up.y + dn.y + zl.y + zh.y, fv.y, ZERO ? 0.f : c.y);
+          if (x0 + 3 < n) c.w = relax(c.z + right + up.w + dn.w + zl.w + zh.w, fv.w, ZERO ? 0.f : c.w);
+          c.y = v1;
+        } else {
+          const float left = leftq(c, E[s0][r + 2]);
+          if (y >= n) continue;
+          const float4 up = E[s0][r + 1][qx], dn = E[s0][r + 3][qx], zl = E[sl][r + 2][qx], zh = E[sh][r + 2][qx];
+          const float4 fv = Fs[sf][r + 1][qx];
+          const float v0 = relax(left + c.y + up.x + dn.x + zl.x + zh.x, fv.x, ZERO ? 0.f : c.x);
+          c.z = relax(c.y + c.w + up.z + dn.z + zl.z + zh.z, fv.z, ZERO ? 0.f : c.z);
+          c.x = v0;
+        }
+        const long long o = kb * plane + (long long)y * g.pitch + x0;
+        if (UPD) {
+          double2 w0 = upre[h][0], w1 = upre[h][1];
+          w0.x += widen_exact(c.x);
+          w0.y += widen_exact(c.y);
+          w1.x += widen_exact(c.z);
+          w1.y += widen_exact(c.w);
+          double2 *uo = (double2 *)(u + b * su + o);
+          uo[0] = w0;
+          uo[1] = w1;
+        } else {
+          *(float4 *)(eout + b * g.slab + o) = c;
+        }
+      }
+    }
+    __syncthreads();  // slots of plane k-1 may be refilled now
+    if (s_bad) {
+      kstop = k;
+      break;
+    }
+    if (++s1 == NE) { s1 = 0; ph1 ^= 1u; }
+    if (++sfk == NF) { sfk = 0; phf ^= 1u; }
+  }
+  if (s_bad && tid == 0) {
+    atomicExch(&g_sweep_timeout, 1);
+    // wait (bounded) for the loads still in flight, as in rbgs_tma_kernel
+    if (!ZERO) {
+      const int last = min(kstop + 1 + DEPTH, z1 + 1);
+      for (int p = max(z0 - 2, last - NE + 1); p <= last; ++p) mbar_wait(&bar[eslot(p)], ((p - z0 + 2) / NE) & 1);
+    }
+    const int lastf = min(kstop + DEPTH, z1);
+    for (int p = max(z0 - 1, lastf - NF + 1); p <= lastf; ++p) mbar_wait(&bar[NE + fslot(p)], ((p - z0 + 1) / NF) & 1);
+  }
+}
+
 // ---------------------------------------------------------------- residual + restriction
 //
 // fc = full weighting of r = f - (I - c Lap_h) e on batched 3D grids (FP32), with the
@@ -418,21 +591,6 @@ __global__ void __launch_bounds__(RNT, 4) resrestrict_tma_kernel(const __grid_co
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
 // tensor map of a batch of padded grid functions: dims (pitch, n, n, batch), box of
 // `rows` whole rows of one plane
 bool make_map(CUtensorMap *m, const void *base, const Grid &g, int batch, int rows) {
@@ -487,6 +645,32 @@ cudaError_t launch_tma(const Launch &L, const Grid &g, float a, float iD, float 
   return cudaGetLastError();
 }
 
+template <int NX, bool ZERO, bool UPD>
+cudaError_t launch_tma4(const Launch &L, const Grid &g, float a, float iD, float omega, const void *ein, void *eout,
+                        const void *f, double *u, long long su, int batch, int zchunk) {
+  constexpr uint32_t EB = TEY * NX * 4, FB = TMY * NX * 4;
+  const size_t smem = NE * EB + NF * FB + (NE + NF) * 8;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(rbgs_tma4_kernel<NX, ZERO, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(rbgs_tma4_kernel<NX, ZERO, UPD>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap me, mf;
+  if (!make_map(&mf, f, g, batch, TMY)) return cudaErrorInvalidValue;
+  if (!make_map(&me, ZERO ? f : ein, g, batch, TEY)) return cudaErrorInvalidValue;  // unused when ZERO
+  if (zchunk <= 0) zchunk = TZC;
+  const int nty = (g.n + TTY - 1) / TTY, nzc = (g.n + zchunk - 1) / zchunk;
+  dim3 gr(1, nty, nzc * batch);
+  rbgs_tma4_kernel<NX, ZERO, UPD><<<gr, 2 * NX, smem, L.stream>>>(me, mf, g, a, iD, omega, (float *)eout, u, su,
+                                                                   nzc, zchunk);
+  return cudaGetLastError();
+}
+
 template <bool ZERO, bool UPD>
 cudaError_t launch_tma_pitch(const Launch &L, const Grid &g, float a, float iD, float omega, const void *ein,
                              void *eout, const void *f, double *u, long long su, int batch, int zchunk) {
@@ -494,9 +678,16 @@ cudaError_t launch_tma_pitch(const Launch &L, const Grid &g, float a, float iD, 
   return launch_tma<128, ZERO, UPD>(L, g, a, iD, omega, ein, eout, f, u, su, batch, zchunk);
 }
 
+template <bool ZERO, bool UPD>
+cudaError_t launch_tma4_pitch(const Launch &L, const Grid &g, float a, float iD, float omega, const void *ein,
+                              void *eout, const void *f, double *u, long long su, int batch, int zchunk) {
+  if (g.pitch == 256) return launch_tma4<256, ZERO, UPD>(L, g, a, iD, omega, ein, eout, f, u, su, batch, zchunk);
+  return launch_tma4<128, ZERO, UPD>(L, g, a, iD, omega, ein, eout, f, u, su, batch, zchunk);
+}
+
 }  // namespace
 
-int rbgs_tma_threads() { return TNT; }
+int rbgs_tma_threads(const Grid &g, bool quad) { return quad ? 2 * g.pitch : TNT; }
 
 bool rbgs_tma_supported(const Grid &g, Prec pr) {
   return pr == F32 && g.dim == 3 && g.order != 4 && (g.pitch == 128 || g.pitch == 256) && encoder() != nullptr;
@@ -504,11 +695,16 @@ bool rbgs_tma_supported(const Grid &g, Prec pr) {
 
 cudaError_t k_rbgs_sweep3d_tma(const Launch &L, const Grid &g, double c, double omega, const void *ein, void *eout,
                                const void *f, double *u, long long su, int batch, bool zero, bool update_u,
-                               int zchunk) {
+                               int zchunk, bool quad) {
   Scope sc(L, zero ? K_RBGS3D_ZERO : (update_u ? K_RBGS3D_UPD : K_RBGS3D), g, batch, F32);
   const float a = (float)(c * g.ih2), D = 1.f + 6.f * a, iD = 1.f / D, w = (float)omega;
   cudaError_t e;
-  if (zero && update_u) e = launch_tma_pitch<true, true>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+  if (quad) {
+    if (zero && update_u) e = launch_tma4_pitch<true, true>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+    else if (zero) e = launch_tma4_pitch<true, false>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+    else if (update_u) e = launch_tma4_pitch<false, true>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+    else e = launch_tma4_pitch<false, false>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
+  } else if (zero && update_u) e = launch_tma_pitch<true, true>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
   else if (zero) e = launch_tma_pitch<true, false>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
   else if (update_u) e = launch_tma_pitch<false, true>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);
   else e = launch_tma_pitch<false, false>(L, g, a, iD, w, ein, eout, f, u, su, batch, zchunk);

@@ -411,6 +411,29 @@ def test_tma_staged_sweep_matches_the_fused_sweep(n, level, zchunk):
     assert err <= 1e-6, err
 
 
+@pytest.mark.parametrize("n,slices,level,zchunk,vcycles", [(127, 2, 0, 32, 2), (255, 2, 1, 16, 2), (127, 3, 0, 7, 1),
+                                                           (255, 1, 0, 64, 1)])
+def test_tma_quad_sweep_is_bitwise_the_pair_sweep(n, slices, level, zchunk, vcycles):
+    """Four x points per thread (128-bit shared loads, one shuffle per half-sweep) against
+    two per thread: the same points, arithmetic and summation order, so the PFASST
+    iterates (the sweep from zero, the plain sweep and the sweep fused with u += e all
+    run) must be identical bit for bit."""
+    wl = inputs.heat3d_c3(n=n, slices=slices)
+    out = []
+    for fused in (2, 3):
+        s = pmg.PFASSTSolver(wl.dim, wl.n, wl.fine_nodes, wl.coarse_nodes, wl.slices, wl.nu, wl.dt,
+                             smoother=wl.smoother, omega=wl.omega, vcycles=vcycles, precision=1, autotune=0)
+        for narrow in (0, 1):
+            pmg.pfasst_mg_set_tuning(s.h, level, narrow, fused, zchunk, 0)
+        t = pmg.pfasst_mg_tuning(s.h, level, 0)
+        assert t[:2] == (fused, zchunk) and t[2] == (512 if fused == 2 else 2 * ((n + 1) >> level)), t
+        s.set_initial(wl.u0())
+        s.iterate(2, 0.0)
+        out.append(s.state(0))
+        s.close()
+    assert np.array_equal(out[0], out[1]), worst_rel(out[1], out[0], "quad vs pair")
+
+
 UNIFORM_CASES = [
     # dim, n, sf, sc, P, nlevels, smoother, vcycles, interp  (uniform nodes, Sec. 3)
     (1, 63, 5, 3, 3, 2, 0, 2, 4),
@@ -611,7 +634,8 @@ def _colloc_state(wl, n, nodes, slices):
     return out
 
 
-def test_mixed_fixed_point_127_with_tma_kernels_pinned():
+@pytest.mark.parametrize("kind", [2, 3])
+def test_mixed_fixed_point_127_with_tma_kernels_pinned(kind):
     """Mixed precision on the 3D workload's coarse-grid size 127^3 (9 slices, so that the
     batched fine level takes the z-marching kernels), with the TMA-staged sweep pinned on
     the finest multigrid level: the pre-smoothing sweep from zero, the plain sweep, the
@@ -622,8 +646,8 @@ def test_mixed_fixed_point_127_with_tma_kernels_pinned():
     s = pmg.PFASSTSolver(3, wl.n, 5, 3, wl.slices, wl.nu, wl.dt, smoother=1, omega=1.0, vcycles=2, precision=1,
                          autotune=0)
     for narrow in (0, 1):
-        pmg.pfasst_mg_set_tuning(s.h, 0, narrow, 2, 32, 512)
-    assert pmg.pfasst_mg_tuning(s.h, 0, 0)[:2] == (2, 32)
+        pmg.pfasst_mg_set_tuning(s.h, 0, narrow, kind, 32, 512)
+    assert pmg.pfasst_mg_tuning(s.h, 0, 0)[:2] == (kind, 32)
     s.set_initial(wl.u0())
     rc, it, res = s.iterate(400, 1e-11)
     assert rc == pmg.PMG_OK, (it, res)
@@ -632,7 +656,8 @@ def test_mixed_fixed_point_127_with_tma_kernels_pinned():
     assert rel(gpu, _colloc_state(wl, wl.n, 5, wl.slices)) < MIXED_TOL
 
 
-def test_fp32_sweep_255_with_tma_kernels_matches_oracle():
+@pytest.mark.parametrize("kind", [2, 3])
+def test_fp32_sweep_255_with_tma_kernels_matches_oracle(kind):
     """One SDC sweep (4 sub-steps, one FP32 V(2,1) red-black cycle each) on two slices of
     the 255^3 grid of the 3D workload with the TMA-staged sweep pinned on the finest
     level (the batch of two takes the TMA-staged residual + restriction too), against
@@ -641,7 +666,7 @@ def test_fp32_sweep_255_with_tma_kernels_matches_oracle():
     s = pmg.PFASSTSolver(3, wl.n, 5, 0, 2, wl.nu, wl.dt, nlevels=1, smoother=1, omega=1.0, vcycles=1, precision=1,
                          autotune=0)
     for narrow in (0, 1):
-        pmg.pfasst_mg_set_tuning(s.h, 0, narrow, 2, 32, 512)
+        pmg.pfasst_mg_set_tuning(s.h, 0, narrow, kind, 32, 512)
     u0 = wl.u0()
     s.set_initial(u0)
     s.sweep(0)
