@@ -535,17 +535,46 @@ __device__ __forceinline__ T interp3d_tap(int t, const T *src, int stride) {
          T(9.0 / 16) * (src[(c + 1) * stride] + src[(c + 2) * stride]);
 }
 
-// the coarse box of a fine tile staged in C (odd reflection at the walls), then the x
-// pass into X and the y pass into Y; Y is complete after the caller's next barrier
+// coarse box entry (a, bb, cc) of the tile with 1-based box origin (cx0, cy0, cz0): the
+// coarse value with odd reflection at the walls (zero on the walls themselves)
+template <typename T>
+__device__ __forceinline__ T interp3d_box_value(const T *__restrict__ src, const Grid &gc, int cx0, int cy0, int cz0,
+                                                int a, int bb, int cc) {
+  float sx, sy, sz;
+  const int ix = reflect_index(cx0 + a, gc.n, &sx);
+  const int iy = reflect_index(cy0 + bb, gc.n, &sy);
+  const int iz = reflect_index(cz0 + cc, gc.n, &sz);
+  const float sg = sx * sy * sz;
+  return sg == 0.f ? T(0) : T(sg) * src[((long long)iz * gc.ny + iy) * gc.pitch + ix];
+}
+
+// whether the coarse box of a tile lies inside the grid (no reflection needed)
+__device__ __forceinline__ bool interp3d_inside(int cx0, int cy0, int cz0, int nc) {
+  return cx0 >= 1 && cx0 + I3CX - 1 <= nc && cy0 >= 1 && cy0 + I3CY - 1 <= nc && cz0 >= 1 && cz0 + I3CZ - 1 <= nc;
+}
+
+// x pass from the staged coarse box (rows of CS entries, box entry 0 at column C0) into
+// X; the y pass from X into Y (after a barrier; Y is complete after the next barrier)
+template <typename T, int ORD, int CS, int C0>
+__device__ __forceinline__ void interp3d_x_pass(const T *C, T *X) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = ty; r < I3CZ * I3CY; r += 8) X[r * ITX + tx] = interp3d_tap<T, ORD>(tx, C + r * CS + C0, 1);
+}
+
+template <typename T, int ORD>
+__device__ __forceinline__ void interp3d_y_pass(const T *X, T *Y) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int zc = 0; zc < I3CZ; ++zc) Y[(zc * ITY + ty) * ITX + tx] = interp3d_tap<T, ORD>(ty, X + zc * I3CY * ITX + tx, ITX);
+}
+
+// the coarse box of a fine tile staged in C by the threads, then the x and y passes
 template <typename T, int ORD>
 __device__ __forceinline__ void interp3d_xy(const T *__restrict__ src, const Grid &gc, int x0, int y0, int z0, T *C,
                                             T *X, T *Y) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = z0 / 2 - 1;  // 1-based coarse index of box entry 0
-  const int nc = gc.n;
-  const bool inside = cx0 >= 1 && cx0 + I3CX - 1 <= nc && cy0 >= 1 && cy0 + I3CY - 1 <= nc && cz0 >= 1 &&
-                      cz0 + I3CZ - 1 <= nc;
-  if (inside) {
+  if (interp3d_inside(cx0, cy0, cz0, gc.n)) {
     for (int q = threadIdx.x; q < I3CZ * I3CY * I3CX; q += 256) {
       const int a = q % I3CX, bb = (q / I3CX) % I3CY, cc = q / (I3CX * I3CY);
       C[q] = src[((long long)(cz0 + cc - 1) * gc.ny + (cy0 + bb - 1)) * gc.pitch + (cx0 + a - 1)];
@@ -553,21 +582,13 @@ __device__ __forceinline__ void interp3d_xy(const T *__restrict__ src, const Gri
   } else {
     for (int q = threadIdx.x; q < I3CZ * I3CY * I3CX; q += 256) {
       const int a = q % I3CX, bb = (q / I3CX) % I3CY, cc = q / (I3CX * I3CY);
-      float sx, sy, sz;
-      const int ix = reflect_index(cx0 + a, nc, &sx);
-      const int iy = reflect_index(cy0 + bb, nc, &sy);
-      const int iz = reflect_index(cz0 + cc, nc, &sz);
-      const float sg = sx * sy * sz;
-      C[q] = sg == 0.f ? T(0) : T(sg) * src[((long long)iz * gc.ny + iy) * gc.pitch + ix];
+      C[q] = interp3d_box_value(src, gc, cx0, cy0, cz0, a, bb, cc);
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int r = ty; r < I3CZ * I3CY; r += 8) X[r * ITX + tx] = interp3d_tap<T, ORD>(tx, C + r * I3CX, 1);  // x pass
+  interp3d_x_pass<T, ORD, I3CX, 0>(C, X);
   __syncthreads();
-#pragma unroll
-  for (int zc = 0; zc < I3CZ; ++zc)  // y pass
-    Y[(zc * ITY + ty) * ITX + tx] = interp3d_tap<T, ORD>(ty, X + zc * I3CY * ITX + tx, ITX);
+  interp3d_y_pass<T, ORD>(X, Y);
 }
 
 template <typename T, int ORD>
@@ -608,43 +629,57 @@ __global__ void __launch_bounds__(256) interp_space3d_kernel(Grid gf, Grid gc, i
   }
 }
 
-// The same interpolation with the FP64 fine tiles streamed through shared memory by TMA:
-// the 32 x 8 x 8 tile of node m+1 is loaded (cp.async.bulk.tensor, one elected thread)
-// while node m's coarse passes run, the z pass adds the interpolated correction to the
-// staged tile in place, and the tile goes back by a TMA bulk store.  No thread touches
-// the fine grid in global memory.  Rows and planes past the grid arrive as zeros and
-// are clipped from the store; the pad column is written back as it was read.  Two tile
-// buffers: a buffer is refilled only after the bulk store of its previous node has read
-// it out.  Same arithmetic as interp_space3d_kernel, so the results are bitwise equal.
+// The same interpolation with every global access done by TMA: the FP64 32 x 8 x 8 fine
+// tile of node m+1 is loaded (cp.async.bulk.tensor, one elected thread) while node m is
+// interpolated, the coarse box of node m+1 as soon as the x pass of node m has consumed
+// the box buffer, the z pass adds the correction to the staged fine tile in place, and
+// the tile goes back by a TMA bulk store.  Rows and planes past the fine grid arrive as
+// zeros and are clipped from the store; the pad column is written back as it was read.
+// The coarse box is loaded 24 entries wide from the 4-aligned x index x0/2 - 4 (the TMA
+// x coordinate must be 16-byte aligned), so box entry 0 is column 2; entries outside the
+// coarse grid arrive as zeros and, in tiles at a wall, are then overwritten with their
+// reflected values by the threads.  Two fine-tile buffers: a buffer is refilled only
+// after the bulk store of its previous node has read it out.  Same arithmetic as
+// interp_space3d_kernel, so the results are bitwise equal.
+constexpr int I3CW = I3CX + 4;  // staged coarse row: 4-aligned start, multiple of 16 bytes
+
 template <typename T, int ORD>
-__global__ void __launch_bounds__(256) interp_space3d_tma_kernel(const __grid_constant__ CUtensorMap tmu, Grid gf,
+__global__ void __launch_bounds__(256) interp_space3d_tma_kernel(const __grid_constant__ CUtensorMap tmu,
+                                                                 const __grid_constant__ CUtensorMap tmc, Grid gf,
                                                                  Grid gc, int sf, const T *__restrict__ dU, int ntz,
                                                                  int m0) {
   using namespace tma;
-  constexpr uint32_t UB = ITX * ITY * ITZ * 8;  // bytes of one FP64 tile
+  constexpr uint32_t UB = ITX * ITY * ITZ * 8;                 // bytes of one FP64 fine tile
+  constexpr uint32_t CB = I3CZ * I3CY * I3CW * sizeof(T);      // bytes of one coarse box
   extern __shared__ __align__(1024) unsigned char sm[];
   double(*Ut)[ITZ][ITY][ITX] = (double(*)[ITZ][ITY][ITX])sm;  // [2]
-  T *C = (T *)(sm + 2 * UB);
-  T *X = C + I3CZ * I3CY * I3CX;
+  T *C = (T *)(sm + 2 * UB);                                    // [I3CZ][I3CY][I3CW]
+  T *X = C + I3CZ * I3CY * I3CW;
   T *Y = X + I3CZ * I3CY * ITX;
-  uint64_t *bar = (uint64_t *)(Y + I3CZ * ITY * ITX);  // [2]
-  __shared__ int s_bad;
+  uint64_t *bar = (uint64_t *)(Y + I3CZ * ITY * ITX);  // [3]: fine tiles 0, 1; coarse box
+  int *s_bad = (int *)(bar + 3);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x0 = blockIdx.x * ITX, y0 = blockIdx.y * ITY;
   const int zt = blockIdx.z % ntz, b = blockIdx.z / ntz, z0 = zt * ITZ;
+  const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = z0 / 2 - 1;  // 1-based coarse index of box entry 0
+  const bool inside = interp3d_inside(cx0, cy0, cz0, gc.n);
   const int i = x0 + tx, j = y0 + ty;
   const bool mine = i < gf.n && j < gf.n;
+  auto load_c = [&](int m) {
+    mbar_expect_tx(&bar[2], CB);
+    tma_load_4d(C, &tmc, x0 / 2 - 4, cy0 - 1, cz0 - 1, b * sf + m, &bar[2]);
+  };
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
+    for (int q = 0; q < 3; ++q) mbar_init(&bar[q]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_proxy_async_smem();
-    s_bad = 0;
+    *s_bad = 0;
     mbar_expect_tx(&bar[0], UB);
     tma_load_4d(&Ut[0][0][0][0], &tmu, x0, y0, z0, b * sf + m0, &bar[0]);
+    load_c(m0);
   }
   __syncthreads();
-  int issued = m0;  // last node whose tile load was issued
+  int issued = m0, issued_c = 1;  // thread 0: last node whose fine tile load was issued; box loads issued
   for (int m = m0; m < sf; ++m) {
     const int t = m - m0, buf = t & 1;
     if (threadIdx.x == 0 && m + 1 < sf) {
@@ -653,11 +688,31 @@ __global__ void __launch_bounds__(256) interp_space3d_tma_kernel(const __grid_co
       tma_load_4d(&Ut[buf ^ 1][0][0][0], &tmu, x0, y0, z0, b * sf + m + 1, &bar[buf ^ 1]);
       issued = m + 1;
     }
-    interp3d_xy<T, ORD>(dU + ((long long)b * sf + m) * gc.slab, gc, x0, y0, z0, C, X, Y);
-    const bool ok = mbar_wait(&bar[buf], (uint32_t)(t >> 1) & 1u);  // the j-th load into a buffer: phase j
-    if (!ok) s_bad = 1;
+    bool ok = mbar_wait(&bar[2], (uint32_t)t & 1u);  // the t-th coarse box: phase t
+    if (ok && !inside) {  // reflected values where the box crosses a wall
+      const T *src = dU + ((long long)b * sf + m) * gc.slab;
+      for (int q = threadIdx.x; q < I3CZ * I3CY * I3CX; q += 256) {
+        const int a = q % I3CX, bb = (q / I3CX) % I3CY, cc = q / (I3CX * I3CY);
+        const int J = cx0 + a, K = cy0 + bb, L = cz0 + cc;
+        if (J < 1 || J > gc.n || K < 1 || K > gc.n || L < 1 || L > gc.n)
+          C[(cc * I3CY + bb) * I3CW + a + 2] = interp3d_box_value(src, gc, cx0, cy0, cz0, a, bb, cc);
+      }
+      fence_proxy_async_smem();  // these writes precede the next box's TMA load
+    }
+    if (!ok) *s_bad = 1;
     __syncthreads();
-    if (s_bad) break;  // uniform: read after the barrier
+    if (*s_bad) break;  // uniform: read after the barrier
+    interp3d_x_pass<T, ORD, I3CW, 2>(C, X);
+    __syncthreads();
+    if (threadIdx.x == 0 && m + 1 < sf) {  // the box buffer is free again
+      load_c(m + 1);
+      ++issued_c;
+    }
+    interp3d_y_pass<T, ORD>(X, Y);
+    ok = mbar_wait(&bar[buf], (uint32_t)(t >> 1) & 1u);  // the j-th load into a buffer: phase j
+    if (!ok) *s_bad = 1;
+    __syncthreads();
+    if (*s_bad) break;
     if (mine) {
 #pragma unroll
       for (int z = 0; z < ITZ; ++z) {  // z pass and the FP64 update, in the staged tile
@@ -676,12 +731,14 @@ __global__ void __launch_bounds__(256) interp_space3d_tma_kernel(const __grid_co
     }
   }
   if (threadIdx.x == 0) {
-    if (s_bad) {
+    if (*s_bad) {
       atomicExch(&g_interp_timeout, 1);
-      // the last two loads issued (one per buffer, phases as numbered above) may still be
-      // in flight: wait for them (bounded) before the CTA's shared memory is released
+      // loads possibly still in flight: the last two fine tiles (one per buffer, phases as
+      // numbered above) and the last coarse box; wait for them (bounded) before the CTA's
+      // shared memory is released
       for (int t = issued - m0 - 1; t <= issued - m0; ++t)
         if (t >= 0) mbar_wait(&bar[t & 1], (uint32_t)(t >> 1) & 1u);
+      mbar_wait(&bar[2], (uint32_t)(issued_c - 1) & 1u);
     }
     bulk_wait_all();  // every bulk store complete before the CTA exits
   }
@@ -835,33 +892,33 @@ __global__ void __launch_bounds__(256, 4) fine_rhs_chain_kernel(Grid g, ResCoef 
       unsigned long long mxb = 0ULL;
       if (valid) {
         const double *Ub = U + b * stride;
-        double Uv[S], Gv[S];
-        if (b == 0) {
-          Uv[0] = Ub[off];
-          Gv[0] = nbsum<DIM>(Ub, g, i, j, k, off) - 2.0 * DIM * Uv[0];
-        } else {
-          Uv[0] = Ulast;
-          Gv[0] = Glast;
-        }
+        // U_1 .. U_{S-1} first: q_m starts from -U_{m+1}; then each node's Laplacian goes
+        // straight into the S-1 sums (the FMA order over nodes is 0 .. S-1 as before), so
+        // the Laplacians are never all live at once
+        double Uv[S], qv[S - 1];
+        Uv[0] = b == 0 ? Ub[off] : Ulast;
 #pragma unroll
-        for (int jn = 1; jn < S; ++jn) {
-          const double *Uj = Ub + jn * g.slab;
-          Uv[jn] = Uj[off];
-          Gv[jn] = nbsum<DIM>(Uj, g, i, j, k, off) - 2.0 * DIM * Uv[jn];
+        for (int jn = 1; jn < S; ++jn) Uv[jn] = Ub[jn * g.slab + off];
+#pragma unroll
+        for (int m = 0; m + 1 < S; ++m) qv[m] = -Uv[m + 1];
+        double G = 0.0;
+#pragma unroll
+        for (int jn = 0; jn < S; ++jn) {
+          if (jn == 0 && b > 0) G = Glast;
+          else G = nbsum<DIM>(Ub + jn * g.slab, g, i, j, k, off) - 2.0 * DIM * Uv[jn];
+#pragma unroll
+          for (int m = 0; m + 1 < S; ++m) qv[m] = fma(cf.dS[m][jn], G, qv[m]);
         }
         double r = 0.0;
 #pragma unroll
         for (int m = 0; m + 1 < S; ++m) {
-          double qm = -Uv[m + 1];
-#pragma unroll
-          for (int jn = 0; jn < S; ++jn) qm = fma(cf.dS[m][jn], Gv[jn], qm);
-          q[b * sq + m * g.slab + off] = qm;
-          r = m == 0 ? Uv[0] + qm : r + (qm + Uv[m]);  // r_{m+1}
+          q[b * sq + m * g.slab + off] = qv[m];
+          r = m == 0 ? Uv[0] + qv[m] : r + (qv[m] + Uv[m]);  // r_{m+1}
           const unsigned long long rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffULL;
           mxb = rb > mxb ? rb : mxb;
         }
         Ulast = Uv[S - 1];
-        Glast = Gv[S - 1];
+        Glast = G;
       }
       if (res) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -1217,7 +1274,8 @@ template <typename T, int ORD>
 cudaError_t launch_interp_space3d_tma(const Launch &L, const Grid &gf, const Grid &gc, int sf, const void *dU,
                                       double *Uf, int batch, int m0) {
   const size_t smem = 2 * (size_t)ITX * ITY * ITZ * 8 +
-                      sizeof(T) * (I3CZ * I3CY * I3CX + I3CZ * I3CY * ITX + I3CZ * ITY * ITX) + 2 * sizeof(uint64_t);
+                      sizeof(T) * (I3CZ * I3CY * I3CW + I3CZ * I3CY * ITX + I3CZ * ITY * ITX) + 3 * sizeof(uint64_t) +
+                      sizeof(int);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(interp_space3d_tma_kernel<T, ORD>,
@@ -1225,19 +1283,28 @@ cudaError_t launch_interp_space3d_tma(const Launch &L, const Grid &gf, const Gri
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  const cuuint32_t es[4] = {1, 1, 1, 1};
   // the fine grid functions of all slices and nodes as one 4D tensor (x, y, z, slice * sf + node)
-  CUtensorMap mu;
+  CUtensorMap mu, mc;
   const cuuint64_t dims[4] = {(cuuint64_t)gf.pitch, (cuuint64_t)gf.ny, (cuuint64_t)gf.nz, (cuuint64_t)batch * sf};
   const cuuint64_t strides[3] = {(cuuint64_t)gf.pitch * 8, (cuuint64_t)gf.ny * gf.pitch * 8, (cuuint64_t)gf.slab * 8};
   const cuuint32_t box[4] = {ITX, ITY, ITZ, 1};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
+  // the coarse corrections likewise, x limited to the interior (the pad column reads as zero)
+  const cuuint64_t cdims[4] = {(cuuint64_t)gc.n, (cuuint64_t)gc.ny, (cuuint64_t)gc.nz, (cuuint64_t)batch * sf};
+  const cuuint64_t cstrides[3] = {(cuuint64_t)gc.pitch * sizeof(T), (cuuint64_t)gc.ny * gc.pitch * sizeof(T),
+                                  (cuuint64_t)gc.slab * sizeof(T)};
+  const cuuint32_t cbox[4] = {I3CW, I3CY, I3CZ, 1};
   if (tma::encoder()(&mu, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, Uf, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      tma::encoder()(&mc, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                     const_cast<void *>(dU), cdims, cstrides, cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int ntx = gf.pitch / ITX, nty = (gf.n + ITY - 1) / ITY, ntz = (gf.n + ITZ - 1) / ITZ;
   dim3 gr(ntx, nty, ntz * batch);
-  interp_space3d_tma_kernel<T, ORD><<<gr, 256, smem, L.stream>>>(mu, gf, gc, sf, (const T *)dU, ntz, m0);
+  interp_space3d_tma_kernel<T, ORD><<<gr, 256, smem, L.stream>>>(mu, mc, gf, gc, sf, (const T *)dU, ntz, m0);
   return cudaGetLastError();
 }
 
@@ -1246,8 +1313,8 @@ cudaError_t launch_interp_space3d(const Launch &L, const Grid &gf, const Grid &g
                                   double *Uf, long long sfine, int batch, int m0) {
   // TMA-staged fine tiles: whole 32-column tiles per row, tiles no larger than the grid,
   // slices stored back to back (sfine = sf slabs), 16-byte aligned base
-  if (gf.pitch % ITX == 0 && gf.n >= 31 && sfine == (long long)sf * gf.slab && ((uintptr_t)Uf & 15) == 0 &&
-      tma::encoder() != nullptr)
+  if (gf.pitch % ITX == 0 && gc.n >= I3CW && gc.pitch % 4 == 0 && sfine == (long long)sf * gf.slab &&
+      ((uintptr_t)Uf & 15) == 0 && ((uintptr_t)dU & 15) == 0 && tma::encoder() != nullptr)
     return order == 2 ? launch_interp_space3d_tma<T, 2>(L, gf, gc, sf, dU, Uf, batch, m0)
                       : launch_interp_space3d_tma<T, 4>(L, gf, gc, sf, dU, Uf, batch, m0);
   const int ntx = (gf.n + ITX - 1) / ITX, nty = (gf.n + ITY - 1) / ITY, ntz = (gf.n + ITZ - 1) / ITZ;

@@ -117,70 +117,115 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 // out[p][o] = sum_t sum_c Wb[t][o][c] act[p + off_t][c]   (Wb: BF16 [27][16][16])
 // MODE 0 (forward):  out_bf[p][o] = relu(. + bias[o])               (BF16)
 // MODE 1 (backward): out_f[p][o]  = . if mask[p][o] > 0, else 0      (FP32)
-// Fragment layout of m16n8k16 (PTX ISA, "Matrix Fragments for mma.m16n8k16"): with
-// g = lane / 4 and q = lane % 4, A registers 0..3 hold (row g, k 2q..2q+1),
-// (row g+8, k 2q..), (row g, k 2q+8..), (row g+8, k 2q+8..); B registers 0..1 hold
-// (k 2q..2q+1, col g), (k 2q+8..2q+9, col g); C holds (row g, col 2q..2q+1) and
-// (row g+8, col 2q..2q+1).  Rows = grid points x0 + 0..15, k = input channel, col =
-// output channel, so every register is one aligned channel pair of one point.
+// An implicit GEMM on mma.sync m16n8k16 (BF16 in, FP32 accumulate): M = 16 consecutive
+// points of a grid row, N = 16 output channels (two 8-wide tiles), K = 27 taps x 16
+// input channels (one k16 step per tap).  Fragment layout (PTX ISA, "Matrix Fragments
+// for mma.m16n8k16"), g = lane / 4, q = lane % 4: A registers 0..3 hold (row g, k
+// 2q..2q+1), (row g+8, k 2q..), (row g, k 2q+8..), (row g+8, k 2q+8..); B registers 0..1
+// hold (k 2q..2q+1, col g), (k 2q+8..2q+9, col g); C holds (row g, col 2q..2q+1) and
+// (row g+8, col 2q..2q+1).  Rows = points, k = input channel, col = output channel.
+//
+// A CTA takes tiles of 16 (x) x 8 (y) x 4 (z) points and stages their 18 x 10 x 6
+// neighbourhood in shared memory once (zeros outside the grid, so no tap needs a bounds
+// check), each point's 16 channels split into two 16-byte halves (channels 0-7, 8-15) in
+// separate arrays, so that the eight rows of an 8 x 8 ldmatrix operand are 128
+// contiguous bytes (no bank conflicts).  Per tap a warp loads the B operands of both
+// N tiles with one ldmatrix.x4 from the staged weights (same half split) and, for each of
+// its four 16-point rows, the A operand with one ldmatrix.x4: matrices (points 0-7,
+// channels 0-7), (points 8-15, ch 0-7), (points 0-7, ch 8-15), (points 8-15, ch 8-15)
+// are A registers 0..3 (ldmatrix gives thread (g, q) row g, elements 2q, 2q+1 of each
+// matrix).
+constexpr int L2X = 16, L2Y = 8, L2Z = 4;                                 // tile
+constexpr int L2HX = L2X + 2, L2HY = L2Y + 2, L2HZ = L2Z + 2;               // with halo
+constexpr int L2HP = L2HX * L2HY * L2HZ;                                    // staged points
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(256) l2_mma_kernel(NetGrid g, const __nv_bfloat16 *__restrict__ act,
-                                                     const __nv_bfloat16 *__restrict__ Wb,
-                                                     const float *__restrict__ bias,
-                                                     const __nv_bfloat16 *__restrict__ mask,
-                                                     __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f) {
-  __shared__ __align__(16) __nv_bfloat16 Ws[27 * NC * NC];
-  for (int i = threadIdx.x; i < 27 * NC * NC / 8; i += blockDim.x) ((uint4 *)Ws)[i] = ((const uint4 *)Wb)[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, gq = lane >> 2, t4 = lane & 3;
-  const int segs = (g.n + 15) / 16;
-  const long long nwarps = (long long)g.batch * g.n * g.n * segs;
-  const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < nwarps; w += wstride) {
-    const int seg = (int)(w % segs);
-    const long long row = w / segs;  // (b, z, y)
-    const int y = (int)(row % g.n), z = (int)((row / g.n) % g.n), b = (int)(row / ((long long)g.n * g.n));
-    const int x0 = seg * 16;
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+__global__ void __launch_bounds__(256) l2_tile_kernel(NetGrid g, const __nv_bfloat16 *__restrict__ act,
+                                                      const __nv_bfloat16 *__restrict__ Wb,
+                                                      const float *__restrict__ bias,
+                                                      const __nv_bfloat16 *__restrict__ mask,
+                                                      __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f) {
+  __shared__ __align__(128) uint4 Wh[2][27][NC];   // [channel half][tap][output channel]
+  __shared__ __align__(128) uint4 Ah[2][L2HP];     // [channel half][staged point]
+  for (int i = threadIdx.x; i < 27 * NC * 2; i += blockDim.x) {
+    const int half = i & 1, to = i >> 1;  // to = t * NC + o
+    Wh[half][to / NC][to % NC] = ((const uint4 *)Wb)[i];
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t4 = lane & 3;
+  // this lane's ldmatrix row: matrix lane / 8, row lane % 8
+  const int mat = lane >> 3, mrow = lane & 7;
+  const int a_pt = (mat & 1) * 8 + mrow, a_half = mat >> 1;  // A: point of the row segment, channel half
+  const int b_half = mat & 1, b_o = (mat >> 1) * 8 + mrow;   // B: channel half, output channel
+  const int ntx = (g.n + L2X - 1) / L2X, nty = (g.n + L2Y - 1) / L2Y, ntz = (g.n + L2Z - 1) / L2Z;
+  const long long ntiles = (long long)g.batch * ntx * nty * ntz;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int tx = (int)(tile % ntx), ty = (int)((tile / ntx) % nty), tz = (int)((tile / ((long long)ntx * nty)) % ntz);
+    const int b = (int)(tile / ((long long)ntx * nty * ntz));
+    const int x0 = tx * L2X, y0 = ty * L2Y, z0 = tz * L2Z;
+    __syncthreads();  // the previous tile's reads are done (and the weights staged)
+    for (int q = threadIdx.x; q < L2HP; q += blockDim.x) {  // one point (both halves) per thread
+      const int xx = x0 - 1 + q % L2HX, yy = y0 - 1 + (q / L2HX) % L2HY, zz = z0 - 1 + q / (L2HX * L2HY);
+      uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+      if (inside(zz, yy, xx, g.n)) {
+        const uint4 *src = (const uint4 *)(act + dense_index(b, zz, yy, xx, g.n) * NC);
+        lo = src[0];
+        hi = src[1];
+      }
+      Ah[0][q] = lo;
+      Ah[1][q] = hi;
+    }
+    __syncthreads();
+    float acc[4][2][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][nt][q] = 0.f;
+#pragma unroll 1
     for (int t = 0; t < 27; ++t) {
       int dz, dy, dx;
       tap_offset(t, dz, dy, dx);
-      const int zz = z + dz, yy = y + dy;
-      unsigned a[4] = {0u, 0u, 0u, 0u};
-      if (zz >= 0 && zz < g.n && yy >= 0 && yy < g.n) {
+      unsigned bf[4];
+      ldsm_x4(bf, &Wh[b_half][t][b_o]);
+      const unsigned b0[2] = {bf[0], bf[1]}, b1[2] = {bf[2], bf[3]};
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // rows gq and gq + 8 of the A tile
-          const int xo = x0 + gq + 8 * h, xx = xo + dx;
-          if (xo < g.n && xx >= 0 && xx < g.n) {
-            const unsigned *src = (const unsigned *)(act + dense_index(b, zz, yy, xx, g.n) * NC);
-            a[h] = src[t4];          // channels 2 t4, 2 t4 + 1
-            a[2 + h] = src[4 + t4];  // channels 2 t4 + 8, 2 t4 + 9
-          }
-        }
-      }
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const unsigned *wr = (const unsigned *)(Ws + (t * NC + nt * 8 + gq) * NC);
-        const unsigned bb[2] = {wr[t4], wr[4 + t4]};
-        mma_bf16(acc[nt], a, bb);
+      for (int r = 0; r < 4; ++r) {
+        const int row = warp + 8 * r, yl = row % L2Y, zl = row / L2Y;  // the warp's rows of the tile
+        const int q = ((zl + dz + 1) * L2HY + (yl + dy + 1)) * L2HX + (dx + 1) + a_pt;
+        unsigned a[4];
+        ldsm_x4(a, &Ah[a_half][q]);
+        mma_bf16(acc[r][0], a, b0);
+        mma_bf16(acc[r][1], a, b1);
       }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int x = x0 + gq + 8 * h;
-      if (x >= g.n) continue;
-      const long long p = dense_index(b, z, y, x, g.n);
+    for (int r = 0; r < 4; ++r) {
+      const int row = warp + 8 * r, y = y0 + row % L2Y, z = z0 + row / L2Y;
+      if (y >= g.n || z >= g.n) continue;
 #pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const int o = nt * 8 + 2 * t4;
-        float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
-        if (MODE == 0) {
-          v0 = fmaxf(v0 + bias[o], 0.f);
-          v1 = fmaxf(v1 + bias[o + 1], 0.f);
-          *(__nv_bfloat162 *)(out_bf + p * NC + o) = __floats2bfloat162_rn(v0, v1);
-        } else {
-          const float2 m = __bfloat1622float2(*(const __nv_bfloat162 *)(mask + p * NC + o));
-          *(float2 *)(out_f + p * NC + o) = make_float2(m.x > 0.f ? v0 : 0.f, m.y > 0.f ? v1 : 0.f);
+      for (int h = 0; h < 2; ++h) {
+        const int x = x0 + gq + 8 * h;
+        if (x >= g.n) continue;
+        const long long p = dense_index(b, z, y, x, g.n);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int o = nt * 8 + 2 * t4;
+          float v0 = acc[r][nt][2 * h], v1 = acc[r][nt][2 * h + 1];
+          if (MODE == 0) {
+            v0 = fmaxf(v0 + bias[o], 0.f);
+            v1 = fmaxf(v1 + bias[o + 1], 0.f);
+            *(__nv_bfloat162 *)(out_bf + p * NC + o) = __floats2bfloat162_rn(v0, v1);
+          } else {
+            const float2 m = __bfloat1622float2(*(const __nv_bfloat162 *)(mask + p * NC + o));
+            *(float2 *)(out_f + p * NC + o) = make_float2(m.x > 0.f ? v0 : 0.f, m.y > 0.f ? v1 : 0.f);
+          }
         }
       }
     }
@@ -578,6 +623,15 @@ __global__ void net_maxabs_kernel(Grid g, const T *__restrict__ e, int batch, un
 
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// CTAs of the tiled 16 -> 16 layer: at most 4 per SM (48 KB of shared memory each), each
+// walking several tiles so that the weights are staged once per CTA
+int l2_tile_blocks(const NetGrid &g) {
+  const long long tiles = (long long)g.batch * ((g.n + L2X - 1) / L2X) * ((g.n + L2Y - 1) / L2Y) *
+                          ((g.n + L2Z - 1) / L2Z);
+  const long long b = tiles < 152 * 4 * 4 ? tiles : 152 * 4 * 4;
+  return (int)(b < 1 ? 1 : b);
+}
+
 cudaError_t net_hidden(const Launch &L, const NetGrid &g, const float *x, const float *prm, const NetScratch &s) {
   const Grid gg = cube(g.n);
   const long long npts = (long long)g.batch * g.n * g.n * g.n;
@@ -587,10 +641,8 @@ cudaError_t net_hidden(const Launch &L, const NetGrid &g, const float *x, const 
     cudaError_t e = sc.done();
     if (e != cudaSuccess) return e;
   }
-  const long long nwarps = (long long)g.batch * g.n * g.n * ((g.n + 15) / 16);
   Scope sc(L, K_NET_L2, gg, g.batch, 1);
-  l2_mma_kernel<0><<<grid_blocks(nwarps * 32, 256), 256, 0, L.stream>>>(g, s.a1, s.w2f, prm + kNetB2, nullptr, s.a2,
-                                                                         nullptr);
+  l2_tile_kernel<0><<<l2_tile_blocks(g), 256, 0, L.stream>>>(g, s.a1, s.w2f, prm + kNetB2, nullptr, s.a2, nullptr);
   return sc.done();
 }
 
@@ -719,9 +771,8 @@ cudaError_t k_net_grads(const Launch &L, const NetGrid &g, const float *x, const
   PMG_NET_STEP(K_NET_L3BWD, (l3_bwd_data_kernel<<<nb, 256, 0, L.stream>>>(g, s.gy, s.a2, prm, s.gz2, s.gz2b)));
   PMG_NET_STEP(K_NET_WGRAD,
                (wgrad_mma_kernel<<<wb, 256, 0, L.stream>>>(g, s.gz2, s.a1, grad + kNetW2, grad + kNetB2)));
-  const long long nwarps = (long long)g.batch * g.n * g.n * ((g.n + 15) / 16);
-  PMG_NET_STEP(K_NET_L2BWD, (l2_mma_kernel<1><<<grid_blocks(nwarps * 32, 256), 256, 0, L.stream>>>(
-                                g, s.gz2b, s.w2t, nullptr, s.a1, nullptr, s.gz1)));
+  PMG_NET_STEP(K_NET_L2BWD, (l2_tile_kernel<1><<<l2_tile_blocks(g), 256, 0, L.stream>>>(g, s.gz2b, s.w2t, nullptr,
+                                                                                       s.a1, nullptr, s.gz1)));
   PMG_NET_STEP(K_NET_WGRAD, (wgrad_kernel<NC, 1, float><<<wb, 256, 0, L.stream>>>(g, s.gz1, x, grad + kNetW1,
                                                                                  grad + kNetB1)));
 #undef PMG_NET_STEP
