@@ -929,6 +929,8 @@ def run_ours(args):
     common = dict(smoother=wl.smoother, omega=wl.omega, vcycles=wl.vcycles, interp_order=4)
     # the measured variant's coarse-level V-cycles (the FP64 reference keeps the workload's)
     variant = dict(coarse_vcycles=args.coarse_vcycles) if args.coarse_vcycles >= 0 else {}
+    if args.vcycle_tail >= 0:
+        variant["vcycle_tail"] = args.vcycle_tail
 
     fp64_ms, fp64_runs = None, []
     r_ref = None
@@ -1093,6 +1095,7 @@ def run_ours(args):
                    "slices": wl.slices, "nodes": f"{wl.fine_nodes}/{wl.coarse_nodes} Gauss-Lobatto",
                    "smoother": "V(2,1) " + ("red-black Gauss-Seidel" if wl.smoother == 1 else "Jacobi 2/3"),
                    "vcycles": wl.vcycles, "coarse_vcycles": args.coarse_vcycles if args.coarse_vcycles >= 0 else wl.vcycles,
+                   "vcycle_tail": pmg.pfasst_mg_default_options().vcycle_tail if args.vcycle_tail < 0 else args.vcycle_tail,
                    "precision": "FP32 V-cycles, FP64 SDC/FAS" if wl.precision else "FP64",
                    "K_ref": k_ref, "residual_target": target, "residual_tolerance": RES_TOL,
                    "fp64_residual_at_K_ref": r_ref, "iterations": [it for _, it, _ in iters],
@@ -1171,7 +1174,8 @@ def main():
     ap.add_argument("--coarse-vcycles", type=int, default=-1,
                     help="measured variant: V-cycles per coarse-level sub-step (-1: the workload's)")
     ap.add_argument("--vcycle-tail", type=int, default=-1,
-                    help="heat1d: 1 = run each V-cycle's levels that fit one CTA in one launch, 0 = per level")
+                    help="1 = run the levels of a single-grid V-cycle that fit one CTA in one launch, 0 = per level "
+                         "(-1: the library default)")
     ap.add_argument("--tma", type=int, nargs="?", const=3, default=0, choices=(0, 2, 3),
                     help="pin the TMA-staged sweep on every level that can run it (profiling runs): "
                          "2 = two x points per thread, 3 (bare flag) = four")

@@ -892,33 +892,33 @@ __global__ void __launch_bounds__(256, 4) fine_rhs_chain_kernel(Grid g, ResCoef 
       unsigned long long mxb = 0ULL;
       if (valid) {
         const double *Ub = U + b * stride;
-        // U_1 .. U_{S-1} first: q_m starts from -U_{m+1}; then each node's Laplacian goes
-        // straight into the S-1 sums (the FMA order over nodes is 0 .. S-1 as before), so
-        // the Laplacians are never all live at once
-        double Uv[S], qv[S - 1];
-        Uv[0] = b == 0 ? Ub[off] : Ulast;
+        double Uv[S], Gv[S];
+        if (b == 0) {
+          Uv[0] = Ub[off];
+          Gv[0] = nbsum<DIM>(Ub, g, i, j, k, off) - 2.0 * DIM * Uv[0];
+        } else {
+          Uv[0] = Ulast;
+          Gv[0] = Glast;
+        }
 #pragma unroll
-        for (int jn = 1; jn < S; ++jn) Uv[jn] = Ub[jn * g.slab + off];
-#pragma unroll
-        for (int m = 0; m + 1 < S; ++m) qv[m] = -Uv[m + 1];
-        double G = 0.0;
-#pragma unroll
-        for (int jn = 0; jn < S; ++jn) {
-          if (jn == 0 && b > 0) G = Glast;
-          else G = nbsum<DIM>(Ub + jn * g.slab, g, i, j, k, off) - 2.0 * DIM * Uv[jn];
-#pragma unroll
-          for (int m = 0; m + 1 < S; ++m) qv[m] = fma(cf.dS[m][jn], G, qv[m]);
+        for (int jn = 1; jn < S; ++jn) {
+          const double *Uj = Ub + jn * g.slab;
+          Uv[jn] = Uj[off];
+          Gv[jn] = nbsum<DIM>(Uj, g, i, j, k, off) - 2.0 * DIM * Uv[jn];
         }
         double r = 0.0;
 #pragma unroll
         for (int m = 0; m + 1 < S; ++m) {
-          q[b * sq + m * g.slab + off] = qv[m];
-          r = m == 0 ? Uv[0] + qv[m] : r + (qv[m] + Uv[m]);  // r_{m+1}
+          double qm = -Uv[m + 1];
+#pragma unroll
+          for (int jn = 0; jn < S; ++jn) qm = fma(cf.dS[m][jn], Gv[jn], qm);
+          q[b * sq + m * g.slab + off] = qm;
+          r = m == 0 ? Uv[0] + qm : r + (qm + Uv[m]);  // r_{m+1}
           const unsigned long long rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffULL;
           mxb = rb > mxb ? rb : mxb;
         }
         Ulast = Uv[S - 1];
-        Glast = G;
+        Glast = Gv[S - 1];
       }
       if (res) {
         for (int o = 16; o > 0; o >>= 1) {

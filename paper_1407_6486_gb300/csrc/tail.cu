@@ -207,9 +207,175 @@ __global__ void __launch_bounds__(kVTailThreads) vtail_kernel(VTailDesc d, const
   }
 }
 
+// The same V-cycle bottom for 3D red-black Gauss-Seidel with a top level of at most
+// 15^3 points: 1024 threads as a 16 x 8 x 8 block, thread (tx, ty, tz) owning the points
+// (tx, ty + 8 s, tz + 8 t) of a level -- four on 15^3, one on 7^3 -- so no index is
+// divided; every level array is stored with a zero halo ((n + 2)^3 entries) so that the
+// stencil needs no bounds test, and a colour pass visits only its own points.  The
+// operations and their order per point are those of vtail_kernel.
+constexpr int kVTail3Threads = 1024;
+
+__host__ __device__ __forceinline__ int vt3_pad(int n) { return (n + 2) * (n + 2) * (n + 2); }
+
+template <typename T>
+__global__ void __launch_bounds__(kVTail3Threads) vtail3d_rb_kernel(VTailDesc d, const T *__restrict__ minv,
+                                                                    const T *__restrict__ fin, long long fslab,
+                                                                    int fpitch, const T *ein, T *eout,
+                                                                    long long eslab, int epitch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = (T *)smem_raw;
+  const int tid = threadIdx.x, tx = tid & 15, ty = (tid >> 4) & 7, tz = tid >> 7;
+  const int b = blockIdx.x;
+  // level arrays by the offsets of the padded layout (vtail3d_layout); the e arrays,
+  // which hold every level's e together, start at 0: zero them (halos and the corrections
+  // that start from zero); f and r are written before they are read
+  for (int q = tid; q < d.off_f[0]; q += kVTail3Threads) sm[q] = T(0);
+  auto E = [&](int l) { return sm + d.off_e[l]; };
+  auto F = [&](int l) { return sm + d.off_f[l]; };
+  auto R = [&](int l) { return sm + d.off_r[l]; };
+  auto coef = [&](int l) { return (T)d.c * (T)((double)(d.n[l] + 1) * (double)(d.n[l] + 1)); };
+  // padded index of interior point (i, j, k) of a level with n points per axis
+  auto P = [](int n, int i, int j, int k) { return (i + 1) + (n + 2) * ((j + 1) + (n + 2) * (k + 1)); };
+  // neighbour sum in the order of dnb: (x- + x+) + (y- + y+) + (z- + z+)
+  auto nb6 = [](const T *u, int p, int s1, int s2) {
+    T s = u[p - 1] + u[p + 1];
+    s += u[p - s1] + u[p + s1];
+    s += u[p - s2] + u[p + s2];
+    return s;
+  };
+  // this thread's points of a level: (tx, ty + 8 s, tz + 8 t) inside n^3
+#define VT3_FOR(n)                                    \
+  for (int k = tz; k < (n); k += 8)                   \
+    for (int j = ty; j < (n); j += 8)                 \
+      if (tx < (n))
+  const T omega = (T)d.omega;
+  // one red-black sweep of level l (first: from a zero correction)
+  auto sweep = [&](int l, bool first) {
+    const int n = d.n[l], s1 = n + 2, s2 = (n + 2) * (n + 2);
+    const T a = coef(l), D = T(1) + T(6) * a;
+    T *e = E(l);
+    const T *f = F(l);
+    for (int colour = 0; colour < 2; ++colour) {  // red = even 1-based index sum, first
+      VT3_FOR(n) {
+        const int i = tx;
+        if (((i + j + k + 3) & 1) != colour) continue;
+        const int p = P(n, i, j, k);
+        if (first && colour == 0) {
+          e[p] = omega * (f[p] / D);  // black entries are already zero
+          continue;
+        }
+        const T gs = (f[p] + a * nb6(e, p, s1, s2)) / D;
+        e[p] = (T(1) - omega) * e[p] + omega * gs;
+      }
+      __syncthreads();
+    }
+  };
+  __syncthreads();
+  {  // right-hand side (and initial correction) of the top level from the padded layout
+    const int n = d.n[0];
+    VT3_FOR(n) {
+      const long long g = ((long long)k * n + j) * fpitch + tx;
+      F(0)[P(n, tx, j, k)] = fin[b * fslab + g];
+      if (ein) E(0)[P(n, tx, j, k)] = ein[b * eslab + ((long long)k * n + j) * epitch + tx];
+    }
+  }
+  __syncthreads();
+  // down: pre-smoothing, residual, full weighting
+  for (int l = 0; l < d.nlev - 1; ++l) {
+    const int n = d.n[l], s1 = n + 2, s2 = (n + 2) * (n + 2);
+    const T a = coef(l);
+    const bool zero = l > 0 || ein == nullptr;
+    for (int s = 0; s < d.nu1; ++s) sweep(l, zero && s == 0);
+    VT3_FOR(n) {
+      const int p = P(n, tx, j, k);
+      const T ec = E(l)[p];
+      R(l)[p] = F(l)[p] - (ec - a * (nb6(E(l), p, s1, s2) - T(6) * ec));
+    }
+    __syncthreads();
+    const int nc = d.n[l + 1];
+    const T w3[3] = {T(0.25), T(0.5), T(0.25)};
+    VT3_FOR(nc) {
+      T acc = T(0);
+      for (int cz = -1; cz <= 1; ++cz)
+        for (int cy = -1; cy <= 1; ++cy)
+          for (int cx = -1; cx <= 1; ++cx) {
+            T w = w3[cx + 1];
+            w *= w3[cy + 1];
+            w *= w3[cz + 1];
+            acc += w * R(l)[P(n, 2 * tx + 1 + cx, 2 * j + 1 + cy, 2 * k + 1 + cz)];
+          }
+      F(l + 1)[P(nc, tx, j, k)] = acc;
+    }
+    __syncthreads();
+  }
+  {  // exact solve on the 3^3 level (dense order i + 3 j + 9 k of the inverse)
+    const int lc = d.nlev - 1;
+    if (tid < 27) {
+      T acc = T(0);
+      for (int q = 0; q < 27; ++q) acc += minv[tid * 27 + q] * F(lc)[P(3, q % 3, (q / 3) % 3, q / 9)];
+      E(lc)[P(3, tid % 3, (tid / 3) % 3, tid / 9)] = acc;
+    }
+    __syncthreads();
+  }
+  // up: linear prolongation added, post-smoothing
+  for (int l = d.nlev - 2; l >= 0; --l) {
+    const int n = d.n[l], nc = d.n[l + 1];
+    VT3_FOR(n) {
+      int ix[2], iy[2], iz[2];
+      float wx[2], wy[2], wz[2];
+      const int ntx = lin_taps_t(tx, nc, ix, wx), nty = lin_taps_t(j, nc, iy, wy), ntz = lin_taps_t(k, nc, iz, wz);
+      T acc = T(0);
+      for (int cz = 0; cz < ntz; ++cz)
+        for (int cy = 0; cy < nty; ++cy)
+          for (int cx = 0; cx < ntx; ++cx)
+            acc += T(wx[cx] * wy[cy] * wz[cz]) * E(l + 1)[P(nc, ix[cx], iy[cy], iz[cz])];
+      E(l)[P(n, tx, j, k)] += acc;
+    }
+    __syncthreads();
+    for (int s = 0; s < d.nu2; ++s) sweep(l, false);
+  }
+  {  // correction of the top level to the padded layout
+    const int n = d.n[0];
+    VT3_FOR(n) eout[b * eslab + ((long long)k * n + j) * epitch + tx] = E(0)[P(n, tx, j, k)];
+  }
+#undef VT3_FOR
+}
+
+// the padded layout of vtail3d_rb_kernel in d's offsets: the e arrays of all levels
+// first, then f and r of each level; returns the shared-memory bytes
+size_t vtail3d_layout(VTailDesc &d, size_t tsize) {
+  int t = 0;
+  for (int l = 0; l < d.nlev; ++l) {
+    d.off_e[l] = t;
+    t += vt3_pad(d.n[l]);
+  }
+  for (int l = 0; l < d.nlev; ++l) {
+    d.off_f[l] = t;
+    t += vt3_pad(d.n[l]);
+    d.off_r[l] = t;
+    t += vt3_pad(d.n[l]);
+  }
+  return (size_t)t * tsize;
+}
+
 template <int DIM, typename T>
 cudaError_t launch_tail(const Launch &L, const VTailDesc &d, const void *minv, const void *f, long long fslab,
                         int fpitch, const void *ein, void *e, long long eslab, int epitch, int batch) {
+  VTailDesc d3 = d;
+  if (DIM == 3 && d.smoother == 1 && d.n[0] <= 15 && d.n[d.nlev - 1] == 3 &&
+      vtail3d_layout(d3, sizeof(T)) <= kVTailMaxSmem) {
+    const size_t smem = vtail3d_layout(d3, sizeof(T));
+    static bool attr3 = false;
+    if (!attr3) {
+      cudaError_t err = cudaFuncSetAttribute(vtail3d_rb_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kVTailMaxSmem);
+      if (err != cudaSuccess) return err;
+      attr3 = true;
+    }
+    vtail3d_rb_kernel<T><<<batch, kVTail3Threads, smem, L.stream>>>(d3, (const T *)minv, (const T *)f, fslab, fpitch,
+                                                                      (const T *)ein, (T *)e, eslab, epitch);
+    return cudaGetLastError();
+  }
   const size_t smem = d.smem_elems * sizeof(T);
   if (smem > kVTailMaxSmem) return cudaErrorInvalidValue;
   static bool attr = false;  // once per instantiation, before any capture uses it
