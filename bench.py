@@ -269,6 +269,8 @@ def run_uneven(args):
     desc = [(p.dim, p.n, p.nodes, p.nu, p.dt) for p in probs]
     u0s = [torch.tensor(p.u0(), device="cuda") for p in probs]
     opts = dict(smoother=1, omega=1.0, vcycles=2, precision=1)
+    if args.vcycle_tail >= 0:
+        opts["vcycle_tail"] = args.vcycle_tail
 
     def job(b):
         for i, u in enumerate(u0s):
@@ -1095,7 +1097,7 @@ def run_ours(args):
                    "slices": wl.slices, "nodes": f"{wl.fine_nodes}/{wl.coarse_nodes} Gauss-Lobatto",
                    "smoother": "V(2,1) " + ("red-black Gauss-Seidel" if wl.smoother == 1 else "Jacobi 2/3"),
                    "vcycles": wl.vcycles, "coarse_vcycles": args.coarse_vcycles if args.coarse_vcycles >= 0 else wl.vcycles,
-                   "vcycle_tail": pmg.pfasst_mg_default_options().vcycle_tail if args.vcycle_tail < 0 else args.vcycle_tail,
+                   "vcycle_tail": "auto" if args.vcycle_tail < 0 else args.vcycle_tail,
                    "precision": "FP32 V-cycles, FP64 SDC/FAS" if wl.precision else "FP64",
                    "K_ref": k_ref, "residual_target": target, "residual_tolerance": RES_TOL,
                    "fp64_residual_at_K_ref": r_ref, "iterations": [it for _, it, _ in iters],

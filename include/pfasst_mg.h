@@ -101,12 +101,15 @@ typedef struct {
                              > g (same results); 0 or 1 = no overlap, at most 8 (2 groups
                              gain 1.5 % on the 3D workload: every fine kernel already fills
                              the GPU)                                                       */
-    int    vcycle_tail;   /* 1: for single grids (the serial coarse chain) the coarsest
-                             multigrid levels (from the first level whose whole remaining
-                             V-cycle fits one CTA's shared memory: 15^3 in 3D, 63^2 in 2D)
-                             run as one kernel launch per V-cycle; 0 (default): one launch
-                             per smoothing sweep, restriction and prolongation (1 % faster
-                             per PFASST iteration on the 3D workload)                      */
+    int    vcycle_tail;   /* for single grids (the serial coarse chain, members of an uneven
+                             batch): 1 = the coarsest multigrid levels (from the first level
+                             whose whole remaining V-cycle fits one CTA's shared memory:
+                             15^3 in 3D, 63^2 in 2D, all of a 1D hierarchy) run as one kernel
+                             launch per V-cycle; 0 = one launch per smoothing sweep,
+                             restriction and prolongation; -1 (default) = automatic: one
+                             launch in 1D and for 3D red-black Gauss-Seidel, per level in 2D
+                             and for 3D Jacobi (the measured-faster choice on the 1D, 2D, 3D
+                             and uneven workloads)                                          */
     int    coarse_vcycles;/* sub-step solves on the coarse PFASST levels (levels >= 1):
                              -1 (default) = vcycles; 0 = solve to mg_tol with the stall
                              rule; > 0 = that many V-cycles.  The paper leaves the coarse
@@ -128,7 +131,7 @@ typedef struct pmg_ctx *pmg_handle;
 
 /* Defaults: Jacobi omega 2/3, V(2,1), 2 V-cycles, tol 1e-12, stall 0.75, cap 50,
  * FP64, 4th-order interpolation, graphs on, autotuning on, slice groups 0 (one group:
- * no overlap), V-cycle tail off, coarse levels as the fine level (coarse_vcycles -1),
+ * no overlap), V-cycle tail automatic (-1), coarse levels as the fine level (coarse_vcycles -1),
  * persistent single-grid V-cycles off. */
 void pfasst_mg_default_options(pmg_options *opt);
 

@@ -362,7 +362,7 @@ int validate(const pmg_grid *grid, const pmg_nodes_desc *fn, const pmg_levels *l
     }
     if (o->precision != PMG_PREC_FP64 && o->precision != PMG_PREC_MIXED) { why = "bad precision"; return PMG_ERR_INVALID_ARG; }
     if (o->interp_order != 2 && o->interp_order != 4) { why = "interp_order must be 2 or 4"; return PMG_ERR_INVALID_ARG; }
-    if (o->vcycle_tail != 0 && o->vcycle_tail != 1) { why = "vcycle_tail must be 0 or 1"; return PMG_ERR_INVALID_ARG; }
+    if (o->vcycle_tail < -1 || o->vcycle_tail > 1) { why = "vcycle_tail must be -1, 0 or 1"; return PMG_ERR_INVALID_ARG; }
     if (o->slice_groups < 0 || o->slice_groups > kMaxGroups) {
       why = "slice_groups must be 0 (automatic) .. 8";
       return PMG_ERR_INVALID_ARG;
@@ -539,7 +539,12 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, vo
   // batches keep the per-level kernels, which spread each level over many CTAs), unless
   // a learned correction acts there
   int lb = H.L;
-  if (o.vcycle_tail && H.tail >= l0 && B <= 2) {
+  // automatic (-1): one launch in 1D and for 3D red-black Gauss-Seidel, where it measured
+  // faster than the per-level launches; per level in 2D and for 3D Jacobi
+  const int dim = H.lev[0].dim;
+  const bool tail_on = o.vcycle_tail == 1 ||
+                       (o.vcycle_tail == -1 && (dim == 1 || (dim == 3 && o.smoother == PMG_SMOOTHER_RBGS)));
+  if (tail_on && H.tail >= l0 && B <= 2) {
     lb = H.tail;
     if (M.net)
       for (int l = H.tail; l < H.L; ++l)
@@ -1388,7 +1393,7 @@ void pfasst_mg_default_options(pmg_options *o) {
   o->use_graphs = 1;
   o->autotune = 1;
   o->slice_groups = 0;
-  o->vcycle_tail = 0;
+  o->vcycle_tail = -1;
   o->coarse_vcycles = -1;
   o->single_grid_vcycle = 0;
 }

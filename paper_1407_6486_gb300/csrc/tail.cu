@@ -215,6 +215,34 @@ __global__ void __launch_bounds__(kVTailThreads) vtail_kernel(VTailDesc d, const
 // operations and their order per point are those of vtail_kernel.
 constexpr int kVTail3Threads = 1024;
 
+// linear-interpolation taps of fine index i as two fixed slots (slot 1 unused at an even
+// 1-based index; a slot outside the coarse grid is marked off): the taps lin_taps_t lists,
+// in the same order
+struct Taps2 {
+  int i[2];
+  float w[2];
+  bool ok[2];
+};
+__device__ __forceinline__ Taps2 taps2(int i, int nc) {
+  Taps2 t;
+  const int i1 = i + 1;
+  if ((i1 & 1) == 0) {
+    t.i[0] = i1 / 2 - 1;
+    t.w[0] = 1.0f;
+    t.ok[0] = true;
+    t.i[1] = 0;
+    t.w[1] = 0.f;
+    t.ok[1] = false;
+  } else {
+    t.i[0] = (i1 - 1) / 2 - 1;
+    t.i[1] = (i1 + 1) / 2 - 1;
+    t.w[0] = t.w[1] = 0.5f;
+    t.ok[0] = t.i[0] >= 0;
+    t.ok[1] = t.i[1] < nc;
+  }
+  return t;
+}
+
 __host__ __device__ __forceinline__ int vt3_pad(int n) { return (n + 2) * (n + 2) * (n + 2); }
 
 template <typename T>
@@ -293,16 +321,20 @@ __global__ void __launch_bounds__(kVTail3Threads) vtail3d_rb_kernel(VTailDesc d,
     }
     __syncthreads();
     const int nc = d.n[l + 1];
-    const T w3[3] = {T(0.25), T(0.5), T(0.25)};
     VT3_FOR(nc) {
+      // unrolled: the weights are exact constants (products of 1/4 and 1/2)
+      const T *r0 = R(l) + P(n, 2 * tx + 1, 2 * j + 1, 2 * k + 1);
       T acc = T(0);
+#pragma unroll
       for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
         for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
           for (int cx = -1; cx <= 1; ++cx) {
-            T w = w3[cx + 1];
-            w *= w3[cy + 1];
-            w *= w3[cz + 1];
-            acc += w * R(l)[P(n, 2 * tx + 1 + cx, 2 * j + 1 + cy, 2 * k + 1 + cz)];
+            T w = cx == 0 ? T(0.5) : T(0.25);
+            w *= cy == 0 ? T(0.5) : T(0.25);
+            w *= cz == 0 ? T(0.5) : T(0.25);
+            acc += w * r0[cx + s1 * (cy + s1 * cz)];
           }
       F(l + 1)[P(nc, tx, j, k)] = acc;
     }
@@ -321,14 +353,17 @@ __global__ void __launch_bounds__(kVTail3Threads) vtail3d_rb_kernel(VTailDesc d,
   for (int l = d.nlev - 2; l >= 0; --l) {
     const int n = d.n[l], nc = d.n[l + 1];
     VT3_FOR(n) {
-      int ix[2], iy[2], iz[2];
-      float wx[2], wy[2], wz[2];
-      const int ntx = lin_taps_t(tx, nc, ix, wx), nty = lin_taps_t(j, nc, iy, wy), ntz = lin_taps_t(k, nc, iz, wz);
+      // the taps of lin_taps_t, in its order, as two fixed slots per axis
+      const Taps2 X = taps2(tx, nc), Y = taps2(j, nc), Z = taps2(k, nc);
       T acc = T(0);
-      for (int cz = 0; cz < ntz; ++cz)
-        for (int cy = 0; cy < nty; ++cy)
-          for (int cx = 0; cx < ntx; ++cx)
-            acc += T(wx[cx] * wy[cy] * wz[cz]) * E(l + 1)[P(nc, ix[cx], iy[cy], iz[cz])];
+#pragma unroll
+      for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+          for (int cx = 0; cx < 2; ++cx)
+            if (Z.ok[cz] && Y.ok[cy] && X.ok[cx])
+              acc += T(X.w[cx] * Y.w[cy] * Z.w[cz]) * E(l + 1)[P(nc, X.i[cx], Y.i[cy], Z.i[cz])];
       E(l)[P(n, tx, j, k)] += acc;
     }
     __syncthreads();

@@ -39,7 +39,7 @@ def test_default_options(lib):
     o = pmg.pfasst_mg_default_options()
     assert o.nu1 == 2 and o.nu2 == 1 and o.vcycles == 2 and abs(o.omega - 2 / 3) < 1e-15
     assert o.interp_order == 4 and o.precision == pmg.PMG_PREC_FP64
-    assert o.slice_groups == 0 and o.vcycle_tail == 0 and o.coarse_vcycles == -1 and o.single_grid_vcycle == 0
+    assert o.slice_groups == 0 and o.vcycle_tail == -1 and o.coarse_vcycles == -1 and o.single_grid_vcycle == 0
 
 
 def _ws(dim, n, sf, nl, sc, P, **kw):
@@ -85,7 +85,8 @@ def test_invalid_descriptions_are_rejected(lib, bad):
 
 @pytest.mark.parametrize("opt", [dict(smoother=5), dict(nu1=0, nu2=0), dict(precision=3),
                                  dict(interp_order=3), dict(omega=0.0), dict(vcycles=-1),
-                                 dict(coarse_vcycles=-2), dict(coarse_vcycles=0, mg_tol=0.0)])
+                                 dict(coarse_vcycles=-2), dict(coarse_vcycles=0, mg_tol=0.0),
+                                 dict(vcycle_tail=2), dict(vcycle_tail=-2)])
 def test_invalid_options_are_rejected(lib, opt):
     with pytest.raises(pmg.PMGError) as ei:
         _ws(2, 31, 5, 2, 3, 4, **opt)
