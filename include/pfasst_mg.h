@@ -107,9 +107,9 @@ typedef struct {
                              15^3 in 3D, 63^2 in 2D, all of a 1D hierarchy) run as one kernel
                              launch per V-cycle; 0 = one launch per smoothing sweep,
                              restriction and prolongation; -1 (default) = automatic: one
-                             launch in 1D and for 3D red-black Gauss-Seidel, per level in 2D
-                             and for 3D Jacobi (the measured-faster choice on the 1D, 2D, 3D
-                             and uneven workloads)                                          */
+                             launch in 1D and for red-black Gauss-Seidel, per level for
+                             weighted Jacobi in 2D and 3D (the measured-faster choice on the
+                             1D, 2D, 3D and uneven workloads)                               */
     int    coarse_vcycles;/* sub-step solves on the coarse PFASST levels (levels >= 1):
                              -1 (default) = vcycles; 0 = solve to mg_tol with the stall
                              rule; > 0 = that many V-cycles.  The paper leaves the coarse

@@ -539,11 +539,12 @@ int vcycle(MGCtx &M, int l0, int B, double c, const void *minv, void *e_init, vo
   // batches keep the per-level kernels, which spread each level over many CTAs), unless
   // a learned correction acts there
   int lb = H.L;
-  // automatic (-1): one launch in 1D and for 3D red-black Gauss-Seidel, where it measured
-  // faster than the per-level launches; per level in 2D and for 3D Jacobi
+  // automatic (-1): one launch in 1D and for red-black Gauss-Seidel, where it measured
+  // faster than the per-level launches (1D, 3D and the uneven batch); per level for
+  // weighted Jacobi in 2D and 3D (slower with the tail on the 2D workload)
   const int dim = H.lev[0].dim;
   const bool tail_on = o.vcycle_tail == 1 ||
-                       (o.vcycle_tail == -1 && (dim == 1 || (dim == 3 && o.smoother == PMG_SMOOTHER_RBGS)));
+                       (o.vcycle_tail == -1 && (dim == 1 || o.smoother == PMG_SMOOTHER_RBGS));
   if (tail_on && H.tail >= l0 && B <= 2) {
     lb = H.tail;
     if (M.net)
