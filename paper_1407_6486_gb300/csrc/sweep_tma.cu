@@ -15,6 +15,11 @@
 // do not interfere, and the black half-sweep then finds the red values of planes k-2,
 // k-1, k and the old black values in the same slots.  Without a separate red buffer the
 // ring holds two planes in flight at two CTAs per SM.
+// One CTA barrier per plane: a thread computes the red points of plane k on the rows of
+// its own black half-sweep of plane k-1, and a black point reads red values of plane k
+// only at its own (x, y), so the only values that cross threads within a plane step --
+// the red values of plane k-1 and the slots refilled by TMA -- are ordered by the barrier
+// that ends the previous plane.
 //
 // Every wait on an mbarrier is bounded (about 2 s of SM clock); on a timeout the
 // kernel records the fact in a device flag, stops at the end of the current plane,
@@ -48,7 +53,7 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
                                                           double *__restrict__ u, long long su, int nzc, int zchunk) {
   constexpr int NP = NX / 2;          // x-pairs per row
   constexpr int RS = TNT / NP;        // rows per round of the CTA
-  constexpr int PF = (TMY + RS - 1) / RS, PB = (TTY + RS - 1) / RS;
+  constexpr int PB = (TTY + RS - 1) / RS;
   constexpr uint32_t EB = TEY * NX * 4, FB = TMY * NX * 4;
   extern __shared__ __align__(1024) unsigned char sm[];
   float2(*E)[TEY][NP] = (float2(*)[TEY][NP])sm;                                   // [NE]
@@ -132,9 +137,18 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
       const int se = edn(s1, 1), sl = edn(s1, 2), sh = s1, sf = sfk;
       const bool kin = k >= 0 && k < n;
 #pragma unroll
-      for (int h = 0; h < PF; ++h) {
-        const int r = ry + RS * h;
-        if (r >= TMY) break;  // uniform per warp (a warp lies in one row)
+      for (int h = 0; h <= PB; ++h) {
+        // a thread takes the rows of its black half-sweep (then the black half-sweep of
+        // plane k-1 finds the red values of plane k it needs -- those of its own points --
+        // without a CTA barrier); the halo rows y0-1 and y0+TTY go to the rows ry = 0, 1
+        int r;
+        if (h < PB) {
+          if (ry + RS * h >= TTY) continue;  // uniform per warp (a warp lies in one row)
+          r = ry + RS * h + 1;
+        } else {
+          if (ry >= 2) continue;
+          r = ry == 0 ? 0 : TMY - 1;
+        }
         const int y = y0 - 1 + r;
         const bool yin = kin && y >= 0 && y < n;
         const float2 fv = Fs[sf][r][px];
@@ -171,7 +185,9 @@ __global__ void __launch_bounds__(TNT, 2) rbgs_tma_kernel(const __grid_constant_
         }
       }
     }
-    __syncthreads();
+    // no barrier here: a black point of plane k-1 reads red values of plane k only at its
+    // own (x, y) -- written above by this thread -- and red values of planes k-1, k-2 and
+    // old black values, all settled before the barrier that ended the previous plane
     const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+TTY-1
     if (kb >= z0 && kb < z1) {
       const int s0 = edn(s1, 2), sl = edn(s1, 3), sh = edn(s1, 1), sf = fdn(sfk, 1);
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(2 * NX, 2) rbgs_tma4_kernel(const __grid_const
                                                               long long su, int nzc, int zchunk) {
   constexpr int NQ = NX / 4;          // quads per row
   constexpr int RS = 8;               // rows per round of the CTA
-  constexpr int PF = (TMY + RS - 1) / RS, PB = (TTY + RS - 1) / RS;
+  constexpr int PB = (TTY + RS - 1) / RS;
   constexpr uint32_t EB = TEY * NX * 4, FB = TMY * NX * 4;
   extern __shared__ __align__(1024) unsigned char sm[];
   float4(*E)[TEY][NQ] = (float4(*)[TEY][NQ])sm;                                   // [NE]
@@ -347,9 +363,16 @@ __global__ void __launch_bounds__(2 * NX, 2) rbgs_tma4_kernel(const __grid_const
       const int se = edn(s1, 1), sl = edn(s1, 2), sh = s1, sf = sfk;
       const bool kin = k >= 0 && k < n;
 #pragma unroll
-      for (int h = 0; h < PF; ++h) {
-        const int r = ry + RS * h;
-        if (r >= TMY) break;  // uniform per warp
+      for (int h = 0; h <= PB; ++h) {
+        // the rows of the thread's black half-sweep, then the halo rows (as rbgs_tma_kernel)
+        int r;
+        if (h < PB) {
+          if (ry + RS * h >= TTY) continue;  // uniform per warp
+          r = ry + RS * h + 1;
+        } else {
+          if (ry >= 2) continue;
+          r = ry == 0 ? 0 : TMY - 1;
+        }
         const int y = y0 - 1 + r;
         const bool yin = kin && y >= 0 && y < n;
         const float4 fv = Fs[sf][r][qx];
@@ -391,7 +414,7 @@ __global__ void __launch_bounds__(2 * NX, 2) rbgs_tma4_kernel(const __grid_const
         }
       }
     }
-    __syncthreads();
+    // no barrier here (see rbgs_tma_kernel)
     const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+TTY-1
     if (kb >= z0 && kb < z1) {
       const int s0 = edn(s1, 2), sl = edn(s1, 3), sh = edn(s1, 1), sf = fdn(sfk, 1);
