@@ -115,7 +115,17 @@ __global__ void __launch_bounds__(256, 4) rbgs_sweep3d_kernel(Grid g, T a, T D, 
     __syncthreads();
     {  // red half-sweep on plane k over the tile and its one-point ring
       const int se = (k + 4) & 3, sl = (k + 3) & 3, sh = (k + 5) & 3, sf = (k + 3) % 3, smk = (k + 3) % 3;
-      for (int r = ty; r < MY; r += 8) {
+      // a thread takes the row of its black half-sweep (row ty + 1) and the rows ty = 0, 1
+      // the halo rows 0 and MY - 1: the black half-sweep of plane k-1 then reads red values
+      // of plane k only at its own points, written here by the same thread
+      for (int h = 0; h < 2; ++h) {
+        int r;
+        if (h == 0) {
+          r = ty + 1;
+        } else {
+          if (ty >= 2) break;
+          r = ty == 0 ? 0 : MY - 1;
+        }
         const int c = 2 + 2 * tx;
         M[smk][r][c] = red_at(k, r, c, se, sl, sh, sf);
         M[smk][r][c + 1] = red_at(k, r, c + 1, se, sl, sh, sf);
@@ -125,7 +135,8 @@ __global__ void __launch_bounds__(256, 4) rbgs_sweep3d_kernel(Grid g, T a, T D, 
         M[smk][r][c] = red_at(k, r, c, se, sl, sh, sf);
       }
     }
-    __syncthreads();
+    // no barrier here: what crosses threads (the halo columns and rows of plane k, the red
+    // values of planes k-1 and k-2) is read only after the barrier of the next plane
     const int kb = k - 1;  // black half-sweep on plane k-1 over the tile
     if (kb >= z0 && kb < z1) {
       const int s0 = (kb + 3) % 3, sl = (kb + 2) % 3, sh = (kb + 4) % 3, sf = (kb + 3) % 3, se = (kb + 4) & 3;
@@ -240,9 +251,18 @@ __global__ void __launch_bounds__(NT, 512 / NT * 2 > 4 ? 4 : 512 / NT * 2) rbgs_
       const int se = (k + 4) & 3, sl = (k + 3) & 3, sh = (k + 5) & 3, s3 = (k + 3) % 3;
       const bool kin = k >= 0 && k < n;
 #pragma unroll
-      for (int h = 0; h < PF; ++h) {
-        const int r = ry + RS * h;
-        if (r >= FMY) break;  // uniform per warp (a warp lies in one row)
+      for (int h = 0; h <= PB; ++h) {
+        // the rows of the thread's black half-sweep, then the halo rows y0-1 and y0+FTY
+        // (rows ry = 0, 1): the black half-sweep of plane k-1 reads red values of plane k
+        // only at its own points, so no barrier separates the two half-sweeps
+        int r;
+        if (h < PB) {
+          if (ry + RS * h >= FTY) continue;  // uniform per warp (a warp lies in one row)
+          r = ry + RS * h + 1;
+        } else {
+          if (ry >= 2) continue;
+          r = ry == 0 ? 0 : FMY - 1;
+        }
         const int y = y0 - 1 + r;
         T2 out;
         out.x = T(0);
@@ -284,7 +304,6 @@ __global__ void __launch_bounds__(NT, 512 / NT * 2 > 4 ? 4 : 512 / NT * 2) rbgs_
         M[s3][r][px] = out;
       }
     }
-    __syncthreads();
     const int kb = k - 1;  // black half-sweep on plane k-1, rows y0 .. y0+FTY-1
     if (kb >= z0 && kb < z1) {
       const int s0 = (kb + 3) % 3, sl = (kb + 2) % 3, sh = (kb + 4) % 3, se = (kb + 4) & 3;
