@@ -979,11 +979,14 @@ def run_ours(args):
                 except pmg.PMGError:
                     pass
     tuning = []
+
+    def kind_of(fz, prm, thr):
+        return {0: f"point x{prm}", 1: f"fused z{prm or 32} x{thr}", 2: f"tma z{prm}", 3: f"tma4 z{prm}"}.get(fz, "?")
     for lev in range(8):
         try:
-            fz, prm, thr = pmg.pfasst_mg_tuning(s.h, lev, 0)
-            kind = {0: f"point x{prm}", 1: f"fused z{prm or 32} x{thr}", 2: f"tma z{prm}", 3: f"tma4 z{prm}"}.get(fz, "?")
-            tuning.append(f"L{lev}:{kind}")
+            wide, narrow = kind_of(*pmg.pfasst_mg_tuning(s.h, lev, 0)), kind_of(*pmg.pfasst_mg_tuning(s.h, lev, 1))
+            # the batch of all slices, and (after "|") single grids where that differs
+            tuning.append(f"L{lev}:{wide}" + (f"|{narrow}" if narrow != wide else ""))
         except pmg.PMGError:
             break
 

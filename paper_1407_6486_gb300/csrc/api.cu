@@ -701,11 +701,26 @@ MGCtx mgctx(pmg_ctx *h) {
 // or 512 threads per block, and for 3D red-black Gauss-Seidel the fused z-marching
 // sweep with z chunks of 8, 16 or 32 planes -- on the level's own buffers and keep the
 // fastest.  Runs once at creation (it synchronises the stream).
+// Candidates are timed the way the solver runs them: their sweeps captured into a CUDA
+// graph (on a private stream, which waits for the work already on the solver's stream)
+// and the graph replayed.  Timed eagerly, a variant of two launches per sweep (the
+// one-point-per-thread kernels) paid the host's launch cost and lost on small grids to a
+// fused sweep that is several times slower inside the graphs.
 int autotune(MGCtx &M, int l0, int Bwide, double c) {
   Hier &H = *M.H;
   cudaEvent_t e0, e1;
   PMG_CUDA(M.h, cudaEventCreate(&e0));
   PMG_CUDA(M.h, cudaEventCreate(&e1));
+  cudaStream_t ts = nullptr;
+  PMG_CUDA(M.h, cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+  PMG_CUDA(M.h, cudaEventRecord(e0, M.stream));
+  PMG_CUDA(M.h, cudaStreamWaitEvent(ts, e0, 0));
+  MGCtx Mt = M;  // the same buffers, launched on ts, without profiling or launch counting
+  Mt.L.stream = ts;
+  Mt.L.counter = nullptr;
+  Mt.L.prof = nullptr;
+  Mt.stream = ts;
+  constexpr int kSweeps = 4, kReplays = 5;  // sweeps per graph (the first from zero), timed replays
   int rc = PMG_OK;
   for (int l = l0; l < H.L - 1 && rc == PMG_OK; ++l)
     for (int cls = 0; cls < 2 && rc == PMG_OK; ++cls) {
@@ -729,13 +744,26 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
       for (const Tune &t : cand) {
         void *cur = H.e[l];
         float ms = 0.f;
-        for (int rep = 0; rep < 4 && rc == PMG_OK; ++rep) {
-          if (rep == 1 && cudaEventRecord(e0, M.stream) != cudaSuccess) rc = PMG_ERR_CUDA;
-          if (rc == PMG_OK) rc = smooth_with(M, t, l, B, c, cur, rep == 0);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          rc = fail(M.h, PMG_ERR_CUDA, "autotune capture failed");
+          break;
         }
-        if (rc != PMG_OK) break;
-        if (cudaEventRecord(e1, M.stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        for (int rep = 0; rep < kSweeps && rc == PMG_OK; ++rep) rc = smooth_with(Mt, t, l, B, c, cur, rep == 0);
+        const cudaError_t ec = cudaStreamEndCapture(ts, &graph);
+        if (rc != PMG_OK || ec != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          if (rc == PMG_OK) rc = fail(M.h, PMG_ERR_CUDA, "autotune capture failed");
+          break;
+        }
+        bool ok = cudaGraphLaunch(exec, ts) == cudaSuccess && cudaEventRecord(e0, ts) == cudaSuccess;
+        for (int r = 0; r < kReplays && ok; ++r) ok = cudaGraphLaunch(exec, ts) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, ts) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (!ok) {
           rc = fail(M.h, PMG_ERR_CUDA, "autotune timing failed");
           break;
         }
@@ -743,6 +771,8 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
       }
       H.tune[l][cls] = pick;
     }
+  if (cudaStreamSynchronize(ts) != cudaSuccess && rc == PMG_OK) rc = fail(M.h, PMG_ERR_CUDA, "autotune sync failed");
+  cudaStreamDestroy(ts);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the timing sweeps left arbitrary values in the correction buffers; they are always
