@@ -93,8 +93,10 @@ typedef struct {
     int    interp_order;  /* spatial interpolation between PFASST levels: 2 or 4    */
     int    use_graphs;    /* 1: replay each PFASST iteration as a captured CUDA graph */
     int    autotune;      /* 1: at creation, time the smoother variants of every multigrid
-                             level (threads per block; fused 3D sweep z chunk) and keep
-                             the fastest; 0: built-in size rules                          */
+                             level (threads per block; fused, TMA-staged 3D sweeps and
+                             their z chunks), each captured into a CUDA graph and replayed
+                             as the solver runs it, and keep the fastest; 0: built-in size
+                             rules                                                        */
     int    slice_groups;  /* two-level PFASST with fixed V-cycle counts: the slices of an
                              iteration are processed in this many groups so that the serial
                              coarse chain of group g overlaps the fine sweeps of groups
