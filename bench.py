@@ -978,13 +978,20 @@ def run_ours(args):
                     pmg.pfasst_mg_set_tuning(s.h, lev, narrow, args.tma, 32, 512)
                 except pmg.PMGError:
                     pass
-    tuning = []
+    if args.pin_tuning:
+        # level:narrow:variant:param:threads entries (the tuning_codes of an earlier bench line)
+        for item in args.pin_tuning.split():
+            lev, narrow, fz, prm, thr = (int(v) for v in item.split(":"))
+            pmg.pfasst_mg_set_tuning(s.h, lev, narrow, fz, prm, thr)
+    tuning, codes = [], []
 
     def kind_of(fz, prm, thr):
         return {0: f"point x{prm}", 1: f"fused z{prm or 32} x{thr}", 2: f"tma z{prm}", 3: f"tma4 z{prm}"}.get(fz, "?")
     for lev in range(8):
         try:
-            wide, narrow = kind_of(*pmg.pfasst_mg_tuning(s.h, lev, 0)), kind_of(*pmg.pfasst_mg_tuning(s.h, lev, 1))
+            tw, tn = pmg.pfasst_mg_tuning(s.h, lev, 0), pmg.pfasst_mg_tuning(s.h, lev, 1)
+            codes += [f"{lev}:0:{tw[0]}:{tw[1]}:{tw[2]}", f"{lev}:1:{tn[0]}:{tn[1]}:{tn[2]}"]
+            wide, narrow = kind_of(*tw), kind_of(*tn)
             # the batch of all slices, and (after "|") single grids where that differs
             tuning.append(f"L{lev}:{wide}" + (f"|{narrow}" if narrow != wide else ""))
         except pmg.PMGError:
@@ -1108,6 +1115,7 @@ def run_ours(args):
                    "l2": "working set > 60 GB, far above the 129 MB L2; no flush" if flush is None
                    else "L2 flushed (512 MB write) before every timed step, outside the timed interval",
                    "autotuned_smoothers": " ".join(tuning),
+                   "tuning_codes": " ".join(codes[:-2]),  # (the exact coarsest level has no smoother)
                    "ms_per_step_median": statistics.median(step_ms),
                    "ms_per_step_min_max": [min(step_ms), max(step_ms)],
                    "fp64_plain_ms_per_step": fp64_ms,
@@ -1184,6 +1192,9 @@ def main():
     ap.add_argument("--tma", type=int, nargs="?", const=3, default=0, choices=(0, 2, 3),
                     help="pin the TMA-staged sweep on every level that can run it (profiling runs): "
                          "2 = two x points per thread, 3 (bare flag) = four")
+    ap.add_argument("--pin-tuning", default="",
+                    help="pin the smoother variants ('level:narrow:variant:param:threads ...', the tuning_codes "
+                         "of an earlier bench line), e.g. for an ncu run whose own autotuning ncu distorts")
     ap.add_argument("--profile-all", action="store_true",
                     help="time every launch (not only fine-grid ones) and print the breakdown to stderr")
     args = ap.parse_args()
