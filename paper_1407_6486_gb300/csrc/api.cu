@@ -730,13 +730,13 @@ int autotune(MGCtx &M, int l0, int Bwide, double c) {
       for (int th : {128, 256, 512}) cand.push_back(Tune{0, th, 256});
       const Grid &g = H.lev[l];
       if (M.o->smoother == PMG_SMOOTHER_RBGS && g.dim == 3 && g.n >= 15 && g.order != 4)
-        for (int zc : {8, 16, 32})
+        for (int zc : {4, 8, 16, 32})  // short z chunks: more CTAs for single grids
           if (zc <= g.n) {
             cand.push_back(Tune{1, zc, 256});
             if (g.pitch >= 128) cand.push_back(Tune{1, zc, 512});
           }
       if (M.o->smoother == PMG_SMOOTHER_RBGS && rbgs_tma_supported(g, H.pr))
-        for (int zc : {16, 32, 64})
+        for (int zc : {8, 16, 32, 64})
           if (zc <= g.n)
             for (int kind : {2, 3}) cand.push_back(Tune{kind, zc, rbgs_tma_threads(g, kind == 3)});
       float best = 1e30f;
