@@ -22,7 +22,7 @@
 namespace pmg {
 namespace {
 
-constexpr int RTX = 64, RTY = 8, RZC = 32;      // sweep: output tile and z chunk
+constexpr int RTX = 64, RTY = 8, RZC = 32;      // sweep: output tile and default z chunk
 constexpr int SX = RTX + 4;                     // smem row: column c <-> x = x0 - 2 + c
 constexpr int EY = RTY + 4, MY = RTY + 2;       // e_in rows (two-point ring), red/f rows (one-point ring)
 
@@ -31,7 +31,8 @@ constexpr int EY = RTY + 4, MY = RTY + 2;       // e_in rows (two-point ring), r
 template <typename T, bool ZERO, bool UPD>
 __global__ void __launch_bounds__(256, 4) rbgs_sweep3d_kernel(Grid g, T a, T D, T omega, const T *__restrict__ ein,
                                                               T *__restrict__ eout, const T *__restrict__ f,
-                                                              double *__restrict__ u, long long su, int nzc) {
+                                                              double *__restrict__ u, long long su, int nzc,
+                                                              int zchunk) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T(*E)[EY][SX] = (T(*)[EY][SX])sm_raw;                      // [4][EY][SX]
   T(*M)[MY][SX] = (T(*)[MY][SX])(sm_raw + sizeof(T) * 4 * EY * SX);   // [3][MY][SX]
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(256, 4) rbgs_sweep3d_kernel(Grid g, T a, T D, 
   const int n = g.n, tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int x0 = blockIdx.x * RTX, y0 = blockIdx.y * RTY;
   const int zc = blockIdx.z % nzc, b = blockIdx.z / nzc;
-  const int z0 = zc * RZC, z1 = min(z0 + RZC, n);
+  const int z0 = zc * zchunk, z1 = min(z0 + zchunk, n);
   const long long plane = (long long)g.ny * g.pitch;
   const T *Eb = ein + b * g.slab;
   const T *Fb = f + b * g.slab;
@@ -546,7 +547,8 @@ void launch_sweep(const Launch &L, const Grid &g, double c, double omega, const 
     return launch_rows<T, 128, ZERO, UPD, 256>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
   }
   if (g.pitch == 64) return launch_rows<T, 64, ZERO, UPD, 256>(L, g, a, D, (T)omega, ein, eout, f, u, su, batch, zchunk);
-  const int ntx = (g.n + RTX - 1) / RTX, nty = (g.n + RTY - 1) / RTY, nzc = (g.n + RZC - 1) / RZC;
+  if (zchunk <= 0) zchunk = RZC;
+  const int ntx = (g.n + RTX - 1) / RTX, nty = (g.n + RTY - 1) / RTY, nzc = (g.n + zchunk - 1) / zchunk;
   const size_t smem = sizeof(T) * (4 * EY + 6 * MY) * SX;
   static bool attr = false;
   if (!attr) {
@@ -555,7 +557,7 @@ void launch_sweep(const Launch &L, const Grid &g, double c, double omega, const 
   }
   dim3 gr(ntx, nty, nzc * batch);
   rbgs_sweep3d_kernel<T, ZERO, UPD><<<gr, 256, smem, L.stream>>>(g, a, D, (T)omega, (const T *)ein, (T *)eout,
-                                                                  (const T *)f, u, su, nzc);
+                                                                  (const T *)f, u, su, nzc, zchunk);
 }
 
 }  // namespace
